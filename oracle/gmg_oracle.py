@@ -1,0 +1,609 @@
+"""Plain FP64 CPU oracle for the GMG-preconditioned FGMRES Poisson-type solve.
+
+TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU
+baseline leg of the benchmark may import this module.  It shares no code with
+the CUDA library; both sides only read the seeded inputs of
+``streamer_inputs``.
+
+It computes, slowly and literally, what the paper's elliptic solver computes
+(Lin, Zhuang, Cai, Zeng, Bao, "An efficient and accurate MPI-based parallel
+simulator for streamer discharges in three dimensions"):
+
+* the cell-centred 7-point finite-volume operator of eq. (e18), Sec. 2.2, with
+  face coefficients equal to the mean of the two adjacent cells;
+* the Dirichlet plates / Neumann side-walls of the model eq. (eM), Sec. 1,
+  imposed through ghost cells (Sec. 2.2 and Sec. 4);
+* FGMRES with right preconditioning, Algorithm 1 (Sec. 3.1), with
+  modified Gram-Schmidt, restarts and the stopping rule eq. (criterion) of
+  Sec. 5.2;
+* one geometric-multigrid V-cycle from a zero guess as the preconditioner
+  (Sec. 3.2, eq. (eRichard), Appendix A);
+* the Chebyshev smoother eq. (smootheq)-(qntn)-(e19) with a one-step SSOR
+  preconditioner and eigen bounds 1.1 / 0.1 times the largest Ritz value of a
+  10-step Arnoldi run (Sec. 3.2);
+* a direct (Cholesky) solve on the coarsest grid (Sec. 3.2);
+* E = -grad(phi) by central differences (Sec. 2.2);
+* the discrete adjoint of the solve (not in the paper; derived from e18).
+
+Readings of points the paper leaves open (each is listed with its reason in
+the design notes of the repository):
+
+R1 boundary-face coefficient on the plates equals the cell's own coefficient;
+R2 Dirichlet ghost phi_g = 2 g - phi_p (linear extrapolation to the plate);
+R3 coarse operators are re-discretised from the 8-child mean of ``a``;
+R4 restriction = mean of 8 children, prolongation = cell-centred trilinear
+   (piecewise constant available as an option);
+R5 "one-step local SSOR" = one symmetric Gauss-Seidel sweep (omega = 1) in
+   red-black order (red = (i+j+k) even): red, black, red half-sweeps;
+R6 "quadratic-polynomial" Chebyshev: the smoother is defined by p_n in
+   eq. (smootheq) with q_{n+1}(x) = 1 - x p_n(x); a quadratic p_2 gives
+   q_3 = T_3 (scaled), i.e. 3 Chebyshev steps per smoothing;
+R7 the 10-step Arnoldi for the eigen bounds runs on the smoother's operator
+   B^{-1} A_l from a splitmix64-hash start vector;
+R8 after FGMRES's own stopping test, the true residual ||b - A x|| / ||b|| is
+   also required to be below the tolerance, else the method restarts.
+
+Array layout: ``(nz, ny, nx)`` float64, x fastest.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg
+
+# ---------------------------------------------------------------------------
+# Grid and parameters
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class OracleParams:
+    """Solver parameters; defaults are the paper's values unless noted."""
+
+    lx: float = 1.0
+    ly: float = 1.0
+    lz: float = 1.0
+    phi_bottom: float = 0.0      # Dirichlet data at z = 0   (eq. (eM) plates)
+    phi_top: float = 1.0         # Dirichlet data at z = lz
+    coarse_min: int = 4          # coarsest grid: smallest side reaches this
+    cheb_steps: int = 3          # R6
+    restart: int = 20            # FGMRES m; the paper uses 30 (Sec. 3.1)
+    max_iters: int = 200
+    rtol: float = 1e-8           # eq. (criterion), Sec. 5.2
+    eig_steps: int = 10          # Sec. 3.2
+    eig_hi: float = 1.1          # Sec. 3.2
+    eig_lo: float = 0.1          # Sec. 3.2
+    prolongation: str = "trilinear"   # R4; or "constant"
+    smoother_pc: str = "sgs"          # R5; or "jacobi", "identity"
+
+
+@dataclass
+class Grid:
+    """Uniform cell-centred grid (Sec. 2.2): cells I_{i,j,k} of size hx*hy*hz."""
+
+    nx: int
+    ny: int
+    nz: int
+    lx: float = 1.0
+    ly: float = 1.0
+    lz: float = 1.0
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def hx(self):
+        return self.lx / self.nx
+
+    @property
+    def hy(self):
+        return self.ly / self.ny
+
+    @property
+    def hz(self):
+        return self.lz / self.nz
+
+    @property
+    def size(self):
+        return self.nx * self.ny * self.nz
+
+    def coarser(self) -> "Grid":
+        return Grid(self.nx // 2, self.ny // 2, self.nz // 2, self.lx, self.ly, self.lz)
+
+
+# ---------------------------------------------------------------------------
+# Operator, eq. (e18)
+# ---------------------------------------------------------------------------
+
+
+def face_coefficients(grid: Grid, a: np.ndarray):
+    """Interior face coefficients divided by h^2 (eq. (e18) and the face means
+    P_{i+1/2,j,k} = (P_{i+1,j,k} + P_{i,j,k}) / 2 of Sec. 2.2).
+
+    Returns (cx, cy, cz) with cx[k,j,i] the coefficient of the face between
+    cells i and i+1 (shape (nz,ny,nx-1)), and likewise for y and z.
+    """
+    cx = 0.5 * (a[:, :, 1:] + a[:, :, :-1]) / grid.hx**2
+    cy = 0.5 * (a[:, 1:, :] + a[:, :-1, :]) / grid.hy**2
+    cz = 0.5 * (a[1:, :, :] + a[:-1, :, :]) / grid.hz**2
+    return cx, cy, cz
+
+
+def plate_coefficients(grid: Grid, a: np.ndarray):
+    """Coefficients 2 a_p / hz^2 of the two Dirichlet plate faces (R1, R2).
+
+    A plate face carries a_f = a_p (R1) and the ghost value 2g - phi_p (R2), so
+    its flux a_p (phi_p - phi_g) / hz^2 = 2 a_p (phi_p - g) / hz^2.
+    """
+    return 2.0 * a[0] / grid.hz**2, 2.0 * a[-1] / grid.hz**2
+
+
+def apply_operator(grid: Grid, a: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """y = A x: the left-hand side of eq. (e18) with zero Dirichlet data.
+
+    (A x)_p = sum over interior faces f=(p,q) of a_f (x_p - x_q) / h_f^2
+            + sum over plate faces of p of 2 a_p x_p / hz^2.
+    Side faces in x and y carry no flux (homogeneous Neumann, eq. (eM)).
+    """
+    cx, cy, cz = face_coefficients(grid, a)
+    y = np.zeros_like(x, dtype=np.float64)
+    flux = cx * (x[:, :, :-1] - x[:, :, 1:])
+    y[:, :, :-1] += flux
+    y[:, :, 1:] -= flux
+    flux = cy * (x[:, :-1, :] - x[:, 1:, :])
+    y[:, :-1, :] += flux
+    y[:, 1:, :] -= flux
+    flux = cz * (x[:-1, :, :] - x[1:, :, :])
+    y[:-1, :, :] += flux
+    y[1:, :, :] -= flux
+    pb, pt = plate_coefficients(grid, a)
+    y[0] += pb * x[0]
+    y[-1] += pt * x[-1]
+    return y
+
+
+def diagonal(grid: Grid, a: np.ndarray) -> np.ndarray:
+    """Diagonal of A: the sum of the face coefficients of each cell."""
+    cx, cy, cz = face_coefficients(grid, a)
+    d = np.zeros(grid.shape)
+    d[:, :, :-1] += cx
+    d[:, :, 1:] += cx
+    d[:, :-1, :] += cy
+    d[:, 1:, :] += cy
+    d[:-1, :, :] += cz
+    d[1:, :, :] += cz
+    pb, pt = plate_coefficients(grid, a)
+    d[0] += pb
+    d[-1] += pt
+    return d
+
+
+def neighbour_sum(grid: Grid, a: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """N x = sum over interior faces f=(p,q) of a_f x_q / h_f^2, so A = D - N."""
+    cx, cy, cz = face_coefficients(grid, a)
+    s = np.zeros(grid.shape)
+    s[:, :, :-1] += cx * x[:, :, 1:]
+    s[:, :, 1:] += cx * x[:, :, :-1]
+    s[:, :-1, :] += cy * x[:, 1:, :]
+    s[:, 1:, :] += cy * x[:, :-1, :]
+    s[:-1, :, :] += cz * x[1:, :, :]
+    s[1:, :, :] += cz * x[:-1, :, :]
+    return s
+
+
+def assemble_rhs(grid: Grid, a: np.ndarray, f: np.ndarray, g_bottom: float, g_top: float) -> np.ndarray:
+    """b = f + the plate terms 2 a_p g / hz^2 (eq. (e18) with ghosts, R1/R2)."""
+    b = np.array(f, dtype=np.float64, copy=True)
+    pb, pt = plate_coefficients(grid, a)
+    b[0] += pb * g_bottom
+    b[-1] += pt * g_top
+    return b
+
+
+def dense_operator(grid: Grid, a: np.ndarray) -> np.ndarray:
+    """A as a dense matrix (columns A e_i); small grids only."""
+    n = grid.size
+    m = np.zeros((n, n))
+    e = np.zeros(n)
+    for i in range(n):
+        e[:] = 0.0
+        e[i] = 1.0
+        m[:, i] = apply_operator(grid, a, e.reshape(grid.shape)).ravel()
+    return m
+
+
+# ---------------------------------------------------------------------------
+# Smoother: preconditioned Chebyshev, eqs. (smootheq), (qntn), (e19); SSOR (R5)
+# ---------------------------------------------------------------------------
+
+
+def red_mask(grid: Grid) -> np.ndarray:
+    k, j, i = np.indices(grid.shape)
+    return (i + j + k) % 2 == 0
+
+
+def sgs_redblack(grid: Grid, a: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """z = B^{-1} r for one symmetric Gauss-Seidel sweep (SSOR, omega = 1) from
+    z = 0 in red-black ordering (R5).
+
+    Forward sweep: red cells, then black cells.  Backward sweep: black cells,
+    then red cells.  In a 7-point stencil a black cell sees only red
+    neighbours, so the backward black update repeats the forward one and the
+    sweep is red, black, red.
+    """
+    dg = diagonal(grid, a)
+    red = red_mask(grid)
+    black = ~red
+    z = np.zeros(grid.shape)
+    z[red] = r[red] / dg[red]
+    nb = neighbour_sum(grid, a, z)
+    z[black] = (r[black] + nb[black]) / dg[black]
+    nb = neighbour_sum(grid, a, z)
+    z[red] = (r[red] + nb[red]) / dg[red]
+    return z
+
+
+def smoother_preconditioner(grid: Grid, a: np.ndarray, r: np.ndarray, kind: str) -> np.ndarray:
+    if kind == "sgs":
+        return sgs_redblack(grid, a, r)
+    if kind == "jacobi":
+        return r / diagonal(grid, a)
+    if kind == "identity":
+        return np.array(r, copy=True)
+    raise ValueError(kind)
+
+
+def chebyshev_smooth(grid: Grid, a: np.ndarray, b: np.ndarray, x: np.ndarray | None,
+                     lam_max: float, lam_min: float, steps: int, pc: str = "sgs") -> np.ndarray:
+    """``steps`` preconditioned Chebyshev iterations for A x = b (Sec. 3.2).
+
+    The error is multiplied by q_s(B^{-1}A), q_s the scaled Chebyshev
+    polynomial of eq. (qntn) on [lam_min, lam_max].  Three-term recurrence of
+    the preconditioned Chebyshev iteration (Saad, Iterative Methods for Sparse
+    Linear Systems, 2nd ed., Sec. 12.3):
+        theta = (lmax + lmin)/2, delta = (lmax - lmin)/2, sigma = theta/delta,
+        rho_0 = 1/sigma;  d_0 = B^{-1} r_0 / theta;  x_1 = x_0 + d_0;
+        rho_k = 1/(2 sigma - rho_{k-1}),
+        d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) B^{-1} r_k,
+        x_{k+1} = x_k + d_k,  with r_k = b - A x_k.
+    ``x is None`` means a zero initial guess (then r_0 = b).
+    """
+    theta = 0.5 * (lam_max + lam_min)
+    delta = 0.5 * (lam_max - lam_min)
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    if x is None:
+        x = np.zeros(grid.shape)
+        r = np.array(b, copy=True)
+    else:
+        x = np.array(x, dtype=np.float64, copy=True)
+        r = b - apply_operator(grid, a, x)
+    d = smoother_preconditioner(grid, a, r, pc) / theta
+    x = x + d
+    for _ in range(1, steps):
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        r = b - apply_operator(grid, a, x)
+        z = smoother_preconditioner(grid, a, r, pc)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * z
+        x = x + d
+        rho = rho_new
+    return x
+
+
+# ---------------------------------------------------------------------------
+# Eigen bounds (Sec. 3.2, R7)
+# ---------------------------------------------------------------------------
+
+_MASK64 = (1 << 64) - 1
+
+
+def splitmix64(index: np.ndarray) -> np.ndarray:
+    """splitmix64 output for counter ``index`` (Steele, Lea, Flood, "Fast
+    splittable pseudorandom number generators", OOPSLA 2014): state =
+    (index + 1) * 0x9E3779B97F4A7C15, then the mix function of the
+    published generator."""
+    with np.errstate(over="ignore"):
+        z = (index.astype(np.uint64) + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def hash_start_vector(n: int) -> np.ndarray:
+    """u_i in [-1, 1): top 53 bits of splitmix64(i) scaled to [0,1), times 2, minus 1."""
+    bits = splitmix64(np.arange(n, dtype=np.uint64)) >> np.uint64(11)
+    return bits.astype(np.float64) * (2.0 ** -53) * 2.0 - 1.0
+
+
+def arnoldi_hessenberg(matvec, v0: np.ndarray, steps: int) -> np.ndarray:
+    """Arnoldi with modified Gram-Schmidt (Algorithm 1, lines 3-10, no
+    preconditioning): returns the square upper Hessenberg H_m (m <= steps)."""
+    n = v0.size
+    V = [v0 / np.linalg.norm(v0)]
+    H = np.zeros((steps + 1, steps))
+    m = steps
+    for j in range(steps):
+        w = matvec(V[j]).ravel().astype(np.float64)
+        for i in range(j + 1):
+            H[i, j] = np.dot(w, V[i])
+            w = w - H[i, j] * V[i]
+        H[j + 1, j] = np.linalg.norm(w)
+        if H[j + 1, j] == 0.0:
+            m = j + 1
+            break
+        V.append(w / H[j + 1, j])
+    del n
+    return H[:m, :m]
+
+
+def estimate_eig_bounds(grid: Grid, a: np.ndarray, params: OracleParams):
+    """lambda_max = eig_hi * lam_hat, lambda* = eig_lo * lam_hat with lam_hat the
+    largest eigenvalue of the Arnoldi H_m of B^{-1} A_l (Sec. 3.2, R7)."""
+    def matvec(v):
+        return smoother_preconditioner(grid, a, apply_operator(grid, a, v.reshape(grid.shape)),
+                                       params.smoother_pc)
+
+    H = arnoldi_hessenberg(matvec, hash_start_vector(grid.size), params.eig_steps)
+    lam_hat = float(np.max(np.linalg.eigvals(H).real))
+    return params.eig_hi * lam_hat, params.eig_lo * lam_hat, lam_hat
+
+
+# ---------------------------------------------------------------------------
+# Grid transfers and hierarchy (Sec. 3.2, R3, R4)
+# ---------------------------------------------------------------------------
+
+
+def restrict(fine: np.ndarray) -> np.ndarray:
+    """Mean of the 8 fine children of each coarse cell (R4)."""
+    nz, ny, nx = fine.shape
+    return fine.reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2).mean(axis=(1, 3, 5))
+
+
+def coarsen_coefficient(a: np.ndarray) -> np.ndarray:
+    """Coarse coefficient = mean of the 8 children (R3)."""
+    return restrict(a)
+
+
+def _prolong_axis(e: np.ndarray, axis: int, dirichlet: bool) -> np.ndarray:
+    """1-D cell-centred linear interpolation along ``axis``: a fine child sits a
+    quarter coarse cell from its parent's centre, so it takes 3/4 of the
+    parent and 1/4 of the neighbour on its side.  Beyond the domain the
+    neighbour is a ghost: equal to the parent at a Neumann wall, minus the
+    parent at a (homogeneous) Dirichlet plate."""
+    e = np.moveaxis(e, axis, 0)
+    n = e.shape[0]
+    ghost_lo = -e[:1] if dirichlet else e[:1]
+    ghost_hi = -e[-1:] if dirichlet else e[-1:]
+    left = np.concatenate([ghost_lo, e[:-1]], axis=0)    # neighbour below each parent
+    right = np.concatenate([e[1:], ghost_hi], axis=0)    # neighbour above each parent
+    out = np.empty((2 * n,) + e.shape[1:])
+    out[0::2] = 0.75 * e + 0.25 * left
+    out[1::2] = 0.75 * e + 0.25 * right
+    return np.moveaxis(out, 0, axis)
+
+
+def prolong(coarse: np.ndarray, kind: str = "trilinear") -> np.ndarray:
+    """Coarse-to-fine interpolation P_{l-1,l} (R4)."""
+    if kind == "constant":
+        return coarse.repeat(2, axis=0).repeat(2, axis=1).repeat(2, axis=2)
+    if kind != "trilinear":
+        raise ValueError(kind)
+    e = _prolong_axis(coarse, 2, dirichlet=False)   # x: Neumann walls
+    e = _prolong_axis(e, 1, dirichlet=False)        # y: Neumann walls
+    e = _prolong_axis(e, 0, dirichlet=True)         # z: Dirichlet plates
+    return e
+
+
+@dataclass
+class Level:
+    grid: Grid
+    a: np.ndarray
+    lam_max: float = 0.0
+    lam_min: float = 0.0
+    lam_hat: float = 0.0
+
+
+@dataclass
+class Hierarchy:
+    params: OracleParams
+    levels: list = field(default_factory=list)   # levels[0] coarsest ... levels[-1] finest
+    coarse_chol: object = None
+
+
+def level_count(nx: int, ny: int, nz: int, coarse_min: int) -> int:
+    """Number of grids: halve every side until the smallest reaches coarse_min."""
+    count = 1
+    while min(nx, ny, nz) > coarse_min:
+        if nx % 2 or ny % 2 or nz % 2:
+            raise ValueError("grid sides must halve down to the coarsest grid")
+        nx, ny, nz = nx // 2, ny // 2, nz // 2
+        count += 1
+    if min(nx, ny, nz) != coarse_min:
+        raise ValueError("smallest side must reach coarse_min by halving")
+    return count
+
+
+def build_hierarchy(grid: Grid, a: np.ndarray, params: OracleParams) -> Hierarchy:
+    """Coefficients per level, eigen bounds per smoothed level, and the Cholesky
+    factor of the coarsest operator (the set-up renewed each time step, Sec. 3)."""
+    nlev = level_count(grid.nx, grid.ny, grid.nz, params.coarse_min)
+    fine_to_coarse = [Level(grid, np.asarray(a, dtype=np.float64))]
+    for _ in range(nlev - 1):
+        prev = fine_to_coarse[-1]
+        fine_to_coarse.append(Level(prev.grid.coarser(), coarsen_coefficient(prev.a)))
+    hier = Hierarchy(params, list(reversed(fine_to_coarse)))
+    for lev in hier.levels[1:]:
+        lev.lam_max, lev.lam_min, lev.lam_hat = estimate_eig_bounds(lev.grid, lev.a, params)
+    coarse = hier.levels[0]
+    hier.coarse_chol = scipy.linalg.cho_factor(dense_operator(coarse.grid, coarse.a), lower=True)
+    return hier
+
+
+def coarse_solve(hier: Hierarchy, b: np.ndarray) -> np.ndarray:
+    """Direct solve A_1 x = b on the coarsest grid (Sec. 3.2): Cholesky."""
+    g = hier.levels[0].grid
+    return scipy.linalg.cho_solve(hier.coarse_chol, b.ravel()).reshape(g.shape)
+
+
+# ---------------------------------------------------------------------------
+# V-cycle preconditioner: eq. (eRichard), Appendix A
+# ---------------------------------------------------------------------------
+
+
+def vcycle(hier: Hierarchy, b: np.ndarray, level: int | None = None) -> np.ndarray:
+    """One V-cycle from a zero guess for A_l x = b (Sec. 3.2, Appendix A):
+    pre-smooth from 0, restrict the residual, recurse, prolong and add the
+    correction, post-smooth with the same polynomial; the coarsest grid is
+    solved directly.  The map b -> x is the matrix M_l of Appendix A."""
+    p = hier.params
+    if level is None:
+        level = len(hier.levels) - 1
+    if level == 0:
+        return coarse_solve(hier, b)
+    lev = hier.levels[level]
+    x = chebyshev_smooth(lev.grid, lev.a, b, None, lev.lam_max, lev.lam_min, p.cheb_steps, p.smoother_pc)
+    r = b - apply_operator(lev.grid, lev.a, x)
+    e = vcycle(hier, restrict(r), level - 1)
+    x = x + prolong(e, p.prolongation)
+    x = chebyshev_smooth(lev.grid, lev.a, b, x, lev.lam_max, lev.lam_min, p.cheb_steps, p.smoother_pc)
+    return x
+
+
+# ---------------------------------------------------------------------------
+# FGMRES, Algorithm 1 (Sec. 3.1) with the stopping rule eq. (criterion)
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class SolveInfo:
+    iterations: int = 0
+    restarts: int = 0
+    converged: bool = False
+    true_rel_residual: float = float("nan")
+    history: list = field(default_factory=list)   # Arnoldi residual estimates / ||b||
+
+
+def _least_squares_residual(Hbar: np.ndarray, beta: float):
+    """min_y || beta e_1 - Hbar y || (Algorithm 1, line 11) by a library
+    least-squares solve; returns (y, residual norm)."""
+    rhs = np.zeros(Hbar.shape[0])
+    rhs[0] = beta
+    y = np.linalg.lstsq(Hbar, rhs, rcond=None)[0]
+    return y, float(np.linalg.norm(rhs - Hbar @ y))
+
+
+def fgmres(grid: Grid, a: np.ndarray, b: np.ndarray, x0: np.ndarray | None, precond,
+           params: OracleParams) -> tuple[np.ndarray, SolveInfo]:
+    """Restarted FGMRES with right preconditioning (Algorithm 1, Sec. 3.1).
+
+    Arnoldi uses modified Gram-Schmidt (line 8); the stopping test (line 12)
+    compares the least-squares residual with rtol * ||b|| (eq. (criterion));
+    after forming x_k (line 15) the true residual is checked (R8) and the
+    method restarts from x_k if it is not below the tolerance (line 16).
+    """
+    info = SolveInfo()
+    m = params.restart
+    x = np.zeros(grid.shape) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    bnorm = float(np.linalg.norm(b))
+    if bnorm == 0.0:
+        info.converged = True
+        info.true_rel_residual = 0.0
+        return np.zeros(grid.shape), info
+    while True:
+        r = b - apply_operator(grid, a, x)
+        beta = float(np.linalg.norm(r))
+        info.true_rel_residual = beta / bnorm
+        if info.true_rel_residual < params.rtol:
+            info.converged = True
+            return x, info
+        if info.iterations >= params.max_iters or beta == 0.0:
+            return x, info
+        V = [r.ravel() / beta]
+        Z = []
+        H = np.zeros((m + 1, m))
+        k = 0
+        y = np.zeros(0)
+        for j in range(m):
+            z = precond(V[j].reshape(grid.shape)).ravel()
+            Z.append(z)
+            w = apply_operator(grid, a, z.reshape(grid.shape)).ravel()
+            for i in range(j + 1):
+                H[i, j] = np.dot(w, V[i])
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            k = j + 1
+            info.iterations += 1
+            y, res = _least_squares_residual(H[: j + 2, : j + 1], beta)
+            info.history.append(res / bnorm)
+            if H[j + 1, j] == 0.0:
+                break                                   # lucky breakdown: exact in K_j
+            V.append(w / H[j + 1, j])
+            if res / bnorm < params.rtol or info.iterations >= params.max_iters:
+                break
+        for i in range(k):
+            x = x + y[i] * Z[i].reshape(grid.shape)
+        info.restarts += 1
+
+
+def solve(params: OracleParams, a: np.ndarray, f: np.ndarray, phi0: np.ndarray | None = None,
+          homogeneous: bool = False, hierarchy: Hierarchy | None = None):
+    """phi solving -div(a grad phi) = f with the plate data of ``params``
+    (or zero plate data if ``homogeneous``), by GMG-preconditioned FGMRES."""
+    nz, ny, nx = a.shape
+    grid = Grid(nx, ny, nz, params.lx, params.ly, params.lz)
+    hier = hierarchy if hierarchy is not None else build_hierarchy(grid, a, params)
+    if homogeneous:
+        b = np.array(f, dtype=np.float64, copy=True)
+    else:
+        b = assemble_rhs(grid, a, f, params.phi_bottom, params.phi_top)
+    phi, info = fgmres(grid, a, b, phi0, lambda v: vcycle(hier, v), params)
+    return phi, info, hier
+
+
+# ---------------------------------------------------------------------------
+# Field and adjoint
+# ---------------------------------------------------------------------------
+
+
+def field_from_potential(grid: Grid, phi: np.ndarray, g_bottom: float, g_top: float):
+    """E = -grad(phi) by cell-centred central differences (Sec. 2.2), with the
+    ghost values of the boundary conditions: mirror (Neumann) on x/y walls and
+    2g - phi (R2) on the plates."""
+    def central(u, axis, h, ghost_lo, ghost_hi):
+        u = np.moveaxis(u, axis, 0)
+        ext = np.concatenate([ghost_lo(u[:1]), u, ghost_hi(u[-1:])], axis=0)
+        return np.moveaxis(-(ext[2:] - ext[:-2]) / (2.0 * h), 0, axis)
+
+    mirror = lambda edge: edge                       # noqa: E731
+    ex = central(phi, 2, grid.hx, mirror, mirror)
+    ey = central(phi, 1, grid.hy, mirror, mirror)
+    ez = central(phi, 0, grid.hz, lambda e: 2.0 * g_bottom - e, lambda e: 2.0 * g_top - e)
+    return ex, ey, ez
+
+
+def adjoint_coefficient_grad(grid: Grid, phi: np.ndarray, lam: np.ndarray,
+                             g_bottom: float, g_top: float) -> np.ndarray:
+    """dL/da for L(phi), phi = A(a)^{-1} b(a, f), given lambda = A^{-1} dL/dphi.
+
+    dL/da_p = lambda^T (d b/d a_p - (d A/d a_p) phi).  With a_f = (a_p+a_q)/2
+    on interior faces and a_f = a_p on plate faces (eq. (e18), R1, R2):
+      dL/da_p = -1/2 sum_{interior f=(p,q)} (lam_p - lam_q)(phi_p - phi_q)/h_f^2
+                - sum_{plate faces of p} 2 lam_p (phi_p - g)/hz^2.
+    Not in the paper: the derivative of its discrete operator.
+    """
+    g = np.zeros(grid.shape)
+    for axis, h in ((2, grid.hx), (1, grid.hy), (0, grid.hz)):
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[axis] = slice(0, -1)
+        hi[axis] = slice(1, None)
+        lo, hi = tuple(lo), tuple(hi)
+        t = 0.5 * (lam[lo] - lam[hi]) * (phi[lo] - phi[hi]) / h**2
+        g[lo] -= t
+        g[hi] -= t
+    g[0] -= 2.0 * lam[0] * (phi[0] - g_bottom) / grid.hz**2
+    g[-1] -= 2.0 * lam[-1] * (phi[-1] - g_top) / grid.hz**2
+    return g

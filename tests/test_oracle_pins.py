@@ -1,0 +1,538 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test fixes one part of the oracle by something the paper or the
+mathematics determines independently: a hand-derived operator (golden file),
+closed-form spectra (DCT-II / DST-II), a manufactured solution, a 1-D
+tridiagonal reduction, dense linear algebra at 8^3, the recursion for the
+V-cycle matrix M_l of Appendix A, the Chebyshev polynomial of eq. (qntn),
+and finite differences for the adjoint.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.fft
+import scipy.linalg
+
+from oracle import gmg_oracle as O
+from streamer_inputs import random_coefficient, random_field, make_inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _grid(shape, l=(1.0, 1.0, 1.0)):
+    nz, ny, nx = shape
+    return O.Grid(nx, ny, nz, *l)
+
+
+# ---------------------------------------------------------------------------
+# Operator eq. (e18) + boundary conditions
+# ---------------------------------------------------------------------------
+
+
+def _read_golden(name):
+    rows = {}
+    A = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            key, *vals = line.split()
+            vals = [float(v) for v in vals]
+            if key == "A":
+                A.append(vals)
+            else:
+                rows[key] = vals
+    rows["A"] = np.array(A)
+    return rows
+
+
+def test_operator_matches_hand_derived_golden():
+    g = _read_golden("operator_2x1x2.txt")
+    nx, ny, nz = (int(v) for v in g["shape"])
+    grid = O.Grid(nx, ny, nz)
+    a = np.array(g["a"]).reshape(grid.shape)
+    np.testing.assert_allclose(O.dense_operator(grid, a), g["A"], rtol=0, atol=1e-12)
+    gb, gt = g["g"]
+    b = O.assemble_rhs(grid, a, np.zeros(grid.shape), gb, gt)
+    np.testing.assert_allclose(b.ravel(), g["b"], rtol=0, atol=1e-12)
+    phi = np.array(g["phi"]).reshape(grid.shape)
+    ex, ey, ez = O.field_from_potential(grid, phi, gb, gt)
+    np.testing.assert_allclose(ex.ravel(), g["Ex"], atol=1e-12)
+    np.testing.assert_allclose(ey.ravel(), g["Ey"], atol=1e-12)
+    np.testing.assert_allclose(ez.ravel(), g["Ez"], atol=1e-12)
+
+
+def test_operator_symmetric_positive_definite():
+    shape = (5, 6, 4)
+    grid = _grid(shape, (0.7, 1.3, 1.0))
+    a = random_coefficient(1, shape, contrast=1e3)
+    A = O.dense_operator(grid, a)
+    np.testing.assert_allclose(A, A.T, rtol=0, atol=1e-12 * np.abs(A).max())
+    lam = np.linalg.eigvalsh(A)
+    assert lam.min() > 0.0
+    np.linalg.cholesky(A)
+    # D - N splitting and diagonal agree with the dense matrix
+    np.testing.assert_allclose(np.diag(A), O.diagonal(grid, a).ravel(), rtol=1e-14)
+    x = random_field(2, shape)
+    np.testing.assert_allclose(O.apply_operator(grid, a, x),
+                               O.diagonal(grid, a) * x - O.neighbour_sum(grid, a, x), rtol=1e-12, atol=1e-10)
+
+
+def _spectral_symbols(grid):
+    """Eigenvalues of the constant-coefficient operator: DCT-II modes (Neumann)
+    in x, y and DST-II modes (Dirichlet through the ghost -phi) in z, each
+    (4/h^2) sin^2(pi m / (2n)); m = 0..n-1 for cosines, 1..n for sines."""
+    lx = 4.0 / grid.hx**2 * np.sin(np.pi * np.arange(grid.nx) / (2 * grid.nx)) ** 2
+    ly = 4.0 / grid.hy**2 * np.sin(np.pi * np.arange(grid.ny) / (2 * grid.ny)) ** 2
+    lz = 4.0 / grid.hz**2 * np.sin(np.pi * np.arange(1, grid.nz + 1) / (2 * grid.nz)) ** 2
+    return lz[:, None, None] + ly[None, :, None] + lx[None, None, :]
+
+
+def _spectral_apply(grid, x, inverse=False):
+    lam = _spectral_symbols(grid)
+    c = scipy.fft.dctn(x, type=2, axes=(1, 2), norm="ortho")
+    c = scipy.fft.dst(c, type=2, axis=0, norm="ortho")
+    c = c / lam if inverse else c * lam
+    c = scipy.fft.idst(c, type=2, axis=0, norm="ortho")
+    return scipy.fft.idctn(c, type=2, axes=(1, 2), norm="ortho")
+
+
+def test_constant_coefficient_operator_is_diagonal_in_dct_dst_basis():
+    shape = (6, 10, 8)
+    grid = _grid(shape, (1.0, 2.0, 0.5))
+    a = np.ones(shape)
+    x = random_field(3, shape)
+    np.testing.assert_allclose(O.apply_operator(grid, a, x), _spectral_apply(grid, x), rtol=1e-11, atol=1e-9)
+
+
+def test_fgmres_const32_matches_spectral_exact_solution():
+    """Workload const32 (a = 1): the solve agrees with the exact discrete
+    solution from the DCT/DST diagonalisation within cond(A) * rtol."""
+    inp = make_inputs("const32")
+    a, f = inp["a"], inp["f"]
+    grid = _grid(a.shape)
+    params = O.OracleParams()
+    phi, info, _ = O.solve(params, a, f)
+    assert info.converged and info.true_rel_residual < 1e-8
+    b = O.assemble_rhs(grid, a, f, params.phi_bottom, params.phi_top)
+    exact = _spectral_apply(grid, b, inverse=True)
+    lam = _spectral_symbols(grid)
+    cond = lam.max() / lam.min()
+    assert np.linalg.norm(phi - exact) / np.linalg.norm(exact) < cond * 1e-8
+    assert np.linalg.norm(phi - exact) / np.linalg.norm(exact) < 1e-7
+
+
+def test_one_dimensional_reduction_matches_tridiagonal_solve():
+    """a = a(z), f = f(z): phi is independent of x, y and equals the solution
+    of the 1-D finite-volume problem (Thomas / banded solve)."""
+    nz, ny, nx = 32, 8, 8
+    grid = O.Grid(nx, ny, nz)
+    z = (np.arange(nz) + 0.5) / nz
+    az = 1.0 + 50.0 * np.exp(-((z - 0.5) / 0.1) ** 2)
+    fz = 100.0 * np.sin(3 * z)
+    a = np.broadcast_to(az[:, None, None], grid.shape).copy()
+    f = np.broadcast_to(fz[:, None, None], grid.shape).copy()
+    params = O.OracleParams(rtol=1e-13, phi_bottom=0.3, phi_top=-1.0, coarse_min=2)
+    phi, info, _ = O.solve(params, a, f)
+    assert info.converged
+    # 1-D system: -(a_{k+1/2}(u_{k+1}-u_k) - a_{k-1/2}(u_k-u_{k-1}))/h^2 = f_k
+    h2 = grid.hz**2
+    af = 0.5 * (az[1:] + az[:-1])
+    upper = np.zeros(nz)
+    diag = np.zeros(nz)
+    lower = np.zeros(nz)
+    rhs = fz.copy()
+    diag[:-1] += af / h2
+    diag[1:] += af / h2
+    upper[1:] = -af / h2
+    lower[:-1] = -af / h2
+    diag[0] += 2 * az[0] / h2
+    diag[-1] += 2 * az[-1] / h2
+    rhs[0] += 2 * az[0] * params.phi_bottom / h2
+    rhs[-1] += 2 * az[-1] * params.phi_top / h2
+    u = scipy.linalg.solve_banded((1, 1), np.vstack([upper, diag, lower]), rhs)
+    np.testing.assert_allclose(phi, np.broadcast_to(u[:, None, None], grid.shape), rtol=1e-9, atol=1e-10)
+
+
+def _mms(variable):
+    sympy = pytest.importorskip("sympy")
+    x, y, z = sympy.symbols("x y z")
+    phi = sympy.cos(sympy.pi * x) * sympy.cos(sympy.pi * y) * sympy.sin(sympy.pi * z) + z
+    if variable:
+        a = 2 + sympy.cos(sympy.pi * x) * sympy.cos(sympy.pi * y) * sympy.cos(sympy.pi * z)
+    else:
+        a = sympy.Integer(1)
+    f = -sum(sympy.diff(a * sympy.diff(phi, v), v) for v in (x, y, z))
+    grads = [-sympy.diff(phi, v) for v in (x, y, z)]
+    mk = lambda e: sympy.lambdify((x, y, z), e, "numpy")   # noqa: E731
+    return mk(phi), mk(a), mk(f), [mk(g) for g in grads]
+
+
+@pytest.mark.parametrize("variable", [False, True])
+def test_manufactured_solution_second_order(variable):
+    """phi = cos(pi x) cos(pi y) sin(pi z) + z satisfies the plate data 0 / 1
+    and zero flux on the side walls; the discrete solution and E converge at
+    second order (Sec. 2.2 expects second-order accuracy)."""
+    phi_fn, a_fn, f_fn, grad_fns = _mms(variable)
+    errs, eerrs = [], []
+    for n in (16, 32, 64):
+        grid = O.Grid(n, n, n)
+        c = (np.arange(n) + 0.5) / n
+        Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+        a = np.broadcast_to(a_fn(X, Y, Z), grid.shape).astype(np.float64).copy()
+        f = np.broadcast_to(f_fn(X, Y, Z), grid.shape).astype(np.float64).copy()
+        params = O.OracleParams(rtol=1e-12, phi_bottom=0.0, phi_top=1.0)
+        phi, info, _ = O.solve(params, a, f)
+        assert info.converged
+        errs.append(np.abs(phi - phi_fn(X, Y, Z)).max())
+        ex, ey, ez = O.field_from_potential(grid, phi, 0.0, 1.0)
+        # a fixed physical interior region, [0.25, 0.75]^3 (the cells next to
+        # the plates converge pre-asymptotically)
+        m = (c > 0.25) & (c < 0.75)
+        s = np.ix_(m, m, m)
+        e = max(np.abs(ex - grad_fns[0](X, Y, Z))[s].max(),
+                np.abs(ey - grad_fns[1](X, Y, Z))[s].max(),
+                np.abs(ez - grad_fns[2](X, Y, Z))[s].max())
+        eerrs.append(e)
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    eorders = np.log2(np.array(eerrs[:-1]) / np.array(eerrs[1:]))
+    assert np.all(orders > 1.8), (errs, orders)
+    assert np.all(eorders > 1.75), (eerrs, eorders)
+
+
+def test_linear_potential_gives_uniform_field():
+    """phi = z at the cell centres with plate data 0 and lz satisfies the ghost
+    rule exactly, so E = (0, 0, -1) in every cell, boundary cells included."""
+    shape = (7, 5, 6)
+    grid = _grid(shape, (1.0, 1.0, 2.0))
+    z = (np.arange(shape[0]) + 0.5) * grid.hz
+    phi = np.broadcast_to(z[:, None, None], shape).copy()
+    ex, ey, ez = O.field_from_potential(grid, phi, 0.0, 2.0)
+    np.testing.assert_allclose(ex, 0.0, atol=1e-14)
+    np.testing.assert_allclose(ey, 0.0, atol=1e-14)
+    np.testing.assert_allclose(ez, -1.0, rtol=1e-13)
+    # and A phi - bc = 0 for a = 1 (a linear potential is harmonic)
+    a = np.ones(shape)
+    r = O.apply_operator(grid, a, phi) - O.assemble_rhs(grid, a, np.zeros(shape), 0.0, 2.0)
+    np.testing.assert_allclose(r, 0.0, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Smoother: eq. (qntn), SSOR in red-black order
+# ---------------------------------------------------------------------------
+
+
+def _cheb_T(s, t):
+    return np.polynomial.chebyshev.chebval(t, [0] * s + [1])
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3, 4])
+def test_chebyshev_smoother_closed_form_on_eigenmode(steps):
+    """With B = I and constant a, an eigenmode u with eigenvalue lam is mapped
+    (b = 0) to q(lam) u, q = T_s((lmax+lmin-2 lam)/(lmax-lmin)) / T_s((lmax+lmin)/(lmax-lmin)),
+    eq. (qntn) with s = n+1 steps."""
+    shape = (8, 8, 8)
+    grid = _grid(shape)
+    a = np.ones(shape)
+    lam_all = _spectral_symbols(grid)
+    lmax, lmin = 1.1 * lam_all.max(), 0.1 * lam_all.max()
+    for (mz, my, mx) in [(0, 0, 0), (2, 3, 1), (7, 7, 7), (4, 0, 6)]:
+        c = np.zeros(shape)
+        c[mz, my, mx] = 1.0
+        u = scipy.fft.idst(scipy.fft.idctn(c, type=2, axes=(1, 2), norm="ortho"), type=2, axis=0, norm="ortho")
+        lam = lam_all[mz, my, mx]
+        out = O.chebyshev_smooth(grid, a, np.zeros(shape), u, lmax, lmin, steps, pc="identity")
+        q = _cheb_T(steps, (lmax + lmin - 2 * lam) / (lmax - lmin)) / _cheb_T(steps, (lmax + lmin) / (lmax - lmin))
+        np.testing.assert_allclose(out, q * u, atol=1e-13 * np.abs(u).max() + 1e-15)
+
+
+def _rb_split(grid, a):
+    A = O.dense_operator(grid, a)
+    red = O.red_mask(grid).ravel()
+    perm = np.concatenate([np.flatnonzero(red), np.flatnonzero(~red)])
+    Ap = A[np.ix_(perm, perm)]
+    D = np.diag(np.diag(Ap))
+    L = np.tril(Ap, -1)
+    U = np.triu(Ap, 1)
+    return A, perm, D, L, U
+
+
+def test_sgs_is_ssor_in_red_black_order():
+    """z = B^{-1} r with B = (D+L) D^{-1} (D+U) in red-black ordering (SSOR, omega = 1)."""
+    shape = (4, 6, 5)
+    grid = _grid(shape)
+    a = random_coefficient(4, shape, contrast=100.0)
+    _, perm, D, L, U = _rb_split(grid, a)
+    B = (D + L) @ np.linalg.inv(D) @ (D + U)
+    r = random_field(5, shape).ravel()
+    zp = np.linalg.solve(B, r[perm])
+    z = np.empty_like(zp)
+    z[perm] = zp
+    np.testing.assert_allclose(O.sgs_redblack(grid, a, r.reshape(shape)).ravel(), z, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("steps", [2, 3])
+def test_preconditioned_chebyshev_matches_matrix_polynomial(steps):
+    """x -> S(x, b=0) equals q_s(B^{-1}A) x, q_s from eq. (qntn), evaluated by
+    the Chebyshev three-term recurrence on the dense matrix B^{-1}A."""
+    shape = (4, 4, 6)
+    grid = _grid(shape)
+    a = random_coefficient(6, shape, contrast=30.0)
+    A, perm, D, L, U = _rb_split(grid, a)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size)
+    B = ((D + L) @ np.linalg.inv(D) @ (D + U))[np.ix_(inv, inv)]
+    C = np.linalg.solve(B, A)
+    lmax, lmin = 1.05, 0.2
+    n = C.shape[0]
+    Y = ((lmax + lmin) * np.eye(n) - 2 * C) / (lmax - lmin)
+    T0, T1 = np.eye(n), Y
+    for _ in range(steps - 1):
+        T0, T1 = T1, 2 * Y @ T1 - T0
+    q = T1 / _cheb_T(steps, (lmax + lmin) / (lmax - lmin))
+    x = random_field(7, shape)
+    out = O.chebyshev_smooth(grid, a, np.zeros(shape), x, lmax, lmin, steps, pc="sgs")
+    np.testing.assert_allclose(out.ravel(), q @ x.ravel(), rtol=1e-11, atol=1e-12)
+
+
+def test_eigen_estimate_bounds_the_sgs_spectrum():
+    """lam_hat (Sec. 3.2) is a Ritz value of B^{-1}A: below its largest
+    eigenvalue, within a few percent of it, and B^{-1}A has spectrum in (0, 1]."""
+    shape = (8, 8, 8)
+    grid = _grid(shape)
+    a = random_coefficient(8, shape, contrast=1e3)
+    A, perm, D, L, U = _rb_split(grid, a)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size)
+    B = ((D + L) @ np.linalg.inv(D) @ (D + U))[np.ix_(inv, inv)]
+    ev = np.linalg.eigvals(np.linalg.solve(B, A)).real
+    assert ev.min() > 0 and ev.max() <= 1.0 + 1e-12
+    lmax, lmin, lam_hat = O.estimate_eig_bounds(grid, a, O.OracleParams())
+    assert lam_hat <= ev.max() * (1 + 1e-12)
+    assert lam_hat > 0.9 * ev.max()
+    assert lmax == pytest.approx(1.1 * lam_hat) and lmin == pytest.approx(0.1 * lam_hat)
+
+
+def test_splitmix64_reference_values():
+    """splitmix64 from the published generator: the first outputs for seed 0
+    (state advanced by the golden gamma before mixing)."""
+    out = O.splitmix64(np.arange(3, dtype=np.uint64))
+    assert [int(v) for v in out] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+# ---------------------------------------------------------------------------
+# Transfers, V-cycle (Appendix A), coarse solve
+# ---------------------------------------------------------------------------
+
+
+def test_transfers_reproduce_constants_and_linears():
+    c = random_field(9, (4, 4, 4))
+    assert O.restrict(np.full((8, 8, 8), 3.5)) == pytest.approx(np.full((4, 4, 4), 3.5))
+    # piecewise-constant prolongation is 8 x the adjoint of restriction
+    f = random_field(10, (8, 8, 8))
+    assert np.dot(O.prolong(c, "constant").ravel(), f.ravel()) == pytest.approx(8 * np.dot(c.ravel(), O.restrict(f).ravel()))
+    # trilinear reproduces a linear function away from the walls
+    n = 8
+    cc = (np.arange(n) + 0.5) / n
+    cf = (np.arange(2 * n) + 0.5) / (2 * n)
+    Zc, Yc, Xc = np.meshgrid(cc, cc, cc, indexing="ij")
+    Zf, Yf, Xf = np.meshgrid(cf, cf, cf, indexing="ij")
+    lin = lambda X, Y, Z: 1 + 2 * X - 3 * Y + 0.5 * Z   # noqa: E731
+    p = O.prolong(lin(Xc, Yc, Zc))
+    np.testing.assert_allclose(p[1:-1, 1:-1, 1:-1], lin(Xf, Yf, Zf)[1:-1, 1:-1, 1:-1], atol=1e-13)
+    # Neumann walls: constants are reproduced up to the wall in x and y
+    pc = O.prolong(np.ones((4, 4, 4)))
+    np.testing.assert_allclose(pc[1:-1], 1.0, atol=1e-15)
+    # Dirichlet plates: odd ghost halves the boundary child in z
+    np.testing.assert_allclose(pc[0], 0.5, atol=1e-15)
+
+
+def _dense_from_map(fn, n, shape):
+    m = np.zeros((n, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        m[:, i] = fn(e.reshape(shape)).ravel()
+    return m
+
+
+@pytest.mark.parametrize("coarse_min,prolongation", [(4, "trilinear"), (2, "trilinear"), (2, "constant")])
+def test_vcycle_equals_appendix_a_recursion(coarse_min, prolongation):
+    """vcycle(v) = M_L v with M_1 = A_1^{-1}, M_l = Q_l P_l + P_l +
+    Q_l P_{l-1,l} M_{l-1} R_{l,l-1} (I - A_l P_l) (Appendix A), where the
+    smoother x -> Q_l x + P_l b (eq. (e19)) is read off as dense matrices."""
+    shape = (8, 8, 8)
+    grid = _grid(shape)
+    a = random_coefficient(11, shape, contrast=50.0)
+    params = O.OracleParams(coarse_min=coarse_min, prolongation=prolongation, cheb_steps=3)
+    hier = O.build_hierarchy(grid, a, params)
+    M = None
+    for li, lev in enumerate(hier.levels):
+        n = lev.grid.size
+        A = O.dense_operator(lev.grid, lev.a)
+        if li == 0:
+            M = np.linalg.inv(A)
+            continue
+        sm = lambda x, b: O.chebyshev_smooth(lev.grid, lev.a, b, x, lev.lam_max, lev.lam_min,   # noqa: E731
+                                             params.cheb_steps, params.smoother_pc)
+        P = _dense_from_map(lambda e: sm(None, e), n, lev.grid.shape)
+        Q = _dense_from_map(lambda e: sm(e, np.zeros(lev.grid.shape)), n, lev.grid.shape)
+        # the smoother is a consistent iteration: Q = I - P A  (eq. (e19))
+        np.testing.assert_allclose(Q, np.eye(n) - P @ A, atol=1e-11)
+        cshape = hier.levels[li - 1].grid.shape
+        nc = hier.levels[li - 1].grid.size
+        R = np.array([O.restrict(e.reshape(lev.grid.shape)).ravel() for e in np.eye(n)]).T
+        Pr = np.array([O.prolong(e.reshape(cshape), prolongation).ravel() for e in np.eye(nc)]).T
+        M = Q @ P + P + Q @ Pr @ M @ R @ (np.eye(n) - A @ P)
+    v = random_field(12, shape)
+    np.testing.assert_allclose(O.vcycle(hier, v).ravel(), M @ v.ravel(), rtol=1e-10, atol=1e-12)
+
+
+def test_coarse_direct_solve_residual():
+    shape = (4, 4, 4)
+    grid = _grid(shape)
+    a = random_coefficient(13, shape, contrast=1e3)
+    hier = O.build_hierarchy(grid, a, O.OracleParams(coarse_min=4))
+    assert len(hier.levels) == 1
+    b = random_field(14, shape)
+    x = O.coarse_solve(hier, b)
+    A = O.dense_operator(grid, a)
+    assert np.linalg.norm(A @ x.ravel() - b.ravel()) <= 1e-14 * np.linalg.norm(A) * np.linalg.norm(x)
+
+
+def test_level_count_rules():
+    assert O.level_count(32, 32, 32, 4) == 4
+    assert O.level_count(512, 512, 512, 4) == 8
+    assert O.level_count(256, 256, 320, 4) == 7          # 4 x 4 x 5 coarsest
+    with pytest.raises(ValueError):
+        O.level_count(12, 12, 10, 4)
+
+
+# ---------------------------------------------------------------------------
+# FGMRES, Algorithm 1
+# ---------------------------------------------------------------------------
+
+
+def test_fgmres_matches_dense_direct_solve_8cube():
+    shape = (8, 8, 8)
+    grid = _grid(shape)
+    a = random_coefficient(15, shape, contrast=1e3)
+    f = random_field(16, shape) * 100
+    for coarse_min in (4, 2):
+        params = O.OracleParams(coarse_min=coarse_min)
+        phi, info, _ = O.solve(params, a, f)
+        assert info.converged and info.true_rel_residual < 1e-8
+        A = O.dense_operator(grid, a)
+        b = O.assemble_rhs(grid, a, f, params.phi_bottom, params.phi_top)
+        exact = np.linalg.solve(A, b.ravel())
+        cond = np.linalg.cond(A)
+        assert np.linalg.norm(phi.ravel() - exact) / np.linalg.norm(exact) <= cond * 1e-8
+
+
+def test_fgmres_exact_preconditioner_converges_in_one_step():
+    shape = (6, 4, 4)
+    grid = _grid(shape)
+    a = random_coefficient(17, shape, contrast=10.0)
+    A = O.dense_operator(grid, a)
+    Ainv = np.linalg.inv(A)
+    b = random_field(18, shape)
+    x, info = O.fgmres(grid, a, b, None, lambda v: (Ainv @ v.ravel()).reshape(shape), O.OracleParams(rtol=1e-12))
+    assert info.iterations == 1 and info.converged
+    np.testing.assert_allclose(x.ravel(), Ainv @ b.ravel(), rtol=1e-10)
+
+
+def test_fgmres_identity_preconditioner_is_gmres():
+    """With M = I, FGMRES is GMRES: least-squares residuals never increase and
+    equal the minimal residual over the Krylov space K_j(A, b)."""
+    shape = (4, 4, 4)
+    grid = _grid(shape)
+    a = random_coefficient(19, shape, contrast=10.0)
+    A = O.dense_operator(grid, a)
+    b = random_field(20, shape)
+    params = O.OracleParams(rtol=1e-10, restart=30, max_iters=12)
+    _, info = O.fgmres(grid, a, b, None, lambda v: np.array(v, copy=True), params)
+    h = np.array(info.history)
+    assert np.all(np.diff(h) <= 1e-12)
+    K = [b.ravel() / np.linalg.norm(b)]
+    for j in range(6):
+        K.append(A @ K[-1])
+        K[-1] /= np.linalg.norm(K[-1])
+        Qk, _ = np.linalg.qr(np.array(K[:-1]).T)
+        AQ = A @ Qk
+        y = np.linalg.lstsq(AQ, b.ravel(), rcond=None)[0]
+        mr = np.linalg.norm(b.ravel() - AQ @ y) / np.linalg.norm(b)
+        assert h[j] == pytest.approx(mr, rel=1e-6, abs=1e-13)
+
+
+def test_restart_and_true_residual_rule():
+    """Restart m = 2 forces several cycles; the returned x has true residual
+    below rtol and the iteration cap reports non-convergence."""
+    inp = make_inputs("channel128", n=16)
+    params = O.OracleParams(restart=2, coarse_min=4)
+    phi, info, _ = O.solve(params, inp["a"], inp["f"])
+    assert info.converged and info.restarts > 2 and info.true_rel_residual < 1e-8
+    params = O.OracleParams(max_iters=2)
+    phi, info, _ = O.solve(params, inp["a"], inp["f"])
+    assert not info.converged and info.iterations == 2
+
+
+def test_scaling_invariance():
+    """(a, f) -> (c a, c f) leaves phi unchanged: A and b both scale by c."""
+    inp = make_inputs("channel128", n=16)
+    params = O.OracleParams(rtol=1e-12)
+    p1, _, _ = O.solve(params, inp["a"], inp["f"])
+    p2, _, _ = O.solve(params, 7.0 * inp["a"], 7.0 * inp["f"])
+    np.testing.assert_allclose(p1, p2, rtol=1e-9, atol=1e-11)
+
+
+# ---------------------------------------------------------------------------
+# Adjoint (not in the paper: derivative of the discrete solve)
+# ---------------------------------------------------------------------------
+
+
+def test_adjoint_matches_finite_differences_dense():
+    """L = w . phi(a, f) with phi from a dense direct solve; central differences
+    in a_p and f_p agree with dL/da from the adjoint face formula and with
+    dL/df = lambda = A^{-1} w."""
+    shape = (4, 3, 5)
+    grid = _grid(shape, (1.0, 0.8, 1.2))
+    a = random_coefficient(21, shape, contrast=20.0)
+    f = random_field(22, shape) * 10
+    w = random_field(23, shape)
+    gb, gt = 0.4, 1.3
+
+    def loss(aa, ff):
+        A = O.dense_operator(grid, aa)
+        b = O.assemble_rhs(grid, aa, ff, gb, gt)
+        return float(np.dot(w.ravel(), np.linalg.solve(A, b.ravel())))
+
+    A = O.dense_operator(grid, a)
+    phi = np.linalg.solve(A, O.assemble_rhs(grid, a, f, gb, gt).ravel()).reshape(shape)
+    lam = np.linalg.solve(A, w.ravel()).reshape(shape)
+    ga = O.adjoint_coefficient_grad(grid, phi, lam, gb, gt)
+    rng = np.random.default_rng(24)
+    for p in rng.choice(a.size, size=12, replace=False):
+        da = np.zeros(a.size)
+        h = 1e-4 * a.ravel()[p]     # truncation ~1e-8, round-off noise ~1e-9 (relative)
+        da[p] = h
+        da = da.reshape(shape)
+        fd = (loss(a + da, f) - loss(a - da, f)) / (2 * h)
+        assert ga.ravel()[p] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+        df = np.zeros(a.size)
+        df[p] = 1e-3
+        df = df.reshape(shape)
+        fdf = (loss(a, f + df) - loss(a, f - df)) / 2e-3
+        assert lam.ravel()[p] == pytest.approx(fdf, rel=1e-8, abs=1e-12)
+
+
+def test_adjoint_dot_product_identity():
+    """w . A^{-1} f = f . A^{-1} w for the solver's (symmetric) operator."""
+    inp = make_inputs("adjoint", n=16)
+    params = O.OracleParams(rtol=1e-12)
+    phi, _, hier = O.solve(params, inp["a"], inp["f"], homogeneous=True)
+    lam, _, _ = O.solve(params, inp["a"], inp["w"], homogeneous=True, hierarchy=hier)
+    lhs = np.dot(inp["w"].ravel(), phi.ravel())
+    rhs = np.dot(inp["f"].ravel(), lam.ravel())
+    assert lhs == pytest.approx(rhs, rel=1e-9)
