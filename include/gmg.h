@@ -1,0 +1,240 @@
+/*
+ * gmg.h - C ABI of the GB300 GMG-preconditioned FGMRES Poisson-type solver.
+ *
+ * Solves -div(a grad phi) = f on a uniform cell-centred 3-D grid
+ * (nx x ny x nz cells on [0,lx] x [0,ly] x [0,lz]) with the 7-point
+ * finite-volume discretisation of eq. (e18) (Sec. 2.2 of Lin, Zhuang, Cai,
+ * Zeng, Bao, "An efficient and accurate MPI-based parallel simulator for
+ * streamer discharges in three dimensions"):
+ *
+ *   (A phi)_p = sum_{interior faces f=(p,q)} a_f (phi_p - phi_q) / h_f^2
+ *             + sum_{plate faces of p} 2 a_p (phi_p - g) / hz^2 ,
+ *   a_f = (a_p + a_q) / 2  (Sec. 2.2, face means of the cell coefficient),
+ *
+ * Dirichlet potential g on the plates z = 0 and z = lz, zero flux through
+ * the side faces x = 0, lx and y = 0, ly (the model eq. (eM), Sec. 1).  The
+ * plate faces use a_f = a_p and the ghost value 2g - phi_p.
+ *
+ * The solver is FGMRES with right preconditioning (Algorithm 1, Sec. 3.1)
+ * whose preconditioner is one geometric-multigrid V-cycle from a zero guess
+ * (Sec. 3.2, eq. (eRichard), Appendix A) with an SSOR-preconditioned
+ * Chebyshev smoother (eqs. (smootheq), (qntn), (e19)) and a direct solve on
+ * the coarsest grid.  It stops when ||b - A phi||_2 / ||b||_2 < rtol
+ * (eq. (criterion), Sec. 5.2), checked on the true FP64 residual.
+ *
+ * Conventions for every entry point below:
+ *  - Layout: every field is a contiguous array of nz*ny*nx elements in
+ *    [k][j][i] order, x fastest; cell (i,j,k) has centre
+ *    ((i+1/2)hx, (j+1/2)hy, (k+1/2)hz).
+ *  - Ownership: pointers named *_dev are device memory owned by the caller,
+ *    read or written only during the call (the library keeps no caller
+ *    pointer).  Pointers named *_host are host memory owned by the caller.
+ *    The context owns all internal device workspace and frees it in
+ *    gmg_destroy().
+ *  - Streams: all device work is enqueued on the context's stream (given to
+ *    gmg_setup / gmg_set_stream; NULL = legacy default stream).  Calls that
+ *    return a result on the host (norms, solve info) synchronise that stream.
+ *  - Errors: every call returns a gmg_status; nothing aborts and no C++
+ *    exception crosses the ABI.  CUDA failures map to GMG_ERR_CUDA, failed
+ *    device allocations to GMG_ERR_ALLOC, invalid arguments to GMG_ERR_ARG.
+ *  - Threads: a context must not be used by two host threads at once.
+ */
+#ifndef GMG_H_
+#define GMG_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GMG_MAX_HISTORY 256
+
+typedef struct gmg_ctx gmg_ctx; /* opaque: level hierarchy + Krylov workspace */
+
+typedef enum gmg_status {
+  GMG_OK = 0,
+  GMG_ERR_ARG = 1,           /* invalid argument, shape or parameter        */
+  GMG_ERR_CUDA = 2,          /* a CUDA runtime call failed                  */
+  GMG_ERR_ALLOC = 3,         /* device memory allocation failed             */
+  GMG_ERR_NOT_CONVERGED = 4, /* max_iters reached; best phi still written    */
+  GMG_ERR_BREAKDOWN = 5,     /* Arnoldi/Givens breakdown that is not lucky  */
+  GMG_ERR_NONFINITE = 6      /* NaN or Inf met in a norm, dot or input      */
+} gmg_status;
+
+/* Precision of the V-cycle preconditioner.  The FGMRES outer vectors, the
+ * Arnoldi orthogonalisation, the Hessenberg least squares and the true
+ * residual are FP64 in both modes. */
+typedef enum gmg_precision { GMG_PREC_FP64 = 0, GMG_PREC_MIXED = 1 } gmg_precision;
+
+typedef enum gmg_prolongation {
+  GMG_PROLONG_TRILINEAR = 0, /* cell-centred trilinear (3/4, 1/4 per axis) */
+  GMG_PROLONG_CONSTANT = 1   /* piecewise constant injection               */
+} gmg_prolongation;
+
+typedef enum gmg_smoother_pc {
+  GMG_PC_SGS = 0,      /* one symmetric Gauss-Seidel sweep, red-black order */
+  GMG_PC_JACOBI = 1,   /* diagonal                                          */
+  GMG_PC_IDENTITY = 2  /* none (plain Chebyshev)                            */
+} gmg_smoother_pc;
+
+typedef enum gmg_orthogonalization {
+  GMG_ORTH_CGS2 = 0, /* classical Gram-Schmidt applied twice, fused passes */
+  GMG_ORTH_MGS = 1   /* modified Gram-Schmidt as printed in Algorithm 1    */
+} gmg_orthogonalization;
+
+typedef struct gmg_params {
+  int nx, ny, nz;              /* cells; halving all three must reach a grid
+                                  whose smallest side equals coarse_min      */
+  double lx, ly, lz;           /* domain lengths (> 0)                       */
+  double phi_bottom, phi_top;  /* Dirichlet data on z = 0 and z = lz         */
+  int coarse_min;              /* smallest side of the coarsest grid (>= 1)  */
+  int cheb_steps;              /* Chebyshev steps per smoothing, 1..8        */
+  int restart;                 /* FGMRES restart length m, 1..64             */
+  int max_iters;               /* cap on total FGMRES iterations (>= 1)      */
+  double rtol;                 /* relative residual tolerance (> 0)          */
+  int eig_steps;               /* Arnoldi steps for the eigen bounds, 1..32  */
+  double eig_hi, eig_lo;       /* lambda_max = eig_hi * lam_hat,
+                                  lambda*    = eig_lo * lam_hat             */
+  int precision;               /* gmg_precision                              */
+  int prolongation;            /* gmg_prolongation                           */
+  int smoother_pc;             /* gmg_smoother_pc                            */
+  int orthogonalization;       /* gmg_orthogonalization                      */
+} gmg_params;
+
+typedef struct gmg_solve_info {
+  int iterations;              /* total FGMRES iterations (preconditioner calls) */
+  int restarts;                /* completed restart cycles                      */
+  int converged;               /* 1 if the true residual met rtol               */
+  double true_rel_residual;    /* ||b - A phi|| / ||b|| in FP64 at return       */
+  double bnorm;                /* ||b||                                         */
+  int n_history;               /* entries used in res_history                   */
+  double res_history[GMG_MAX_HISTORY]; /* least-squares residual / ||b|| per iteration */
+  float setup_ms;              /* last set-up (gmg_setup / update) time, ms    */
+  float solve_ms;              /* this solve, ms (host wall clock incl. syncs) */
+} gmg_solve_info;
+
+/* Fill *p with the paper's defaults for an nx x ny x nz unit-cube grid:
+ * plate data 0 / 1, coarse_min 4, 3 Chebyshev steps (a quadratic p_n, Sec.
+ * 3.2), restart 20 (the paper uses 30, Sec. 3.1), rtol 1e-8 (Sec. 5.2),
+ * 10 Arnoldi steps with factors 1.1 / 0.1 (Sec. 3.2), mixed precision,
+ * trilinear prolongation, SGS smoother preconditioner, CGS2. */
+void gmg_default_params(gmg_params* p, int nx, int ny, int nz);
+
+/* Build a context: copy the cell coefficient a (a_dev, FP64, > 0 and finite),
+ * form the coarse coefficients (8-child means), estimate the Chebyshev
+ * bounds of every smoothed level by Arnoldi on B^{-1} A_l (Sec. 3.2) and
+ * factor the coarsest operator (Sec. 3.2, "sequential direct solver").
+ * stream: a cudaStream_t or NULL.  On success *out owns all workspace.
+ * Errors: GMG_ERR_ARG (bad params, a <= 0 or non-finite), GMG_ERR_ALLOC,
+ * GMG_ERR_CUDA.  On error *out is NULL. */
+gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg_ctx** out);
+
+/* Renew the coefficient for a new time step (the matrix and preconditioner
+ * are rebuilt each step, Sec. 3): same work as gmg_setup on the existing
+ * workspace.  a_dev: FP64, nz*ny*nx. */
+gmg_status gmg_update_coefficient(gmg_ctx* ctx, const double* a_dev);
+
+/* Solve A phi = b with b = f + plate terms (or b = f if homogeneous_bc != 0,
+ * the form used by the adjoint solve).  phi_dev holds the initial guess x0
+ * on entry (zeros for a cold start; the previous step's phi for a warm
+ * start, Sec. 3.2) and the solution on return, also when the solve did not
+ * converge.  f_dev, phi_dev: FP64.  info may be NULL.
+ * Returns GMG_OK, GMG_ERR_NOT_CONVERGED, GMG_ERR_NONFINITE or a CUDA error. */
+gmg_status fgmres_solve(gmg_ctx* ctx, const double* f_dev, double* phi_dev, int homogeneous_bc,
+                        gmg_solve_info* info);
+
+/* y = A x (the operator of eq. (e18) with zero Dirichlet data), FP64. */
+gmg_status apply_operator(gmg_ctx* ctx, const double* x_dev, double* y_dev);
+
+/* b = f + 2 a_p g / hz^2 on the plate layers (eq. (e18) with the ghost
+ * cells of the Dirichlet plates), FP64. */
+gmg_status assemble_rhs(gmg_ctx* ctx, const double* f_dev, double* b_dev);
+
+/* E = -grad(phi) by cell-centred central differences (Sec. 2.2) with the
+ * boundary ghosts (mirror on side walls, 2g - phi on plates).  ex, ey, ez:
+ * device arrays of nz*ny*nx floats if out_fp32 != 0, else doubles. */
+gmg_status field_from_potential(gmg_ctx* ctx, const double* phi_dev, void* ex_dev, void* ey_dev,
+                                void* ez_dev, int out_fp32);
+
+/* Gradient of a loss L(phi) with respect to the cell coefficient, given phi
+ * and lambda = A^{-1} dL/dphi (the adjoint solve: fgmres_solve with
+ * homogeneous_bc = 1 on dL/dphi; dL/df = lambda).  Not in the paper: it is
+ * the derivative of the discrete operator of eq. (e18):
+ *   dL/da_p = -1/2 sum_{interior f=(p,q)} (lam_p-lam_q)(phi_p-phi_q)/h_f^2
+ *             - sum_{plate faces of p} 2 lam_p (phi_p - g)/hz^2 .
+ * All arrays FP64. */
+gmg_status adjoint_coefficient_grad(gmg_ctx* ctx, const double* phi_dev, const double* lambda_dev,
+                                    double* dlda_dev);
+
+/* End-to-end step with HOST buffers: copy a_host (may be NULL to keep the
+ * current coefficient; else the set-up is renewed), f_host and the initial
+ * guess phi_host to the device, solve, optionally form E, and copy phi (and
+ * E) back into the host buffers.  ex/ey/ez_host may be NULL (no field);
+ * they hold floats if field_fp32 != 0, else doubles.  Host buffers should be
+ * pinned for full copy bandwidth.  Staging buffers are allocated on first
+ * use and kept by the context. */
+gmg_status gmg_solve_host(gmg_ctx* ctx, const double* a_host, const double* f_host, double* phi_host,
+                          void* ex_host, void* ey_host, void* ez_host, int field_fp32,
+                          gmg_solve_info* info);
+
+gmg_status gmg_set_stream(gmg_ctx* ctx, void* stream);
+void gmg_destroy(gmg_ctx* ctx);
+const char* gmg_status_string(gmg_status s);
+
+/* ---- Inspection entry points (used by the kernel-by-kernel parity tests) ----
+ * Levels are numbered 0 = coarsest ... gmg_num_levels()-1 = finest.
+ * "level precision" is FP32 in GMG_PREC_MIXED and FP64 in GMG_PREC_FP64. */
+int gmg_num_levels(const gmg_ctx* ctx);
+
+/* Grid size and Chebyshev bounds (lambda_max, lambda*) of a level; the
+ * coarsest level reports 0 bounds (it is solved directly). */
+gmg_status gmg_level_info(const gmg_ctx* ctx, int level, int* nx, int* ny, int* nz, double* lam_max,
+                          double* lam_min);
+
+/* Copy the FP64 coefficient of a level (8-child means of the finer level)
+ * into out_dev (FP64, that level's size). */
+gmg_status gmg_level_coefficient(gmg_ctx* ctx, int level, double* out_dev);
+
+/* One V-cycle from a zero guess, z = M v (Appendix A): v_dev, z_dev FP64 of
+ * the finest size.  In mixed mode v is rounded to FP32 and the V-cycle runs
+ * in FP32; z is widened back to FP64. */
+gmg_status gmg_apply_preconditioner(gmg_ctx* ctx, const double* v_dev, double* z_dev);
+
+/* y = A_l x on a level, in level precision (x_dev, y_dev of that type). */
+gmg_status gmg_level_apply(gmg_ctx* ctx, int level, const void* x_dev, void* y_dev);
+
+/* cheb_steps preconditioned Chebyshev steps on level l (l >= 1) for
+ * A_l x = b, in level precision; x_is_zero != 0 ignores x_dev's contents
+ * (the pre-smoothing from a zero guess). */
+gmg_status gmg_level_smooth(gmg_ctx* ctx, int level, const void* b_dev, void* x_dev, int x_is_zero);
+
+/* z = B^{-1} r for the smoother preconditioner on level l, level precision. */
+gmg_status gmg_level_smoother_pc(gmg_ctx* ctx, int level, const void* r_dev, void* z_dev);
+
+/* coarse_dev = mean of 8 children of (b - A_l x) on level l (the fused
+ * residual + restriction); level precision; coarse_dev has level l-1's size. */
+gmg_status gmg_level_residual_restrict(gmg_ctx* ctx, int level, const void* b_dev, const void* x_dev,
+                                       void* coarse_dev);
+
+/* x_l += P e (prolongation from level l-1, then correction), level precision. */
+gmg_status gmg_level_prolong_add(gmg_ctx* ctx, int level, const void* e_dev, void* x_dev);
+
+/* x = A_0^{-1} b on the coarsest level (direct solve), level precision. */
+gmg_status gmg_coarse_solve(gmg_ctx* ctx, const void* b_dev, void* x_dev);
+
+/* Largest real part of the eigenvalues of an m x m upper Hessenberg matrix
+ * (row-major, m <= 64), by Francis double-shift QR on the host; used for
+ * lam_hat of the eigen bounds (Sec. 3.2).  Host memory only; needs no GPU.
+ * Returns GMG_ERR_ARG for m out of range, GMG_ERR_BREAKDOWN if QR fails to
+ * converge. */
+gmg_status gmg_hessenberg_max_real_eig(const double* h_host, int m, double* out);
+
+/* Test hook: make the n-th next device allocation of the library fail
+ * (n >= 1), as if the device were out of memory; n = 0 disables it.  Lets
+ * the host-side error paths be tested without exhausting a shared GPU. */
+void gmg_test_fail_allocation_after(int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMG_H_ */

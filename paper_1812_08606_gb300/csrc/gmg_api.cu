@@ -1,0 +1,914 @@
+// Host side of libgmg: the C ABI of include/gmg.h.
+//
+// Set-up (renewed every time step, Sec. 3): coefficient check, 8-child
+// coefficient coarsening, Chebyshev eigen bounds per level from a 10-step
+// Arnoldi run on B^{-1} A_l (Sec. 3.2), dense Cholesky of the coarsest
+// operator (Sec. 3.2).  Solve: FGMRES with right preconditioning (Algorithm
+// 1, Sec. 3.1), one V-cycle from zero per iteration (Sec. 3.2, Appendix A),
+// stopping on the least-squares residual and then on the true FP64 residual
+// (eq. (criterion), Sec. 5.2).  Every vector operation runs in the kernels of
+// k_*.cu; the host keeps only the (m+1) x m Hessenberg matrix, its Givens
+// rotations and the 10 x 10 eigenvalue problem.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "../../include/gmg.h"
+#include "gmg_internal.cuh"
+
+using namespace gmg;
+
+namespace {
+
+int g_fail_alloc_countdown = 0;
+
+gmg_status map_err(cudaError_t e) {
+  if (e == cudaSuccess) return GMG_OK;
+  (void)cudaGetLastError();  // clear a non-sticky error so the context stays usable
+  return e == cudaErrorMemoryAllocation ? GMG_ERR_ALLOC : GMG_ERR_CUDA;
+}
+
+#define CK(...)                                \
+  do {                                         \
+    cudaError_t e_ = (__VA_ARGS__);            \
+    if (e_ != cudaSuccess) return map_err(e_); \
+  } while (0)
+
+#define CKS(...)                    \
+  do {                              \
+    gmg_status s_ = (__VA_ARGS__);  \
+    if (s_ != GMG_OK) return s_;    \
+  } while (0)
+
+constexpr int MAX_COARSE = 1024;  // unknowns of the dense coarsest grid
+constexpr int MAXV = 64;          // Krylov vectors
+// device scalar slots
+constexpr int SL_H1 = 0, SL_H2 = 64, SL_NORM = 128, SL_Y = 136, SL_CHECK = 200, N_SCAL = 256;
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------------------
+// Largest real eigenvalue of a small upper Hessenberg matrix: Francis
+// double-shift QR (Golub & Van Loan, Matrix Computations, Sec. 7.5) working
+// on the active diagonal block only, since only eigenvalues are wanted.
+// ---------------------------------------------------------------------------
+int hessenberg_eigs(std::vector<double>& H, int n, std::vector<double>& wr, std::vector<double>& wi) {
+  auto h = [&](int r, int c) -> double& { return H[(size_t)r * n + c]; };
+  wr.assign(n, 0.0);
+  wi.assign(n, 0.0);
+  double anorm = 0.0;
+  for (int r = 0; r < n; ++r)
+    for (int c = std::max(0, r - 1); c < n; ++c) anorm += fabs(h(r, c));
+  const double eps = 2.220446049250313e-16;
+  int hi = n - 1, iter = 0, total = 0;
+  while (hi >= 0) {
+    int l = hi;
+    while (l > 0) {
+      double s = fabs(h(l - 1, l - 1)) + fabs(h(l, l));
+      if (s == 0.0) s = anorm;
+      if (fabs(h(l, l - 1)) <= eps * s) {
+        h(l, l - 1) = 0.0;
+        break;
+      }
+      --l;
+    }
+    if (l == hi) {
+      wr[hi] = h(hi, hi);
+      --hi;
+      iter = 0;
+      continue;
+    }
+    if (l == hi - 1) {
+      const double a = h(hi - 1, hi - 1), b = h(hi - 1, hi), c = h(hi, hi - 1), d = h(hi, hi);
+      const double m = 0.5 * (a + d), p = 0.5 * (a - d), disc = p * p + b * c;
+      if (disc >= 0.0) {
+        const double q = sqrt(disc);
+        wr[hi - 1] = m + q;
+        wr[hi] = m - q;
+      } else {
+        wr[hi - 1] = wr[hi] = m;
+        wi[hi - 1] = sqrt(-disc);
+        wi[hi] = -wi[hi - 1];
+      }
+      hi -= 2;
+      iter = 0;
+      continue;
+    }
+    if (++iter > 60 || ++total > 60 * n) return -1;
+    double s, t;
+    if (iter % 11 == 10) {  // exceptional shift to break a cycle
+      const double w = fabs(h(hi, hi - 1)) + fabs(h(hi - 1, hi - 2));
+      s = 1.5 * w;
+      t = w * w;
+    } else {
+      s = h(hi - 1, hi - 1) + h(hi, hi);
+      t = h(hi - 1, hi - 1) * h(hi, hi) - h(hi - 1, hi) * h(hi, hi - 1);
+    }
+    // first column of (H - mu1)(H - mu2) restricted to the active block
+    double x = h(l, l) * h(l, l) + h(l, l + 1) * h(l + 1, l) - s * h(l, l) + t;
+    double y = h(l + 1, l) * (h(l, l) + h(l + 1, l + 1) - s);
+    double z = h(l + 1, l) * h(l + 2, l + 1);
+    for (int k = l; k <= hi - 2; ++k) {
+      double alpha = sqrt(x * x + y * y + z * z);
+      if (x > 0) alpha = -alpha;
+      const double u0 = x - alpha, u1 = y, u2 = z;
+      const double uu = u0 * u0 + u1 * u1 + u2 * u2;
+      if (uu != 0.0) {
+        const double beta = 2.0 / uu;
+        for (int c = std::max(l, k - 1); c <= hi; ++c) {
+          const double dd = beta * (u0 * h(k, c) + u1 * h(k + 1, c) + u2 * h(k + 2, c));
+          h(k, c) -= dd * u0;
+          h(k + 1, c) -= dd * u1;
+          h(k + 2, c) -= dd * u2;
+        }
+        for (int r = l; r <= std::min(k + 3, hi); ++r) {
+          const double dd = beta * (h(r, k) * u0 + h(r, k + 1) * u1 + h(r, k + 2) * u2);
+          h(r, k) -= dd * u0;
+          h(r, k + 1) -= dd * u1;
+          h(r, k + 2) -= dd * u2;
+        }
+      }
+      if (k > l) {
+        h(k + 1, k - 1) = 0.0;
+        h(k + 2, k - 1) = 0.0;
+      }
+      x = h(k + 1, k);
+      y = h(k + 2, k);
+      z = (k < hi - 2) ? h(k + 3, k) : 0.0;
+    }
+    {
+      const int k = hi - 1;
+      double alpha = sqrt(x * x + y * y);
+      if (x > 0) alpha = -alpha;
+      const double u0 = x - alpha, u1 = y;
+      const double uu = u0 * u0 + u1 * u1;
+      if (uu != 0.0) {
+        const double beta = 2.0 / uu;
+        for (int c = std::max(l, k - 1); c <= hi; ++c) {
+          const double dd = beta * (u0 * h(k, c) + u1 * h(k + 1, c));
+          h(k, c) -= dd * u0;
+          h(k + 1, c) -= dd * u1;
+        }
+        for (int r = l; r <= hi; ++r) {
+          const double dd = beta * (h(r, k) * u0 + h(r, k + 1) * u1);
+          h(r, k) -= dd * u0;
+          h(r, k + 1) -= dd * u1;
+        }
+      }
+      if (k > l) h(k + 1, k - 1) = 0.0;
+    }
+  }
+  return 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+
+struct LevelData {
+  int nx = 0, ny = 0, nz = 0;
+  size_t n = 0;
+  Grid3 g{};
+  double* a64 = nullptr;
+  float* a32 = nullptr;
+  void *x = nullptr, *b = nullptr, *r = nullptr, *z = nullptr, *d = nullptr;  // level precision
+  double lam_max = 0, lam_min = 0, lam_hat = 0;
+};
+
+struct gmg_ctx {
+  gmg_params p{};
+  cudaStream_t s = nullptr;
+  bool mixed = false;
+  size_t esz = 8;
+  std::vector<LevelData> lev;  // 0 = coarsest
+  int nc = 0;
+  double *cA = nullptr, *cW = nullptr, *cinv64 = nullptr;
+  float* cinv32 = nullptr;
+  int* cstatus = nullptr;
+  int nv = 0;
+  double* V = nullptr;
+  void* Z = nullptr;
+  double* w = nullptr;
+  double* bvec = nullptr;
+  double* partial = nullptr;
+  double* dscal = nullptr;
+  double* hpin = nullptr;
+  int* hstat = nullptr;
+  double *st_a = nullptr, *st_f = nullptr, *st_phi = nullptr;
+  void *st_ex = nullptr, *st_ey = nullptr, *st_ez = nullptr;
+  int st_fp32 = -1;  // element type of the field staging buffers (-1: none yet)
+  float setup_ms = 0.f;
+  std::vector<void*> dev_allocs;
+  std::vector<void*> host_allocs;
+
+  size_t N() const { return lev.back().n; }
+  const LevelData& fine() const { return lev.back(); }
+};
+
+namespace {
+
+gmg_status dev_alloc(gmg_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (g_fail_alloc_countdown > 0 && --g_fail_alloc_countdown == 0) return GMG_ERR_ALLOC;
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return map_err(e);
+  }
+  c->dev_allocs.push_back(*p);
+  return GMG_OK;
+}
+
+template <typename P>
+gmg_status dalloc(gmg_ctx* c, P** p, size_t count, size_t elem = sizeof(P)) {
+  void* v = nullptr;
+  gmg_status st = dev_alloc(c, &v, count * elem);
+  *p = (P*)v;
+  return st;
+}
+
+gmg_status validate(const gmg_params* p, int* nlevels) {
+  if (!p) return GMG_ERR_ARG;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return GMG_ERR_ARG;
+  if (!(p->lx > 0 && p->ly > 0 && p->lz > 0) || !isfinite(p->lx) || !isfinite(p->ly) || !isfinite(p->lz))
+    return GMG_ERR_ARG;
+  if (!isfinite(p->phi_bottom) || !isfinite(p->phi_top)) return GMG_ERR_ARG;
+  if (p->coarse_min < 1 || p->cheb_steps < 1 || p->cheb_steps > 8) return GMG_ERR_ARG;
+  if (p->restart < 1 || p->restart > MAXV - 1 || p->max_iters < 1) return GMG_ERR_ARG;
+  if (!(p->rtol > 0) || !isfinite(p->rtol)) return GMG_ERR_ARG;
+  if (p->eig_steps < 1 || p->eig_steps > 32) return GMG_ERR_ARG;
+  if (!(p->eig_hi > p->eig_lo) || !(p->eig_lo > 0) || !isfinite(p->eig_hi)) return GMG_ERR_ARG;
+  if (p->precision != GMG_PREC_FP64 && p->precision != GMG_PREC_MIXED) return GMG_ERR_ARG;
+  if (p->prolongation != 0 && p->prolongation != 1) return GMG_ERR_ARG;
+  if (p->smoother_pc < 0 || p->smoother_pc > 2) return GMG_ERR_ARG;
+  if (p->orthogonalization != 0 && p->orthogonalization != 1) return GMG_ERR_ARG;
+  if ((double)p->nx * p->ny * p->nz > 4.0e9) return GMG_ERR_ARG;
+  int nx = p->nx, ny = p->ny, nz = p->nz, L = 1;
+  while (std::min(nx, std::min(ny, nz)) > p->coarse_min) {
+    if ((nx | ny | nz) & 1) return GMG_ERR_ARG;
+    nx /= 2;
+    ny /= 2;
+    nz /= 2;
+    ++L;
+  }
+  if (std::min(nx, std::min(ny, nz)) != p->coarse_min) return GMG_ERR_ARG;
+  if ((long long)nx * ny * nz > MAX_COARSE) return GMG_ERR_ARG;
+  *nlevels = L;
+  return GMG_OK;
+}
+
+// Read `count` device scalars from slot `slot` into ctx->hpin[slot...]; synchronises.
+gmg_status read_scalars(gmg_ctx* c, int slot, int count) {
+  CK(cudaMemcpyAsync(c->hpin + slot, c->dscal + slot, sizeof(double) * count, cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  return GMG_OK;
+}
+
+// Device: out slots [slot, slot+2) = (||w||, 1/||w||).
+gmg_status norm_dev(gmg_ctx* c, size_t n, const double* w, int slot) {
+  CK(launch_multi_dot(n, w, w, 0, 1, c->partial, c->s));
+  CK(launch_finalize_norm(c->partial, reduce_blocks(n), c->dscal + slot, c->s));
+  return GMG_OK;
+}
+
+// Orthogonalise w against the k vectors V[0..k) (row stride ld), leaving the
+// coefficients in slots SL_H1 (+ SL_H2 for the second CGS pass) and the norm
+// of the result and its reciprocal in SL_NORM.
+gmg_status orthogonalize(gmg_ctx* c, size_t n, const double* V, size_t ld, int k, double* w) {
+  const int nb = reduce_blocks(n);
+  if (c->p.orthogonalization == GMG_ORTH_MGS) {
+    for (int i = 0; i < k; ++i) {
+      CK(launch_multi_dot(n, w, V + (size_t)i * ld, ld, 1, c->partial, c->s));
+      CK(launch_finalize(c->partial, nb, 1, c->dscal + SL_H1 + i, 0, c->s));
+      CK(launch_multi_axpy(n, w, V + (size_t)i * ld, ld, 1, c->dscal + SL_H1 + i, c->s));
+    }
+  } else {
+    for (int pass = 0; pass < 2; ++pass) {
+      double* hslot = c->dscal + (pass == 0 ? SL_H1 : SL_H2);
+      for (int c0 = 0; c0 < k; c0 += 8) {
+        const int kc = std::min(8, k - c0);
+        CK(launch_multi_dot(n, w, V + (size_t)c0 * ld, ld, kc, c->partial, c->s));
+        CK(launch_finalize(c->partial, nb, kc, hslot + c0, 0, c->s));
+      }
+      CK(launch_multi_axpy(n, w, V, ld, k, hslot, c->s));
+    }
+  }
+  return norm_dev(c, n, w, SL_NORM);
+}
+
+// Column of H after orthogonalize (host copy): h[0..k) and h[k] = ||w||.
+void gather_column(gmg_ctx* c, int k, double* h) {
+  for (int i = 0; i < k; ++i) {
+    h[i] = c->hpin[SL_H1 + i];
+    if (c->p.orthogonalization == GMG_ORTH_CGS2) h[i] += c->hpin[SL_H2 + i];
+  }
+  h[k] = c->hpin[SL_NORM];
+}
+
+gmg_status read_column(gmg_ctx* c, int k, double* h) {
+  CKS(read_scalars(c, 0, SL_NORM + 2));
+  gather_column(c, k, h);
+  return GMG_OK;
+}
+
+// z = B^{-1} r on a level in FP64 (used by the eigen estimate), r FP64 buffer.
+gmg_status smoother_pc_fp64(gmg_ctx* c, const LevelData& L, const double* r, double* z) {
+  const int pc = c->p.smoother_pc;
+  if (pc == GMG_PC_IDENTITY) return map_err(launch_copy_d(L.n, r, z, c->s));
+  CK(launch_residual<double>(L.g, L.a64, r, nullptr, nullptr, z, pc == GMG_PC_SGS ? PC_SGS : PC_JACOBI, c->s));
+  if (pc == GMG_PC_SGS) {
+    CK(launch_sgs_half<double>(L.g, L.a64, r, z, 1, nullptr, nullptr, 0, 0, 0, c->s));
+    CK(launch_sgs_half<double>(L.g, L.a64, r, z, 0, nullptr, nullptr, 0, 0, 0, c->s));
+  }
+  return GMG_OK;
+}
+
+// lambda_max, lambda* of level l: Arnoldi on B^{-1} A_l (Sec. 3.2).
+gmg_status eig_bounds(gmg_ctx* c, int l) {
+  LevelData& L = c->lev[l];
+  const size_t n = L.n;
+  const int steps = c->p.eig_steps;
+  double* V = c->V;  // (steps+1) vectors of n, stride n
+  CK(launch_hash_vector(n, V, c->s));
+  CKS(norm_dev(c, n, V, SL_NORM));
+  CK(launch_scale(n, V, V, c->dscal + SL_NORM + 1, c->s));
+  std::vector<double> H((size_t)(steps + 1) * steps, 0.0);
+  int m = steps;
+  std::vector<double> col(steps + 2);
+  for (int j = 0; j < steps; ++j) {
+    CK(launch_apply<double, double, double>(L.g, L.a64, V + (size_t)j * n, c->bvec, c->s));
+    CKS(smoother_pc_fp64(c, L, c->bvec, c->w));
+    CKS(orthogonalize(c, n, V, n, j + 1, c->w));
+    CKS(read_column(c, j + 1, col.data()));
+    for (int i = 0; i <= j + 1; ++i) {
+      if (!isfinite(col[i])) return GMG_ERR_NONFINITE;
+      H[(size_t)i * steps + j] = col[i];
+    }
+    if (col[j + 1] == 0.0) {
+      m = j + 1;
+      break;
+    }
+    CK(launch_scale(n, c->w, V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));
+  }
+  std::vector<double> Hm((size_t)m * m);
+  for (int r = 0; r < m; ++r)
+    for (int q = 0; q < m; ++q) Hm[(size_t)r * m + q] = H[(size_t)r * steps + q];
+  std::vector<double> wr, wi;
+  if (hessenberg_eigs(Hm, m, wr, wi) != 0) return GMG_ERR_BREAKDOWN;
+  double lam = -1e300;
+  for (int i = 0; i < m; ++i) lam = std::max(lam, wr[i]);
+  if (!(lam > 0) || !isfinite(lam)) return GMG_ERR_BREAKDOWN;
+  L.lam_hat = lam;
+  L.lam_max = c->p.eig_hi * lam;
+  L.lam_min = c->p.eig_lo * lam;
+  return GMG_OK;
+}
+
+gmg_status build(gmg_ctx* c, const double* a_dev) {
+  const double t0 = now_ms();
+  LevelData& F = c->lev.back();
+  // coefficient must be finite and positive
+  CK(launch_coef_check(F.n, a_dev, c->partial, c->s));
+  CK(launch_finalize_check(c->partial, reduce_blocks(F.n), c->dscal + SL_CHECK, c->s));
+  CKS(read_scalars(c, SL_CHECK, 2));
+  if (c->hpin[SL_CHECK + 1] != 0.0) return GMG_ERR_ARG;
+  CK(launch_copy_d(F.n, a_dev, F.a64, c->s));
+  if (c->mixed) CK(launch_cast_d2f(F.n, F.a64, F.a32, c->s));
+  for (int l = (int)c->lev.size() - 1; l >= 1; --l)
+    CK(launch_coarsen_coef(c->lev[l].g, c->lev[l].a64, c->lev[l - 1].a64, c->mixed ? c->lev[l - 1].a32 : nullptr,
+                           c->s));
+  for (int l = 1; l < (int)c->lev.size(); ++l) CKS(eig_bounds(c, l));
+  // coarsest: dense Cholesky and explicit inverse
+  const LevelData& C0 = c->lev[0];
+  CK(launch_coarse_assemble(C0.g, C0.a64, c->cA, c->s));
+  CK(launch_coarse_factor(c->nc, c->cA, c->cW, c->cinv64, c->cinv32, c->cstatus, c->s));
+  CK(cudaMemcpyAsync(c->hstat, c->cstatus, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  if (c->hstat[0] != 0) return GMG_ERR_BREAKDOWN;
+  c->setup_ms = (float)(now_ms() - t0);
+  return GMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle (Sec. 3.2, Appendix A)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+const T* level_a(const LevelData& L);
+template <>
+const float* level_a<float>(const LevelData& L) { return L.a32; }
+template <>
+const double* level_a<double>(const LevelData& L) { return L.a64; }
+
+template <typename T>
+const T* coarse_inv(const gmg_ctx* c);
+template <>
+const float* coarse_inv<float>(const gmg_ctx* c) { return c->cinv32; }
+template <>
+const double* coarse_inv<double>(const gmg_ctx* c) { return c->cinv64; }
+
+// cheb_steps Chebyshev steps with the smoother preconditioner; x_is_zero
+// starts from x = 0 (then r = b and x's contents are ignored).
+template <typename T>
+gmg_status smooth(gmg_ctx* c, int l, const T* b, T* x, bool x_is_zero) {
+  const LevelData& L = c->lev[l];
+  const T* a = level_a<T>(L);
+  T* r = (T*)L.r;
+  T* z = (T*)L.z;
+  T* d = (T*)L.d;
+  const double theta = 0.5 * (L.lam_max + L.lam_min), delta = 0.5 * (L.lam_max - L.lam_min);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  const int pc = c->p.smoother_pc;
+  for (int st = 0; st < c->p.cheb_steps; ++st) {
+    double c1 = 0.0, c2 = 1.0 / theta;
+    int flags = CHEB_UPDATE;
+    if (st == 0) {
+      flags |= CHEB_FIRST;
+      if (x_is_zero) flags |= CHEB_XZERO;
+    } else {
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      c1 = rho_new * rho;
+      c2 = 2.0 * rho_new / delta;
+      rho = rho_new;
+    }
+    const T* rr;
+    if (st == 0 && x_is_zero) {
+      CK(launch_residual<T>(L.g, a, b, nullptr, nullptr, z, pc, c->s));
+      rr = b;
+    } else {
+      CK(launch_residual<T>(L.g, a, b, x, r, z, pc, c->s));
+      rr = r;
+    }
+    if (pc == GMG_PC_SGS) {
+      CK(launch_sgs_half<T>(L.g, a, rr, z, 1, d, x, c1, c2, flags, c->s));
+      CK(launch_sgs_half<T>(L.g, a, rr, z, 0, d, x, c1, c2, flags, c->s));
+    } else {
+      CK(launch_cheb_update<T>(L.n, z, d, x, c1, c2, flags, c->s));
+    }
+  }
+  return GMG_OK;
+}
+
+template <typename T>
+gmg_status vcycle(gmg_ctx* c, int l, const T* b, T* x) {
+  if (l == 0) return map_err(launch_coarse_apply<T>(c->nc, coarse_inv<T>(c), b, x, c->s));
+  const LevelData& L = c->lev[l];
+  const LevelData& Lc = c->lev[l - 1];
+  const T* a = level_a<T>(L);
+  CKS(smooth<T>(c, l, b, x, true));
+  CK(launch_residual_restrict<T>(L.g, a, b, x, (T*)Lc.b, c->s));
+  CKS(vcycle<T>(c, l - 1, (const T*)Lc.b, (T*)Lc.x));
+  CK(launch_prolong_add<T>(L.g, (const T*)Lc.x, x, c->p.prolongation, c->s));
+  CKS(smooth<T>(c, l, b, x, false));
+  return GMG_OK;
+}
+
+// z (level precision, finest size) = M v, v FP64.
+gmg_status precondition(gmg_ctx* c, const double* v, void* z) {
+  const int top = (int)c->lev.size() - 1;
+  if (c->mixed) {
+    float* bf = (float*)c->lev[top].b;
+    CK(launch_cast_d2f(c->N(), v, bf, c->s));
+    return vcycle<float>(c, top, bf, (float*)z);
+  }
+  return vcycle<double>(c, top, v, (double*)z);
+}
+
+// w = A z (FP64 operator on a level-precision vector of the finest size).
+gmg_status apply_outer(gmg_ctx* c, const void* z, double* w) {
+  const LevelData& F = c->fine();
+  if (c->mixed) return map_err(launch_apply<double, float, double>(F.g, F.a64, (const float*)z, w, c->s));
+  return map_err(launch_apply<double, double, double>(F.g, F.a64, (const double*)z, w, c->s));
+}
+
+void* zvec(gmg_ctx* c, int j) { return (char*)c->Z + (size_t)j * c->N() * c->esz; }
+
+gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, gmg_solve_info* info) {
+  const double t0 = now_ms();
+  const LevelData& F = c->fine();
+  const size_t n = F.n;
+  const int m = c->p.restart;
+  gmg_solve_info loc;
+  memset(&loc, 0, sizeof(loc));
+  loc.setup_ms = c->setup_ms;
+  gmg_status result = GMG_OK;
+
+  CK(launch_rhs(F.g, F.a64, f, c->bvec, c->p.phi_bottom, c->p.phi_top, homogeneous, c->s));
+  CKS(norm_dev(c, n, c->bvec, SL_NORM));
+  CKS(read_scalars(c, SL_NORM, 2));
+  const double bnorm = c->hpin[SL_NORM];
+  loc.bnorm = bnorm;
+  if (!isfinite(bnorm)) {
+    result = GMG_ERR_NONFINITE;
+    goto done;
+  }
+  if (bnorm == 0.0) {
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), c->s));
+    loc.converged = 1;
+    loc.true_rel_residual = 0.0;
+    goto done;
+  }
+  {
+    std::vector<double> R((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), col(m + 2), y(m);
+    for (;;) {
+      // r0 = b - A x0, beta, v1 (Algorithm 1, line 3)
+      CK(launch_residual<double>(F.g, F.a64, c->bvec, x, c->V, nullptr, PC_NONE, c->s));
+      CKS(norm_dev(c, n, c->V, SL_NORM));
+      CKS(read_scalars(c, SL_NORM, 2));
+      const double beta = c->hpin[SL_NORM];
+      if (!isfinite(beta)) {
+        result = GMG_ERR_NONFINITE;
+        break;
+      }
+      loc.true_rel_residual = beta / bnorm;
+      if (loc.true_rel_residual < c->p.rtol) {
+        loc.converged = 1;
+        break;
+      }
+      if (loc.iterations >= c->p.max_iters) {
+        result = GMG_ERR_NOT_CONVERGED;
+        break;
+      }
+      CK(launch_scale_value(n, c->V, c->V, 1.0 / beta, c->s));
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int k = 0;
+      bool fail = false;
+      for (int j = 0; j < m; ++j) {
+        double* vj = c->V + (size_t)j * n;
+        CKS(precondition(c, vj, zvec(c, j)));           // line 5: z_j = M v_j
+        CKS(apply_outer(c, zvec(c, j), c->w));            // line 6: w = A z_j
+        CKS(orthogonalize(c, n, c->V, n, j + 1, c->w));   // lines 7-9
+        CKS(read_column(c, j + 1, col.data()));          // line 10: h_{j+1,j}
+        for (int i = 0; i <= j + 1; ++i)
+          if (!isfinite(col[i])) fail = true;
+        if (fail) {
+          result = GMG_ERR_NONFINITE;
+          break;
+        }
+        const double hnext = col[j + 1];
+        // line 11: least squares by Givens rotations on the new column
+        for (int i = 0; i < j; ++i) {
+          const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+          col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+          col[i] = t;
+        }
+        const double rr = hypot(col[j], col[j + 1]);
+        if (rr == 0.0) {
+          result = GMG_ERR_BREAKDOWN;
+          fail = true;
+          break;
+        }
+        cs[j] = col[j] / rr;
+        sn[j] = col[j + 1] / rr;
+        col[j] = rr;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        for (int i = 0; i <= j; ++i) R[(size_t)i * m + j] = col[i];
+        k = j + 1;
+        loc.iterations++;
+        const double est = fabs(g[j + 1]) / bnorm;
+        if (loc.n_history < GMG_MAX_HISTORY) loc.res_history[loc.n_history++] = est;
+        if (hnext == 0.0) break;  // lucky breakdown: the solution is in K_j
+        CK(launch_scale(n, c->w, c->V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));
+        if (est < c->p.rtol || loc.iterations >= c->p.max_iters) break;  // line 12
+      }
+      if (fail) break;
+      // line 15: y_k from the triangular system, x_k = x_0 + Z_k y_k
+      for (int i = k - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int q = i + 1; q < k; ++q) t -= R[(size_t)i * m + q] * y[q];
+        y[i] = t / R[(size_t)i * m + i];
+      }
+      for (int i = 0; i < k; ++i) c->hpin[SL_Y + i] = y[i];
+      CK(cudaMemcpyAsync(c->dscal + SL_Y, c->hpin + SL_Y, sizeof(double) * k, cudaMemcpyHostToDevice, c->s));
+      if (c->mixed)
+        CK(launch_update_solution<float>(n, x, (const float*)c->Z, n, k, c->dscal + SL_Y, c->s));
+      else
+        CK(launch_update_solution<double>(n, x, (const double*)c->Z, n, k, c->dscal + SL_Y, c->s));
+      loc.restarts++;  // line 16: restart from x_k (the true residual is checked at the loop top)
+    }
+  }
+done:
+  CK(cudaStreamSynchronize(c->s));
+  loc.solve_ms = (float)(now_ms() - t0);
+  if (info) *info = loc;
+  return result;
+}
+
+LevelData* level_ptr(gmg_ctx* c, int level) {
+  if (!c || level < 0 || level >= (int)c->lev.size()) return nullptr;
+  return &c->lev[level];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+void gmg_default_params(gmg_params* p, int nx, int ny, int nz) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->nx = nx;
+  p->ny = ny;
+  p->nz = nz;
+  p->lx = p->ly = p->lz = 1.0;
+  p->phi_bottom = 0.0;
+  p->phi_top = 1.0;
+  p->coarse_min = 4;
+  p->cheb_steps = 3;
+  p->restart = 20;
+  p->max_iters = 200;
+  p->rtol = 1e-8;
+  p->eig_steps = 10;
+  p->eig_hi = 1.1;
+  p->eig_lo = 0.1;
+  p->precision = GMG_PREC_MIXED;
+  p->prolongation = GMG_PROLONG_TRILINEAR;
+  p->smoother_pc = GMG_PC_SGS;
+  p->orthogonalization = GMG_ORTH_CGS2;
+}
+
+const char* gmg_status_string(gmg_status s) {
+  switch (s) {
+    case GMG_OK: return "ok";
+    case GMG_ERR_ARG: return "invalid argument";
+    case GMG_ERR_CUDA: return "CUDA error";
+    case GMG_ERR_ALLOC: return "device allocation failed";
+    case GMG_ERR_NOT_CONVERGED: return "not converged within max_iters";
+    case GMG_ERR_BREAKDOWN: return "breakdown";
+    case GMG_ERR_NONFINITE: return "non-finite value";
+  }
+  return "unknown status";
+}
+
+void gmg_destroy(gmg_ctx* c) {
+  if (!c) return;
+  if (c->s) cudaStreamSynchronize(c->s);
+  for (void* p : c->dev_allocs) cudaFree(p);
+  for (void* p : c->host_allocs) cudaFreeHost(p);
+  delete c;
+}
+
+gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg_ctx** out) {
+  if (!out) return GMG_ERR_ARG;
+  *out = nullptr;
+  int L = 0;
+  CKS(validate(p, &L));
+  if (!a_dev) return GMG_ERR_ARG;
+  gmg_ctx* c = new (std::nothrow) gmg_ctx();
+  if (!c) return GMG_ERR_ALLOC;
+  c->p = *p;
+  c->s = (cudaStream_t)stream;
+  c->mixed = p->precision == GMG_PREC_MIXED;
+  c->esz = c->mixed ? sizeof(float) : sizeof(double);
+  auto fail = [&](gmg_status st) {
+    gmg_destroy(c);
+    return st;
+  };
+  // level grids, finest last
+  c->lev.resize(L);
+  int nx = p->nx, ny = p->ny, nz = p->nz;
+  for (int l = L - 1; l >= 0; --l) {
+    LevelData& D = c->lev[l];
+    D.nx = nx;
+    D.ny = ny;
+    D.nz = nz;
+    D.n = (size_t)nx * ny * nz;
+    D.g = make_grid(nx, ny, nz, p->lx, p->ly, p->lz);
+    nx /= 2;
+    ny /= 2;
+    nz /= 2;
+  }
+  c->nc = (int)c->lev[0].n;
+  gmg_status st;
+  for (int l = 0; l < L; ++l) {
+    LevelData& D = c->lev[l];
+    const bool top = l == L - 1;
+    if ((st = dalloc(c, &D.a64, D.n)) != GMG_OK) return fail(st);
+    if (c->mixed && (st = dalloc(c, &D.a32, D.n)) != GMG_OK) return fail(st);
+    if (!top && (st = dev_alloc(c, &D.x, D.n * c->esz)) != GMG_OK) return fail(st);
+    if ((!top || c->mixed) && (st = dev_alloc(c, &D.b, D.n * c->esz)) != GMG_OK) return fail(st);
+    if (l > 0 || L == 1) {
+      if ((st = dev_alloc(c, &D.r, D.n * c->esz)) != GMG_OK) return fail(st);
+      if ((st = dev_alloc(c, &D.z, D.n * c->esz)) != GMG_OK) return fail(st);
+      if ((st = dev_alloc(c, &D.d, D.n * c->esz)) != GMG_OK) return fail(st);
+    }
+  }
+  const size_t N = c->lev.back().n;
+  c->nv = std::max(p->restart, p->eig_steps) + 1;
+  if ((st = dalloc(c, &c->V, (size_t)c->nv * N)) != GMG_OK) return fail(st);
+  if ((st = dev_alloc(c, &c->Z, (size_t)p->restart * N * c->esz)) != GMG_OK) return fail(st);
+  if ((st = dalloc(c, &c->w, N)) != GMG_OK) return fail(st);
+  if ((st = dalloc(c, &c->bvec, N)) != GMG_OK) return fail(st);
+  if ((st = dalloc(c, &c->partial, (size_t)1024 * 16)) != GMG_OK) return fail(st);
+  if ((st = dalloc(c, &c->dscal, N_SCAL)) != GMG_OK) return fail(st);
+  if ((st = dalloc(c, &c->cA, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
+  if ((st = dalloc(c, &c->cW, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
+  if ((st = dalloc(c, &c->cinv64, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
+  if ((st = dalloc(c, &c->cinv32, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
+  if ((st = dalloc(c, &c->cstatus, 4)) != GMG_OK) return fail(st);
+  {
+    void* h = nullptr;
+    if (cudaMallocHost(&h, sizeof(double) * N_SCAL) != cudaSuccess) return fail(GMG_ERR_ALLOC);
+    c->host_allocs.push_back(h);
+    c->hpin = (double*)h;
+    if (cudaMallocHost(&h, sizeof(int) * 4) != cudaSuccess) return fail(GMG_ERR_ALLOC);
+    c->host_allocs.push_back(h);
+    c->hstat = (int*)h;
+  }
+  if ((st = build(c, a_dev)) != GMG_OK) return fail(st);
+  *out = c;
+  return GMG_OK;
+}
+
+gmg_status gmg_update_coefficient(gmg_ctx* c, const double* a_dev) {
+  if (!c || !a_dev) return GMG_ERR_ARG;
+  return build(c, a_dev);
+}
+
+gmg_status fgmres_solve(gmg_ctx* c, const double* f_dev, double* phi_dev, int homogeneous_bc,
+                        gmg_solve_info* info) {
+  if (!c || !f_dev || !phi_dev) return GMG_ERR_ARG;
+  return solve_impl(c, f_dev, phi_dev, homogeneous_bc, info);
+}
+
+gmg_status apply_operator(gmg_ctx* c, const double* x_dev, double* y_dev) {
+  if (!c || !x_dev || !y_dev) return GMG_ERR_ARG;
+  const LevelData& F = c->fine();
+  return map_err(launch_apply<double, double, double>(F.g, F.a64, x_dev, y_dev, c->s));
+}
+
+gmg_status assemble_rhs(gmg_ctx* c, const double* f_dev, double* b_dev) {
+  if (!c || !f_dev || !b_dev) return GMG_ERR_ARG;
+  const LevelData& F = c->fine();
+  return map_err(launch_rhs(F.g, F.a64, f_dev, b_dev, c->p.phi_bottom, c->p.phi_top, 0, c->s));
+}
+
+gmg_status field_from_potential(gmg_ctx* c, const double* phi_dev, void* ex, void* ey, void* ez, int out_fp32) {
+  if (!c || !phi_dev || !ex || !ey || !ez) return GMG_ERR_ARG;
+  const LevelData& F = c->fine();
+  const gmg_params& p = c->p;
+  return map_err(launch_field(F.g, p.lx / p.nx, p.ly / p.ny, p.lz / p.nz, phi_dev, ex, ey, ez, out_fp32,
+                              p.phi_bottom, p.phi_top, c->s));
+}
+
+gmg_status adjoint_coefficient_grad(gmg_ctx* c, const double* phi_dev, const double* lambda_dev,
+                                    double* dlda_dev) {
+  if (!c || !phi_dev || !lambda_dev || !dlda_dev) return GMG_ERR_ARG;
+  const LevelData& F = c->fine();
+  return map_err(launch_adjoint_grad(F.g, phi_dev, lambda_dev, dlda_dev, c->p.phi_bottom, c->p.phi_top, c->s));
+}
+
+gmg_status gmg_solve_host(gmg_ctx* c, const double* a_host, const double* f_host, double* phi_host, void* ex_host,
+                          void* ey_host, void* ez_host, int field_fp32, gmg_solve_info* info) {
+  if (!c || !f_host || !phi_host) return GMG_ERR_ARG;
+  const bool want_e = ex_host && ey_host && ez_host;
+  if ((ex_host || ey_host || ez_host) && !want_e) return GMG_ERR_ARG;
+  const size_t n = c->N(), bytes = n * sizeof(double);
+  if (!c->st_f) {
+    CKS(dalloc(c, &c->st_f, n));
+    CKS(dalloc(c, &c->st_phi, n));
+  }
+  if (a_host && !c->st_a) CKS(dalloc(c, &c->st_a, n));
+  const size_t esz = field_fp32 ? sizeof(float) : sizeof(double);
+  if (want_e && c->st_fp32 != (field_fp32 ? 1 : 0)) {
+    if (c->st_ex) return GMG_ERR_ARG;  // staging already sized for the other field type
+    CKS(dev_alloc(c, &c->st_ex, n * esz));
+    CKS(dev_alloc(c, &c->st_ey, n * esz));
+    CKS(dev_alloc(c, &c->st_ez, n * esz));
+    c->st_fp32 = field_fp32 ? 1 : 0;
+  }
+  if (a_host) {
+    CK(cudaMemcpyAsync(c->st_a, a_host, bytes, cudaMemcpyHostToDevice, c->s));
+    CKS(build(c, c->st_a));
+  }
+  CK(cudaMemcpyAsync(c->st_f, f_host, bytes, cudaMemcpyHostToDevice, c->s));
+  CK(cudaMemcpyAsync(c->st_phi, phi_host, bytes, cudaMemcpyHostToDevice, c->s));
+  gmg_status st = solve_impl(c, c->st_f, c->st_phi, 0, info);
+  if (st != GMG_OK && st != GMG_ERR_NOT_CONVERGED) return st;
+  if (want_e) CKS(field_from_potential(c, c->st_phi, c->st_ex, c->st_ey, c->st_ez, field_fp32));
+  CK(cudaMemcpyAsync(phi_host, c->st_phi, bytes, cudaMemcpyDeviceToHost, c->s));
+  if (want_e) {
+    CK(cudaMemcpyAsync(ex_host, c->st_ex, n * esz, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(ey_host, c->st_ey, n * esz, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(ez_host, c->st_ez, n * esz, cudaMemcpyDeviceToHost, c->s));
+  }
+  CK(cudaStreamSynchronize(c->s));
+  return st;
+}
+
+gmg_status gmg_set_stream(gmg_ctx* c, void* stream) {
+  if (!c) return GMG_ERR_ARG;
+  CK(cudaStreamSynchronize(c->s));
+  c->s = (cudaStream_t)stream;
+  return GMG_OK;
+}
+
+int gmg_num_levels(const gmg_ctx* c) { return c ? (int)c->lev.size() : 0; }
+
+gmg_status gmg_level_info(const gmg_ctx* c, int level, int* nx, int* ny, int* nz, double* lam_max,
+                          double* lam_min) {
+  if (!c || level < 0 || level >= (int)c->lev.size()) return GMG_ERR_ARG;
+  const LevelData& L = c->lev[level];
+  if (nx) *nx = L.nx;
+  if (ny) *ny = L.ny;
+  if (nz) *nz = L.nz;
+  if (lam_max) *lam_max = L.lam_max;
+  if (lam_min) *lam_min = L.lam_min;
+  return GMG_OK;
+}
+
+gmg_status gmg_level_coefficient(gmg_ctx* c, int level, double* out_dev) {
+  LevelData* L = level_ptr(c, level);
+  if (!L || !out_dev) return GMG_ERR_ARG;
+  return map_err(launch_copy_d(L->n, L->a64, out_dev, c->s));
+}
+
+gmg_status gmg_apply_preconditioner(gmg_ctx* c, const double* v_dev, double* z_dev) {
+  if (!c || !v_dev || !z_dev) return GMG_ERR_ARG;
+  CKS(precondition(c, v_dev, c->Z));
+  if (c->mixed) return map_err(launch_cast_f2d(c->N(), (const float*)c->Z, z_dev, c->s));
+  return map_err(launch_copy_d(c->N(), (const double*)c->Z, z_dev, c->s));
+}
+
+gmg_status gmg_level_apply(gmg_ctx* c, int level, const void* x, void* y) {
+  LevelData* L = level_ptr(c, level);
+  if (!L || !x || !y) return GMG_ERR_ARG;
+  if (c->mixed) return map_err(launch_apply<float, float, float>(L->g, L->a32, (const float*)x, (float*)y, c->s));
+  return map_err(launch_apply<double, double, double>(L->g, L->a64, (const double*)x, (double*)y, c->s));
+}
+
+gmg_status gmg_level_smooth(gmg_ctx* c, int level, const void* b, void* x, int x_is_zero) {
+  LevelData* L = level_ptr(c, level);
+  if (!L || level == 0 || !b || !x || !L->r) return GMG_ERR_ARG;
+  if (c->mixed) return smooth<float>(c, level, (const float*)b, (float*)x, x_is_zero != 0);
+  return smooth<double>(c, level, (const double*)b, (double*)x, x_is_zero != 0);
+}
+
+gmg_status gmg_level_smoother_pc(gmg_ctx* c, int level, const void* r, void* z) {
+  LevelData* L = level_ptr(c, level);
+  if (!L || !r || !z) return GMG_ERR_ARG;
+  const int pc = c->p.smoother_pc;
+  if (c->mixed) {
+    const float* a = L->a32;
+    if (pc == GMG_PC_IDENTITY) return map_err(cudaMemcpyAsync(z, r, L->n * 4, cudaMemcpyDeviceToDevice, c->s));
+    CK(launch_residual<float>(L->g, a, (const float*)r, nullptr, nullptr, (float*)z,
+                              pc == GMG_PC_SGS ? PC_SGS : PC_JACOBI, c->s));
+    if (pc == GMG_PC_SGS) {
+      CK(launch_sgs_half<float>(L->g, a, (const float*)r, (float*)z, 1, nullptr, nullptr, 0, 0, 0, c->s));
+      CK(launch_sgs_half<float>(L->g, a, (const float*)r, (float*)z, 0, nullptr, nullptr, 0, 0, 0, c->s));
+    }
+    return GMG_OK;
+  }
+  return smoother_pc_fp64(c, *L, (const double*)r, (double*)z);
+}
+
+gmg_status gmg_level_residual_restrict(gmg_ctx* c, int level, const void* b, const void* x, void* coarse) {
+  LevelData* L = level_ptr(c, level);
+  if (!L || level == 0 || !b || !x || !coarse) return GMG_ERR_ARG;
+  if (c->mixed)
+    return map_err(launch_residual_restrict<float>(L->g, L->a32, (const float*)b, (const float*)x, (float*)coarse,
+                                                   c->s));
+  return map_err(launch_residual_restrict<double>(L->g, L->a64, (const double*)b, (const double*)x,
+                                                  (double*)coarse, c->s));
+}
+
+gmg_status gmg_level_prolong_add(gmg_ctx* c, int level, const void* e, void* x) {
+  LevelData* L = level_ptr(c, level);
+  if (!L || level == 0 || !e || !x) return GMG_ERR_ARG;
+  if (c->mixed) return map_err(launch_prolong_add<float>(L->g, (const float*)e, (float*)x, c->p.prolongation, c->s));
+  return map_err(launch_prolong_add<double>(L->g, (const double*)e, (double*)x, c->p.prolongation, c->s));
+}
+
+gmg_status gmg_coarse_solve(gmg_ctx* c, const void* b, void* x) {
+  if (!c || !b || !x) return GMG_ERR_ARG;
+  if (c->mixed) return map_err(launch_coarse_apply<float>(c->nc, c->cinv32, (const float*)b, (float*)x, c->s));
+  return map_err(launch_coarse_apply<double>(c->nc, c->cinv64, (const double*)b, (double*)x, c->s));
+}
+
+gmg_status gmg_hessenberg_max_real_eig(const double* h_host, int m, double* out) {
+  if (!h_host || !out || m < 1 || m > 64) return GMG_ERR_ARG;
+  std::vector<double> H(h_host, h_host + (size_t)m * m), wr, wi;
+  if (hessenberg_eigs(H, m, wr, wi) != 0) return GMG_ERR_BREAKDOWN;
+  double lam = -INFINITY;
+  for (int i = 0; i < m; ++i) lam = std::max(lam, wr[i]);
+  *out = lam;
+  return GMG_OK;
+}
+
+void gmg_test_fail_allocation_after(int n) { g_fail_alloc_countdown = n > 0 ? n : 0; }
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// Internal declarations shared by the CUDA translation units of libgmg.
+//
+// Every field is a contiguous [nz][ny][nx] array (x fastest).  The operator
+// is the 7-point finite-volume stencil of eq. (e18), Sec. 2.2:
+//   (A x)_p = sum_{interior faces f=(p,q)} a_f (x_p - x_q)/h_f^2
+//           + sum_{plate faces of p} 2 a_p x_p / hz^2,   a_f = (a_p + a_q)/2,
+// with zero flux through the x/y side walls (eq. (eM)).  Kernels form the face
+// coefficients on the fly from the cell coefficient a.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace gmg {
+
+// Grid of one multigrid level plus the stencil scale factors.
+struct Grid3 {
+  int nx, ny, nz;
+  double cx, cy, cz;  // 0.5 / h^2 per axis: a_f / h^2 = (a_p + a_q) * c
+  double cp;          // 2 / hz^2: plate-face coefficient per unit a_p
+  __host__ __device__ size_t n() const { return (size_t)nx * ny * nz; }
+  __host__ __device__ size_t plane() const { return (size_t)nx * ny; }
+};
+
+Grid3 make_grid(int nx, int ny, int nz, double lx, double ly, double lz);
+
+// Smoother-preconditioner choice, matching gmg_smoother_pc.
+enum PcKind : int { PC_SGS = 0, PC_JACOBI = 1, PC_IDENTITY = 2, PC_NONE = 3 };
+
+// Flags of the Chebyshev update fused into the smoother kernels.
+enum ChebFlags : int { CHEB_UPDATE = 1, CHEB_FIRST = 2, CHEB_XZERO = 4 };
+
+// ----------------------------------------------------------------------------
+// Device helpers
+// ----------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// Diagonal D_p and the neighbour sum N_p = sum_f c_f x_q (so (A x)_p = D_p x_p - N_p),
+// and the difference form sum_f c_f (x_p - x_q) + plate terms, which keeps the
+// accuracy of A x for smooth x.  C is the arithmetic type.
+template <typename C, typename TA, typename TX>
+__device__ __forceinline__ void stencil_diff(const Grid3& g, const TA* __restrict__ a,
+                                             const TX* __restrict__ x, int i, int j, int k,
+                                             size_t p, C& ax) {
+  const C ap = (C)ldg(a + p);
+  const C xp = (C)ldg(x + p);
+  const size_t pl = g.plane();
+  C acc = (C)0;
+  if (i > 0) acc += (ap + (C)ldg(a + p - 1)) * (C)g.cx * (xp - (C)ldg(x + p - 1));
+  if (i < g.nx - 1) acc += (ap + (C)ldg(a + p + 1)) * (C)g.cx * (xp - (C)ldg(x + p + 1));
+  if (j > 0) acc += (ap + (C)ldg(a + p - g.nx)) * (C)g.cy * (xp - (C)ldg(x + p - g.nx));
+  if (j < g.ny - 1) acc += (ap + (C)ldg(a + p + g.nx)) * (C)g.cy * (xp - (C)ldg(x + p + g.nx));
+  if (k > 0) acc += (ap + (C)ldg(a + p - pl)) * (C)g.cz * (xp - (C)ldg(x + p - pl));
+  else acc += ap * (C)g.cp * xp;
+  if (k < g.nz - 1) acc += (ap + (C)ldg(a + p + pl)) * (C)g.cz * (xp - (C)ldg(x + p + pl));
+  else acc += ap * (C)g.cp * xp;
+  ax = acc;
+}
+
+// Diagonal and neighbour sum (N z)_p; z may be null (treated as zero).
+template <typename C, typename TA, typename TZ>
+__device__ __forceinline__ void stencil_split(const Grid3& g, const TA* __restrict__ a,
+                                              const TZ* z, int i, int j, int k,
+                                              size_t p, C& diag, C& nsum) {
+  const C ap = (C)ldg(a + p);
+  const size_t pl = g.plane();
+  C d = (C)0, s = (C)0;
+  if (i > 0) { C c = (ap + (C)ldg(a + p - 1)) * (C)g.cx; d += c; if (z) s += c * (C)z[p - 1]; }
+  if (i < g.nx - 1) { C c = (ap + (C)ldg(a + p + 1)) * (C)g.cx; d += c; if (z) s += c * (C)z[p + 1]; }
+  if (j > 0) { C c = (ap + (C)ldg(a + p - g.nx)) * (C)g.cy; d += c; if (z) s += c * (C)z[p - g.nx]; }
+  if (j < g.ny - 1) { C c = (ap + (C)ldg(a + p + g.nx)) * (C)g.cy; d += c; if (z) s += c * (C)z[p + g.nx]; }
+  if (k > 0) { C c = (ap + (C)ldg(a + p - pl)) * (C)g.cz; d += c; if (z) s += c * (C)z[p - pl]; }
+  else d += ap * (C)g.cp;
+  if (k < g.nz - 1) { C c = (ap + (C)ldg(a + p + pl)) * (C)g.cz; d += c; if (z) s += c * (C)z[p + pl]; }
+  else d += ap * (C)g.cp;
+  diag = d;
+  nsum = s;
+}
+
+// ----------------------------------------------------------------------------
+// Host launchers (all enqueue on `s`; return the launch error)
+// ----------------------------------------------------------------------------
+
+// y = A x.  TA/TX/TY in {float,double}; arithmetic in double if any is double.
+template <typename TA, typename TX, typename TY>
+cudaError_t launch_apply(const Grid3& g, const TA* a, const TX* x, TY* y, cudaStream_t s);
+
+// r = b - A x (x may be null = zero; r may be null = not stored) and, for the
+// smoother, z = first part of B^{-1} r: red cells r/D (SGS), all cells r/D
+// (Jacobi), z = r (identity), nothing (PC_NONE).
+template <typename T>
+cudaError_t launch_residual(const Grid3& g, const T* a, const T* b, const T* x, T* r, T* z, int pc,
+                            cudaStream_t s);
+
+// One Gauss-Seidel half-sweep on the cells of `color` ((i+j+k)&1 == color):
+// z_p = (r_p + (N z)_p) / D_p, with the Chebyshev update fused (flags).
+template <typename T>
+cudaError_t launch_sgs_half(const Grid3& g, const T* a, const T* r, T* z, int color, T* d, T* x,
+                            double c1, double c2, int flags, cudaStream_t s);
+
+// Pointwise Chebyshev update on all cells: d = c1 d + c2 z; x += d.
+template <typename T>
+cudaError_t launch_cheb_update(size_t n, const T* z, T* d, T* x, double c1, double c2, int flags,
+                               cudaStream_t s);
+
+// coarse = mean over the 8 children of (b - A x) on the fine grid g.
+template <typename T>
+cudaError_t launch_residual_restrict(const Grid3& g, const T* a, const T* b, const T* x, T* coarse,
+                                     cudaStream_t s);
+
+// x_fine += P e_coarse; mode 0 trilinear, 1 constant.
+template <typename T>
+cudaError_t launch_prolong_add(const Grid3& g_fine, const T* e, T* x, int mode, cudaStream_t s);
+
+// coarse coefficient = mean of the 8 children (FP64), plus an FP32 copy if c32.
+cudaError_t launch_coarsen_coef(const Grid3& g_fine, const double* a, double* ac, float* ac32,
+                                cudaStream_t s);
+cudaError_t launch_cast_d2f(size_t n, const double* src, float* dst, cudaStream_t s);
+cudaError_t launch_cast_f2d(size_t n, const float* src, double* dst, cudaStream_t s);
+cudaError_t launch_copy_d(size_t n, const double* src, double* dst, cudaStream_t s);
+
+// b = f (+ plate terms 2 a_p g / hz^2 on the first and last layer unless homogeneous).
+cudaError_t launch_rhs(const Grid3& g, const double* a, const double* f, double* b, double g_bot,
+                       double g_top, int homogeneous, cudaStream_t s);
+
+// E = -grad phi, central differences with boundary ghosts.
+cudaError_t launch_field(const Grid3& g, double hx, double hy, double hz, const double* phi,
+                         void* ex, void* ey, void* ez, int out_fp32, double g_bot, double g_top,
+                         cudaStream_t s);
+
+// dL/da from phi and lambda.
+cudaError_t launch_adjoint_grad(const Grid3& g, const double* phi, const double* lam, double* out,
+                                double g_bot, double g_top, cudaStream_t s);
+
+// u_i = splitmix64-based start vector in [-1, 1).
+cudaError_t launch_hash_vector(size_t n, double* u, cudaStream_t s);
+
+// ---- Reductions (deterministic: fixed block count and summation order) ----
+int reduce_blocks(size_t n);  // number of partial sums a reduction over n produces
+
+// partial[b*k + i] = block b's part of sum_p w_p v_i,p  (i < k <= 8), V row stride ldv.
+cudaError_t launch_multi_dot(size_t n, const double* w, const double* V, size_t ldv, int k,
+                             double* partial, cudaStream_t s);
+// out[i] = sum_b partial[b*k + i] (+ out[i] if accumulate) for i < k; one block per output.
+cudaError_t launch_finalize(const double* partial, int nblocks, int k, double* out, int accumulate,
+                            cudaStream_t s);
+// out[0] = sqrt(sum_b partial[b]); out[1] = (out[0] != 0) ? 1/out[0] : 0.
+cudaError_t launch_finalize_norm(const double* partial, int nblocks, double* out, cudaStream_t s);
+// w -= sum_i h[i] v_i  (i < k <= 8), h read from device memory.
+cudaError_t launch_multi_axpy(size_t n, double* w, const double* V, size_t ldv, int k,
+                              const double* h, cudaStream_t s);
+// dst = src * scale[0] (scale read from device memory).
+cudaError_t launch_scale(size_t n, const double* src, double* dst, const double* scale, cudaStream_t s);
+// dst = src * alpha (alpha by value).
+cudaError_t launch_scale_value(size_t n, const double* src, double* dst, double alpha, cudaStream_t s);
+// x += sum_i y[i] z_i, Z row stride ldz, k <= 64, y on the device.
+template <typename TZ>
+cudaError_t launch_update_solution(size_t n, double* x, const TZ* Z, size_t ldz, int k,
+                                   const double* y, cudaStream_t s);
+// partial[b*2 + 0] = min over block of a; partial[b*2+1] = count of non-finite / non-positive.
+cudaError_t launch_coef_check(size_t n, const double* a, double* partial, cudaStream_t s);
+cudaError_t launch_finalize_check(const double* partial, int nblocks, double* out, cudaStream_t s);
+
+// ---- Coarsest level: dense SPD operator, Cholesky, explicit inverse ----
+// A (n x n, row-major, n = g.n()) from the coarse coefficient.
+cudaError_t launch_coarse_assemble(const Grid3& g, const double* a, double* A, cudaStream_t s);
+// In place: A -> L (lower Cholesky factor), then Ainv = A^{-1} (FP64) and an FP32 copy.
+// status[0] = 0 on success, 1 + column if a pivot was not positive.
+cudaError_t launch_coarse_factor(int n, double* A, double* work, double* Ainv, float* Ainv32,
+                                 int* status, cudaStream_t s);
+// x = Ainv b (dense matvec), level precision.
+template <typename T>
+cudaError_t launch_coarse_apply(int n, const T* Ainv, const T* b, T* x, cudaStream_t s);
+
+}  // namespace gmg

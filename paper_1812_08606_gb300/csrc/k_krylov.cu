@@ -1,0 +1,260 @@
+// FP64 vector kernels of the FGMRES outer loop (Algorithm 1, Sec. 3.1):
+// deterministic multi-dot reductions for the Gram-Schmidt coefficients
+// h_{i,j} = (w, v_i), the multi-axpy w -= sum_i h_{i,j} v_i, norms and
+// scaling for v_{j+1} = w / h_{j+1,j}, and the solution update x = x0 + Z_k y_k.
+// Reductions use a fixed number of blocks and a fixed summation order, so a
+// result does not depend on scheduling.
+#include "gmg_internal.cuh"
+
+namespace gmg {
+
+namespace {
+
+constexpr int RT = 256;          // reduction block size
+constexpr int MAX_RBLOCKS = 1024;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum a per-thread value over the block; result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = (lane < NT / 32) ? sh[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  __syncthreads();
+  return t;
+}
+
+template <int K>
+__global__ void __launch_bounds__(RT) k_multi_dot(size_t n, const double* __restrict__ w,
+                                                  const double* __restrict__ V, size_t ldv,
+                                                  double* __restrict__ partial) {
+  __shared__ double sh[RT / 32];
+  double acc[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) acc[i] = 0.0;
+  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
+    const double wp = w[p];
+#pragma unroll
+    for (int i = 0; i < K; ++i) acc[i] = fma(wp, V[i * ldv + p], acc[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const double t = block_sum<RT>(acc[i], sh);
+    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * K + i] = t;
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_finalize(const double* __restrict__ partial, int nblocks, int k,
+                                                 double* __restrict__ out, int accumulate) {
+  __shared__ double sh[RT / 32];
+  const int i = blockIdx.x;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += RT) v += partial[(size_t)b * k + i];
+  v = block_sum<RT>(v, sh);
+  if (threadIdx.x == 0) out[i] = accumulate ? out[i] + v : v;
+}
+
+__global__ void __launch_bounds__(RT) k_finalize_norm(const double* __restrict__ partial, int nblocks,
+                                                      double* __restrict__ out) {
+  __shared__ double sh[RT / 32];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += RT) v += partial[b];
+  v = block_sum<RT>(v, sh);
+  if (threadIdx.x == 0) {
+    const double nrm = sqrt(v);
+    out[0] = nrm;
+    out[1] = (nrm != 0.0) ? 1.0 / nrm : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_multi_axpy(size_t n, double* __restrict__ w, const double* __restrict__ V,
+                                                   size_t ldv, int k, const double* __restrict__ h) {
+  __shared__ double hs[64];
+  if (threadIdx.x < k) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
+    double v = w[p];
+    for (int i = 0; i < k; ++i) v = fma(-hs[i], V[i * ldv + p], v);
+    w[p] = v;
+  }
+}
+
+__global__ void k_scale(size_t n, const double* __restrict__ src, double* __restrict__ dst,
+                        const double* __restrict__ scale) {
+  const double s = scale[0];
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+    dst[p] = src[p] * s;
+}
+
+__global__ void k_scale_value(size_t n, const double* __restrict__ src, double* __restrict__ dst, double s) {
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+    dst[p] = src[p] * s;
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(RT) k_update_solution(size_t n, double* __restrict__ x,
+                                                        const TZ* __restrict__ Z, size_t ldz, int k,
+                                                        const double* __restrict__ y) {
+  __shared__ double ys[64];
+  if (threadIdx.x < k) ys[threadIdx.x] = y[threadIdx.x];
+  __syncthreads();
+  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
+    double v = x[p];
+    for (int i = 0; i < k; ++i) v = fma(ys[i], (double)Z[i * ldz + p], v);
+    x[p] = v;
+  }
+}
+
+__global__ void __launch_bounds__(RT) k_coef_check(size_t n, const double* __restrict__ a,
+                                                   double* __restrict__ partial) {
+  __shared__ double sh[RT / 32];
+  __shared__ double shm[RT / 32];
+  double mn = 1.0e300, bad = 0.0;
+  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
+    const double v = a[p];
+    if (!isfinite(v) || !(v > 0.0)) bad += 1.0;
+    else mn = fmin(mn, v);
+  }
+  // block min
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) shm[warp] = mn;
+  __syncthreads();
+  if (warp == 0) {
+    double t = (lane < RT / 32) ? shm[lane] : 1.0e300;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmin(t, __shfl_down_sync(0xffffffffu, t, o));
+    mn = t;
+  }
+  __syncthreads();
+  const double nb = block_sum<RT>(bad, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * (size_t)blockIdx.x] = mn;
+    partial[2 * (size_t)blockIdx.x + 1] = nb;
+  }
+}
+
+__global__ void k_finalize_check(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double mn = 1.0e300, bad = 0.0;
+  for (int b = 0; b < nblocks; ++b) {
+    mn = fmin(mn, partial[2 * b]);
+    bad += partial[2 * b + 1];
+  }
+  out[0] = mn;
+  out[1] = bad;
+}
+
+// splitmix64 (Steele, Lea, Flood, OOPSLA 2014) at counter p: state = (p+1) * gamma.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t p) {
+  uint64_t z = (p + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_hash_vector(size_t n, double* __restrict__ u) {
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t bits = splitmix64_at((uint64_t)p) >> 11;
+    u[p] = (double)bits * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+  }
+}
+
+inline unsigned flat_blocks(size_t n) {
+  size_t b = (n + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  if (b == 0) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+int reduce_blocks(size_t n) {
+  size_t b = (n + (size_t)RT * 8 - 1) / ((size_t)RT * 8);
+  if (b > MAX_RBLOCKS) b = MAX_RBLOCKS;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+cudaError_t launch_multi_dot(size_t n, const double* w, const double* V, size_t ldv, int k, double* partial,
+                             cudaStream_t s) {
+  const int nb = reduce_blocks(n);
+  switch (k) {
+#define GMG_CASE(K) \
+  case K: k_multi_dot<K><<<nb, RT, 0, s>>>(n, w, V, ldv, partial); break;
+    GMG_CASE(1) GMG_CASE(2) GMG_CASE(3) GMG_CASE(4) GMG_CASE(5) GMG_CASE(6) GMG_CASE(7) GMG_CASE(8)
+#undef GMG_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double* partial, int nblocks, int k, double* out, int accumulate,
+                            cudaStream_t s) {
+  k_finalize<<<k, RT, 0, s>>>(partial, nblocks, k, out, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_norm(const double* partial, int nblocks, double* out, cudaStream_t s) {
+  k_finalize_norm<<<1, RT, 0, s>>>(partial, nblocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_axpy(size_t n, double* w, const double* V, size_t ldv, int k, const double* h,
+                              cudaStream_t s) {
+  if (k < 1 || k > 64) return cudaErrorInvalidValue;
+  k_multi_axpy<<<reduce_blocks(n), RT, 0, s>>>(n, w, V, ldv, k, h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(size_t n, const double* src, double* dst, const double* scale, cudaStream_t s) {
+  k_scale<<<flat_blocks(n), 256, 0, s>>>(n, src, dst, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_value(size_t n, const double* src, double* dst, double alpha, cudaStream_t s) {
+  k_scale_value<<<flat_blocks(n), 256, 0, s>>>(n, src, dst, alpha);
+  return cudaGetLastError();
+}
+
+template <typename TZ>
+cudaError_t launch_update_solution(size_t n, double* x, const TZ* Z, size_t ldz, int k, const double* y,
+                                   cudaStream_t s) {
+  if (k < 1 || k > 64) return cudaErrorInvalidValue;
+  k_update_solution<TZ><<<reduce_blocks(n), RT, 0, s>>>(n, x, Z, ldz, k, y);
+  return cudaGetLastError();
+}
+template cudaError_t launch_update_solution<float>(size_t, double*, const float*, size_t, int, const double*,
+                                                   cudaStream_t);
+template cudaError_t launch_update_solution<double>(size_t, double*, const double*, size_t, int, const double*,
+                                                    cudaStream_t);
+
+cudaError_t launch_coef_check(size_t n, const double* a, double* partial, cudaStream_t s) {
+  k_coef_check<<<reduce_blocks(n), RT, 0, s>>>(n, a, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_check(const double* partial, int nblocks, double* out, cudaStream_t s) {
+  k_finalize_check<<<1, 32, 0, s>>>(partial, nblocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hash_vector(size_t n, double* u, cudaStream_t s) {
+  k_hash_vector<<<flat_blocks(n), 256, 0, s>>>(n, u);
+  return cudaGetLastError();
+}
+
+}  // namespace gmg

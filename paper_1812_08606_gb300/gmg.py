@@ -1,0 +1,353 @@
+"""Thin ctypes binding of libgmg (include/gmg.h), same names as the C ABI.
+
+Only argument marshalling lives here: tensors are passed as raw device
+pointers and the CUDA stream as a ``cudaStream_t``; every step of the solve
+runs in the library's CUDA kernels.  PyTorch supplies device memory and
+streams.  If libgmg.so is missing or cannot be loaded, every call raises:
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+GMG_MAX_HISTORY = 256
+
+GMG_OK = 0
+GMG_ERR_ARG = 1
+GMG_ERR_CUDA = 2
+GMG_ERR_ALLOC = 3
+GMG_ERR_NOT_CONVERGED = 4
+GMG_ERR_BREAKDOWN = 5
+GMG_ERR_NONFINITE = 6
+
+GMG_PREC_FP64 = 0
+GMG_PREC_MIXED = 1
+GMG_PROLONG_TRILINEAR = 0
+GMG_PROLONG_CONSTANT = 1
+GMG_PC_SGS = 0
+GMG_PC_JACOBI = 1
+GMG_PC_IDENTITY = 2
+GMG_ORTH_CGS2 = 0
+GMG_ORTH_MGS = 1
+
+
+class gmg_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+        ("phi_bottom", ctypes.c_double), ("phi_top", ctypes.c_double),
+        ("coarse_min", ctypes.c_int), ("cheb_steps", ctypes.c_int), ("restart", ctypes.c_int),
+        ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double), ("eig_steps", ctypes.c_int),
+        ("eig_hi", ctypes.c_double), ("eig_lo", ctypes.c_double), ("precision", ctypes.c_int),
+        ("prolongation", ctypes.c_int), ("smoother_pc", ctypes.c_int), ("orthogonalization", ctypes.c_int),
+    ]
+
+
+class gmg_solve_info(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
+        ("true_rel_residual", ctypes.c_double), ("bnorm", ctypes.c_double), ("n_history", ctypes.c_int),
+        ("res_history", ctypes.c_double * GMG_MAX_HISTORY), ("setup_ms", ctypes.c_float),
+        ("solve_ms", ctypes.c_float),
+    ]
+
+    @property
+    def history(self):
+        return [self.res_history[i] for i in range(self.n_history)]
+
+
+class GMGError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+_LIB = None
+
+# name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "gmg_default_params": (None, [ctypes.POINTER(gmg_params), ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "gmg_setup": (ctypes.c_int, [ctypes.POINTER(gmg_params), _P, _P, ctypes.POINTER(_P)]),
+    "gmg_update_coefficient": (ctypes.c_int, [_P, _P]),
+    "fgmres_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(gmg_solve_info)]),
+    "apply_operator": (ctypes.c_int, [_P, _P, _P]),
+    "assemble_rhs": (ctypes.c_int, [_P, _P, _P]),
+    "field_from_potential": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
+    "adjoint_coefficient_grad": (ctypes.c_int, [_P, _P, _P, _P]),
+    "gmg_solve_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int, ctypes.POINTER(gmg_solve_info)]),
+    "gmg_set_stream": (ctypes.c_int, [_P, _P]),
+    "gmg_destroy": (None, [_P]),
+    "gmg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "gmg_num_levels": (ctypes.c_int, [_P]),
+    "gmg_level_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "gmg_level_coefficient": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "gmg_apply_preconditioner": (ctypes.c_int, [_P, _P, _P]),
+    "gmg_level_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "gmg_level_smooth": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int]),
+    "gmg_level_smoother_pc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "gmg_level_residual_restrict": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+    "gmg_level_prolong_add": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "gmg_coarse_solve": (ctypes.c_int, [_P, _P, _P]),
+    "gmg_hessenberg_max_real_eig": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "gmg_test_fail_allocation_after": (None, [ctypes.c_int]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = False):
+    """Load libgmg.so (building it first if asked).  Raises if unavailable."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libgmg.so not built at {path}; run paper_1812_08606_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def gmg_status_string(status: int) -> str:
+    return load().gmg_status_string(int(status)).decode()
+
+
+status_string = gmg_status_string
+
+
+def _check(status: int, where: str, allow=(GMG_OK,)):
+    if status not in allow:
+        raise GMGError(status, where)
+    return status
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype=torch.float64, numel=None, name="tensor") -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def _host(t: torch.Tensor, dtype=torch.float64, numel=None, name="tensor") -> int:
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} host tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements")
+    return t.data_ptr()
+
+
+def gmg_default_params(nx: int, ny: int, nz: int, **overrides) -> gmg_params:
+    p = gmg_params()
+    load().gmg_default_params(ctypes.byref(p), int(nx), int(ny), int(nz))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """Owner of one gmg_ctx*; freed by close() or garbage collection."""
+
+    def __init__(self, handle: int, params: gmg_params, stream):
+        self.handle = ctypes.c_void_p(handle)
+        self.params = params
+        self.stream = stream
+        self.n = params.nx * params.ny * params.nz
+        self.shape = (params.nz, params.ny, params.nx)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load().gmg_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def level_dtype(self):
+        return torch.float32 if self.params.precision == GMG_PREC_MIXED else torch.float64
+
+
+def gmg_setup(params: gmg_params, a: torch.Tensor, stream=None) -> Context:
+    n = params.nx * params.ny * params.nz
+    out = ctypes.c_void_p()
+    st = load().gmg_setup(ctypes.byref(params), _dev(a, numel=n, name="a"), _stream_ptr(stream), ctypes.byref(out))
+    _check(st, "gmg_setup")
+    return Context(out.value, params, stream)
+
+
+def gmg_update_coefficient(ctx: Context, a: torch.Tensor):
+    _check(load().gmg_update_coefficient(ctx.handle, _dev(a, numel=ctx.n, name="a")), "gmg_update_coefficient")
+
+
+def fgmres_solve(ctx: Context, f: torch.Tensor, phi: torch.Tensor, homogeneous_bc: bool = False) -> gmg_solve_info:
+    """Solve in place into phi (initial guess on entry).  Returns the info;
+    a solve that hit max_iters returns info.converged == 0 without raising."""
+    info = gmg_solve_info()
+    st = load().fgmres_solve(ctx.handle, _dev(f, numel=ctx.n, name="f"), _dev(phi, numel=ctx.n, name="phi"),
+                             int(bool(homogeneous_bc)), ctypes.byref(info))
+    _check(st, "fgmres_solve", allow=(GMG_OK, GMG_ERR_NOT_CONVERGED))
+    return info
+
+
+def apply_operator(ctx: Context, x: torch.Tensor, y: torch.Tensor):
+    _check(load().apply_operator(ctx.handle, _dev(x, numel=ctx.n, name="x"), _dev(y, numel=ctx.n, name="y")),
+           "apply_operator")
+
+
+def assemble_rhs(ctx: Context, f: torch.Tensor, b: torch.Tensor):
+    _check(load().assemble_rhs(ctx.handle, _dev(f, numel=ctx.n, name="f"), _dev(b, numel=ctx.n, name="b")),
+           "assemble_rhs")
+
+
+def field_from_potential(ctx: Context, phi: torch.Tensor, ex: torch.Tensor, ey: torch.Tensor, ez: torch.Tensor):
+    dt = ex.dtype
+    if dt not in (torch.float32, torch.float64) or ey.dtype != dt or ez.dtype != dt:
+        raise ValueError("ex, ey, ez must all be float32 or all float64")
+    _check(load().field_from_potential(ctx.handle, _dev(phi, numel=ctx.n, name="phi"),
+                                       _dev(ex, dt, ctx.n, "ex"), _dev(ey, dt, ctx.n, "ey"),
+                                       _dev(ez, dt, ctx.n, "ez"), int(dt == torch.float32)),
+           "field_from_potential")
+
+
+def adjoint_coefficient_grad(ctx: Context, phi: torch.Tensor, lam: torch.Tensor, dlda: torch.Tensor):
+    _check(load().adjoint_coefficient_grad(ctx.handle, _dev(phi, numel=ctx.n, name="phi"),
+                                           _dev(lam, numel=ctx.n, name="lambda"),
+                                           _dev(dlda, numel=ctx.n, name="dlda")), "adjoint_coefficient_grad")
+
+
+def gmg_solve_host(ctx: Context, a_host, f_host, phi_host, ex_host=None, ey_host=None, ez_host=None):
+    """End-to-end solve on host tensors (pinned for full bandwidth)."""
+    info = gmg_solve_info()
+    a_ptr = _host(a_host, numel=ctx.n, name="a") if a_host is not None else None
+    fp32 = 0
+    eptrs = [None, None, None]
+    if ex_host is not None:
+        fp32 = int(ex_host.dtype == torch.float32)
+        dt = torch.float32 if fp32 else torch.float64
+        eptrs = [_host(t, dt, ctx.n, nm) for t, nm in ((ex_host, "ex"), (ey_host, "ey"), (ez_host, "ez"))]
+    st = load().gmg_solve_host(ctx.handle, a_ptr, _host(f_host, numel=ctx.n, name="f"),
+                               _host(phi_host, numel=ctx.n, name="phi"), eptrs[0], eptrs[1], eptrs[2], fp32,
+                               ctypes.byref(info))
+    _check(st, "gmg_solve_host", allow=(GMG_OK, GMG_ERR_NOT_CONVERGED))
+    return info
+
+
+def gmg_set_stream(ctx: Context, stream):
+    _check(load().gmg_set_stream(ctx.handle, _stream_ptr(stream)), "gmg_set_stream")
+    ctx.stream = stream
+
+
+def gmg_destroy(ctx: Context):
+    ctx.close()
+
+
+def gmg_num_levels(ctx: Context) -> int:
+    return load().gmg_num_levels(ctx.handle)
+
+
+def gmg_level_info(ctx: Context, level: int):
+    nx, ny, nz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    lmax, lmin = ctypes.c_double(), ctypes.c_double()
+    _check(load().gmg_level_info(ctx.handle, int(level), ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(nz),
+                                 ctypes.byref(lmax), ctypes.byref(lmin)), "gmg_level_info")
+    return {"shape": (nz.value, ny.value, nx.value), "lam_max": lmax.value, "lam_min": lmin.value}
+
+
+def _level_n(ctx, level):
+    s = gmg_level_info(ctx, level)["shape"]
+    return s[0] * s[1] * s[2]
+
+
+def gmg_level_coefficient(ctx: Context, level: int, out: torch.Tensor):
+    _check(load().gmg_level_coefficient(ctx.handle, int(level), _dev(out, numel=_level_n(ctx, level), name="out")),
+           "gmg_level_coefficient")
+
+
+def gmg_apply_preconditioner(ctx: Context, v: torch.Tensor, z: torch.Tensor):
+    _check(load().gmg_apply_preconditioner(ctx.handle, _dev(v, numel=ctx.n, name="v"),
+                                           _dev(z, numel=ctx.n, name="z")), "gmg_apply_preconditioner")
+
+
+def gmg_level_apply(ctx: Context, level: int, x: torch.Tensor, y: torch.Tensor):
+    n, dt = _level_n(ctx, level), ctx.level_dtype
+    _check(load().gmg_level_apply(ctx.handle, int(level), _dev(x, dt, n, "x"), _dev(y, dt, n, "y")),
+           "gmg_level_apply")
+
+
+def gmg_level_smooth(ctx: Context, level: int, b: torch.Tensor, x: torch.Tensor, x_is_zero: bool):
+    n, dt = _level_n(ctx, level), ctx.level_dtype
+    _check(load().gmg_level_smooth(ctx.handle, int(level), _dev(b, dt, n, "b"), _dev(x, dt, n, "x"),
+                                   int(bool(x_is_zero))), "gmg_level_smooth")
+
+
+def gmg_level_smoother_pc(ctx: Context, level: int, r: torch.Tensor, z: torch.Tensor):
+    n, dt = _level_n(ctx, level), ctx.level_dtype
+    _check(load().gmg_level_smoother_pc(ctx.handle, int(level), _dev(r, dt, n, "r"), _dev(z, dt, n, "z")),
+           "gmg_level_smoother_pc")
+
+
+def gmg_level_residual_restrict(ctx: Context, level: int, b: torch.Tensor, x: torch.Tensor, coarse: torch.Tensor):
+    n, nc, dt = _level_n(ctx, level), _level_n(ctx, level - 1), ctx.level_dtype
+    _check(load().gmg_level_residual_restrict(ctx.handle, int(level), _dev(b, dt, n, "b"), _dev(x, dt, n, "x"),
+                                              _dev(coarse, dt, nc, "coarse")), "gmg_level_residual_restrict")
+
+
+def gmg_level_prolong_add(ctx: Context, level: int, e: torch.Tensor, x: torch.Tensor):
+    n, nc, dt = _level_n(ctx, level), _level_n(ctx, level - 1), ctx.level_dtype
+    _check(load().gmg_level_prolong_add(ctx.handle, int(level), _dev(e, dt, nc, "e"), _dev(x, dt, n, "x")),
+           "gmg_level_prolong_add")
+
+
+def gmg_coarse_solve(ctx: Context, b: torch.Tensor, x: torch.Tensor):
+    n, dt = _level_n(ctx, 0), ctx.level_dtype
+    _check(load().gmg_coarse_solve(ctx.handle, _dev(b, dt, n, "b"), _dev(x, dt, n, "x")), "gmg_coarse_solve")
+
+
+def gmg_hessenberg_max_real_eig(h) -> float:
+    """Largest real part of the eigenvalues of a square upper Hessenberg
+    matrix (host computation inside the library; needs no GPU)."""
+    import numpy as np
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    m = h.shape[0]
+    out = ctypes.c_double()
+    _check(load().gmg_hessenberg_max_real_eig(h.ctypes.data_as(ctypes.c_void_p), int(m), ctypes.byref(out)),
+           "gmg_hessenberg_max_real_eig")
+    return out.value
+
+
+def gmg_test_fail_allocation_after(n: int):
+    load().gmg_test_fail_allocation_after(int(n))

@@ -1,0 +1,469 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Element-by-element comparisons on seeded inputs, kernel by kernel (operator,
+smoother preconditioner, Chebyshev smoothing, fused residual + restriction,
+prolongation, coarse solve), then the V-cycle, then whole solves.
+
+Tolerances: FP64 kernels agree with the oracle to ~1e-13 relative (different
+summation order only).  FP32 kernels are compared with the oracle evaluated
+on the same FP32-rounded inputs, to a few FP32 ulps scaled by the stencil's
+cancellation (5e-5 relative to the operator norm).  FP64 solves must match the
+oracle's phi within 1e-10 relative with the same iteration count; every solve
+must reach a true FP64 residual below 1e-8.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import gmg_oracle as O  # noqa: E402
+from streamer_inputs import make_inputs, random_coefficient, random_field  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1812_08606_gb300 import gmg  # noqa: E402
+
+DEV = torch.device("cuda:0")
+RAGGED = (16, 24, 40)     # (nz, ny, nx): x not a multiple of the 32-wide tile; coarsest 2 x 3 x 5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1812_08606_gb300 import build
+    build.build()
+    gmg.load()
+
+
+def _t(x, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV, dtype)
+
+
+def _np(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _params(shape, **kw):
+    nz, ny, nx = shape
+    return gmg.gmg_default_params(nx, ny, nz, **kw)
+
+
+def _ogrid(shape, p=None):
+    nz, ny, nx = shape
+    if p is None:
+        return O.Grid(nx, ny, nz)
+    return O.Grid(nx, ny, nz, p.lx, p.ly, p.lz)
+
+
+def _rel(x, ref):
+    return np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300)
+
+
+def _oracle_hierarchy(a, p):
+    op = O.OracleParams(lx=p.lx, ly=p.ly, lz=p.lz, phi_bottom=p.phi_bottom, phi_top=p.phi_top,
+                        coarse_min=p.coarse_min, cheb_steps=p.cheb_steps, restart=p.restart,
+                        max_iters=p.max_iters, rtol=p.rtol, eig_steps=p.eig_steps, eig_hi=p.eig_hi,
+                        eig_lo=p.eig_lo, prolongation=["trilinear", "constant"][p.prolongation],
+                        smoother_pc=["sgs", "jacobi", "identity"][p.smoother_pc])
+    return op
+
+
+# ---------------------------------------------------------------------------
+# Operator and right-hand side
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("shape,lengths", [(RAGGED, (1.0, 1.0, 1.0)), ((32, 32, 32), (0.5, 1.5, 1.0)),
+                                           ((8, 8, 10), (1.0, 1.0, 1.25))])
+def test_apply_operator_and_rhs_fp64(shape, lengths):
+    a = random_coefficient(101, shape, contrast=1e3)
+    x = random_field(102, shape)
+    f = random_field(103, shape)
+    cm = 2 if shape == RAGGED else 4
+    p = _params(shape, coarse_min=cm, lx=lengths[0], ly=lengths[1], lz=lengths[2], phi_bottom=0.3, phi_top=-2.0)
+    ctx = gmg.gmg_setup(p, _t(a))
+    y = torch.empty(shape, dtype=torch.float64, device=DEV)
+    gmg.apply_operator(ctx, _t(x), y)
+    grid = _ogrid(shape, p)
+    ref = O.apply_operator(grid, a, x)
+    assert _rel(_np(y), ref) < 1e-14
+    b = torch.empty_like(y)
+    gmg.assemble_rhs(ctx, _t(f), b)
+    np.testing.assert_allclose(_np(b), O.assemble_rhs(grid, a, f, 0.3, -2.0), rtol=1e-14, atol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [gmg.GMG_PREC_FP64, gmg.GMG_PREC_MIXED])
+def test_level_coefficients_and_operators(prec):
+    shape = RAGGED
+    a = random_coefficient(104, shape, contrast=1e3)
+    p = _params(shape, coarse_min=2, precision=prec)
+    ctx = gmg.gmg_setup(p, _t(a))
+    L = gmg.gmg_num_levels(ctx)
+    assert L == 4
+    ref_a = a
+    dt = ctx.level_dtype
+    for lev in range(L - 1, -1, -1):
+        info = gmg.gmg_level_info(ctx, lev)
+        s = info["shape"]
+        assert s == ref_a.shape
+        ac = torch.empty(s, dtype=torch.float64, device=DEV)
+        gmg.gmg_level_coefficient(ctx, lev, ac)
+        np.testing.assert_allclose(_np(ac), ref_a, rtol=1e-15)
+        x = random_field(105 + lev, s)
+        xin = x.astype(np.float32).astype(np.float64) if dt == torch.float32 else x
+        ain = ref_a.astype(np.float32).astype(np.float64) if dt == torch.float32 else ref_a
+        y = torch.empty(s, dtype=dt, device=DEV)
+        gmg.gmg_level_apply(ctx, lev, _t(xin, dt), y)
+        ref = O.apply_operator(_ogrid(s), ain, xin)
+        tol = 1e-14 if dt == torch.float64 else 5e-6
+        assert _rel(_np(y), ref) < tol, lev
+        ref_a = O.coarsen_coefficient(ref_a)
+
+
+# ---------------------------------------------------------------------------
+# Smoother
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("prec", [gmg.GMG_PREC_FP64, gmg.GMG_PREC_MIXED])
+@pytest.mark.parametrize("pc", [gmg.GMG_PC_SGS, gmg.GMG_PC_JACOBI, gmg.GMG_PC_IDENTITY])
+def test_smoother_preconditioner_and_chebyshev(prec, pc):
+    shape = RAGGED
+    a = random_coefficient(110, shape, contrast=1e2)
+    p = _params(shape, coarse_min=2, precision=prec, smoother_pc=pc)
+    op = _oracle_hierarchy(a, p)
+    ctx = gmg.gmg_setup(p, _t(a))
+    dt = ctx.level_dtype
+    fp32 = dt == torch.float32
+    q = (lambda v: v.astype(np.float32).astype(np.float64)) if fp32 else (lambda v: v)
+    tol = 2e-5 if fp32 else 1e-13
+    oa = a
+    for lev in range(gmg.gmg_num_levels(ctx) - 1, 0, -1):
+        info = gmg.gmg_level_info(ctx, lev)
+        s = info["shape"]
+        g = _ogrid(s)
+        r = q(random_field(111 + lev, s))
+        z = torch.empty(s, dtype=dt, device=DEV)
+        gmg.gmg_level_smoother_pc(ctx, lev, _t(r, dt), z)
+        ref = O.smoother_preconditioner(g, q(oa), r, op.smoother_pc)
+        assert _rel(_np(z), ref) < tol, ("pc", lev)
+        # Chebyshev from zero and from a given x, with the GPU's bounds
+        b = q(random_field(121 + lev, s))
+        x0 = q(random_field(131 + lev, s))
+        for x_is_zero in (True, False):
+            x = _t(x0, dt)
+            gmg.gmg_level_smooth(ctx, lev, _t(b, dt), x, x_is_zero)
+            ref = O.chebyshev_smooth(g, q(oa), b, None if x_is_zero else x0, info["lam_max"], info["lam_min"],
+                                     p.cheb_steps, op.smoother_pc)
+            assert _rel(_np(x), ref) < 5 * tol, ("cheb", lev, x_is_zero)
+        oa = O.coarsen_coefficient(oa)
+
+
+def test_eigen_bounds_match_oracle():
+    shape = RAGGED
+    a = random_coefficient(140, shape, contrast=1e3)
+    p = _params(shape, coarse_min=2, precision=gmg.GMG_PREC_FP64, orthogonalization=gmg.GMG_ORTH_MGS)
+    ctx = gmg.gmg_setup(p, _t(a))
+    hier = O.build_hierarchy(_ogrid(shape), a, _oracle_hierarchy(a, p))
+    for lev in range(1, gmg.gmg_num_levels(ctx)):
+        info = gmg.gmg_level_info(ctx, lev)
+        assert info["lam_max"] == pytest.approx(hier.levels[lev].lam_max, rel=1e-11)
+        assert info["lam_min"] == pytest.approx(hier.levels[lev].lam_min, rel=1e-11)
+
+
+@pytest.mark.parametrize("prec", [gmg.GMG_PREC_FP64, gmg.GMG_PREC_MIXED])
+@pytest.mark.parametrize("mode", [gmg.GMG_PROLONG_TRILINEAR, gmg.GMG_PROLONG_CONSTANT])
+def test_transfers_and_coarse_solve(prec, mode):
+    shape = RAGGED
+    a = random_coefficient(150, shape, contrast=1e2)
+    p = _params(shape, coarse_min=2, precision=prec, prolongation=mode)
+    ctx = gmg.gmg_setup(p, _t(a))
+    dt = ctx.level_dtype
+    fp32 = dt == torch.float32
+    q = (lambda v: v.astype(np.float32).astype(np.float64)) if fp32 else (lambda v: v)
+    tol = 2e-6 if fp32 else 1e-14
+    oa = a
+    L = gmg.gmg_num_levels(ctx)
+    for lev in range(L - 1, 0, -1):
+        s = gmg.gmg_level_info(ctx, lev)["shape"]
+        sc = gmg.gmg_level_info(ctx, lev - 1)["shape"]
+        b, x = q(random_field(151 + lev, s)), q(random_field(161 + lev, s))
+        coarse = torch.empty(sc, dtype=dt, device=DEV)
+        gmg.gmg_level_residual_restrict(ctx, lev, _t(b, dt), _t(x, dt), coarse)
+        ref = O.restrict(b - O.apply_operator(_ogrid(s), q(oa), x))
+        assert _rel(_np(coarse), ref) < (5e-5 if fp32 else 1e-13), ("restrict", lev)
+        e = q(random_field(171 + lev, sc))
+        xt = _t(x, dt)
+        gmg.gmg_level_prolong_add(ctx, lev, _t(e, dt), xt)
+        ref = x + O.prolong(e, ["trilinear", "constant"][mode])
+        assert _rel(_np(xt), ref) < tol, ("prolong", lev)
+        oa = O.coarsen_coefficient(oa)
+    # coarsest direct solve
+    sc = gmg.gmg_level_info(ctx, 0)["shape"]
+    b = q(random_field(180, sc))
+    x = torch.empty(sc, dtype=dt, device=DEV)
+    gmg.gmg_coarse_solve(ctx, _t(b, dt), x)
+    A = O.dense_operator(_ogrid(sc), oa)
+    ref = np.linalg.solve(A, b.ravel()).reshape(sc)
+    assert _rel(_np(x), ref) < (1e-5 if fp32 else 1e-12)
+
+
+@pytest.mark.parametrize("shape,cm", [(RAGGED, 2), ((32, 32, 32), 4), ((20, 16, 16), 4)])
+def test_vcycle_fp64_matches_oracle(shape, cm):
+    a = make_inputs("channel128", shape=shape)["a"]
+    p = _params(shape, coarse_min=cm, precision=gmg.GMG_PREC_FP64, orthogonalization=gmg.GMG_ORTH_MGS)
+    ctx = gmg.gmg_setup(p, _t(a))
+    hier = O.build_hierarchy(_ogrid(shape), a, _oracle_hierarchy(a, p))
+    v = random_field(190, shape)
+    z = torch.empty(shape, dtype=torch.float64, device=DEV)
+    gmg.gmg_apply_preconditioner(ctx, _t(v), z)
+    assert _rel(_np(z), O.vcycle(hier, v)) < 1e-12
+
+
+def test_vcycle_mixed_close_to_oracle():
+    shape = (32, 32, 32)
+    a = make_inputs("channel128", n=32)["a"]
+    p = _params(shape, precision=gmg.GMG_PREC_MIXED)
+    ctx = gmg.gmg_setup(p, _t(a))
+    hier = O.build_hierarchy(_ogrid(shape), a, _oracle_hierarchy(a, p))
+    v = random_field(191, shape)
+    z = torch.empty(shape, dtype=torch.float64, device=DEV)
+    gmg.gmg_apply_preconditioner(ctx, _t(v), z)
+    assert _rel(_np(z), O.vcycle(hier, v)) < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Whole solves
+# ---------------------------------------------------------------------------
+
+
+def _true_residual(shape, p, a, f, phi, homogeneous=False):
+    g = _ogrid(shape, p)
+    b = f if homogeneous else O.assemble_rhs(g, a, f, p.phi_bottom, p.phi_top)
+    return np.linalg.norm(b - O.apply_operator(g, a, phi)) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("workload,n,orth", [("const32", 32, gmg.GMG_ORTH_MGS), ("channel128", 32, gmg.GMG_ORTH_CGS2),
+                                             ("channel128", 64, gmg.GMG_ORTH_MGS),
+                                             ("twochannel512", 32, gmg.GMG_ORTH_CGS2)])
+def test_fp64_solve_matches_oracle(workload, n, orth):
+    inp = make_inputs(workload, n=n)
+    shape = inp["a"].shape
+    p = _params(shape, precision=gmg.GMG_PREC_FP64, orthogonalization=orth)
+    ref, rinfo, _ = O.solve(_oracle_hierarchy(inp["a"], p), inp["a"], inp["f"])
+    ctx = gmg.gmg_setup(p, _t(inp["a"]))
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    info = gmg.fgmres_solve(ctx, _t(inp["f"]), phi)
+    out = _np(phi)
+    assert info.converged and info.iterations == rinfo.iterations
+    assert _true_residual(shape, p, inp["a"], inp["f"], out) < 1e-8
+    assert info.true_rel_residual == pytest.approx(rinfo.true_rel_residual, rel=1e-4)
+    np.testing.assert_allclose(info.history, rinfo.history, rtol=1e-5)
+    assert _rel(out, ref) < 1e-10
+
+
+@pytest.mark.parametrize("workload,n,kappa", [("const32", 32, None), ("channel128", 64, None),
+                                              ("channel256", 64, 1e4), ("twochannel512", 64, None)])
+def test_mixed_solve_residual_and_error(workload, n, kappa):
+    inp = make_inputs(workload, n=n, kappa=kappa)
+    shape = inp["a"].shape
+    p = _params(shape, precision=gmg.GMG_PREC_MIXED)
+    ref, rinfo, _ = O.solve(_oracle_hierarchy(inp["a"], p), inp["a"], inp["f"])
+    ctx = gmg.gmg_setup(p, _t(inp["a"]))
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    info = gmg.fgmres_solve(ctx, _t(inp["f"]), phi)
+    out = _np(phi)
+    tr = _true_residual(shape, p, inp["a"], inp["f"], out)
+    print(f"{workload} n={n} mixed iters {info.iterations} (oracle {rinfo.iterations}) true {tr:.2e} "
+          f"phi rel err {_rel(out, ref):.2e}")
+    assert info.converged and tr < 1e-8
+    assert abs(info.iterations - rinfo.iterations) <= 2
+    assert _rel(out, ref) < 1e-6
+
+
+def test_warm_start_and_restart():
+    inp = make_inputs("channel128", n=32)
+    shape = inp["a"].shape
+    p = _params(shape, precision=gmg.GMG_PREC_MIXED, restart=3)
+    ctx = gmg.gmg_setup(p, _t(inp["a"]))
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    info = gmg.fgmres_solve(ctx, _t(inp["f"]), phi)
+    assert info.converged and info.restarts >= 2
+    # warm start from the converged phi: converges at once (0 iterations)
+    info2 = gmg.fgmres_solve(ctx, _t(inp["f"]), phi)
+    assert info2.converged and info2.iterations == 0
+
+
+def test_edge_cases():
+    shape = (8, 8, 8)
+    a = random_coefficient(200, shape, contrast=10.0)
+    # zero right-hand side and zero plate data -> phi = 0
+    p = _params(shape, phi_top=0.0)
+    ctx = gmg.gmg_setup(p, _t(a))
+    phi = torch.ones(shape, dtype=torch.float64, device=DEV)
+    info = gmg.fgmres_solve(ctx, torch.zeros(shape, dtype=torch.float64, device=DEV), phi)
+    assert info.converged and float(phi.abs().max()) == 0.0
+    # iteration cap
+    p = _params(shape, max_iters=1)
+    ctx = gmg.gmg_setup(p, _t(a))
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    info = gmg.fgmres_solve(ctx, _t(random_field(201, shape)), phi)
+    assert not info.converged and info.iterations == 1
+    # non-finite input
+    f = random_field(202, shape)
+    f[3, 3, 3] = np.nan
+    with pytest.raises(gmg.GMGError) as e:
+        gmg.fgmres_solve(ctx, _t(f), torch.zeros(shape, dtype=torch.float64, device=DEV))
+    assert e.value.status == gmg.GMG_ERR_NONFINITE
+    # bad coefficient
+    bad = a.copy()
+    bad[0, 0, 0] = -1.0
+    with pytest.raises(gmg.GMGError) as e:
+        gmg.gmg_setup(_params(shape), _t(bad))
+    assert e.value.status == gmg.GMG_ERR_ARG
+    # shape that does not halve to coarse_min
+    with pytest.raises(gmg.GMGError):
+        gmg.gmg_setup(gmg.gmg_default_params(12, 12, 10), _t(np.ones((10, 12, 12))))
+    # only the coarsest grid: the direct solve answers in one iteration
+    p = _params((4, 4, 4), precision=gmg.GMG_PREC_FP64)
+    a4 = random_coefficient(203, (4, 4, 4), 10.0)
+    ctx = gmg.gmg_setup(p, _t(a4))
+    phi = torch.zeros((4, 4, 4), dtype=torch.float64, device=DEV)
+    info = gmg.fgmres_solve(ctx, _t(random_field(204, (4, 4, 4))), phi)
+    assert info.converged and info.iterations == 1
+
+
+def test_allocation_failure_is_reported_and_recoverable():
+    shape = (16, 16, 16)
+    a = _t(random_coefficient(210, shape, 10.0))
+    for k in (1, 3, 7):
+        gmg.gmg_test_fail_allocation_after(k)
+        with pytest.raises(gmg.GMGError) as e:
+            gmg.gmg_setup(_params(shape), a)
+        assert e.value.status == gmg.GMG_ERR_ALLOC
+    gmg.gmg_test_fail_allocation_after(0)
+    ctx = gmg.gmg_setup(_params(shape), a)
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    assert gmg.fgmres_solve(ctx, _t(random_field(211, shape)), phi).converged
+
+
+def test_host_buffer_solve_matches_device_solve():
+    inp = make_inputs("channel128", n=32)
+    shape = inp["a"].shape
+    p = _params(shape)
+    ctx = gmg.gmg_setup(p, _t(inp["a"]))
+    phi_d = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    gmg.fgmres_solve(ctx, _t(inp["f"]), phi_d)
+    ctx2 = gmg.gmg_setup(p, _t(np.ones(shape)))
+    a_h = torch.from_numpy(inp["a"]).pin_memory()
+    f_h = torch.from_numpy(inp["f"]).pin_memory()
+    phi_h = torch.zeros(shape, dtype=torch.float64).pin_memory()
+    e = [torch.empty(shape, dtype=torch.float32).pin_memory() for _ in range(3)]
+    info = gmg.gmg_solve_host(ctx2, a_h, f_h, phi_h, *e)
+    assert info.converged
+    np.testing.assert_array_equal(phi_h.numpy(), _np(phi_d))
+    ex, ey, ez = O.field_from_potential(_ogrid(shape), phi_h.numpy(), 0.0, 1.0)
+    for got, ref in zip(e, (ex, ey, ez)):
+        assert _rel(got.numpy().astype(np.float64), ref) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Field and adjoint
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_field_matches_oracle(dtype):
+    shape = RAGGED
+    p = _params(shape, coarse_min=2, phi_bottom=0.2, phi_top=3.0, lx=2.0, lz=0.5)
+    ctx = gmg.gmg_setup(p, _t(np.ones(shape)))
+    phi = random_field(220, shape)
+    e = [torch.empty(shape, dtype=dtype, device=DEV) for _ in range(3)]
+    gmg.field_from_potential(ctx, _t(phi), *e)
+    ref = O.field_from_potential(_ogrid(shape, p), phi, 0.2, 3.0)
+    for got, r in zip(e, ref):
+        np.testing.assert_allclose(_np(got), r, rtol=1e-13 if dtype == torch.float64 else 1e-6,
+                                   atol=1e-12 if dtype == torch.float64 else 1e-5 * np.abs(r).max())
+
+
+def test_adjoint_grad_kernel_matches_oracle():
+    shape = RAGGED
+    p = _params(shape, coarse_min=2, phi_bottom=0.4, phi_top=1.3, ly=0.8)
+    ctx = gmg.gmg_setup(p, _t(np.ones(shape)))
+    phi, lam = random_field(230, shape), random_field(231, shape)
+    out = torch.empty(shape, dtype=torch.float64, device=DEV)
+    gmg.adjoint_coefficient_grad(ctx, _t(phi), _t(lam), out)
+    ref = O.adjoint_coefficient_grad(_ogrid(shape, p), phi, lam, 0.4, 1.3)
+    assert _rel(_np(out), ref) < 1e-14
+
+
+def test_autograd_finite_differences_and_cpu_adjoint():
+    """Central differences on 64 seeded entries of a 32^3 instance.
+
+    L is linear in f, so a large step (1 or |f_q|) is exact up to the solve
+    error.  For a, the step is 1e-3 relative: the truncation error is ~1e-6
+    relative, while a 1e-6 step would sit below the noise floor left by the
+    solve tolerance (|dL| ~ |lambda . r| with ||r|| ~ rtol ||b||)."""
+    from paper_1812_08606_gb300 import PoissonSolver
+    inp = make_inputs("adjoint", n=32)
+    shape = inp["a"].shape
+    solver = PoissonSolver(shape, rtol=1e-12, precision=gmg.GMG_PREC_MIXED)
+    a = _t(inp["a"]).requires_grad_(True)
+    f = _t(inp["f"]).requires_grad_(True)
+    w = _t(inp["w"])
+    loss = (w * solver.solve(a, f)).sum()
+    loss.backward()
+    ga, gf = _np(a.grad), _np(f.grad)
+    rng = np.random.default_rng(20181225)
+    idx = rng.choice(a.numel(), size=64, replace=False)
+
+    def L(av, fv):
+        with torch.no_grad():
+            return float((w * solver.solve(av, fv)).sum())
+
+    base_a, base_f = a.detach().clone(), f.detach().clone()
+    worst = 0.0
+    for q in idx:
+        for grad, base, which in ((ga, base_a, "a"), (gf, base_f, "f")):
+            v = abs(float(base.view(-1)[q]))
+            h = 1e-3 * v if which == "a" else max(v, 1.0)
+            plus, minus = base.clone(), base.clone()
+            plus.view(-1)[q] += h
+            minus.view(-1)[q] -= h
+            if which == "a":
+                fd = (L(plus, base_f) - L(minus, base_f)) / (2 * h)
+            else:
+                fd = (L(base_a, plus) - L(base_a, minus)) / (2 * h)
+            g = grad.ravel()[q]
+            err = abs(g - fd) / max(abs(fd), 1e-4 * np.abs(grad).max())
+            worst = max(worst, err)
+            assert err < 1e-4, (which, q, g, fd)
+    print(f"worst FD relative mismatch {worst:.2e}")
+    # dot test: w . A^{-1} f = f . A^{-1} w on the homogeneous problem
+    ctx = solver.ctx
+    solver.set_coefficient(base_a)
+    x1 = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    x2 = torch.zeros_like(x1)
+    gmg.fgmres_solve(ctx, base_f, x1, homogeneous_bc=True)
+    gmg.fgmres_solve(ctx, w, x2, homogeneous_bc=True)
+    assert float((w * x1).sum()) == pytest.approx(float((base_f * x2).sum()), rel=1e-10)
+
+
+def test_autograd_matches_cpu_adjoint_64():
+    from paper_1812_08606_gb300 import PoissonSolver
+    inp = make_inputs("adjoint", n=64)
+    shape = inp["a"].shape
+    solver = PoissonSolver(shape, rtol=1e-12)
+    a = _t(inp["a"]).requires_grad_(True)
+    f = _t(inp["f"]).requires_grad_(True)
+    (_t(inp["w"]) * solver.solve(a, f)).sum().backward()
+    op = O.OracleParams(rtol=1e-12)
+    phi, _, hier = O.solve(op, inp["a"], inp["f"])
+    lam, _, _ = O.solve(op, inp["a"], inp["w"], homogeneous=True, hierarchy=hier)
+    ga = O.adjoint_coefficient_grad(_ogrid(shape), phi, lam, 0.0, 1.0)
+    ef, ea = _rel(_np(f.grad), lam), _rel(_np(a.grad), ga)
+    print(f"adjoint vs CPU at 64^3: dL/df {ef:.2e}, dL/da {ea:.2e}")
+    assert ef < 1e-7 and ea < 1e-6
