@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""Benchmark of the GMG-preconditioned FGMRES Poisson-type solve on GB300.
+
+One step = one pass of the whole solve path on one synthetic time step:
+coefficient set-up (8-child coarsening, Chebyshev eigen bounds per level,
+coarsest Cholesky), the FGMRES solve from a zero guess to a true relative
+residual of 1e-8 with the FP32 V-cycle preconditioner, and E = -grad(phi) in
+FP32.  Default workload: the two-channel streamer problem at 512^3
+(134,217,728 cells, kappa = 1e4).  Inputs are larger than L2 (1.07 GB per FP64
+field), so no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+# The CPU oracle is timed single-threaded; set before numpy is imported.
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+DEFAULT_WORKLOAD = "twochannel512"
+SAMPLE_N = 64          # CPU-oracle sample grid (same workload shape, 262,144 cells)
+L2_BYTES = 129 * 2**20
+
+# DRAM bytes per launch from one ncu capture, keyed by kernel class, with the
+# sha1 of the source file the kernel was built from at capture time.  A
+# mismatch (the kernel changed since) reports traffic as null.
+NCU_TRAFFIC = {}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--n", type=int, default=None, help="cells per side (default: the workload's size)")
+    ap.add_argument("--kappa", type=float, default=None)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 V-cycle comparison arm")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas: each rank solves its own copy)
+# ---------------------------------------------------------------------------
+
+
+class Dist:
+    def __init__(self):
+        import torch
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as td
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if torch.cuda.is_available():
+                torch.cuda.set_device(self.local)
+            td.init_process_group(backend)
+            self.pg = td
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        dev = torch.device("cuda", self.local) if torch.cuda.is_available() else torch.device("cpu")
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+_CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={_CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "power_w_max": max(power),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def source_sha(path):
+    import hashlib
+    with open(os.path.join(ROOT, path), "rb") as fh:
+        return hashlib.sha1(fh.read()).hexdigest()
+
+
+def make_workload(args):
+    from streamer_inputs import WORKLOADS, make_inputs
+    n = args.n if args.n is not None else WORKLOADS[args.workload][1]
+    inp = make_inputs(args.workload, n=n, kappa=args.kappa)
+    return inp, n
+
+
+def cpu_baseline(args, steps=1):
+    """The FP64 CPU oracle, as it stands, on a bounded sample: the same
+    workload at SAMPLE_N^3 cells, one step = set-up + solve + E."""
+    from oracle import gmg_oracle as O
+    from streamer_inputs import make_inputs
+    inp = make_inputs(args.workload, n=SAMPLE_N, kappa=args.kappa)
+    params = O.OracleParams()
+    grid = O.Grid(SAMPLE_N, SAMPLE_N, SAMPLE_N)
+    times, iters = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        phi, info, _ = O.solve(params, inp["a"], inp["f"])
+        O.field_from_potential(grid, phi, params.phi_bottom, params.phi_top)
+        times.append(time.perf_counter() - t0)
+        iters.append(info.iterations)
+    cells = SAMPLE_N**3
+    sec = statistics.median(times)
+    return {"value": cells / sec / 1e6, "unit": "Mcells/s", "cores": 1, "kind": "oracle",
+            "sample": f"{args.workload} shape at {SAMPLE_N}^3 ({cells} cells), set-up + solve to 1e-8 + E, "
+                      f"median of {steps} step(s) of {sec:.2f} s, {iters[-1]} FGMRES iterations, numpy single thread"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+
+def run_ours(args, dist):
+    import torch
+
+    from paper_1812_08606_gb300 import build as gbuild
+    from paper_1812_08606_gb300 import gmg
+
+    if dist.rank == 0 or not os.path.exists(gbuild.LIB_PATH):
+        gbuild.build()
+    dist.barrier()
+    gmg.load()
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    inp, n = make_workload(args)
+    N = n**3
+    a = torch.from_numpy(inp["a"]).to(dev)
+    f = torch.from_numpy(inp["f"]).to(dev)
+    phi = torch.zeros_like(f)
+    ex, ey, ez = (torch.empty((n, n, n), dtype=torch.float32, device=dev) for _ in range(3))
+    stream = torch.cuda.current_stream()
+    params = gmg.gmg_default_params(n, n, n, precision=gmg.GMG_PREC_MIXED)
+    ctx = gmg.gmg_setup(params, a, stream)
+
+    infos = []
+
+    def step(c):
+        gmg.gmg_update_coefficient(c, a)
+        phi.zero_()
+        info = gmg.fgmres_solve(c, f, phi)
+        gmg.field_from_potential(c, phi, ex, ey, ez)
+        infos.append(info)
+        return info
+
+    for _ in range(args.warmup):
+        step(ctx)
+    torch.cuda.synchronize()
+    infos.clear()
+    gmg.gmg_profile_reset(ctx)
+    gmg.gmg_profile_enable(ctx, True)
+    clocks = ClockSampler(dist.local)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms_total = dist.max(e0.elapsed_time(e1))
+    prof = gmg.profile(ctx)
+    gmg.gmg_profile_enable(ctx, False)
+    ms_step = ms_total / args.steps
+    value = dist.world * N * args.steps / (ms_total / 1e3) / 1e6
+    last = infos[-1]
+
+    # roofline of the dominant kernel (largest share of event time)
+    peak, peak_kind = measured_peaks()
+    top = prof[0]
+    per_launch_bytes = top["bytes"] / max(top["timed"], 1)
+    avg_ms = top["ms"] / max(top["timed"], 1)
+    achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
+    tr = NCU_TRAFFIC.get(top["name"])
+    traffic = None
+    if tr and tr.get("sha") == source_sha(tr["source"]):
+        traffic = tr["bytes_per_launch"]
+    total_prof_ms = sum(r["ms"] for r in prof)
+    kernels = [{"name": r["name"], "launches": r["launches"], "ms": round(r["ms"], 3),
+                "share": round(r["ms"] / total_prof_ms, 4) if total_prof_ms else None,
+                "GB/s": round(r["bytes"] / (r["ms"] / 1e3) / 1e9, 1) if r["ms"] > 0 else None}
+               for r in prof[:12]]
+    gpu_launches = sum(r["launches"] for r in prof)
+
+    out = {
+        "metric": "Mcells/s per solve step (set-up + GMG-FGMRES to 1e-8 true residual + E field)",
+        "value": round(value, 2),
+        "unit": "Mcells/s",
+        "n_gpus": dist.world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 V-cycle + f64 Krylov",
+        "data": "synthetic (seeded streamer-shaped a and f)",
+        "config": {"workload": f"{args.workload} {n}^3", "cells": N, "kappa": inp["kappa"],
+                   "precision": "mixed: FP32 V-cycle inside FP64 FGMRES", "restart": params.restart,
+                   "rtol": params.rtol, "cheb_steps": params.cheb_steps, "levels": gmg.gmg_num_levels(ctx),
+                   "l2": "inputs larger than L2 (1 FP64 field = %.2f GB > 129 MB)" % (8 * N / 1e9) if 8 * N > L2_BYTES
+                   else "inputs smaller than L2", "parallelism": "replicas" if dist.world > 1 else "single GPU"},
+        "iterations": last.iterations,
+        "true_rel_residual": last.true_rel_residual,
+        "setup_ms": round(statistics.mean(i.setup_ms for i in infos), 3),
+        "solve_ms": round(statistics.mean(i.solve_ms for i in infos), 3),
+        "res_history": [float("%.3e" % h) for h in last.history],
+        "roofline": {"bound": "hbm", "kernel": top["name"], "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": round(avg_ms, 5),
+                     "peak_source": f"{peak_kind} HBM copy bandwidth"},
+        "kernels": kernels,
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+    }
+
+    # FP64 V-cycle on the same workload (the comparison the metric names)
+    if not args.no_fp64:
+        out["fp64"] = fp64_arm(args, gmg, a, f, phi, ex, ey, ez, N, n, stream)
+
+    # end to end through the host-buffer C ABI call
+    if not args.no_e2e:
+        out["e2e"] = e2e_arm(args, gmg, ctx, inp, n, N, stream, dist)
+
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(args)
+    ctx.close()
+    return out
+
+
+def fp64_arm(args, gmg, a, f, phi, ex, ey, ez, N, n, stream):
+    import torch
+    p = gmg.gmg_default_params(n, n, n, precision=gmg.GMG_PREC_FP64)
+    ctx = gmg.gmg_setup(p, a, stream)
+    infos = []
+    for i in range(args.fp64_steps + 1):
+        if i == 1:
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.clear()
+        gmg.gmg_update_coefficient(ctx, a)
+        phi.zero_()
+        infos.append(gmg.fgmres_solve(ctx, f, phi))
+        gmg.field_from_potential(ctx, phi, ex, ey, ez)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.fp64_steps
+    ctx.close()
+    last = infos[-1]
+    return {"ms_per_step": round(ms, 3), "value": round(N / (ms / 1e3) / 1e6, 2), "unit": "Mcells/s",
+            "solve_ms": round(statistics.mean(i.solve_ms for i in infos), 3), "iterations": last.iterations,
+            "true_rel_residual": last.true_rel_residual, "steps": args.fp64_steps}
+
+
+def e2e_arm(args, gmg, ctx, inp, n, N, stream, dist):
+    import torch
+    a_h = torch.from_numpy(inp["a"]).pin_memory()
+    f_h = torch.from_numpy(inp["f"]).pin_memory()
+    phi_h = torch.empty((n, n, n), dtype=torch.float64).pin_memory()
+    e_h = [torch.empty((n, n, n), dtype=torch.float32).pin_memory() for _ in range(3)]
+    gmg.gmg_solve_host(ctx, a_h, f_h, phi_h, None, *e_h)        # warm-up (allocates staging)
+    steps = max(1, min(args.steps, 5))
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        gmg.gmg_solve_host(ctx, a_h, f_h, phi_h, None, *e_h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = dist.max(e0.elapsed_time(e1))
+    return {"value": round(dist.world * N * steps / (ms / 1e3) / 1e6, 2), "unit": "Mcells/s",
+            "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 8 * N + 12 * N, "steps": steps,
+            "api": "gmg_solve_host (pinned host a, f -> phi, E fp32)"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return None
+    from oracle import gmg_oracle as O
+    from streamer_inputs import make_inputs
+    inp = make_inputs(args.workload, n=SAMPLE_N, kappa=args.kappa)
+    params = O.OracleParams()
+    grid = O.Grid(SAMPLE_N, SAMPLE_N, SAMPLE_N)
+
+    def step():
+        phi, info, _ = O.solve(params, inp["a"], inp["f"])
+        O.field_from_potential(grid, phi, params.phi_bottom, params.phi_top)
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        info = step()
+    sec = time.perf_counter() - t0
+    cells = SAMPLE_N**3
+    value = cells * args.steps / sec / 1e6
+    return {
+        "impl": "reference",
+        "metric": "Mcells/s per solve step (set-up + GMG-FGMRES to 1e-8 true residual + E field)",
+        "value": round(value, 4), "unit": "Mcells/s", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded streamer-shaped a and f)",
+        "config": {"workload": f"{args.workload} sample at {SAMPLE_N}^3", "cells": cells},
+        "iterations": info.iterations,
+        "cpu_baseline": {"value": round(value, 4), "unit": "Mcells/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.workload} shape at {SAMPLE_N}^3, FP64 numpy oracle, single thread"},
+        "e2e": {"value": round(value, 4), "unit": "Mcells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    dist = Dist()
+    try:
+        out = run_reference(args, dist) if args.impl == "reference" else run_ours(args, dist)
+        if dist.rank == 0 and out is not None:
+            print(json.dumps(out), flush=True)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

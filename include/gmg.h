@@ -166,14 +166,15 @@ gmg_status adjoint_coefficient_grad(gmg_ctx* ctx, const double* phi_dev, const d
                                     double* dlda_dev);
 
 /* End-to-end step with HOST buffers: copy a_host (may be NULL to keep the
- * current coefficient; else the set-up is renewed), f_host and the initial
- * guess phi_host to the device, solve, optionally form E, and copy phi (and
- * E) back into the host buffers.  ex/ey/ez_host may be NULL (no field);
- * they hold floats if field_fp32 != 0, else doubles.  Host buffers should be
- * pinned for full copy bandwidth.  Staging buffers are allocated on first
- * use and kept by the context. */
-gmg_status gmg_solve_host(gmg_ctx* ctx, const double* a_host, const double* f_host, double* phi_host,
-                          void* ex_host, void* ey_host, void* ez_host, int field_fp32,
+ * current coefficient; else the set-up is renewed) and f_host to the device,
+ * take the initial guess from phi0_host (NULL: zero, a cold start), solve,
+ * optionally form E, and copy phi (and E) back into phi_host (and
+ * ex/ey/ez_host).  ex/ey/ez_host may all be NULL (no field); they hold
+ * floats if field_fp32 != 0, else doubles.  Host buffers should be pinned for
+ * full copy bandwidth.  Device staging buffers are allocated on first use and
+ * kept by the context.  Returns like fgmres_solve. */
+gmg_status gmg_solve_host(gmg_ctx* ctx, const double* a_host, const double* f_host, const double* phi0_host,
+                          double* phi_host, void* ex_host, void* ey_host, void* ez_host, int field_fp32,
                           gmg_solve_info* info);
 
 gmg_status gmg_set_stream(gmg_ctx* ctx, void* stream);
@@ -227,6 +228,21 @@ gmg_status gmg_coarse_solve(gmg_ctx* ctx, const void* b_dev, void* x_dev);
  * Returns GMG_ERR_ARG for m out of range, GMG_ERR_BREAKDOWN if QR fails to
  * converge. */
 gmg_status gmg_hessenberg_max_real_eig(const double* h_host, int m, double* out);
+
+/* ---- Per-kernel profile (tracing) ----
+ * Launch counts are always kept.  With profiling enabled, every kernel launch
+ * is bracketed by CUDA events on the context's stream, and each launch's
+ * algorithmic bytes (every array the kernel must touch, read or written
+ * once) are accumulated per kernel class.  Timing adds two event records per
+ * launch and no synchronisation beyond the solver's own. */
+gmg_status gmg_profile_enable(gmg_ctx* ctx, int on);
+gmg_status gmg_profile_reset(gmg_ctx* ctx);
+int gmg_profile_num_kernels(void);
+/* Totals of kernel class k (0 <= k < gmg_profile_num_kernels()): its name
+ * (static string), launches, launches timed, summed event time in ms and
+ * summed algorithmic bytes of the timed launches.  Synchronises the stream. */
+gmg_status gmg_profile_get(gmg_ctx* ctx, int k, const char** name, long long* launches,
+                           long long* timed_launches, double* total_ms, double* total_bytes);
 
 /* Test hook: make the n-th next device allocation of the library fail
  * (n >= 1), as if the device were out of memory; n = 0 disables it.  Lets

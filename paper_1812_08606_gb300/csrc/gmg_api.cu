@@ -173,6 +173,27 @@ int hessenberg_eigs(std::vector<double>& H, int n, std::vector<double>& wr, std:
 // Context
 // ---------------------------------------------------------------------------
 
+// Kernel classes of the per-kernel profile (launch counts, CUDA-event time and
+// algorithmic bytes: each array a kernel must touch, read or written once).
+enum KernelClass : int {
+  K_APPLY_F64, K_APPLY_OUTER, K_APPLY_F32, K_RESIDUAL_F64, K_RESIDUAL_F32, K_SGS_F64, K_SGS_F32,
+  K_CHEB_F64, K_CHEB_F32, K_RESTRICT_F64, K_RESTRICT_F32, K_PROLONG_F64, K_PROLONG_F32, K_COARSE_F64,
+  K_COARSE_F32, K_DOT, K_FINALIZE, K_AXPY, K_SCALE, K_UPDATE_X, K_CAST, K_COPY, K_RHS, K_FIELD, K_ADJOINT,
+  K_COARSEN, K_COEF_CHECK, K_HASH, K_COARSE_ASSEMBLE, K_COARSE_FACTOR, NK
+};
+static const char* const kKernelNames[NK] = {
+    "apply_f64", "apply_outer_f64a_f32x", "apply_f32", "residual_f64", "residual_f32", "sgs_half_f64",
+    "sgs_half_f32", "cheb_update_f64", "cheb_update_f32", "residual_restrict_f64", "residual_restrict_f32",
+    "prolong_add_f64", "prolong_add_f32", "coarse_apply_f64", "coarse_apply_f32", "multi_dot", "finalize",
+    "multi_axpy", "scale", "update_solution", "cast", "copy", "rhs", "field", "adjoint_grad", "coarsen_coef",
+    "coef_check", "hash_vector", "coarse_assemble", "coarse_factor"};
+
+struct ProfPending {
+  int cls;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
 struct LevelData {
   int nx = 0, ny = 0, nz = 0;
   size_t n = 0;
@@ -206,6 +227,14 @@ struct gmg_ctx {
   void *st_ex = nullptr, *st_ey = nullptr, *st_ez = nullptr;
   int st_fp32 = -1;  // element type of the field staging buffers (-1: none yet)
   float setup_ms = 0.f;
+  // per-kernel profile
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<ProfPending> pend;
+  double k_ms[NK] = {};
+  double k_bytes[NK] = {};
+  long long k_launch[NK] = {};
+  long long k_timed[NK] = {};
   std::vector<void*> dev_allocs;
   std::vector<void*> host_allocs;
 
@@ -234,6 +263,169 @@ gmg_status dalloc(gmg_ctx* c, P** p, size_t count, size_t elem = sizeof(P)) {
   *p = (P*)v;
   return st;
 }
+
+// ---- per-kernel profile ----
+cudaEvent_t prof_event(gmg_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Fold finished launches into the totals; the stream must be synchronised.
+void prof_collect(gmg_ctx* c) {
+  for (const ProfPending& q : c->pend) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+      c->k_ms[q.cls] += ms;
+      c->k_bytes[q.cls] += q.bytes;
+      c->k_timed[q.cls] += 1;
+    }
+    c->ev_pool.push_back(q.a);
+    c->ev_pool.push_back(q.b);
+  }
+  c->pend.clear();
+}
+
+template <typename F>
+gmg_status run_kernel(gmg_ctx* c, int cls, double bytes, F&& launch) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->prof_on && (e0 = prof_event(c)) != nullptr) cudaEventRecord(e0, c->s);
+  const cudaError_t e = launch();
+  c->k_launch[cls] += 1;
+  if (e != cudaSuccess) {
+    if (e0) c->ev_pool.push_back(e0);
+    return map_err(e);
+  }
+  if (e0) {
+    if ((e1 = prof_event(c)) != nullptr && cudaEventRecord(e1, c->s) == cudaSuccess)
+      c->pend.push_back({cls, e0, e1, bytes});
+    else
+      c->ev_pool.push_back(e0);
+  }
+  return GMG_OK;
+}
+
+template <typename T>
+constexpr bool is_f32() { return sizeof(T) == 4; }
+
+#define GMG_RUN(cls, bytes, ...) return run_kernel(c, (cls), (double)(bytes), [&]() { return __VA_ARGS__; })
+
+template <typename TA, typename TX, typename TY>
+gmg_status prof_apply(gmg_ctx* c, const Grid3& g, const TA* a, const TX* x, TY* y, cudaStream_t s) {
+  const int cls = is_f32<TA>() ? K_APPLY_F32 : (is_f32<TX>() ? K_APPLY_OUTER : K_APPLY_F64);
+  GMG_RUN(cls, g.n() * (sizeof(TA) + sizeof(TX) + sizeof(TY)), launch_apply<TA, TX, TY>(g, a, x, y, s));
+}
+template <typename T>
+gmg_status prof_residual(gmg_ctx* c, const Grid3& g, const T* a, const T* b, const T* x, T* r, T* z, int pc,
+                         cudaStream_t s) {
+  const double n = (double)g.n(), e = sizeof(T);
+  const double zw = pc == PC_SGS ? 0.5 * n : (pc == PC_NONE ? 0.0 : n);
+  const double bytes = n * e * (2 + (x ? 1 : 0) + (r ? 1 : 0)) + zw * e;
+  GMG_RUN(is_f32<T>() ? K_RESIDUAL_F32 : K_RESIDUAL_F64, bytes, launch_residual<T>(g, a, b, x, r, z, pc, s));
+}
+template <typename T>
+gmg_status prof_sgs_half(gmg_ctx* c, const Grid3& g, const T* a, const T* r, T* z, int color, T* d, T* x,
+                         double c1, double c2, int flags, cudaStream_t s) {
+  const double n = (double)g.n(), e = sizeof(T), h = 0.5 * n;
+  double bytes = n * e + h * e * 3;
+  if (flags & CHEB_UPDATE) bytes += h * e * (((flags & CHEB_FIRST) ? 1 : 2) + ((flags & CHEB_XZERO) ? 1 : 2));
+  GMG_RUN(is_f32<T>() ? K_SGS_F32 : K_SGS_F64, bytes, launch_sgs_half<T>(g, a, r, z, color, d, x, c1, c2, flags, s));
+}
+template <typename T>
+gmg_status prof_cheb_update(gmg_ctx* c, size_t n, const T* z, T* d, T* x, double c1, double c2, int flags,
+                            cudaStream_t s) {
+  const double bytes = (double)n * sizeof(T) * (1 + ((flags & CHEB_FIRST) ? 1 : 2) + ((flags & CHEB_XZERO) ? 1 : 2));
+  GMG_RUN(is_f32<T>() ? K_CHEB_F32 : K_CHEB_F64, bytes, launch_cheb_update<T>(n, z, d, x, c1, c2, flags, s));
+}
+template <typename T>
+gmg_status prof_residual_restrict(gmg_ctx* c, const Grid3& g, const T* a, const T* b, const T* x, T* coarse,
+                                  cudaStream_t s) {
+  GMG_RUN(is_f32<T>() ? K_RESTRICT_F32 : K_RESTRICT_F64, (double)g.n() * sizeof(T) * (3.0 + 0.125),
+          launch_residual_restrict<T>(g, a, b, x, coarse, s));
+}
+template <typename T>
+gmg_status prof_prolong_add(gmg_ctx* c, const Grid3& g, const T* e, T* x, int mode, cudaStream_t s) {
+  GMG_RUN(is_f32<T>() ? K_PROLONG_F32 : K_PROLONG_F64, (double)g.n() * sizeof(T) * (2.0 + 0.125),
+          launch_prolong_add<T>(g, e, x, mode, s));
+}
+template <typename T>
+gmg_status prof_coarse_apply(gmg_ctx* c, int n, const T* Ainv, const T* b, T* x, cudaStream_t s) {
+  GMG_RUN(is_f32<T>() ? K_COARSE_F32 : K_COARSE_F64, ((double)n * n + 2.0 * n) * sizeof(T),
+          launch_coarse_apply<T>(n, Ainv, b, x, s));
+}
+gmg_status prof_multi_dot(gmg_ctx* c, size_t n, const double* w, const double* V, size_t ldv, int k, double* partial,
+                          cudaStream_t s) {
+  const double bytes = (V == w && ldv == 0) ? 8.0 * n : 8.0 * n * (1 + k);
+  GMG_RUN(K_DOT, bytes, launch_multi_dot(n, w, V, ldv, k, partial, s));
+}
+gmg_status prof_finalize(gmg_ctx* c, const double* partial, int nblocks, int k, double* out, int acc, cudaStream_t s) {
+  GMG_RUN(K_FINALIZE, 8.0 * nblocks * k, launch_finalize(partial, nblocks, k, out, acc, s));
+}
+gmg_status prof_finalize_norm(gmg_ctx* c, const double* partial, int nblocks, double* out, cudaStream_t s) {
+  GMG_RUN(K_FINALIZE, 8.0 * nblocks, launch_finalize_norm(partial, nblocks, out, s));
+}
+gmg_status prof_finalize_check(gmg_ctx* c, const double* partial, int nblocks, double* out, cudaStream_t s) {
+  GMG_RUN(K_FINALIZE, 16.0 * nblocks, launch_finalize_check(partial, nblocks, out, s));
+}
+gmg_status prof_multi_axpy(gmg_ctx* c, size_t n, double* w, const double* V, size_t ldv, int k, const double* h,
+                           cudaStream_t s) {
+  GMG_RUN(K_AXPY, 8.0 * n * (k + 2), launch_multi_axpy(n, w, V, ldv, k, h, s));
+}
+gmg_status prof_scale(gmg_ctx* c, size_t n, const double* src, double* dst, const double* sc, cudaStream_t s) {
+  GMG_RUN(K_SCALE, 16.0 * n, launch_scale(n, src, dst, sc, s));
+}
+gmg_status prof_scale_value(gmg_ctx* c, size_t n, const double* src, double* dst, double alpha, cudaStream_t s) {
+  GMG_RUN(K_SCALE, 16.0 * n, launch_scale_value(n, src, dst, alpha, s));
+}
+template <typename TZ>
+gmg_status prof_update_solution(gmg_ctx* c, size_t n, double* x, const TZ* Z, size_t ldz, int k, const double* y,
+                                cudaStream_t s) {
+  GMG_RUN(K_UPDATE_X, (double)n * (16.0 + k * sizeof(TZ)), launch_update_solution<TZ>(n, x, Z, ldz, k, y, s));
+}
+gmg_status prof_cast_d2f(gmg_ctx* c, size_t n, const double* src, float* dst, cudaStream_t s) {
+  GMG_RUN(K_CAST, 12.0 * n, launch_cast_d2f(n, src, dst, s));
+}
+gmg_status prof_cast_f2d(gmg_ctx* c, size_t n, const float* src, double* dst, cudaStream_t s) {
+  GMG_RUN(K_CAST, 12.0 * n, launch_cast_f2d(n, src, dst, s));
+}
+gmg_status prof_copy_d(gmg_ctx* c, size_t n, const double* src, double* dst, cudaStream_t s) {
+  GMG_RUN(K_COPY, 16.0 * n, launch_copy_d(n, src, dst, s));
+}
+gmg_status prof_rhs(gmg_ctx* c, const Grid3& g, const double* a, const double* f, double* b, double gb, double gt,
+                    int homogeneous, cudaStream_t s) {
+  GMG_RUN(K_RHS, 16.0 * g.n() + 16.0 * g.plane(), launch_rhs(g, a, f, b, gb, gt, homogeneous, s));
+}
+gmg_status prof_field(gmg_ctx* c, const Grid3& g, double hx, double hy, double hz, const double* phi, void* ex,
+                      void* ey, void* ez, int fp32, double gb, double gt, cudaStream_t s) {
+  GMG_RUN(K_FIELD, (double)g.n() * (8.0 + 3.0 * (fp32 ? 4 : 8)),
+          launch_field(g, hx, hy, hz, phi, ex, ey, ez, fp32, gb, gt, s));
+}
+gmg_status prof_adjoint_grad(gmg_ctx* c, const Grid3& g, const double* phi, const double* lam, double* out,
+                             double gb, double gt, cudaStream_t s) {
+  GMG_RUN(K_ADJOINT, 24.0 * g.n(), launch_adjoint_grad(g, phi, lam, out, gb, gt, s));
+}
+gmg_status prof_hash_vector(gmg_ctx* c, size_t n, double* u, cudaStream_t s) {
+  GMG_RUN(K_HASH, 8.0 * n, launch_hash_vector(n, u, s));
+}
+gmg_status prof_coef_check(gmg_ctx* c, size_t n, const double* a, double* partial, cudaStream_t s) {
+  GMG_RUN(K_COEF_CHECK, 8.0 * n, launch_coef_check(n, a, partial, s));
+}
+gmg_status prof_coarsen_coef(gmg_ctx* c, const Grid3& g, const double* a, double* ac, float* ac32, cudaStream_t s) {
+  GMG_RUN(K_COARSEN, 8.0 * g.n() + g.n() / 8.0 * (8.0 + (ac32 ? 4.0 : 0.0)), launch_coarsen_coef(g, a, ac, ac32, s));
+}
+gmg_status prof_coarse_assemble(gmg_ctx* c, const Grid3& g, const double* a, double* A, cudaStream_t s) {
+  GMG_RUN(K_COARSE_ASSEMBLE, 8.0 * g.n() * g.n(), launch_coarse_assemble(g, a, A, s));
+}
+gmg_status prof_coarse_factor(gmg_ctx* c, int n, double* A, double* work, double* Ainv, float* Ainv32, int* st,
+                              cudaStream_t s) {
+  GMG_RUN(K_COARSE_FACTOR, 36.0 * n * n, launch_coarse_factor(n, A, work, Ainv, Ainv32, st, s));
+}
+#undef GMG_RUN
 
 gmg_status validate(const gmg_params* p, int* nlevels) {
   if (!p) return GMG_ERR_ARG;
@@ -269,13 +461,14 @@ gmg_status validate(const gmg_params* p, int* nlevels) {
 gmg_status read_scalars(gmg_ctx* c, int slot, int count) {
   CK(cudaMemcpyAsync(c->hpin + slot, c->dscal + slot, sizeof(double) * count, cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
+  prof_collect(c);
   return GMG_OK;
 }
 
 // Device: out slots [slot, slot+2) = (||w||, 1/||w||).
 gmg_status norm_dev(gmg_ctx* c, size_t n, const double* w, int slot) {
-  CK(launch_multi_dot(n, w, w, 0, 1, c->partial, c->s));
-  CK(launch_finalize_norm(c->partial, reduce_blocks(n), c->dscal + slot, c->s));
+  CKS(prof_multi_dot(c, n, w, w, 0, 1, c->partial, c->s));
+  CKS(prof_finalize_norm(c, c->partial, reduce_blocks(n), c->dscal + slot, c->s));
   return GMG_OK;
 }
 
@@ -286,19 +479,19 @@ gmg_status orthogonalize(gmg_ctx* c, size_t n, const double* V, size_t ld, int k
   const int nb = reduce_blocks(n);
   if (c->p.orthogonalization == GMG_ORTH_MGS) {
     for (int i = 0; i < k; ++i) {
-      CK(launch_multi_dot(n, w, V + (size_t)i * ld, ld, 1, c->partial, c->s));
-      CK(launch_finalize(c->partial, nb, 1, c->dscal + SL_H1 + i, 0, c->s));
-      CK(launch_multi_axpy(n, w, V + (size_t)i * ld, ld, 1, c->dscal + SL_H1 + i, c->s));
+      CKS(prof_multi_dot(c, n, w, V + (size_t)i * ld, ld, 1, c->partial, c->s));
+      CKS(prof_finalize(c, c->partial, nb, 1, c->dscal + SL_H1 + i, 0, c->s));
+      CKS(prof_multi_axpy(c, n, w, V + (size_t)i * ld, ld, 1, c->dscal + SL_H1 + i, c->s));
     }
   } else {
     for (int pass = 0; pass < 2; ++pass) {
       double* hslot = c->dscal + (pass == 0 ? SL_H1 : SL_H2);
       for (int c0 = 0; c0 < k; c0 += 8) {
         const int kc = std::min(8, k - c0);
-        CK(launch_multi_dot(n, w, V + (size_t)c0 * ld, ld, kc, c->partial, c->s));
-        CK(launch_finalize(c->partial, nb, kc, hslot + c0, 0, c->s));
+        CKS(prof_multi_dot(c, n, w, V + (size_t)c0 * ld, ld, kc, c->partial, c->s));
+        CKS(prof_finalize(c, c->partial, nb, kc, hslot + c0, 0, c->s));
       }
-      CK(launch_multi_axpy(n, w, V, ld, k, hslot, c->s));
+      CKS(prof_multi_axpy(c, n, w, V, ld, k, hslot, c->s));
     }
   }
   return norm_dev(c, n, w, SL_NORM);
@@ -322,11 +515,11 @@ gmg_status read_column(gmg_ctx* c, int k, double* h) {
 // z = B^{-1} r on a level in FP64 (used by the eigen estimate), r FP64 buffer.
 gmg_status smoother_pc_fp64(gmg_ctx* c, const LevelData& L, const double* r, double* z) {
   const int pc = c->p.smoother_pc;
-  if (pc == GMG_PC_IDENTITY) return map_err(launch_copy_d(L.n, r, z, c->s));
-  CK(launch_residual<double>(L.g, L.a64, r, nullptr, nullptr, z, pc == GMG_PC_SGS ? PC_SGS : PC_JACOBI, c->s));
+  if (pc == GMG_PC_IDENTITY) return (prof_copy_d(c, L.n, r, z, c->s));
+  CKS(prof_residual<double>(c, L.g, L.a64, r, nullptr, nullptr, z, pc == GMG_PC_SGS ? PC_SGS : PC_JACOBI, c->s));
   if (pc == GMG_PC_SGS) {
-    CK(launch_sgs_half<double>(L.g, L.a64, r, z, 1, nullptr, nullptr, 0, 0, 0, c->s));
-    CK(launch_sgs_half<double>(L.g, L.a64, r, z, 0, nullptr, nullptr, 0, 0, 0, c->s));
+    CKS(prof_sgs_half<double>(c, L.g, L.a64, r, z, 1, nullptr, nullptr, 0, 0, 0, c->s));
+    CKS(prof_sgs_half<double>(c, L.g, L.a64, r, z, 0, nullptr, nullptr, 0, 0, 0, c->s));
   }
   return GMG_OK;
 }
@@ -337,14 +530,14 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
   const size_t n = L.n;
   const int steps = c->p.eig_steps;
   double* V = c->V;  // (steps+1) vectors of n, stride n
-  CK(launch_hash_vector(n, V, c->s));
+  CKS(prof_hash_vector(c, n, V, c->s));
   CKS(norm_dev(c, n, V, SL_NORM));
-  CK(launch_scale(n, V, V, c->dscal + SL_NORM + 1, c->s));
+  CKS(prof_scale(c, n, V, V, c->dscal + SL_NORM + 1, c->s));
   std::vector<double> H((size_t)(steps + 1) * steps, 0.0);
   int m = steps;
   std::vector<double> col(steps + 2);
   for (int j = 0; j < steps; ++j) {
-    CK(launch_apply<double, double, double>(L.g, L.a64, V + (size_t)j * n, c->bvec, c->s));
+    CKS(prof_apply<double, double, double>(c, L.g, L.a64, V + (size_t)j * n, c->bvec, c->s));
     CKS(smoother_pc_fp64(c, L, c->bvec, c->w));
     CKS(orthogonalize(c, n, V, n, j + 1, c->w));
     CKS(read_column(c, j + 1, col.data()));
@@ -356,7 +549,7 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
       m = j + 1;
       break;
     }
-    CK(launch_scale(n, c->w, V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));
+    CKS(prof_scale(c, n, c->w, V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));
   }
   std::vector<double> Hm((size_t)m * m);
   for (int r = 0; r < m; ++r)
@@ -376,20 +569,20 @@ gmg_status build(gmg_ctx* c, const double* a_dev) {
   const double t0 = now_ms();
   LevelData& F = c->lev.back();
   // coefficient must be finite and positive
-  CK(launch_coef_check(F.n, a_dev, c->partial, c->s));
-  CK(launch_finalize_check(c->partial, reduce_blocks(F.n), c->dscal + SL_CHECK, c->s));
+  CKS(prof_coef_check(c, F.n, a_dev, c->partial, c->s));
+  CKS(prof_finalize_check(c, c->partial, reduce_blocks(F.n), c->dscal + SL_CHECK, c->s));
   CKS(read_scalars(c, SL_CHECK, 2));
   if (c->hpin[SL_CHECK + 1] != 0.0) return GMG_ERR_ARG;
-  CK(launch_copy_d(F.n, a_dev, F.a64, c->s));
-  if (c->mixed) CK(launch_cast_d2f(F.n, F.a64, F.a32, c->s));
+  CKS(prof_copy_d(c, F.n, a_dev, F.a64, c->s));
+  if (c->mixed) CKS(prof_cast_d2f(c, F.n, F.a64, F.a32, c->s));
   for (int l = (int)c->lev.size() - 1; l >= 1; --l)
-    CK(launch_coarsen_coef(c->lev[l].g, c->lev[l].a64, c->lev[l - 1].a64, c->mixed ? c->lev[l - 1].a32 : nullptr,
+    CKS(prof_coarsen_coef(c, c->lev[l].g, c->lev[l].a64, c->lev[l - 1].a64, c->mixed ? c->lev[l - 1].a32 : nullptr,
                            c->s));
   for (int l = 1; l < (int)c->lev.size(); ++l) CKS(eig_bounds(c, l));
   // coarsest: dense Cholesky and explicit inverse
   const LevelData& C0 = c->lev[0];
-  CK(launch_coarse_assemble(C0.g, C0.a64, c->cA, c->s));
-  CK(launch_coarse_factor(c->nc, c->cA, c->cW, c->cinv64, c->cinv32, c->cstatus, c->s));
+  CKS(prof_coarse_assemble(c, C0.g, C0.a64, c->cA, c->s));
+  CKS(prof_coarse_factor(c, c->nc, c->cA, c->cW, c->cinv64, c->cinv32, c->cstatus, c->s));
   CK(cudaMemcpyAsync(c->hstat, c->cstatus, sizeof(int), cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
   if (c->hstat[0] != 0) return GMG_ERR_BREAKDOWN;
@@ -442,17 +635,17 @@ gmg_status smooth(gmg_ctx* c, int l, const T* b, T* x, bool x_is_zero) {
     }
     const T* rr;
     if (st == 0 && x_is_zero) {
-      CK(launch_residual<T>(L.g, a, b, nullptr, nullptr, z, pc, c->s));
+      CKS(prof_residual<T>(c, L.g, a, b, nullptr, nullptr, z, pc, c->s));
       rr = b;
     } else {
-      CK(launch_residual<T>(L.g, a, b, x, r, z, pc, c->s));
+      CKS(prof_residual<T>(c, L.g, a, b, x, r, z, pc, c->s));
       rr = r;
     }
     if (pc == GMG_PC_SGS) {
-      CK(launch_sgs_half<T>(L.g, a, rr, z, 1, d, x, c1, c2, flags, c->s));
-      CK(launch_sgs_half<T>(L.g, a, rr, z, 0, d, x, c1, c2, flags, c->s));
+      CKS(prof_sgs_half<T>(c, L.g, a, rr, z, 1, d, x, c1, c2, flags, c->s));
+      CKS(prof_sgs_half<T>(c, L.g, a, rr, z, 0, d, x, c1, c2, flags, c->s));
     } else {
-      CK(launch_cheb_update<T>(L.n, z, d, x, c1, c2, flags, c->s));
+      CKS(prof_cheb_update<T>(c, L.n, z, d, x, c1, c2, flags, c->s));
     }
   }
   return GMG_OK;
@@ -460,14 +653,14 @@ gmg_status smooth(gmg_ctx* c, int l, const T* b, T* x, bool x_is_zero) {
 
 template <typename T>
 gmg_status vcycle(gmg_ctx* c, int l, const T* b, T* x) {
-  if (l == 0) return map_err(launch_coarse_apply<T>(c->nc, coarse_inv<T>(c), b, x, c->s));
+  if (l == 0) return (prof_coarse_apply<T>(c, c->nc, coarse_inv<T>(c), b, x, c->s));
   const LevelData& L = c->lev[l];
   const LevelData& Lc = c->lev[l - 1];
   const T* a = level_a<T>(L);
   CKS(smooth<T>(c, l, b, x, true));
-  CK(launch_residual_restrict<T>(L.g, a, b, x, (T*)Lc.b, c->s));
+  CKS(prof_residual_restrict<T>(c, L.g, a, b, x, (T*)Lc.b, c->s));
   CKS(vcycle<T>(c, l - 1, (const T*)Lc.b, (T*)Lc.x));
-  CK(launch_prolong_add<T>(L.g, (const T*)Lc.x, x, c->p.prolongation, c->s));
+  CKS(prof_prolong_add<T>(c, L.g, (const T*)Lc.x, x, c->p.prolongation, c->s));
   CKS(smooth<T>(c, l, b, x, false));
   return GMG_OK;
 }
@@ -477,7 +670,7 @@ gmg_status precondition(gmg_ctx* c, const double* v, void* z) {
   const int top = (int)c->lev.size() - 1;
   if (c->mixed) {
     float* bf = (float*)c->lev[top].b;
-    CK(launch_cast_d2f(c->N(), v, bf, c->s));
+    CKS(prof_cast_d2f(c, c->N(), v, bf, c->s));
     return vcycle<float>(c, top, bf, (float*)z);
   }
   return vcycle<double>(c, top, v, (double*)z);
@@ -486,8 +679,8 @@ gmg_status precondition(gmg_ctx* c, const double* v, void* z) {
 // w = A z (FP64 operator on a level-precision vector of the finest size).
 gmg_status apply_outer(gmg_ctx* c, const void* z, double* w) {
   const LevelData& F = c->fine();
-  if (c->mixed) return map_err(launch_apply<double, float, double>(F.g, F.a64, (const float*)z, w, c->s));
-  return map_err(launch_apply<double, double, double>(F.g, F.a64, (const double*)z, w, c->s));
+  if (c->mixed) return (prof_apply<double, float, double>(c, F.g, F.a64, (const float*)z, w, c->s));
+  return (prof_apply<double, double, double>(c, F.g, F.a64, (const double*)z, w, c->s));
 }
 
 void* zvec(gmg_ctx* c, int j) { return (char*)c->Z + (size_t)j * c->N() * c->esz; }
@@ -502,7 +695,7 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
   loc.setup_ms = c->setup_ms;
   gmg_status result = GMG_OK;
 
-  CK(launch_rhs(F.g, F.a64, f, c->bvec, c->p.phi_bottom, c->p.phi_top, homogeneous, c->s));
+  CKS(prof_rhs(c, F.g, F.a64, f, c->bvec, c->p.phi_bottom, c->p.phi_top, homogeneous, c->s));
   CKS(norm_dev(c, n, c->bvec, SL_NORM));
   CKS(read_scalars(c, SL_NORM, 2));
   const double bnorm = c->hpin[SL_NORM];
@@ -521,7 +714,7 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
     std::vector<double> R((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), col(m + 2), y(m);
     for (;;) {
       // r0 = b - A x0, beta, v1 (Algorithm 1, line 3)
-      CK(launch_residual<double>(F.g, F.a64, c->bvec, x, c->V, nullptr, PC_NONE, c->s));
+      CKS(prof_residual<double>(c, F.g, F.a64, c->bvec, x, c->V, nullptr, PC_NONE, c->s));
       CKS(norm_dev(c, n, c->V, SL_NORM));
       CKS(read_scalars(c, SL_NORM, 2));
       const double beta = c->hpin[SL_NORM];
@@ -538,7 +731,7 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
         result = GMG_ERR_NOT_CONVERGED;
         break;
       }
-      CK(launch_scale_value(n, c->V, c->V, 1.0 / beta, c->s));
+      CKS(prof_scale_value(c, n, c->V, c->V, 1.0 / beta, c->s));
       std::fill(g.begin(), g.end(), 0.0);
       g[0] = beta;
       int k = 0;
@@ -579,7 +772,7 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
         const double est = fabs(g[j + 1]) / bnorm;
         if (loc.n_history < GMG_MAX_HISTORY) loc.res_history[loc.n_history++] = est;
         if (hnext == 0.0) break;  // lucky breakdown: the solution is in K_j
-        CK(launch_scale(n, c->w, c->V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));
+        CKS(prof_scale(c, n, c->w, c->V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));
         if (est < c->p.rtol || loc.iterations >= c->p.max_iters) break;  // line 12
       }
       if (fail) break;
@@ -592,14 +785,15 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
       for (int i = 0; i < k; ++i) c->hpin[SL_Y + i] = y[i];
       CK(cudaMemcpyAsync(c->dscal + SL_Y, c->hpin + SL_Y, sizeof(double) * k, cudaMemcpyHostToDevice, c->s));
       if (c->mixed)
-        CK(launch_update_solution<float>(n, x, (const float*)c->Z, n, k, c->dscal + SL_Y, c->s));
+        CKS(prof_update_solution<float>(c, n, x, (const float*)c->Z, n, k, c->dscal + SL_Y, c->s));
       else
-        CK(launch_update_solution<double>(n, x, (const double*)c->Z, n, k, c->dscal + SL_Y, c->s));
+        CKS(prof_update_solution<double>(c, n, x, (const double*)c->Z, n, k, c->dscal + SL_Y, c->s));
       loc.restarts++;  // line 16: restart from x_k (the true residual is checked at the loop top)
     }
   }
 done:
   CK(cudaStreamSynchronize(c->s));
+  prof_collect(c);
   loc.solve_ms = (float)(now_ms() - t0);
   if (info) *info = loc;
   return result;
@@ -657,6 +851,8 @@ const char* gmg_status_string(gmg_status s) {
 void gmg_destroy(gmg_ctx* c) {
   if (!c) return;
   if (c->s) cudaStreamSynchronize(c->s);
+  prof_collect(c);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->dev_allocs) cudaFree(p);
   for (void* p : c->host_allocs) cudaFreeHost(p);
   delete c;
@@ -748,20 +944,20 @@ gmg_status fgmres_solve(gmg_ctx* c, const double* f_dev, double* phi_dev, int ho
 gmg_status apply_operator(gmg_ctx* c, const double* x_dev, double* y_dev) {
   if (!c || !x_dev || !y_dev) return GMG_ERR_ARG;
   const LevelData& F = c->fine();
-  return map_err(launch_apply<double, double, double>(F.g, F.a64, x_dev, y_dev, c->s));
+  return (prof_apply<double, double, double>(c, F.g, F.a64, x_dev, y_dev, c->s));
 }
 
 gmg_status assemble_rhs(gmg_ctx* c, const double* f_dev, double* b_dev) {
   if (!c || !f_dev || !b_dev) return GMG_ERR_ARG;
   const LevelData& F = c->fine();
-  return map_err(launch_rhs(F.g, F.a64, f_dev, b_dev, c->p.phi_bottom, c->p.phi_top, 0, c->s));
+  return (prof_rhs(c, F.g, F.a64, f_dev, b_dev, c->p.phi_bottom, c->p.phi_top, 0, c->s));
 }
 
 gmg_status field_from_potential(gmg_ctx* c, const double* phi_dev, void* ex, void* ey, void* ez, int out_fp32) {
   if (!c || !phi_dev || !ex || !ey || !ez) return GMG_ERR_ARG;
   const LevelData& F = c->fine();
   const gmg_params& p = c->p;
-  return map_err(launch_field(F.g, p.lx / p.nx, p.ly / p.ny, p.lz / p.nz, phi_dev, ex, ey, ez, out_fp32,
+  return (prof_field(c, F.g, p.lx / p.nx, p.ly / p.ny, p.lz / p.nz, phi_dev, ex, ey, ez, out_fp32,
                               p.phi_bottom, p.phi_top, c->s));
 }
 
@@ -769,11 +965,12 @@ gmg_status adjoint_coefficient_grad(gmg_ctx* c, const double* phi_dev, const dou
                                     double* dlda_dev) {
   if (!c || !phi_dev || !lambda_dev || !dlda_dev) return GMG_ERR_ARG;
   const LevelData& F = c->fine();
-  return map_err(launch_adjoint_grad(F.g, phi_dev, lambda_dev, dlda_dev, c->p.phi_bottom, c->p.phi_top, c->s));
+  return (prof_adjoint_grad(c, F.g, phi_dev, lambda_dev, dlda_dev, c->p.phi_bottom, c->p.phi_top, c->s));
 }
 
-gmg_status gmg_solve_host(gmg_ctx* c, const double* a_host, const double* f_host, double* phi_host, void* ex_host,
-                          void* ey_host, void* ez_host, int field_fp32, gmg_solve_info* info) {
+gmg_status gmg_solve_host(gmg_ctx* c, const double* a_host, const double* f_host, const double* phi0_host,
+                          double* phi_host, void* ex_host, void* ey_host, void* ez_host, int field_fp32,
+                          gmg_solve_info* info) {
   if (!c || !f_host || !phi_host) return GMG_ERR_ARG;
   const bool want_e = ex_host && ey_host && ez_host;
   if ((ex_host || ey_host || ez_host) && !want_e) return GMG_ERR_ARG;
@@ -796,7 +993,10 @@ gmg_status gmg_solve_host(gmg_ctx* c, const double* a_host, const double* f_host
     CKS(build(c, c->st_a));
   }
   CK(cudaMemcpyAsync(c->st_f, f_host, bytes, cudaMemcpyHostToDevice, c->s));
-  CK(cudaMemcpyAsync(c->st_phi, phi_host, bytes, cudaMemcpyHostToDevice, c->s));
+  if (phi0_host)
+    CK(cudaMemcpyAsync(c->st_phi, phi0_host, bytes, cudaMemcpyHostToDevice, c->s));
+  else
+    CK(cudaMemsetAsync(c->st_phi, 0, bytes, c->s));
   gmg_status st = solve_impl(c, c->st_f, c->st_phi, 0, info);
   if (st != GMG_OK && st != GMG_ERR_NOT_CONVERGED) return st;
   if (want_e) CKS(field_from_potential(c, c->st_phi, c->st_ex, c->st_ey, c->st_ez, field_fp32));
@@ -834,21 +1034,21 @@ gmg_status gmg_level_info(const gmg_ctx* c, int level, int* nx, int* ny, int* nz
 gmg_status gmg_level_coefficient(gmg_ctx* c, int level, double* out_dev) {
   LevelData* L = level_ptr(c, level);
   if (!L || !out_dev) return GMG_ERR_ARG;
-  return map_err(launch_copy_d(L->n, L->a64, out_dev, c->s));
+  return (prof_copy_d(c, L->n, L->a64, out_dev, c->s));
 }
 
 gmg_status gmg_apply_preconditioner(gmg_ctx* c, const double* v_dev, double* z_dev) {
   if (!c || !v_dev || !z_dev) return GMG_ERR_ARG;
   CKS(precondition(c, v_dev, c->Z));
-  if (c->mixed) return map_err(launch_cast_f2d(c->N(), (const float*)c->Z, z_dev, c->s));
-  return map_err(launch_copy_d(c->N(), (const double*)c->Z, z_dev, c->s));
+  if (c->mixed) return (prof_cast_f2d(c, c->N(), (const float*)c->Z, z_dev, c->s));
+  return (prof_copy_d(c, c->N(), (const double*)c->Z, z_dev, c->s));
 }
 
 gmg_status gmg_level_apply(gmg_ctx* c, int level, const void* x, void* y) {
   LevelData* L = level_ptr(c, level);
   if (!L || !x || !y) return GMG_ERR_ARG;
-  if (c->mixed) return map_err(launch_apply<float, float, float>(L->g, L->a32, (const float*)x, (float*)y, c->s));
-  return map_err(launch_apply<double, double, double>(L->g, L->a64, (const double*)x, (double*)y, c->s));
+  if (c->mixed) return (prof_apply<float, float, float>(c, L->g, L->a32, (const float*)x, (float*)y, c->s));
+  return (prof_apply<double, double, double>(c, L->g, L->a64, (const double*)x, (double*)y, c->s));
 }
 
 gmg_status gmg_level_smooth(gmg_ctx* c, int level, const void* b, void* x, int x_is_zero) {
@@ -865,11 +1065,11 @@ gmg_status gmg_level_smoother_pc(gmg_ctx* c, int level, const void* r, void* z) 
   if (c->mixed) {
     const float* a = L->a32;
     if (pc == GMG_PC_IDENTITY) return map_err(cudaMemcpyAsync(z, r, L->n * 4, cudaMemcpyDeviceToDevice, c->s));
-    CK(launch_residual<float>(L->g, a, (const float*)r, nullptr, nullptr, (float*)z,
+    CKS(prof_residual<float>(c, L->g, a, (const float*)r, nullptr, nullptr, (float*)z,
                               pc == GMG_PC_SGS ? PC_SGS : PC_JACOBI, c->s));
     if (pc == GMG_PC_SGS) {
-      CK(launch_sgs_half<float>(L->g, a, (const float*)r, (float*)z, 1, nullptr, nullptr, 0, 0, 0, c->s));
-      CK(launch_sgs_half<float>(L->g, a, (const float*)r, (float*)z, 0, nullptr, nullptr, 0, 0, 0, c->s));
+      CKS(prof_sgs_half<float>(c, L->g, a, (const float*)r, (float*)z, 1, nullptr, nullptr, 0, 0, 0, c->s));
+      CKS(prof_sgs_half<float>(c, L->g, a, (const float*)r, (float*)z, 0, nullptr, nullptr, 0, 0, 0, c->s));
     }
     return GMG_OK;
   }
@@ -880,23 +1080,23 @@ gmg_status gmg_level_residual_restrict(gmg_ctx* c, int level, const void* b, con
   LevelData* L = level_ptr(c, level);
   if (!L || level == 0 || !b || !x || !coarse) return GMG_ERR_ARG;
   if (c->mixed)
-    return map_err(launch_residual_restrict<float>(L->g, L->a32, (const float*)b, (const float*)x, (float*)coarse,
+    return (prof_residual_restrict<float>(c, L->g, L->a32, (const float*)b, (const float*)x, (float*)coarse,
                                                    c->s));
-  return map_err(launch_residual_restrict<double>(L->g, L->a64, (const double*)b, (const double*)x,
+  return (prof_residual_restrict<double>(c, L->g, L->a64, (const double*)b, (const double*)x,
                                                   (double*)coarse, c->s));
 }
 
 gmg_status gmg_level_prolong_add(gmg_ctx* c, int level, const void* e, void* x) {
   LevelData* L = level_ptr(c, level);
   if (!L || level == 0 || !e || !x) return GMG_ERR_ARG;
-  if (c->mixed) return map_err(launch_prolong_add<float>(L->g, (const float*)e, (float*)x, c->p.prolongation, c->s));
-  return map_err(launch_prolong_add<double>(L->g, (const double*)e, (double*)x, c->p.prolongation, c->s));
+  if (c->mixed) return (prof_prolong_add<float>(c, L->g, (const float*)e, (float*)x, c->p.prolongation, c->s));
+  return (prof_prolong_add<double>(c, L->g, (const double*)e, (double*)x, c->p.prolongation, c->s));
 }
 
 gmg_status gmg_coarse_solve(gmg_ctx* c, const void* b, void* x) {
   if (!c || !b || !x) return GMG_ERR_ARG;
-  if (c->mixed) return map_err(launch_coarse_apply<float>(c->nc, c->cinv32, (const float*)b, (float*)x, c->s));
-  return map_err(launch_coarse_apply<double>(c->nc, c->cinv64, (const double*)b, (double*)x, c->s));
+  if (c->mixed) return (prof_coarse_apply<float>(c, c->nc, c->cinv32, (const float*)b, (float*)x, c->s));
+  return (prof_coarse_apply<double>(c, c->nc, c->cinv64, (const double*)b, (double*)x, c->s));
 }
 
 gmg_status gmg_hessenberg_max_real_eig(const double* h_host, int m, double* out) {
@@ -910,5 +1110,39 @@ gmg_status gmg_hessenberg_max_real_eig(const double* h_host, int m, double* out)
 }
 
 void gmg_test_fail_allocation_after(int n) { g_fail_alloc_countdown = n > 0 ? n : 0; }
+
+gmg_status gmg_profile_enable(gmg_ctx* c, int on) {
+  if (!c) return GMG_ERR_ARG;
+  CK(cudaStreamSynchronize(c->s));
+  prof_collect(c);
+  c->prof_on = on != 0;
+  return GMG_OK;
+}
+
+gmg_status gmg_profile_reset(gmg_ctx* c) {
+  if (!c) return GMG_ERR_ARG;
+  CK(cudaStreamSynchronize(c->s));
+  prof_collect(c);
+  for (int k = 0; k < NK; ++k) {
+    c->k_ms[k] = c->k_bytes[k] = 0.0;
+    c->k_launch[k] = c->k_timed[k] = 0;
+  }
+  return GMG_OK;
+}
+
+int gmg_profile_num_kernels(void) { return NK; }
+
+gmg_status gmg_profile_get(gmg_ctx* c, int k, const char** name, long long* launches, long long* timed_launches,
+                           double* total_ms, double* total_bytes) {
+  if (!c || k < 0 || k >= NK) return GMG_ERR_ARG;
+  CK(cudaStreamSynchronize(c->s));
+  prof_collect(c);
+  if (name) *name = kKernelNames[k];
+  if (launches) *launches = c->k_launch[k];
+  if (timed_launches) *timed_launches = c->k_timed[k];
+  if (total_ms) *total_ms = c->k_ms[k];
+  if (total_bytes) *total_bytes = c->k_bytes[k];
+  return GMG_OK;
+}
 
 }  // extern "C"

@@ -80,7 +80,8 @@ _SIGS = {
     "assemble_rhs": (ctypes.c_int, [_P, _P, _P]),
     "field_from_potential": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
     "adjoint_coefficient_grad": (ctypes.c_int, [_P, _P, _P, _P]),
-    "gmg_solve_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int, ctypes.POINTER(gmg_solve_info)]),
+    "gmg_solve_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int,
+                                      ctypes.POINTER(gmg_solve_info)]),
     "gmg_set_stream": (ctypes.c_int, [_P, _P]),
     "gmg_destroy": (None, [_P]),
     "gmg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -98,6 +99,12 @@ _SIGS = {
     "gmg_coarse_solve": (ctypes.c_int, [_P, _P, _P]),
     "gmg_hessenberg_max_real_eig": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gmg_test_fail_allocation_after": (None, [ctypes.c_int]),
+    "gmg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gmg_profile_reset": (ctypes.c_int, [_P]),
+    "gmg_profile_num_kernels": (ctypes.c_int, []),
+    "gmg_profile_get": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                       ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -249,17 +256,20 @@ def adjoint_coefficient_grad(ctx: Context, phi: torch.Tensor, lam: torch.Tensor,
                                            _dev(dlda, numel=ctx.n, name="dlda")), "adjoint_coefficient_grad")
 
 
-def gmg_solve_host(ctx: Context, a_host, f_host, phi_host, ex_host=None, ey_host=None, ez_host=None):
-    """End-to-end solve on host tensors (pinned for full bandwidth)."""
+def gmg_solve_host(ctx: Context, a_host, f_host, phi_host, phi0_host=None, ex_host=None, ey_host=None,
+                   ez_host=None):
+    """End-to-end solve on host tensors (pinned for full bandwidth): the
+    result lands in phi_host; phi0_host=None means a zero initial guess."""
     info = gmg_solve_info()
     a_ptr = _host(a_host, numel=ctx.n, name="a") if a_host is not None else None
+    x0_ptr = _host(phi0_host, numel=ctx.n, name="phi0") if phi0_host is not None else None
     fp32 = 0
     eptrs = [None, None, None]
     if ex_host is not None:
         fp32 = int(ex_host.dtype == torch.float32)
         dt = torch.float32 if fp32 else torch.float64
         eptrs = [_host(t, dt, ctx.n, nm) for t, nm in ((ex_host, "ex"), (ey_host, "ey"), (ez_host, "ez"))]
-    st = load().gmg_solve_host(ctx.handle, a_ptr, _host(f_host, numel=ctx.n, name="f"),
+    st = load().gmg_solve_host(ctx.handle, a_ptr, _host(f_host, numel=ctx.n, name="f"), x0_ptr,
                                _host(phi_host, numel=ctx.n, name="phi"), eptrs[0], eptrs[1], eptrs[2], fp32,
                                ctypes.byref(info))
     _check(st, "gmg_solve_host", allow=(GMG_OK, GMG_ERR_NOT_CONVERGED))
@@ -351,3 +361,31 @@ def gmg_hessenberg_max_real_eig(h) -> float:
 
 def gmg_test_fail_allocation_after(n: int):
     load().gmg_test_fail_allocation_after(int(n))
+
+
+def gmg_profile_enable(ctx: Context, on: bool = True):
+    _check(load().gmg_profile_enable(ctx.handle, int(bool(on))), "gmg_profile_enable")
+
+
+def gmg_profile_reset(ctx: Context):
+    _check(load().gmg_profile_reset(ctx.handle), "gmg_profile_reset")
+
+
+def gmg_profile_num_kernels() -> int:
+    return load().gmg_profile_num_kernels()
+
+
+def gmg_profile_get(ctx: Context, k: int) -> dict:
+    name = ctypes.c_char_p()
+    launches, timed = ctypes.c_longlong(), ctypes.c_longlong()
+    ms, nbytes = ctypes.c_double(), ctypes.c_double()
+    _check(load().gmg_profile_get(ctx.handle, int(k), ctypes.byref(name), ctypes.byref(launches), ctypes.byref(timed),
+                                  ctypes.byref(ms), ctypes.byref(nbytes)), "gmg_profile_get")
+    return {"name": name.value.decode(), "launches": launches.value, "timed": timed.value, "ms": ms.value,
+            "bytes": nbytes.value}
+
+
+def profile(ctx: Context) -> list:
+    """All kernel classes with at least one launch, sorted by time."""
+    rows = [gmg_profile_get(ctx, k) for k in range(gmg_profile_num_kernels())]
+    return sorted((r for r in rows if r["launches"]), key=lambda r: -r["ms"])

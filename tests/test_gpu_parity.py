@@ -120,7 +120,8 @@ def test_level_coefficients_and_operators(prec):
         ref = O.apply_operator(_ogrid(s), ain, xin)
         tol = 1e-14 if dt == torch.float64 else 5e-6
         assert _rel(_np(y), ref) < tol, lev
-        ref_a = O.coarsen_coefficient(ref_a)
+        if lev > 0:
+            ref_a = O.coarsen_coefficient(ref_a)
 
 
 # ---------------------------------------------------------------------------
@@ -362,7 +363,7 @@ def test_host_buffer_solve_matches_device_solve():
     f_h = torch.from_numpy(inp["f"]).pin_memory()
     phi_h = torch.zeros(shape, dtype=torch.float64).pin_memory()
     e = [torch.empty(shape, dtype=torch.float32).pin_memory() for _ in range(3)]
-    info = gmg.gmg_solve_host(ctx2, a_h, f_h, phi_h, *e)
+    info = gmg.gmg_solve_host(ctx2, a_h, f_h, phi_h, None, *e)
     assert info.converged
     np.testing.assert_array_equal(phi_h.numpy(), _np(phi_d))
     ex, ey, ez = O.field_from_potential(_ogrid(shape), phi_h.numpy(), 0.0, 1.0)
