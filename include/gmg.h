@@ -81,6 +81,17 @@ typedef enum gmg_orthogonalization {
   GMG_ORTH_MGS = 1   /* modified Gram-Schmidt as printed in Algorithm 1    */
 } gmg_orthogonalization;
 
+/* Arithmetic of the FGMRES matrix-vector product w = A z_j when z_j is the
+ * FP32 V-cycle output (GMG_PREC_MIXED).  w, a and all Krylov vectors stay
+ * FP64 in memory either way.  GB300 runs FP64 instructions at 1/64 of the FP32
+ * rate, so the default evaluates the stencil in double-float arithmetic
+ * (pairs of FP32 numbers with error-free sums and products, a 48-bit
+ * significand, about 1e-14 relative to an FP64 evaluation). */
+typedef enum gmg_outer_arith {
+  GMG_OUTER_FP64 = 0,        /* native FP64 instructions                     */
+  GMG_OUTER_DOUBLE_FLOAT = 1 /* FP32 pairs (default)                         */
+} gmg_outer_arith;
+
 typedef struct gmg_params {
   int nx, ny, nz;              /* cells; halving all three must reach a grid
                                   whose smallest side equals coarse_min      */
@@ -98,6 +109,8 @@ typedef struct gmg_params {
   int prolongation;            /* gmg_prolongation                           */
   int smoother_pc;             /* gmg_smoother_pc                            */
   int orthogonalization;       /* gmg_orthogonalization                      */
+  int outer_arith;             /* gmg_outer_arith: arithmetic of the Arnoldi
+                                  product w = A z_j in GMG_PREC_MIXED        */
 } gmg_params;
 
 typedef struct gmg_solve_info {
@@ -116,7 +129,8 @@ typedef struct gmg_solve_info {
  * plate data 0 / 1, coarse_min 4, 3 Chebyshev steps (a quadratic p_n, Sec.
  * 3.2), restart 20 (the paper uses 30, Sec. 3.1), rtol 1e-8 (Sec. 5.2),
  * 10 Arnoldi steps with factors 1.1 / 0.1 (Sec. 3.2), mixed precision,
- * trilinear prolongation, SGS smoother preconditioner, CGS2. */
+ * trilinear prolongation, SGS smoother preconditioner, CGS2, double-float
+ * Arnoldi product in mixed precision. */
 void gmg_default_params(gmg_params* p, int nx, int ny, int nz);
 
 /* Build a context: copy the cell coefficient a (a_dev, FP64, > 0 and finite),
@@ -199,6 +213,11 @@ gmg_status gmg_level_coefficient(gmg_ctx* ctx, int level, double* out_dev);
  * the finest size.  In mixed mode v is rounded to FP32 and the V-cycle runs
  * in FP32; z is widened back to FP64. */
 gmg_status gmg_apply_preconditioner(gmg_ctx* ctx, const double* v_dev, double* z_dev);
+
+/* w = A z for an FP32 z of the finest size, as FGMRES forms its Arnoldi
+ * product in GMG_PREC_MIXED (arithmetic per params.outer_arith); w FP64.
+ * GMG_ERR_ARG in GMG_PREC_FP64 mode, where z_j is FP64 (use apply_operator). */
+gmg_status gmg_apply_outer(gmg_ctx* ctx, const float* z_dev, double* w_dev);
 
 /* y = A_l x on a level, in level precision (x_dev, y_dev of that type). */
 gmg_status gmg_level_apply(gmg_ctx* ctx, int level, const void* x_dev, void* y_dev);

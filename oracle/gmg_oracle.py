@@ -319,8 +319,8 @@ def hash_start_vector(n: int) -> np.ndarray:
 
 
 def arnoldi_hessenberg(matvec, v0: np.ndarray, steps: int) -> np.ndarray:
-    """Arnoldi with modified Gram-Schmidt (Algorithm 1, lines 3-10, no
-    preconditioning): returns the square upper Hessenberg H_m (m <= steps)."""
+    """The Arnoldi process of Algorithm 1 with modified Gram-Schmidt and no
+    preconditioning: returns the square upper Hessenberg H_m (m <= steps)."""
     n = v0.size
     V = [v0 / np.linalg.norm(v0)]
     H = np.zeros((steps + 1, steps))
@@ -487,8 +487,8 @@ class SolveInfo:
 
 
 def _least_squares_residual(Hbar: np.ndarray, beta: float):
-    """min_y || beta e_1 - Hbar y || (Algorithm 1, line 11) by a library
-    least-squares solve; returns (y, residual norm)."""
+    """min_y || beta e_1 - Hbar y || (the least-squares step of Algorithm 1)
+    by a library least-squares solve; returns (y, residual norm)."""
     rhs = np.zeros(Hbar.shape[0])
     rhs[0] = beta
     y = np.linalg.lstsq(Hbar, rhs, rcond=None)[0]
@@ -499,10 +499,10 @@ def fgmres(grid: Grid, a: np.ndarray, b: np.ndarray, x0: np.ndarray | None, prec
            params: OracleParams) -> tuple[np.ndarray, SolveInfo]:
     """Restarted FGMRES with right preconditioning (Algorithm 1, Sec. 3.1).
 
-    Arnoldi uses modified Gram-Schmidt (line 8); the stopping test (line 12)
-    compares the least-squares residual with rtol * ||b|| (eq. (criterion));
-    after forming x_k (line 15) the true residual is checked (R8) and the
-    method restarts from x_k if it is not below the tolerance (line 16).
+    Arnoldi uses modified Gram-Schmidt; the stopping test compares the
+    least-squares residual with rtol * ||b|| (eq. (criterion)); after forming
+    x_k = x_0 + Z_k y_k the true residual is checked (R8) and the method
+    restarts from x_k if it is not below the tolerance.
     """
     info = SolveInfo()
     m = params.restart

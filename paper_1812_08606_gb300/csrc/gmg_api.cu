@@ -179,14 +179,16 @@ enum KernelClass : int {
   K_APPLY_F64, K_APPLY_OUTER, K_APPLY_F32, K_RESIDUAL_F64, K_RESIDUAL_F32, K_SGS_F64, K_SGS_F32,
   K_CHEB_F64, K_CHEB_F32, K_RESTRICT_F64, K_RESTRICT_F32, K_PROLONG_F64, K_PROLONG_F32, K_COARSE_F64,
   K_COARSE_F32, K_DOT, K_FINALIZE, K_AXPY, K_SCALE, K_UPDATE_X, K_CAST, K_COPY, K_RHS, K_FIELD, K_ADJOINT,
-  K_COARSEN, K_COEF_CHECK, K_HASH, K_COARSE_ASSEMBLE, K_COARSE_FACTOR, NK
+  K_COARSEN, K_COEF_CHECK, K_HASH, K_COARSE_ASSEMBLE, K_COARSE_FACTOR, K_DOT_F32, K_AXPY_F32, K_APPLY_DF64,
+  K_SPLIT, NK
 };
 static const char* const kKernelNames[NK] = {
     "apply_f64", "apply_outer_f64a_f32x", "apply_f32", "residual_f64", "residual_f32", "sgs_half_f64",
     "sgs_half_f32", "cheb_update_f64", "cheb_update_f32", "residual_restrict_f64", "residual_restrict_f32",
     "prolong_add_f64", "prolong_add_f32", "coarse_apply_f64", "coarse_apply_f32", "multi_dot", "finalize",
     "multi_axpy", "scale", "update_solution", "cast", "copy", "rhs", "field", "adjoint_grad", "coarsen_coef",
-    "coef_check", "hash_vector", "coarse_assemble", "coarse_factor"};
+    "coef_check", "hash_vector", "coarse_assemble", "coarse_factor", "multi_dot_f32", "multi_axpy_f32",
+    "apply_outer_df64", "split_coef"};
 
 struct ProfPending {
   int cls;
@@ -200,6 +202,8 @@ struct LevelData {
   Grid3 g{};
   double* a64 = nullptr;
   float* a32 = nullptr;
+  float2* a2 = nullptr;  // finest level, mixed + double-float outer product: (hi, lo) split of a64
+  DfCoef dc{};
   void *x = nullptr, *b = nullptr, *r = nullptr, *z = nullptr, *d = nullptr;  // level precision
   double lam_max = 0, lam_min = 0, lam_hat = 0;
 };
@@ -358,10 +362,11 @@ gmg_status prof_coarse_apply(gmg_ctx* c, int n, const T* Ainv, const T* b, T* x,
   GMG_RUN(is_f32<T>() ? K_COARSE_F32 : K_COARSE_F64, ((double)n * n + 2.0 * n) * sizeof(T),
           launch_coarse_apply<T>(n, Ainv, b, x, s));
 }
-gmg_status prof_multi_dot(gmg_ctx* c, size_t n, const double* w, const double* V, size_t ldv, int k, double* partial,
+template <typename T>
+gmg_status prof_multi_dot(gmg_ctx* c, size_t n, const T* w, const T* V, size_t ldv, int k, double* partial,
                           cudaStream_t s) {
-  const double bytes = (V == w && ldv == 0) ? 8.0 * n : 8.0 * n * (1 + k);
-  GMG_RUN(K_DOT, bytes, launch_multi_dot(n, w, V, ldv, k, partial, s));
+  const double bytes = (V == w && ldv == 0) ? (double)sizeof(T) * n : (double)sizeof(T) * n * (1 + k);
+  GMG_RUN(is_f32<T>() ? K_DOT_F32 : K_DOT, bytes, launch_multi_dot<T>(n, w, V, ldv, k, partial, s));
 }
 gmg_status prof_finalize(gmg_ctx* c, const double* partial, int nblocks, int k, double* out, int acc, cudaStream_t s) {
   GMG_RUN(K_FINALIZE, 8.0 * nblocks * k, launch_finalize(partial, nblocks, k, out, acc, s));
@@ -372,12 +377,15 @@ gmg_status prof_finalize_norm(gmg_ctx* c, const double* partial, int nblocks, do
 gmg_status prof_finalize_check(gmg_ctx* c, const double* partial, int nblocks, double* out, cudaStream_t s) {
   GMG_RUN(K_FINALIZE, 16.0 * nblocks, launch_finalize_check(partial, nblocks, out, s));
 }
-gmg_status prof_multi_axpy(gmg_ctx* c, size_t n, double* w, const double* V, size_t ldv, int k, const double* h,
+template <typename T>
+gmg_status prof_multi_axpy(gmg_ctx* c, size_t n, T* w, const T* V, size_t ldv, int k, const double* h,
                            cudaStream_t s) {
-  GMG_RUN(K_AXPY, 8.0 * n * (k + 2), launch_multi_axpy(n, w, V, ldv, k, h, s));
+  GMG_RUN(is_f32<T>() ? K_AXPY_F32 : K_AXPY, (double)sizeof(T) * n * (k + 2),
+          launch_multi_axpy<T>(n, w, V, ldv, k, h, s));
 }
-gmg_status prof_scale(gmg_ctx* c, size_t n, const double* src, double* dst, const double* sc, cudaStream_t s) {
-  GMG_RUN(K_SCALE, 16.0 * n, launch_scale(n, src, dst, sc, s));
+template <typename T>
+gmg_status prof_scale(gmg_ctx* c, size_t n, const T* src, T* dst, const double* sc, cudaStream_t s) {
+  GMG_RUN(K_SCALE, 2.0 * sizeof(T) * n, launch_scale<T>(n, src, dst, sc, s));
 }
 gmg_status prof_scale_value(gmg_ctx* c, size_t n, const double* src, double* dst, double alpha, cudaStream_t s) {
   GMG_RUN(K_SCALE, 16.0 * n, launch_scale_value(n, src, dst, alpha, s));
@@ -409,8 +417,9 @@ gmg_status prof_adjoint_grad(gmg_ctx* c, const Grid3& g, const double* phi, cons
                              double gb, double gt, cudaStream_t s) {
   GMG_RUN(K_ADJOINT, 24.0 * g.n(), launch_adjoint_grad(g, phi, lam, out, gb, gt, s));
 }
-gmg_status prof_hash_vector(gmg_ctx* c, size_t n, double* u, cudaStream_t s) {
-  GMG_RUN(K_HASH, 8.0 * n, launch_hash_vector(n, u, s));
+template <typename T>
+gmg_status prof_hash_vector(gmg_ctx* c, size_t n, T* u, cudaStream_t s) {
+  GMG_RUN(K_HASH, (double)sizeof(T) * n, launch_hash_vector(n, u, s));
 }
 gmg_status prof_coef_check(gmg_ctx* c, size_t n, const double* a, double* partial, cudaStream_t s) {
   GMG_RUN(K_COEF_CHECK, 8.0 * n, launch_coef_check(n, a, partial, s));
@@ -424,6 +433,13 @@ gmg_status prof_coarse_assemble(gmg_ctx* c, const Grid3& g, const double* a, dou
 gmg_status prof_coarse_factor(gmg_ctx* c, int n, double* A, double* work, double* Ainv, float* Ainv32, int* st,
                               cudaStream_t s) {
   GMG_RUN(K_COARSE_FACTOR, 36.0 * n * n, launch_coarse_factor(n, A, work, Ainv, Ainv32, st, s));
+}
+gmg_status prof_apply_df64(gmg_ctx* c, const Grid3& g, const DfCoef& dc, const float2* a2, const float* z, double* w,
+                           cudaStream_t s) {
+  GMG_RUN(K_APPLY_DF64, 20.0 * g.n(), launch_apply_df64(g, dc, a2, z, w, s));
+}
+gmg_status prof_split(gmg_ctx* c, size_t n, const double* a, float2* a2, cudaStream_t s) {
+  GMG_RUN(K_SPLIT, 16.0 * n, launch_split(n, a, a2, s));
 }
 #undef GMG_RUN
 
@@ -442,6 +458,7 @@ gmg_status validate(const gmg_params* p, int* nlevels) {
   if (p->prolongation != 0 && p->prolongation != 1) return GMG_ERR_ARG;
   if (p->smoother_pc < 0 || p->smoother_pc > 2) return GMG_ERR_ARG;
   if (p->orthogonalization != 0 && p->orthogonalization != 1) return GMG_ERR_ARG;
+  if (p->outer_arith != GMG_OUTER_FP64 && p->outer_arith != GMG_OUTER_DOUBLE_FLOAT) return GMG_ERR_ARG;
   if ((double)p->nx * p->ny * p->nz > 4.0e9) return GMG_ERR_ARG;
   int nx = p->nx, ny = p->ny, nz = p->nz, L = 1;
   while (std::min(nx, std::min(ny, nz)) > p->coarse_min) {
@@ -466,8 +483,9 @@ gmg_status read_scalars(gmg_ctx* c, int slot, int count) {
 }
 
 // Device: out slots [slot, slot+2) = (||w||, 1/||w||).
-gmg_status norm_dev(gmg_ctx* c, size_t n, const double* w, int slot) {
-  CKS(prof_multi_dot(c, n, w, w, 0, 1, c->partial, c->s));
+template <typename T>
+gmg_status norm_dev(gmg_ctx* c, size_t n, const T* w, int slot) {
+  CKS(prof_multi_dot<T>(c, n, w, w, 0, 1, c->partial, c->s));
   CKS(prof_finalize_norm(c, c->partial, reduce_blocks(n), c->dscal + slot, c->s));
   return GMG_OK;
 }
@@ -475,26 +493,27 @@ gmg_status norm_dev(gmg_ctx* c, size_t n, const double* w, int slot) {
 // Orthogonalise w against the k vectors V[0..k) (row stride ld), leaving the
 // coefficients in slots SL_H1 (+ SL_H2 for the second CGS pass) and the norm
 // of the result and its reciprocal in SL_NORM.
-gmg_status orthogonalize(gmg_ctx* c, size_t n, const double* V, size_t ld, int k, double* w) {
+template <typename T>
+gmg_status orthogonalize(gmg_ctx* c, size_t n, const T* V, size_t ld, int k, T* w) {
   const int nb = reduce_blocks(n);
   if (c->p.orthogonalization == GMG_ORTH_MGS) {
     for (int i = 0; i < k; ++i) {
-      CKS(prof_multi_dot(c, n, w, V + (size_t)i * ld, ld, 1, c->partial, c->s));
+      CKS(prof_multi_dot<T>(c, n, w, V + (size_t)i * ld, ld, 1, c->partial, c->s));
       CKS(prof_finalize(c, c->partial, nb, 1, c->dscal + SL_H1 + i, 0, c->s));
-      CKS(prof_multi_axpy(c, n, w, V + (size_t)i * ld, ld, 1, c->dscal + SL_H1 + i, c->s));
+      CKS(prof_multi_axpy<T>(c, n, w, V + (size_t)i * ld, ld, 1, c->dscal + SL_H1 + i, c->s));
     }
   } else {
     for (int pass = 0; pass < 2; ++pass) {
       double* hslot = c->dscal + (pass == 0 ? SL_H1 : SL_H2);
       for (int c0 = 0; c0 < k; c0 += 8) {
         const int kc = std::min(8, k - c0);
-        CKS(prof_multi_dot(c, n, w, V + (size_t)c0 * ld, ld, kc, c->partial, c->s));
+        CKS(prof_multi_dot<T>(c, n, w, V + (size_t)c0 * ld, ld, kc, c->partial, c->s));
         CKS(prof_finalize(c, c->partial, nb, kc, hslot + c0, 0, c->s));
       }
-      CKS(prof_multi_axpy(c, n, w, V, ld, k, hslot, c->s));
+      CKS(prof_multi_axpy<T>(c, n, w, V, ld, k, hslot, c->s));
     }
   }
-  return norm_dev(c, n, w, SL_NORM);
+  return norm_dev<T>(c, n, w, SL_NORM);
 }
 
 // Column of H after orthogonalize (host copy): h[0..k) and h[k] = ||w||.
@@ -512,34 +531,51 @@ gmg_status read_column(gmg_ctx* c, int k, double* h) {
   return GMG_OK;
 }
 
-// z = B^{-1} r on a level in FP64 (used by the eigen estimate), r FP64 buffer.
-gmg_status smoother_pc_fp64(gmg_ctx* c, const LevelData& L, const double* r, double* z) {
+template <typename T>
+const T* level_a(const LevelData& L);
+template <>
+const float* level_a<float>(const LevelData& L) { return L.a32; }
+template <>
+const double* level_a<double>(const LevelData& L) { return L.a64; }
+
+// z = B^{-1} r on a level in precision T (the smoother's preconditioner).
+template <typename T>
+gmg_status smoother_pc(gmg_ctx* c, const LevelData& L, const T* r, T* z) {
   const int pc = c->p.smoother_pc;
-  if (pc == GMG_PC_IDENTITY) return (prof_copy_d(c, L.n, r, z, c->s));
-  CKS(prof_residual<double>(c, L.g, L.a64, r, nullptr, nullptr, z, pc == GMG_PC_SGS ? PC_SGS : PC_JACOBI, c->s));
+  const T* a = level_a<T>(L);
+  if (pc == GMG_PC_IDENTITY) return map_err(cudaMemcpyAsync(z, r, L.n * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
+  CKS(prof_residual<T>(c, L.g, a, r, nullptr, nullptr, z, pc == GMG_PC_SGS ? PC_SGS : PC_JACOBI, c->s));
   if (pc == GMG_PC_SGS) {
-    CKS(prof_sgs_half<double>(c, L.g, L.a64, r, z, 1, nullptr, nullptr, 0, 0, 0, c->s));
-    CKS(prof_sgs_half<double>(c, L.g, L.a64, r, z, 0, nullptr, nullptr, 0, 0, 0, c->s));
+    CKS(prof_sgs_half<T>(c, L.g, a, r, z, 1, nullptr, nullptr, 0, 0, 0, c->s));
+    CKS(prof_sgs_half<T>(c, L.g, a, r, z, 0, nullptr, nullptr, 0, 0, 0, c->s));
   }
   return GMG_OK;
 }
 
-// lambda_max, lambda* of level l: Arnoldi on B^{-1} A_l (Sec. 3.2).
+// lambda_max, lambda* of level l: Arnoldi on B^{-1} A_l (Sec. 3.2) in the
+// level precision T.  FP64: basis in V, temporaries bvec / w.  FP32 (the
+// mixed-precision set-up; the bounds only steer the FP32 smoother): basis in
+// Z, temporaries the level's r / z.
+template <typename T>
 gmg_status eig_bounds(gmg_ctx* c, int l) {
   LevelData& L = c->lev[l];
   const size_t n = L.n;
   const int steps = c->p.eig_steps;
-  double* V = c->V;  // (steps+1) vectors of n, stride n
-  CKS(prof_hash_vector(c, n, V, c->s));
-  CKS(norm_dev(c, n, V, SL_NORM));
-  CKS(prof_scale(c, n, V, V, c->dscal + SL_NORM + 1, c->s));
+  const bool f32 = sizeof(T) == 4;
+  T* V = f32 ? (T*)c->Z : (T*)(void*)c->V;  // (steps+1) vectors of n, stride n
+  T* t1 = f32 ? (T*)L.r : (T*)(void*)c->bvec;
+  T* t2 = f32 ? (T*)L.z : (T*)(void*)c->w;
+  const T* a = level_a<T>(L);
+  CKS(prof_hash_vector<T>(c, n, V, c->s));
+  CKS(norm_dev<T>(c, n, V, SL_NORM));
+  CKS(prof_scale<T>(c, n, V, V, c->dscal + SL_NORM + 1, c->s));
   std::vector<double> H((size_t)(steps + 1) * steps, 0.0);
   int m = steps;
   std::vector<double> col(steps + 2);
   for (int j = 0; j < steps; ++j) {
-    CKS(prof_apply<double, double, double>(c, L.g, L.a64, V + (size_t)j * n, c->bvec, c->s));
-    CKS(smoother_pc_fp64(c, L, c->bvec, c->w));
-    CKS(orthogonalize(c, n, V, n, j + 1, c->w));
+    CKS(prof_apply<T, T, T>(c, L.g, a, V + (size_t)j * n, t1, c->s));
+    CKS(smoother_pc<T>(c, L, t1, t2));
+    CKS(orthogonalize<T>(c, n, V, n, j + 1, t2));
     CKS(read_column(c, j + 1, col.data()));
     for (int i = 0; i <= j + 1; ++i) {
       if (!isfinite(col[i])) return GMG_ERR_NONFINITE;
@@ -549,7 +585,7 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
       m = j + 1;
       break;
     }
-    CKS(prof_scale(c, n, c->w, V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));
+    CKS(prof_scale<T>(c, n, t2, V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));
   }
   std::vector<double> Hm((size_t)m * m);
   for (int r = 0; r < m; ++r)
@@ -575,10 +611,11 @@ gmg_status build(gmg_ctx* c, const double* a_dev) {
   if (c->hpin[SL_CHECK + 1] != 0.0) return GMG_ERR_ARG;
   CKS(prof_copy_d(c, F.n, a_dev, F.a64, c->s));
   if (c->mixed) CKS(prof_cast_d2f(c, F.n, F.a64, F.a32, c->s));
+  if (F.a2) CKS(prof_split(c, F.n, F.a64, F.a2, c->s));
   for (int l = (int)c->lev.size() - 1; l >= 1; --l)
     CKS(prof_coarsen_coef(c, c->lev[l].g, c->lev[l].a64, c->lev[l - 1].a64, c->mixed ? c->lev[l - 1].a32 : nullptr,
                            c->s));
-  for (int l = 1; l < (int)c->lev.size(); ++l) CKS(eig_bounds(c, l));
+  for (int l = 1; l < (int)c->lev.size(); ++l) CKS(c->mixed ? eig_bounds<float>(c, l) : eig_bounds<double>(c, l));
   // coarsest: dense Cholesky and explicit inverse
   const LevelData& C0 = c->lev[0];
   CKS(prof_coarse_assemble(c, C0.g, C0.a64, c->cA, c->s));
@@ -593,13 +630,6 @@ gmg_status build(gmg_ctx* c, const double* a_dev) {
 // ---------------------------------------------------------------------------
 // V-cycle (Sec. 3.2, Appendix A)
 // ---------------------------------------------------------------------------
-
-template <typename T>
-const T* level_a(const LevelData& L);
-template <>
-const float* level_a<float>(const LevelData& L) { return L.a32; }
-template <>
-const double* level_a<double>(const LevelData& L) { return L.a64; }
 
 template <typename T>
 const T* coarse_inv(const gmg_ctx* c);
@@ -679,6 +709,7 @@ gmg_status precondition(gmg_ctx* c, const double* v, void* z) {
 // w = A z (FP64 operator on a level-precision vector of the finest size).
 gmg_status apply_outer(gmg_ctx* c, const void* z, double* w) {
   const LevelData& F = c->fine();
+  if (c->mixed && F.a2) return prof_apply_df64(c, F.g, F.dc, F.a2, (const float*)z, w, c->s);
   if (c->mixed) return (prof_apply<double, float, double>(c, F.g, F.a64, (const float*)z, w, c->s));
   return (prof_apply<double, double, double>(c, F.g, F.a64, (const double*)z, w, c->s));
 }
@@ -713,7 +744,7 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
   {
     std::vector<double> R((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), col(m + 2), y(m);
     for (;;) {
-      // r0 = b - A x0, beta, v1 (Algorithm 1, line 3)
+      // r0 = b - A x0, beta = ||r0||, v1 = r0 / beta (start of an Arnoldi cycle)
       CKS(prof_residual<double>(c, F.g, F.a64, c->bvec, x, c->V, nullptr, PC_NONE, c->s));
       CKS(norm_dev(c, n, c->V, SL_NORM));
       CKS(read_scalars(c, SL_NORM, 2));
@@ -738,10 +769,10 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
       bool fail = false;
       for (int j = 0; j < m; ++j) {
         double* vj = c->V + (size_t)j * n;
-        CKS(precondition(c, vj, zvec(c, j)));           // line 5: z_j = M v_j
-        CKS(apply_outer(c, zvec(c, j), c->w));            // line 6: w = A z_j
-        CKS(orthogonalize(c, n, c->V, n, j + 1, c->w));   // lines 7-9
-        CKS(read_column(c, j + 1, col.data()));          // line 10: h_{j+1,j}
+        CKS(precondition(c, vj, zvec(c, j)));           // z_j = M v_j (one V-cycle)
+        CKS(apply_outer(c, zvec(c, j), c->w));            // w = A z_j
+        CKS(orthogonalize(c, n, c->V, n, j + 1, c->w));   // Gram-Schmidt: h_{i,j}
+        CKS(read_column(c, j + 1, col.data()));          // h_{j+1,j} = ||w||
         for (int i = 0; i <= j + 1; ++i)
           if (!isfinite(col[i])) fail = true;
         if (fail) {
@@ -749,7 +780,7 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
           break;
         }
         const double hnext = col[j + 1];
-        // line 11: least squares by Givens rotations on the new column
+        // least-squares residual min ||beta e_1 - Hbar_j y|| by Givens rotations
         for (int i = 0; i < j; ++i) {
           const double t = cs[i] * col[i] + sn[i] * col[i + 1];
           col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
@@ -773,10 +804,10 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
         if (loc.n_history < GMG_MAX_HISTORY) loc.res_history[loc.n_history++] = est;
         if (hnext == 0.0) break;  // lucky breakdown: the solution is in K_j
         CKS(prof_scale(c, n, c->w, c->V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));
-        if (est < c->p.rtol || loc.iterations >= c->p.max_iters) break;  // line 12
+        if (est < c->p.rtol || loc.iterations >= c->p.max_iters) break;  // stopping test
       }
       if (fail) break;
-      // line 15: y_k from the triangular system, x_k = x_0 + Z_k y_k
+      // y_k from the triangular system, x_k = x_0 + Z_k y_k
       for (int i = k - 1; i >= 0; --i) {
         double t = g[i];
         for (int q = i + 1; q < k; ++q) t -= R[(size_t)i * m + q] * y[q];
@@ -788,7 +819,7 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
         CKS(prof_update_solution<float>(c, n, x, (const float*)c->Z, n, k, c->dscal + SL_Y, c->s));
       else
         CKS(prof_update_solution<double>(c, n, x, (const double*)c->Z, n, k, c->dscal + SL_Y, c->s));
-      loc.restarts++;  // line 16: restart from x_k (the true residual is checked at the loop top)
+      loc.restarts++;  // restart from x_k (the true residual is checked at the loop top)
     }
   }
 done:
@@ -833,6 +864,7 @@ void gmg_default_params(gmg_params* p, int nx, int ny, int nz) {
   p->prolongation = GMG_PROLONG_TRILINEAR;
   p->smoother_pc = GMG_PC_SGS;
   p->orthogonalization = GMG_ORTH_CGS2;
+  p->outer_arith = GMG_OUTER_DOUBLE_FLOAT;
 }
 
 const char* gmg_status_string(gmg_status s) {
@@ -895,6 +927,10 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
     const bool top = l == L - 1;
     if ((st = dalloc(c, &D.a64, D.n)) != GMG_OK) return fail(st);
     if (c->mixed && (st = dalloc(c, &D.a32, D.n)) != GMG_OK) return fail(st);
+    if (top && c->mixed && p->outer_arith == GMG_OUTER_DOUBLE_FLOAT) {
+      if ((st = dalloc(c, &D.a2, D.n)) != GMG_OK) return fail(st);
+      D.dc = make_df_coef(D.g);
+    }
     if (!top && (st = dev_alloc(c, &D.x, D.n * c->esz)) != GMG_OK) return fail(st);
     if ((!top || c->mixed) && (st = dev_alloc(c, &D.b, D.n * c->esz)) != GMG_OK) return fail(st);
     if (l > 0 || L == 1) {
@@ -906,7 +942,9 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
   const size_t N = c->lev.back().n;
   c->nv = std::max(p->restart, p->eig_steps) + 1;
   if ((st = dalloc(c, &c->V, (size_t)c->nv * N)) != GMG_OK) return fail(st);
-  if ((st = dev_alloc(c, &c->Z, (size_t)p->restart * N * c->esz)) != GMG_OK) return fail(st);
+  // Z also holds the FP32 eigen-estimate basis of the mixed set-up (eig_steps + 1 vectors)
+  const size_t nz_vec = (size_t)std::max(p->restart, c->mixed ? p->eig_steps + 1 : 0);
+  if ((st = dev_alloc(c, &c->Z, nz_vec * N * c->esz)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->w, N)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->bvec, N)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->partial, (size_t)1024 * 16)) != GMG_OK) return fail(st);
@@ -1044,6 +1082,11 @@ gmg_status gmg_apply_preconditioner(gmg_ctx* c, const double* v_dev, double* z_d
   return (prof_copy_d(c, c->N(), (const double*)c->Z, z_dev, c->s));
 }
 
+gmg_status gmg_apply_outer(gmg_ctx* c, const float* z, double* w) {
+  if (!c || !z || !w || !c->mixed) return GMG_ERR_ARG;
+  return apply_outer(c, z, w);
+}
+
 gmg_status gmg_level_apply(gmg_ctx* c, int level, const void* x, void* y) {
   LevelData* L = level_ptr(c, level);
   if (!L || !x || !y) return GMG_ERR_ARG;
@@ -1061,19 +1104,8 @@ gmg_status gmg_level_smooth(gmg_ctx* c, int level, const void* b, void* x, int x
 gmg_status gmg_level_smoother_pc(gmg_ctx* c, int level, const void* r, void* z) {
   LevelData* L = level_ptr(c, level);
   if (!L || !r || !z) return GMG_ERR_ARG;
-  const int pc = c->p.smoother_pc;
-  if (c->mixed) {
-    const float* a = L->a32;
-    if (pc == GMG_PC_IDENTITY) return map_err(cudaMemcpyAsync(z, r, L->n * 4, cudaMemcpyDeviceToDevice, c->s));
-    CKS(prof_residual<float>(c, L->g, a, (const float*)r, nullptr, nullptr, (float*)z,
-                              pc == GMG_PC_SGS ? PC_SGS : PC_JACOBI, c->s));
-    if (pc == GMG_PC_SGS) {
-      CKS(prof_sgs_half<float>(c, L->g, a, (const float*)r, (float*)z, 1, nullptr, nullptr, 0, 0, 0, c->s));
-      CKS(prof_sgs_half<float>(c, L->g, a, (const float*)r, (float*)z, 0, nullptr, nullptr, 0, 0, 0, c->s));
-    }
-    return GMG_OK;
-  }
-  return smoother_pc_fp64(c, *L, (const double*)r, (double*)z);
+  if (c->mixed) return smoother_pc<float>(c, *L, (const float*)r, (float*)z);
+  return smoother_pc<double>(c, *L, (const double*)r, (double*)z);
 }
 
 gmg_status gmg_level_residual_restrict(gmg_ctx* c, int level, const void* b, const void* x, void* coarse) {

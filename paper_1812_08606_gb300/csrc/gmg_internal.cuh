@@ -19,8 +19,29 @@ struct Grid3 {
   int nx, ny, nz;
   double cx, cy, cz;  // 0.5 / h^2 per axis: a_f / h^2 = (a_p + a_q) * c
   double cp;          // 2 / hz^2: plate-face coefficient per unit a_p
+  // FP32 copies: an FP32 kernel must not convert from double per cell (on
+  // GB300 every FP64 instruction, conversions included, runs at 1/64 rate).
+  float fx, fy, fz, fp;
   __host__ __device__ size_t n() const { return (size_t)nx * ny * nz; }
   __host__ __device__ size_t plane() const { return (size_t)nx * ny; }
+};
+
+// Stencil scale factors in the arithmetic type C.
+template <typename C>
+struct GridCoef;
+template <>
+struct GridCoef<float> {
+  __device__ __forceinline__ static float x(const Grid3& g) { return g.fx; }
+  __device__ __forceinline__ static float y(const Grid3& g) { return g.fy; }
+  __device__ __forceinline__ static float z(const Grid3& g) { return g.fz; }
+  __device__ __forceinline__ static float p(const Grid3& g) { return g.fp; }
+};
+template <>
+struct GridCoef<double> {
+  __device__ __forceinline__ static double x(const Grid3& g) { return g.cx; }
+  __device__ __forceinline__ static double y(const Grid3& g) { return g.cy; }
+  __device__ __forceinline__ static double z(const Grid3& g) { return g.cz; }
+  __device__ __forceinline__ static double p(const Grid3& g) { return g.cp; }
 };
 
 Grid3 make_grid(int nx, int ny, int nz, double lx, double ly, double lz);
@@ -49,14 +70,14 @@ __device__ __forceinline__ void stencil_diff(const Grid3& g, const TA* __restric
   const C xp = (C)ldg(x + p);
   const size_t pl = g.plane();
   C acc = (C)0;
-  if (i > 0) acc += (ap + (C)ldg(a + p - 1)) * (C)g.cx * (xp - (C)ldg(x + p - 1));
-  if (i < g.nx - 1) acc += (ap + (C)ldg(a + p + 1)) * (C)g.cx * (xp - (C)ldg(x + p + 1));
-  if (j > 0) acc += (ap + (C)ldg(a + p - g.nx)) * (C)g.cy * (xp - (C)ldg(x + p - g.nx));
-  if (j < g.ny - 1) acc += (ap + (C)ldg(a + p + g.nx)) * (C)g.cy * (xp - (C)ldg(x + p + g.nx));
-  if (k > 0) acc += (ap + (C)ldg(a + p - pl)) * (C)g.cz * (xp - (C)ldg(x + p - pl));
-  else acc += ap * (C)g.cp * xp;
-  if (k < g.nz - 1) acc += (ap + (C)ldg(a + p + pl)) * (C)g.cz * (xp - (C)ldg(x + p + pl));
-  else acc += ap * (C)g.cp * xp;
+  if (i > 0) acc += (ap + (C)ldg(a + p - 1)) * GridCoef<C>::x(g) * (xp - (C)ldg(x + p - 1));
+  if (i < g.nx - 1) acc += (ap + (C)ldg(a + p + 1)) * GridCoef<C>::x(g) * (xp - (C)ldg(x + p + 1));
+  if (j > 0) acc += (ap + (C)ldg(a + p - g.nx)) * GridCoef<C>::y(g) * (xp - (C)ldg(x + p - g.nx));
+  if (j < g.ny - 1) acc += (ap + (C)ldg(a + p + g.nx)) * GridCoef<C>::y(g) * (xp - (C)ldg(x + p + g.nx));
+  if (k > 0) acc += (ap + (C)ldg(a + p - pl)) * GridCoef<C>::z(g) * (xp - (C)ldg(x + p - pl));
+  else acc += ap * GridCoef<C>::p(g) * xp;
+  if (k < g.nz - 1) acc += (ap + (C)ldg(a + p + pl)) * GridCoef<C>::z(g) * (xp - (C)ldg(x + p + pl));
+  else acc += ap * GridCoef<C>::p(g) * xp;
   ax = acc;
 }
 
@@ -68,14 +89,14 @@ __device__ __forceinline__ void stencil_split(const Grid3& g, const TA* __restri
   const C ap = (C)ldg(a + p);
   const size_t pl = g.plane();
   C d = (C)0, s = (C)0;
-  if (i > 0) { C c = (ap + (C)ldg(a + p - 1)) * (C)g.cx; d += c; if (z) s += c * (C)z[p - 1]; }
-  if (i < g.nx - 1) { C c = (ap + (C)ldg(a + p + 1)) * (C)g.cx; d += c; if (z) s += c * (C)z[p + 1]; }
-  if (j > 0) { C c = (ap + (C)ldg(a + p - g.nx)) * (C)g.cy; d += c; if (z) s += c * (C)z[p - g.nx]; }
-  if (j < g.ny - 1) { C c = (ap + (C)ldg(a + p + g.nx)) * (C)g.cy; d += c; if (z) s += c * (C)z[p + g.nx]; }
-  if (k > 0) { C c = (ap + (C)ldg(a + p - pl)) * (C)g.cz; d += c; if (z) s += c * (C)z[p - pl]; }
-  else d += ap * (C)g.cp;
-  if (k < g.nz - 1) { C c = (ap + (C)ldg(a + p + pl)) * (C)g.cz; d += c; if (z) s += c * (C)z[p + pl]; }
-  else d += ap * (C)g.cp;
+  if (i > 0) { C c = (ap + (C)ldg(a + p - 1)) * GridCoef<C>::x(g); d += c; if (z) s += c * (C)z[p - 1]; }
+  if (i < g.nx - 1) { C c = (ap + (C)ldg(a + p + 1)) * GridCoef<C>::x(g); d += c; if (z) s += c * (C)z[p + 1]; }
+  if (j > 0) { C c = (ap + (C)ldg(a + p - g.nx)) * GridCoef<C>::y(g); d += c; if (z) s += c * (C)z[p - g.nx]; }
+  if (j < g.ny - 1) { C c = (ap + (C)ldg(a + p + g.nx)) * GridCoef<C>::y(g); d += c; if (z) s += c * (C)z[p + g.nx]; }
+  if (k > 0) { C c = (ap + (C)ldg(a + p - pl)) * GridCoef<C>::z(g); d += c; if (z) s += c * (C)z[p - pl]; }
+  else d += ap * GridCoef<C>::p(g);
+  if (k < g.nz - 1) { C c = (ap + (C)ldg(a + p + pl)) * GridCoef<C>::z(g); d += c; if (z) s += c * (C)z[p + pl]; }
+  else d += ap * GridCoef<C>::p(g);
   diag = d;
   nsum = s;
 }
@@ -100,6 +121,13 @@ cudaError_t launch_residual(const Grid3& g, const T* a, const T* b, const T* x, 
 template <typename T>
 cudaError_t launch_sgs_half(const Grid3& g, const T* a, const T* r, T* z, int color, T* d, T* x,
                             double c1, double c2, int flags, cudaStream_t s);
+
+// One Chebyshev step with the red-black SSOR preconditioner in one pass
+// (FP32): x_out = x_in + d, d = c1 d + c2 B^{-1}(b - A x_in); xin null means
+// x_in = 0.  x_out must not alias x_in; d is updated in place.
+bool fused_smoother_eligible(const Grid3& g);
+cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b, const float* xin, float* xout,
+                                  float* d, double c1, double c2, int flags, cudaStream_t s);
 
 // Pointwise Chebyshev update on all cells: d = c1 d + c2 z; x += d.
 template <typename T>
@@ -137,23 +165,26 @@ cudaError_t launch_adjoint_grad(const Grid3& g, const double* phi, const double*
 
 // u_i = splitmix64-based start vector in [-1, 1).
 cudaError_t launch_hash_vector(size_t n, double* u, cudaStream_t s);
+cudaError_t launch_hash_vector(size_t n, float* u, cudaStream_t s);
 
 // ---- Reductions (deterministic: fixed block count and summation order) ----
 int reduce_blocks(size_t n);  // number of partial sums a reduction over n produces
 
 // partial[b*k + i] = block b's part of sum_p w_p v_i,p  (i < k <= 8), V row stride ldv.
-cudaError_t launch_multi_dot(size_t n, const double* w, const double* V, size_t ldv, int k,
-                             double* partial, cudaStream_t s);
+template <typename T>
+cudaError_t launch_multi_dot(size_t n, const T* w, const T* V, size_t ldv, int k, double* partial,
+                             cudaStream_t s);
 // out[i] = sum_b partial[b*k + i] (+ out[i] if accumulate) for i < k; one block per output.
 cudaError_t launch_finalize(const double* partial, int nblocks, int k, double* out, int accumulate,
                             cudaStream_t s);
 // out[0] = sqrt(sum_b partial[b]); out[1] = (out[0] != 0) ? 1/out[0] : 0.
 cudaError_t launch_finalize_norm(const double* partial, int nblocks, double* out, cudaStream_t s);
-// w -= sum_i h[i] v_i  (i < k <= 8), h read from device memory.
-cudaError_t launch_multi_axpy(size_t n, double* w, const double* V, size_t ldv, int k,
-                              const double* h, cudaStream_t s);
+// w -= sum_i h[i] v_i  (i < k <= 64), h read from device memory.
+template <typename T>
+cudaError_t launch_multi_axpy(size_t n, T* w, const T* V, size_t ldv, int k, const double* h, cudaStream_t s);
 // dst = src * scale[0] (scale read from device memory).
-cudaError_t launch_scale(size_t n, const double* src, double* dst, const double* scale, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scale(size_t n, const T* src, T* dst, const double* scale, cudaStream_t s);
 // dst = src * alpha (alpha by value).
 cudaError_t launch_scale_value(size_t n, const double* src, double* dst, double alpha, cudaStream_t s);
 // x += sum_i y[i] z_i, Z row stride ldz, k <= 64, y on the device.
@@ -163,6 +194,18 @@ cudaError_t launch_update_solution(size_t n, double* x, const TZ* Z, size_t ldz,
 // partial[b*2 + 0] = min over block of a; partial[b*2+1] = count of non-finite / non-positive.
 cudaError_t launch_coef_check(size_t n, const double* a, double* partial, cudaStream_t s);
 cudaError_t launch_finalize_check(const double* partial, int nblocks, double* out, cudaStream_t s);
+
+// ---- Double-float outer operator (mixed precision) ----
+// Stencil scale factors as (hi, lo) FP32 pairs.
+struct DfCoef {
+  float xh, xl, yh, yl, zh, zl, ph, pl;
+};
+DfCoef make_df_coef(const Grid3& g);
+// w = A z with a stored as (hi, lo) pairs, z FP32, w FP64; double-float arithmetic.
+cudaError_t launch_apply_df64(const Grid3& g, const DfCoef& c, const float2* a2, const float* z, double* w,
+                              cudaStream_t s);
+// a2 = (fl32(a), fl32(a - fl32(a))).
+cudaError_t launch_split(size_t n, const double* a, float2* a2, cudaStream_t s);
 
 // ---- Coarsest level: dense SPD operator, Cholesky, explicit inverse ----
 // A (n x n, row-major, n = g.n()) from the coarse coefficient.

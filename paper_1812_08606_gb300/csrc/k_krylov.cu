@@ -35,22 +35,23 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
-template <int K>
-__global__ void __launch_bounds__(RT) k_multi_dot(size_t n, const double* __restrict__ w,
-                                                  const double* __restrict__ V, size_t ldv,
-                                                  double* __restrict__ partial) {
+// T = double: FP64 products and sums.  T = float (the FP32 eigen estimate of
+// the mixed-precision set-up): per-thread FP32 sums, FP64 across threads.
+template <int K, typename T>
+__global__ void __launch_bounds__(RT) k_multi_dot(size_t n, const T* __restrict__ w, const T* __restrict__ V,
+                                                  size_t ldv, double* __restrict__ partial) {
   __shared__ double sh[RT / 32];
-  double acc[K];
+  T acc[K];
 #pragma unroll
-  for (int i = 0; i < K; ++i) acc[i] = 0.0;
+  for (int i = 0; i < K; ++i) acc[i] = (T)0;
   for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
-    const double wp = w[p];
+    const T wp = w[p];
 #pragma unroll
     for (int i = 0; i < K; ++i) acc[i] = fma(wp, V[i * ldv + p], acc[i]);
   }
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    const double t = block_sum<RT>(acc[i], sh);
+    const double t = block_sum<RT>((double)acc[i], sh);
     if (threadIdx.x == 0) partial[(size_t)blockIdx.x * K + i] = t;
   }
 }
@@ -78,21 +79,22 @@ __global__ void __launch_bounds__(RT) k_finalize_norm(const double* __restrict__
   }
 }
 
-__global__ void __launch_bounds__(RT) k_multi_axpy(size_t n, double* __restrict__ w, const double* __restrict__ V,
-                                                   size_t ldv, int k, const double* __restrict__ h) {
-  __shared__ double hs[64];
-  if (threadIdx.x < k) hs[threadIdx.x] = h[threadIdx.x];
+template <typename T>
+__global__ void __launch_bounds__(RT) k_multi_axpy(size_t n, T* __restrict__ w, const T* __restrict__ V, size_t ldv,
+                                                   int k, const double* __restrict__ h) {
+  __shared__ T hs[64];
+  if (threadIdx.x < k) hs[threadIdx.x] = (T)h[threadIdx.x];
   __syncthreads();
   for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
-    double v = w[p];
+    T v = w[p];
     for (int i = 0; i < k; ++i) v = fma(-hs[i], V[i * ldv + p], v);
     w[p] = v;
   }
 }
 
-__global__ void k_scale(size_t n, const double* __restrict__ src, double* __restrict__ dst,
-                        const double* __restrict__ scale) {
-  const double s = scale[0];
+template <typename T>
+__global__ void k_scale(size_t n, const T* __restrict__ src, T* __restrict__ dst, const double* __restrict__ scale) {
+  const T s = (T)scale[0];
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
     dst[p] = src[p] * s;
 }
@@ -172,6 +174,15 @@ __global__ void k_hash_vector(size_t n, double* __restrict__ u) {
   }
 }
 
+// FP32 start vector: the top 24 bits of the same splitmix64 draws, so the
+// value is the FP64 start vector truncated to FP32 precision (no FP64 math).
+__global__ void k_hash_vector_f32(size_t n, float* __restrict__ u) {
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t bits = (uint32_t)(splitmix64_at((uint64_t)p) >> 40);
+    u[p] = (float)bits * (1.0f / 16777216.0f) * 2.0f - 1.0f;
+  }
+}
+
 inline unsigned flat_blocks(size_t n) {
   size_t b = (n + 255) / 256;
   if (b > 152 * 32) b = 152 * 32;
@@ -188,12 +199,12 @@ int reduce_blocks(size_t n) {
   return (int)b;
 }
 
-cudaError_t launch_multi_dot(size_t n, const double* w, const double* V, size_t ldv, int k, double* partial,
-                             cudaStream_t s) {
+template <typename T>
+cudaError_t launch_multi_dot(size_t n, const T* w, const T* V, size_t ldv, int k, double* partial, cudaStream_t s) {
   const int nb = reduce_blocks(n);
   switch (k) {
 #define GMG_CASE(K) \
-  case K: k_multi_dot<K><<<nb, RT, 0, s>>>(n, w, V, ldv, partial); break;
+  case K: k_multi_dot<K, T><<<nb, RT, 0, s>>>(n, w, V, ldv, partial); break;
     GMG_CASE(1) GMG_CASE(2) GMG_CASE(3) GMG_CASE(4) GMG_CASE(5) GMG_CASE(6) GMG_CASE(7) GMG_CASE(8)
 #undef GMG_CASE
     default:
@@ -213,17 +224,26 @@ cudaError_t launch_finalize_norm(const double* partial, int nblocks, double* out
   return cudaGetLastError();
 }
 
-cudaError_t launch_multi_axpy(size_t n, double* w, const double* V, size_t ldv, int k, const double* h,
-                              cudaStream_t s) {
+template <typename T>
+cudaError_t launch_multi_axpy(size_t n, T* w, const T* V, size_t ldv, int k, const double* h, cudaStream_t s) {
   if (k < 1 || k > 64) return cudaErrorInvalidValue;
-  k_multi_axpy<<<reduce_blocks(n), RT, 0, s>>>(n, w, V, ldv, k, h);
+  k_multi_axpy<T><<<reduce_blocks(n), RT, 0, s>>>(n, w, V, ldv, k, h);
   return cudaGetLastError();
 }
 
-cudaError_t launch_scale(size_t n, const double* src, double* dst, const double* scale, cudaStream_t s) {
-  k_scale<<<flat_blocks(n), 256, 0, s>>>(n, src, dst, scale);
+template <typename T>
+cudaError_t launch_scale(size_t n, const T* src, T* dst, const double* scale, cudaStream_t s) {
+  k_scale<T><<<flat_blocks(n), 256, 0, s>>>(n, src, dst, scale);
   return cudaGetLastError();
 }
+
+#define GMG_INST(T)                                                                                           \
+  template cudaError_t launch_multi_dot<T>(size_t, const T*, const T*, size_t, int, double*, cudaStream_t);  \
+  template cudaError_t launch_multi_axpy<T>(size_t, T*, const T*, size_t, int, const double*, cudaStream_t); \
+  template cudaError_t launch_scale<T>(size_t, const T*, T*, const double*, cudaStream_t);
+GMG_INST(float)
+GMG_INST(double)
+#undef GMG_INST
 
 cudaError_t launch_scale_value(size_t n, const double* src, double* dst, double alpha, cudaStream_t s) {
   k_scale_value<<<flat_blocks(n), 256, 0, s>>>(n, src, dst, alpha);
@@ -254,6 +274,11 @@ cudaError_t launch_finalize_check(const double* partial, int nblocks, double* ou
 
 cudaError_t launch_hash_vector(size_t n, double* u, cudaStream_t s) {
   k_hash_vector<<<flat_blocks(n), 256, 0, s>>>(n, u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hash_vector(size_t n, float* u, cudaStream_t s) {
+  k_hash_vector_f32<<<flat_blocks(n), 256, 0, s>>>(n, u);
   return cudaGetLastError();
 }
 

@@ -212,6 +212,10 @@ Grid3 make_grid(int nx, int ny, int nz, double lx, double ly, double lz) {
   g.cy = 0.5 / (hy * hy);
   g.cz = 0.5 / (hz * hz);
   g.cp = 2.0 / (hz * hz);
+  g.fx = (float)g.cx;
+  g.fy = (float)g.cy;
+  g.fz = (float)g.cz;
+  g.fp = (float)g.cp;
   return g;
 }
 

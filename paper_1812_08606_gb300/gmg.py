@@ -34,6 +34,8 @@ GMG_PC_JACOBI = 1
 GMG_PC_IDENTITY = 2
 GMG_ORTH_CGS2 = 0
 GMG_ORTH_MGS = 1
+GMG_OUTER_FP64 = 0
+GMG_OUTER_DOUBLE_FLOAT = 1
 
 
 class gmg_params(ctypes.Structure):
@@ -45,6 +47,7 @@ class gmg_params(ctypes.Structure):
         ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double), ("eig_steps", ctypes.c_int),
         ("eig_hi", ctypes.c_double), ("eig_lo", ctypes.c_double), ("precision", ctypes.c_int),
         ("prolongation", ctypes.c_int), ("smoother_pc", ctypes.c_int), ("orthogonalization", ctypes.c_int),
+        ("outer_arith", ctypes.c_int),
     ]
 
 
@@ -91,6 +94,7 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_double)]),
     "gmg_level_coefficient": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "gmg_apply_preconditioner": (ctypes.c_int, [_P, _P, _P]),
+    "gmg_apply_outer": (ctypes.c_int, [_P, _P, _P]),
     "gmg_level_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "gmg_level_smooth": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int]),
     "gmg_level_smoother_pc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
@@ -310,6 +314,11 @@ def gmg_level_coefficient(ctx: Context, level: int, out: torch.Tensor):
 def gmg_apply_preconditioner(ctx: Context, v: torch.Tensor, z: torch.Tensor):
     _check(load().gmg_apply_preconditioner(ctx.handle, _dev(v, numel=ctx.n, name="v"),
                                            _dev(z, numel=ctx.n, name="z")), "gmg_apply_preconditioner")
+
+
+def gmg_apply_outer(ctx: Context, z: torch.Tensor, w: torch.Tensor):
+    _check(load().gmg_apply_outer(ctx.handle, _dev(z, torch.float32, ctx.n, "z"), _dev(w, numel=ctx.n, name="w")),
+           "gmg_apply_outer")
 
 
 def gmg_level_apply(ctx: Context, level: int, x: torch.Tensor, y: torch.Tensor):

@@ -95,6 +95,37 @@ def test_apply_operator_and_rhs_fp64(shape, lengths):
     np.testing.assert_allclose(_np(b), O.assemble_rhs(grid, a, f, 0.3, -2.0), rtol=1e-14, atol=1e-12)
 
 
+@pytest.mark.parametrize("arith,tol", [(gmg.GMG_OUTER_DOUBLE_FLOAT, 2e-14), (gmg.GMG_OUTER_FP64, 1e-15)])
+@pytest.mark.parametrize("shape", [RAGGED, (64, 64, 64), (10, 8, 8)])
+def test_outer_arnoldi_product(arith, tol, shape):
+    """w = A z_j for an FP32 z_j (the mixed-precision Arnoldi product) against
+    the FP64 oracle operator on the same z; double-float arithmetic keeps a
+    48-bit significand, so it agrees to ~1e-14."""
+    a = make_inputs("twochannel512", shape=shape)["a"] if shape[0] >= 16 else random_coefficient(240, shape, 1e4)
+    z = random_field(241, shape).astype(np.float32)
+    cm = 2 if shape == RAGGED else 4
+    p = _params(shape, coarse_min=cm, precision=gmg.GMG_PREC_MIXED, outer_arith=arith)
+    ctx = gmg.gmg_setup(p, _t(a))
+    w = torch.empty(shape, dtype=torch.float64, device=DEV)
+    gmg.gmg_apply_outer(ctx, _t(z, torch.float32), w)
+    ref = O.apply_operator(_ogrid(shape), a, z.astype(np.float64))
+    err = np.abs(_np(w) - ref).max() / np.abs(ref).max()
+    assert err < tol, err
+
+
+def test_mixed_eigen_bounds_close_to_fp64():
+    """The mixed set-up runs its eigen estimate in FP32 (the bounds only steer
+    the FP32 smoother); they agree with the FP64 oracle's to ~1e-5."""
+    shape = RAGGED
+    a = random_coefficient(242, shape, contrast=1e3)
+    p = _params(shape, coarse_min=2, precision=gmg.GMG_PREC_MIXED)
+    ctx = gmg.gmg_setup(p, _t(a))
+    hier = O.build_hierarchy(_ogrid(shape), a, _oracle_hierarchy(a, p))
+    for lev in range(1, gmg.gmg_num_levels(ctx)):
+        info = gmg.gmg_level_info(ctx, lev)
+        assert info["lam_max"] == pytest.approx(hier.levels[lev].lam_max, rel=1e-4)
+
+
 @pytest.mark.parametrize("prec", [gmg.GMG_PREC_FP64, gmg.GMG_PREC_MIXED])
 def test_level_coefficients_and_operators(prec):
     shape = RAGGED
@@ -266,12 +297,13 @@ def test_fp64_solve_matches_oracle(workload, n, orth):
     assert _rel(out, ref) < 1e-10
 
 
-@pytest.mark.parametrize("workload,n,kappa", [("const32", 32, None), ("channel128", 64, None),
-                                              ("channel256", 64, 1e4), ("twochannel512", 64, None)])
-def test_mixed_solve_residual_and_error(workload, n, kappa):
+@pytest.mark.parametrize("workload,n,kappa,arith", [("const32", 32, None, 1), ("channel128", 64, None, 1),
+                                                    ("channel256", 64, 1e4, 1), ("twochannel512", 64, None, 1),
+                                                    ("twochannel512", 64, None, 0)])
+def test_mixed_solve_residual_and_error(workload, n, kappa, arith):
     inp = make_inputs(workload, n=n, kappa=kappa)
     shape = inp["a"].shape
-    p = _params(shape, precision=gmg.GMG_PREC_MIXED)
+    p = _params(shape, precision=gmg.GMG_PREC_MIXED, outer_arith=arith)
     ref, rinfo, _ = O.solve(_oracle_hierarchy(inp["a"], p), inp["a"], inp["f"])
     ctx = gmg.gmg_setup(p, _t(inp["a"]))
     phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
