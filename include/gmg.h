@@ -111,6 +111,10 @@ typedef struct gmg_params {
   int orthogonalization;       /* gmg_orthogonalization                      */
   int outer_arith;             /* gmg_outer_arith: arithmetic of the Arnoldi
                                   product w = A z_j in GMG_PREC_MIXED        */
+  int smoother_kernel;         /* 0: one fused pass per Chebyshev step where
+                                  the level allows it (FP32, SGS, nx >= 32,
+                                  ny >= 16, nz >= 8); 1: separate residual
+                                  and half-sweep kernels everywhere          */
 } gmg_params;
 
 typedef struct gmg_solve_info {

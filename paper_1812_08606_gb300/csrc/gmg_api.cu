@@ -180,7 +180,7 @@ enum KernelClass : int {
   K_CHEB_F64, K_CHEB_F32, K_RESTRICT_F64, K_RESTRICT_F32, K_PROLONG_F64, K_PROLONG_F32, K_COARSE_F64,
   K_COARSE_F32, K_DOT, K_FINALIZE, K_AXPY, K_SCALE, K_UPDATE_X, K_CAST, K_COPY, K_RHS, K_FIELD, K_ADJOINT,
   K_COARSEN, K_COEF_CHECK, K_HASH, K_COARSE_ASSEMBLE, K_COARSE_FACTOR, K_DOT_F32, K_AXPY_F32, K_APPLY_DF64,
-  K_SPLIT, NK
+  K_SPLIT, K_CHEB_FUSED, NK
 };
 static const char* const kKernelNames[NK] = {
     "apply_f64", "apply_outer_f64a_f32x", "apply_f32", "residual_f64", "residual_f32", "sgs_half_f64",
@@ -188,7 +188,7 @@ static const char* const kKernelNames[NK] = {
     "prolong_add_f64", "prolong_add_f32", "coarse_apply_f64", "coarse_apply_f32", "multi_dot", "finalize",
     "multi_axpy", "scale", "update_solution", "cast", "copy", "rhs", "field", "adjoint_grad", "coarsen_coef",
     "coef_check", "hash_vector", "coarse_assemble", "coarse_factor", "multi_dot_f32", "multi_axpy_f32",
-    "apply_outer_df64", "split_coef"};
+    "apply_outer_df64", "split_coef", "cheb_sgs_fused_f32"};
 
 struct ProfPending {
   int cls;
@@ -205,6 +205,8 @@ struct LevelData {
   float2* a2 = nullptr;  // finest level, mixed + double-float outer product: (hi, lo) split of a64
   DfCoef dc{};
   void *x = nullptr, *b = nullptr, *r = nullptr, *z = nullptr, *d = nullptr;  // level precision
+  float* x2 = nullptr;  // second x buffer of the fused smoother (ping-pong), when fused
+  bool fused = false;
   double lam_max = 0, lam_min = 0, lam_hat = 0;
 };
 
@@ -438,6 +440,11 @@ gmg_status prof_apply_df64(gmg_ctx* c, const Grid3& g, const DfCoef& dc, const f
                            cudaStream_t s) {
   GMG_RUN(K_APPLY_DF64, 20.0 * g.n(), launch_apply_df64(g, dc, a2, z, w, s));
 }
+gmg_status prof_cheb_sgs_fused(gmg_ctx* c, const Grid3& g, const float* a, const float* b, const float* xin,
+                               float* xout, float* d, double c1, double c2, int flags, cudaStream_t s) {
+  const double words = 2.0 + (xin ? 1.0 : 0.0) + ((flags & CHEB_FIRST) ? 0.0 : 1.0) + 2.0;
+  GMG_RUN(K_CHEB_FUSED, 4.0 * words * g.n(), launch_cheb_sgs_fused(g, a, b, xin, xout, d, c1, c2, flags, s));
+}
 gmg_status prof_split(gmg_ctx* c, size_t n, const double* a, float2* a2, cudaStream_t s) {
   GMG_RUN(K_SPLIT, 16.0 * n, launch_split(n, a, a2, s));
 }
@@ -459,6 +466,7 @@ gmg_status validate(const gmg_params* p, int* nlevels) {
   if (p->smoother_pc < 0 || p->smoother_pc > 2) return GMG_ERR_ARG;
   if (p->orthogonalization != 0 && p->orthogonalization != 1) return GMG_ERR_ARG;
   if (p->outer_arith != GMG_OUTER_FP64 && p->outer_arith != GMG_OUTER_DOUBLE_FLOAT) return GMG_ERR_ARG;
+  if (p->smoother_kernel != 0 && p->smoother_kernel != 1) return GMG_ERR_ARG;
   if ((double)p->nx * p->ny * p->nz > 4.0e9) return GMG_ERR_ARG;
   int nx = p->nx, ny = p->ny, nz = p->nz, L = 1;
   while (std::min(nx, std::min(ny, nz)) > p->coarse_min) {
@@ -681,12 +689,54 @@ gmg_status smooth(gmg_ctx* c, int l, const T* b, T* x, bool x_is_zero) {
   return GMG_OK;
 }
 
+// cheb_steps fused Chebyshev steps on an FP32 level, x_in = xin (null: 0).
+// Step st writes `target` if (steps-1-st) is even, else `alt`, so the last
+// step writes `target`; the first step's output buffer must differ from xin.
+gmg_status smooth_fused(gmg_ctx* c, int l, const float* b, const float* xin, float* target, float* alt) {
+  const LevelData& L = c->lev[l];
+  const double theta = 0.5 * (L.lam_max + L.lam_min), delta = 0.5 * (L.lam_max - L.lam_min);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  const int s = c->p.cheb_steps;
+  const float* cur = xin;
+  for (int st = 0; st < s; ++st) {
+    double c1 = 0.0, c2 = 1.0 / theta;
+    int flags = CHEB_UPDATE;
+    if (st == 0) {
+      flags |= CHEB_FIRST;
+    } else {
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      c1 = rho_new * rho;
+      c2 = 2.0 * rho_new / delta;
+      rho = rho_new;
+    }
+    float* dst = ((s - 1 - st) % 2 == 0) ? target : alt;
+    if (dst == cur) return GMG_ERR_ARG;
+    CKS(prof_cheb_sgs_fused(c, L.g, L.a32, b, cur, dst, (float*)L.d, c1, c2, flags, c->s));
+    cur = dst;
+  }
+  return GMG_OK;
+}
+
 template <typename T>
 gmg_status vcycle(gmg_ctx* c, int l, const T* b, T* x) {
   if (l == 0) return (prof_coarse_apply<T>(c, c->nc, coarse_inv<T>(c), b, x, c->s));
   const LevelData& L = c->lev[l];
   const LevelData& Lc = c->lev[l - 1];
   const T* a = level_a<T>(L);
+  if constexpr (sizeof(T) == 4) {
+    if (L.fused) {
+      // pre-smoothing ends in the buffer that post-smoothing does not write first
+      float* U = L.x2;
+      float* pre = (c->p.cheb_steps % 2) ? U : x;
+      float* pre_alt = (pre == U) ? x : U;
+      CKS(smooth_fused(c, l, b, nullptr, pre, pre_alt));
+      CKS(prof_residual_restrict<float>(c, L.g, a, b, pre, (float*)Lc.b, c->s));
+      CKS(vcycle<float>(c, l - 1, (const float*)Lc.b, (float*)Lc.x));
+      CKS(prof_prolong_add<float>(c, L.g, (const float*)Lc.x, pre, c->p.prolongation, c->s));
+      return smooth_fused(c, l, b, pre, x, U);
+    }
+  }
   CKS(smooth<T>(c, l, b, x, true));
   CKS(prof_residual_restrict<T>(c, L.g, a, b, x, (T*)Lc.b, c->s));
   CKS(vcycle<T>(c, l - 1, (const T*)Lc.b, (T*)Lc.x));
@@ -865,6 +915,7 @@ void gmg_default_params(gmg_params* p, int nx, int ny, int nz) {
   p->smoother_pc = GMG_PC_SGS;
   p->orthogonalization = GMG_ORTH_CGS2;
   p->outer_arith = GMG_OUTER_DOUBLE_FLOAT;
+  p->smoother_kernel = 0;
 }
 
 const char* gmg_status_string(gmg_status s) {
@@ -933,6 +984,9 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
     }
     if (!top && (st = dev_alloc(c, &D.x, D.n * c->esz)) != GMG_OK) return fail(st);
     if ((!top || c->mixed) && (st = dev_alloc(c, &D.b, D.n * c->esz)) != GMG_OK) return fail(st);
+    D.fused = c->mixed && l > 0 && p->smoother_pc == GMG_PC_SGS && p->smoother_kernel == 0 &&
+              fused_smoother_eligible(D.g);
+    if (D.fused && (st = dalloc(c, &D.x2, D.n)) != GMG_OK) return fail(st);
     if (l > 0 || L == 1) {
       if ((st = dev_alloc(c, &D.r, D.n * c->esz)) != GMG_OK) return fail(st);
       if ((st = dev_alloc(c, &D.z, D.n * c->esz)) != GMG_OK) return fail(st);
@@ -1097,6 +1151,13 @@ gmg_status gmg_level_apply(gmg_ctx* c, int level, const void* x, void* y) {
 gmg_status gmg_level_smooth(gmg_ctx* c, int level, const void* b, void* x, int x_is_zero) {
   LevelData* L = level_ptr(c, level);
   if (!L || level == 0 || !b || !x || !L->r) return GMG_ERR_ARG;
+  if (c->mixed && L->fused) {
+    float* X = (float*)x;
+    if (x_is_zero) return smooth_fused(c, level, (const float*)b, nullptr, X, L->x2);
+    if (c->p.cheb_steps % 2 == 0) return smooth_fused(c, level, (const float*)b, X, X, L->x2);
+    CK(cudaMemcpyAsync(L->x2, X, L->n * sizeof(float), cudaMemcpyDeviceToDevice, c->s));
+    return smooth_fused(c, level, (const float*)b, L->x2, X, L->x2);
+  }
   if (c->mixed) return smooth<float>(c, level, (const float*)b, (float*)x, x_is_zero != 0);
   return smooth<double>(c, level, (const double*)b, (double*)x, x_is_zero != 0);
 }

@@ -47,7 +47,7 @@ class gmg_params(ctypes.Structure):
         ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double), ("eig_steps", ctypes.c_int),
         ("eig_hi", ctypes.c_double), ("eig_lo", ctypes.c_double), ("precision", ctypes.c_int),
         ("prolongation", ctypes.c_int), ("smoother_pc", ctypes.c_int), ("orthogonalization", ctypes.c_int),
-        ("outer_arith", ctypes.c_int),
+        ("outer_arith", ctypes.c_int), ("smoother_kernel", ctypes.c_int),
     ]
 
 

@@ -194,6 +194,48 @@ def test_smoother_preconditioner_and_chebyshev(prec, pc):
         oa = O.coarsen_coefficient(oa)
 
 
+@pytest.mark.parametrize("shape,cm", [((48, 40, 72), 5), ((64, 64, 64), 4), (RAGGED, 2)])
+def test_fused_smoother_matches_separate_kernels_and_oracle(shape, cm):
+    """The fused one-pass Chebyshev + red-black SSOR step against the
+    separate residual / half-sweep kernels and the oracle, on grids with
+    partial 64 x 16 tiles and several z-chunks."""
+    a = make_inputs("twochannel512", shape=shape)["a"]
+    ctxs = [gmg.gmg_setup(_params(shape, coarse_min=cm, smoother_kernel=k), _t(a)) for k in (0, 1)]
+    oa = a
+    for lev in range(gmg.gmg_num_levels(ctxs[0]) - 1, 0, -1):
+        info = gmg.gmg_level_info(ctxs[0], lev)
+        s = info["shape"]
+        b = random_field(300 + lev, s).astype(np.float32)
+        x0 = random_field(310 + lev, s).astype(np.float32)
+        for x_is_zero in (True, False):
+            outs = []
+            for ctx in ctxs:
+                x = _t(x0, torch.float32)
+                gmg.gmg_level_smooth(ctx, lev, _t(b, torch.float32), x, x_is_zero)
+                outs.append(_np(x))
+            ref = O.chebyshev_smooth(_ogrid(s), oa.astype(np.float32).astype(np.float64), b.astype(np.float64),
+                                     None if x_is_zero else x0.astype(np.float64), info["lam_max"],
+                                     info["lam_min"], 3, "sgs")
+            assert _rel(outs[0], outs[1]) < 1e-5, (lev, x_is_zero)
+            assert _rel(outs[0], ref) < 1e-4, (lev, x_is_zero)
+        oa = O.coarsen_coefficient(oa)
+    v = random_field(320, shape)
+    zs = []
+    for ctx in ctxs:
+        z = torch.empty(shape, dtype=torch.float64, device=DEV)
+        gmg.gmg_apply_preconditioner(ctx, _t(v), z)
+        zs.append(_np(z))
+    assert _rel(zs[0], zs[1]) < 1e-5
+    f = make_inputs("twochannel512", shape=shape)["f"]
+    its = []
+    for ctx in ctxs:
+        phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+        info = gmg.fgmres_solve(ctx, _t(f), phi)
+        assert info.converged and _true_residual(shape, ctx.params, a, f, _np(phi)) < 1e-8
+        its.append(info.iterations)
+    assert abs(its[0] - its[1]) <= 1
+
+
 def test_eigen_bounds_match_oracle():
     shape = RAGGED
     a = random_coefficient(140, shape, contrast=1e3)
