@@ -267,6 +267,31 @@ int gmg_profile_num_kernels(void);
 gmg_status gmg_profile_get(gmg_ctx* ctx, int k, const char** name, long long* launches,
                            long long* timed_launches, double* total_ms, double* total_bytes);
 
+/* ---- Coarsest-grid direct solve without allocation ----
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory (device memory wholly reserved by a
+ * framework's pool, real-time loops that must not take cudaMalloc's implicit
+ * device synchronisation or out-of-memory failure, code under a fixed memory
+ * budget).  It does what gmg_setup does for the coarsest grid and what
+ * gmg_coarse_solve then applies, in FP64: assemble the dense operator of the
+ * grid described by p (nx, ny, nz, lx, ly, lz; other fields ignored) from the
+ * cell coefficient a_dev, factor it (Cholesky), and write x = A^{-1} b.
+ * a_dev, b_dev, x_dev: FP64 device arrays of nx*ny*nz elements, caller-owned;
+ * stream: cudaStream_t or NULL.
+ * Scratch: one file-scope __device__ array sized for
+ * GMG_NOALLOC_MAX_UNKNOWNS unknowns (about 6 MB), held by every GPU that
+ * loads the library until the process exits; the call makes no device or
+ * pinned-host allocation.  The array's address is looked up on the first call
+ * made on each device (with that device current).  Every call overwrites the
+ * whole array; calls that overlap on the GPU race on it.
+ * Errors: GMG_ERR_ARG if nx*ny*nz > GMG_NOALLOC_MAX_UNKNOWNS or an argument is
+ * invalid, GMG_ERR_BREAKDOWN if the operator is not positive definite,
+ * GMG_ERR_CUDA.  Synchronises the stream once (to read the factorisation
+ * status). */
+#define GMG_NOALLOC_MAX_UNKNOWNS 512
+gmg_status gmg_coarse_solve_noalloc(const gmg_params* p, const double* a_dev, const double* b_dev,
+                                    double* x_dev, void* stream);
+
 /* Test hook: make the n-th next device allocation of the library fail
  * (n >= 1), as if the device were out of memory; n = 0 disables it.  Lets
  * the host-side error paths be tested without exhausting a shared GPU. */

@@ -103,6 +103,7 @@ _SIGS = {
     "gmg_coarse_solve": (ctypes.c_int, [_P, _P, _P]),
     "gmg_hessenberg_max_real_eig": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gmg_test_fail_allocation_after": (None, [ctypes.c_int]),
+    "gmg_coarse_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(gmg_params), _P, _P, _P, _P]),
     "gmg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "gmg_profile_reset": (ctypes.c_int, [_P]),
     "gmg_profile_num_kernels": (ctypes.c_int, []),
@@ -398,3 +399,15 @@ def profile(ctx: Context) -> list:
     """All kernel classes with at least one launch, sorted by time."""
     rows = [gmg_profile_get(ctx, k) for k in range(gmg_profile_num_kernels())]
     return sorted((r for r in rows if r["launches"]), key=lambda r: -r["ms"])
+
+
+GMG_NOALLOC_MAX_UNKNOWNS = 512
+
+
+def gmg_coarse_solve_noalloc(params: gmg_params, a: torch.Tensor, b: torch.Tensor, x: torch.Tensor, stream=None):
+    """Dense direct solve A(a) x = b on a small grid (<= 512 cells) with no
+    device allocation: the scratch lives in a fixed array inside libgmg."""
+    n = params.nx * params.ny * params.nz
+    _check(load().gmg_coarse_solve_noalloc(ctypes.byref(params), _dev(a, numel=n, name="a"),
+                                           _dev(b, numel=n, name="b"), _dev(x, numel=n, name="x"),
+                                           _stream_ptr(stream)), "gmg_coarse_solve_noalloc")
