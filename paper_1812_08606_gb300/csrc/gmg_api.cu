@@ -180,7 +180,7 @@ enum KernelClass : int {
   K_CHEB_F64, K_CHEB_F32, K_RESTRICT_F64, K_RESTRICT_F32, K_PROLONG_F64, K_PROLONG_F32, K_COARSE_F64,
   K_COARSE_F32, K_DOT, K_FINALIZE, K_AXPY, K_SCALE, K_UPDATE_X, K_CAST, K_COPY, K_RHS, K_FIELD, K_ADJOINT,
   K_COARSEN, K_COEF_CHECK, K_HASH, K_COARSE_ASSEMBLE, K_COARSE_FACTOR, K_DOT_F32, K_AXPY_F32, K_APPLY_DF64,
-  K_SPLIT, K_CHEB_FUSED, NK
+  K_SPLIT, K_CHEB_FUSED, K_CGS_DOTS, K_CGS_DOTS_F32, K_CGS_UPDATE, K_CGS_UPDATE_F32, NK
 };
 static const char* const kKernelNames[NK] = {
     "apply_f64", "apply_outer_f64a_f32x", "apply_f32", "residual_f64", "residual_f32", "sgs_half_f64",
@@ -188,7 +188,8 @@ static const char* const kKernelNames[NK] = {
     "prolong_add_f64", "prolong_add_f32", "coarse_apply_f64", "coarse_apply_f32", "multi_dot", "finalize",
     "multi_axpy", "scale", "update_solution", "cast", "copy", "rhs", "field", "adjoint_grad", "coarsen_coef",
     "coef_check", "hash_vector", "coarse_assemble", "coarse_factor", "multi_dot_f32", "multi_axpy_f32",
-    "apply_outer_df64", "split_coef", "cheb_sgs_fused_f32"};
+    "apply_outer_df64", "split_coef", "cheb_sgs_fused_f32", "cgs_dots", "cgs_dots_f32", "cgs_update",
+    "cgs_update_f32"};
 
 struct ProfPending {
   int cls;
@@ -380,6 +381,18 @@ gmg_status prof_finalize_check(gmg_ctx* c, const double* partial, int nblocks, d
   GMG_RUN(K_FINALIZE, 16.0 * nblocks, launch_finalize_check(partial, nblocks, out, s));
 }
 template <typename T>
+gmg_status prof_cgs_dots(gmg_ctx* c, size_t n, const T* w, const T* V, size_t ldv, int k, const double* h,
+                         double* partial, cudaStream_t s) {
+  GMG_RUN(is_f32<T>() ? K_CGS_DOTS_F32 : K_CGS_DOTS, (double)sizeof(T) * n * (1 + k),
+          launch_cgs_dots<T>(n, w, V, ldv, k, h, partial, s));
+}
+template <typename T>
+gmg_status prof_cgs_update(gmg_ctx* c, size_t n, T* w, const T* V, size_t ldv, int k, const double* h1,
+                           const double* h2, double* partial, cudaStream_t s) {
+  GMG_RUN(is_f32<T>() ? K_CGS_UPDATE_F32 : K_CGS_UPDATE, (double)sizeof(T) * n * (2 + k),
+          launch_cgs_update<T>(n, w, V, ldv, k, h1, h2, partial, s));
+}
+template <typename T>
 gmg_status prof_multi_axpy(gmg_ctx* c, size_t n, T* w, const T* V, size_t ldv, int k, const double* h,
                            cudaStream_t s) {
   GMG_RUN(is_f32<T>() ? K_AXPY_F32 : K_AXPY, (double)sizeof(T) * n * (k + 2),
@@ -510,6 +523,15 @@ gmg_status orthogonalize(gmg_ctx* c, size_t n, const T* V, size_t ld, int k, T* 
       CKS(prof_finalize(c, c->partial, nb, 1, c->dscal + SL_H1 + i, 0, c->s));
       CKS(prof_multi_axpy<T>(c, n, w, V + (size_t)i * ld, ld, 1, c->dscal + SL_H1 + i, c->s));
     }
+  } else if (k <= kCgsMaxVectors) {
+    // three fused passes: h1 = V^T w; h2 = V^T (w - V h1); w -= V (h1 + h2) with ||w||^2
+    CKS(prof_cgs_dots<T>(c, n, w, V, ld, k, nullptr, c->partial, c->s));
+    CKS(prof_finalize(c, c->partial, nb, k, c->dscal + SL_H1, 0, c->s));
+    CKS(prof_cgs_dots<T>(c, n, w, V, ld, k, c->dscal + SL_H1, c->partial, c->s));
+    CKS(prof_finalize(c, c->partial, nb, k, c->dscal + SL_H2, 0, c->s));
+    CKS(prof_cgs_update<T>(c, n, w, V, ld, k, c->dscal + SL_H1, c->dscal + SL_H2, c->partial, c->s));
+    CKS(prof_finalize_norm(c, c->partial, nb, c->dscal + SL_NORM, c->s));
+    return GMG_OK;
   } else {
     for (int pass = 0; pass < 2; ++pass) {
       double* hslot = c->dscal + (pass == 0 ? SL_H1 : SL_H2);
@@ -580,9 +602,18 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
   std::vector<double> H((size_t)(steps + 1) * steps, 0.0);
   int m = steps;
   std::vector<double> col(steps + 2);
+  // On levels with the fused smoother, one fused step forms the product:
+  // with b = 0, x_in = v and c2 = -1 its direction d equals B^{-1}(A v).
+  const bool fused_mv = sizeof(T) == 4 && L.fused;
+  if (fused_mv) CK(cudaMemsetAsync(L.b, 0, n * sizeof(float), c->s));
   for (int j = 0; j < steps; ++j) {
-    CKS(prof_apply<T, T, T>(c, L.g, a, V + (size_t)j * n, t1, c->s));
-    CKS(smoother_pc<T>(c, L, t1, t2));
+    if (fused_mv) {
+      CKS(prof_cheb_sgs_fused(c, L.g, L.a32, (const float*)L.b, (const float*)(V + (size_t)j * n), L.x2,
+                              (float*)t2, 0.0, -1.0, CHEB_UPDATE | CHEB_FIRST, c->s));
+    } else {
+      CKS(prof_apply<T, T, T>(c, L.g, a, V + (size_t)j * n, t1, c->s));
+      CKS(smoother_pc<T>(c, L, t1, t2));
+    }
     CKS(orthogonalize<T>(c, n, V, n, j + 1, t2));
     CKS(read_column(c, j + 1, col.data()));
     for (int i = 0; i <= j + 1; ++i) {
@@ -1001,7 +1032,7 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
   if ((st = dev_alloc(c, &c->Z, nz_vec * N * c->esz)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->w, N)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->bvec, N)) != GMG_OK) return fail(st);
-  if ((st = dalloc(c, &c->partial, (size_t)1024 * 16)) != GMG_OK) return fail(st);
+  if ((st = dalloc(c, &c->partial, (size_t)1024 * 64)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->dscal, N_SCAL)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->cA, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->cW, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);

@@ -174,6 +174,16 @@ int reduce_blocks(size_t n);  // number of partial sums a reduction over n produ
 template <typename T>
 cudaError_t launch_multi_dot(size_t n, const T* w, const T* V, size_t ldv, int k, double* partial,
                              cudaStream_t s);
+// Fused classical Gram-Schmidt passes over k <= 32 vectors: partial sums of
+// h = V^T w (h_prev null) or of h = V^T (w - V h_prev); and w -= V (h1 + h2)
+// with partial sums of ||w||^2.  Partials: [block * k + i] / [block].
+constexpr int kCgsMaxVectors = 32;
+template <typename T>
+cudaError_t launch_cgs_dots(size_t n, const T* w, const T* V, size_t ldv, int k, const double* h_prev,
+                            double* partial, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cgs_update(size_t n, T* w, const T* V, size_t ldv, int k, const double* h1, const double* h2,
+                              double* partial, cudaStream_t s);
 // out[i] = sum_b partial[b*k + i] (+ out[i] if accumulate) for i < k; one block per output.
 cudaError_t launch_finalize(const double* partial, int nblocks, int k, double* out, int accumulate,
                             cudaStream_t s);

@@ -13,6 +13,7 @@ namespace {
 constexpr int RT = 256;          // reduction block size
 constexpr int MAX_RBLOCKS = 1024;
 
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -54,6 +55,63 @@ __global__ void __launch_bounds__(RT) k_multi_dot(size_t n, const T* __restrict_
     const double t = block_sum<RT>((double)acc[i], sh);
     if (threadIdx.x == 0) partial[(size_t)blockIdx.x * K + i] = t;
   }
+}
+
+// ---- Fused classical Gram-Schmidt passes (K <= CGS_KMAX vectors) ----
+// K is a template parameter: a loop over a runtime count would issue every
+// unrolled (predicated-off) load and FMA, which on GB300's 1/64-rate FP64 pipe
+// costs as much as the real ones.
+// Pass 1: partial sums of h1 = V^T w.  Pass 2 (h != null): partial sums of
+// h2 = V^T (w - V h), forming w - V h on the fly without storing it.
+template <int K, typename T>
+__global__ void __launch_bounds__(RT) k_cgs_dots(size_t n, const T* __restrict__ w, const T* __restrict__ V,
+                                                 size_t ldv, const double* __restrict__ h,
+                                                 double* __restrict__ partial) {
+  __shared__ double sh[RT / 32];
+  __shared__ T hs[K];
+  if (threadIdx.x < K) hs[threadIdx.x] = h ? (T)h[threadIdx.x] : (T)0;
+  __syncthreads();
+  T acc[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) acc[i] = (T)0;
+  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
+    T v[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) v[i] = V[i * ldv + p];
+    T wp = w[p];
+    if (h) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) wp = fma(-hs[i], v[i], wp);
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) acc[i] = fma(wp, v[i], acc[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const double t = block_sum<RT>((double)acc[i], sh);
+    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * K + i] = t;
+  }
+}
+
+// Pass 3: w -= V (h1 + h2) in place, and partial sums of ||w||^2.
+template <int K, typename T>
+__global__ void __launch_bounds__(RT) k_cgs_update(size_t n, T* __restrict__ w, const T* __restrict__ V, size_t ldv,
+                                                   const double* __restrict__ h1, const double* __restrict__ h2,
+                                                   double* __restrict__ partial) {
+  __shared__ double sh[RT / 32];
+  __shared__ T hs[K];
+  if (threadIdx.x < K) hs[threadIdx.x] = (T)(h1[threadIdx.x] + h2[threadIdx.x]);
+  __syncthreads();
+  T acc = (T)0;
+  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
+    T wp = w[p];
+#pragma unroll
+    for (int i = 0; i < K; ++i) wp = fma(-hs[i], V[i * ldv + p], wp);
+    w[p] = wp;
+    acc = fma(wp, wp, acc);
+  }
+  const double t = block_sum<RT>((double)acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
 __global__ void __launch_bounds__(RT) k_finalize(const double* __restrict__ partial, int nblocks, int k,
@@ -237,7 +295,45 @@ cudaError_t launch_scale(size_t n, const T* src, T* dst, const double* scale, cu
   return cudaGetLastError();
 }
 
+#define GMG_CASES32(X)                                                                                   \
+  X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18) X(19) \
+  X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31) X(32)
+
+template <typename T>
+cudaError_t launch_cgs_dots(size_t n, const T* w, const T* V, size_t ldv, int k, const double* h, double* partial,
+                            cudaStream_t s) {
+  const int nb = reduce_blocks(n);
+  switch (k) {
+#define GMG_CASE(K) \
+  case K: k_cgs_dots<K, T><<<nb, RT, 0, s>>>(n, w, V, ldv, h, partial); break;
+    GMG_CASES32(GMG_CASE)
+#undef GMG_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cgs_update(size_t n, T* w, const T* V, size_t ldv, int k, const double* h1, const double* h2,
+                              double* partial, cudaStream_t s) {
+  const int nb = reduce_blocks(n);
+  switch (k) {
+#define GMG_CASE(K) \
+  case K: k_cgs_update<K, T><<<nb, RT, 0, s>>>(n, w, V, ldv, h1, h2, partial); break;
+    GMG_CASES32(GMG_CASE)
+#undef GMG_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 #define GMG_INST(T)                                                                                           \
+  template cudaError_t launch_cgs_dots<T>(size_t, const T*, const T*, size_t, int, const double*, double*,   \
+                                          cudaStream_t);                                                     \
+  template cudaError_t launch_cgs_update<T>(size_t, T*, const T*, size_t, int, const double*, const double*, \
+                                            double*, cudaStream_t);                                          \
   template cudaError_t launch_multi_dot<T>(size_t, const T*, const T*, size_t, int, double*, cudaStream_t);  \
   template cudaError_t launch_multi_axpy<T>(size_t, T*, const T*, size_t, int, const double*, cudaStream_t); \
   template cudaError_t launch_scale<T>(size_t, const T*, T*, const double*, cudaStream_t);

@@ -6,18 +6,21 @@
 //   z = B^{-1} r:  red  z = r / D,  black z = (r + N z)/D,  red z = (r + N z)/D
 //   d = c1 d + c2 z   (d = c2 z on the first step),   x_out = x_in + d
 //
-// Each thread block owns a 56 x 16 tile of the xy-plane and marches through a
-// range of z-planes.  Shared-memory rings hold the last planes of x_in and a
-// on the tile plus a 3-cell halo, and of r and z on the tile plus a 2-cell
-// halo.  With plane kk just loaded, the block forms r (and the red z) on plane
-// kk-1 over the tile + 2 halo, the black z on plane kk-2 over the tile + 1
-// halo, and the final red z and the update on plane kk-3 over the tile.  The
-// halos are recomputed by neighbouring blocks instead of exchanged, so blocks
-// never wait on one another; x_out is a different buffer from x_in, so no
-// block reads a value another block has already updated.  d is updated in
-// place (each cell reads only its own d).  Global traffic per cell: x_in, a, b,
-// d read, x_out and d written (6 words), plus the halo re-reads, which mostly
-// hit L2.
+// Each thread block owns a 56 x 24 tile of the xy-plane (plus halos) and
+// marches through a range of z-planes; each thread owns one adjacent cell pair
+// (always one red and one black cell) of one region row.  With plane t just
+// committed, the block forms r, 1/D and the red z on plane t-1 over the tile +
+// 2 halo, the black z on plane t-2 over the tile + 1 halo, and the final red z
+// plus the update on plane t-3 over the tile.  Along z every value a thread
+// needs for its own pair (a, x_in, r, 1/D, red and black z of the neighbouring
+// planes) stays in its registers; shared memory holds only what x/y neighbours
+// read, and the three stages write slots that nobody reads in the same plane
+// iteration, so one barrier per plane suffices.  The halos are recomputed by
+// neighbouring blocks instead of exchanged, so blocks never wait on one
+// another; x_out is a different buffer from x_in, so no block reads a value
+// another block has already updated.  d is updated in place (each cell reads
+// only its own d).  Global traffic per cell: x_in, a, b, d read, x_out and d
+// written (6 words), plus the halo re-reads, which mostly hit L2.
 #include <algorithm>
 
 #include "gmg_internal.cuh"
@@ -26,22 +29,16 @@ namespace gmg {
 
 namespace {
 
-// Block = 32 x 8 threads; thread (tx, ty) owns the cell pair (2 tx, 2 tx + 1)
-// of region rows ty, ty + 8, ..., so every thread holds one red and one black cell and the
-// residual stage runs in packed FP32x2 arithmetic with 64-bit shared and global
-// accesses.  Region: 64 cells (32 pairs) x 22 rows = tile 56 x 16 plus a
-// 4-cell halo in x (which keeps the pairs 8-byte aligned in global memory) and
-// a 3-cell halo in y.
-constexpr int RP = 32, RW = 2 * RP, HX = 4, HY = 3, FTX = RW - 2 * HX, FTY = 16, RH = FTY + 2 * HY;
-constexpr int PSZ = RP * RH;                       // pairs per plane of the region
-constexpr int NXR = 4, NAR = 5, NRR = 3, NZR = 4, NDR = 3;  // ring depths (planes)
-constexpr int BDX = RP, BDY = 8, FTHREADS = BDX * BDY;
-// rows per thread of each stage (region rows handled: BDY apart)
-constexpr int NLROW = (RH + BDY - 1) / BDY;          // loads, rows 0..21
-constexpr int NRROW = (RH - 2 + BDY - 1) / BDY;      // residual, rows 1..20
-constexpr int NBROW = (RH - 4 + BDY - 1) / BDY;      // black, rows 2..19
-constexpr int NFROW = FTY / BDY;                     // final, rows 3..18
-constexpr size_t FUSED_SMEM = (size_t)(NXR + NAR + NRR + NZR + NDR) * PSZ * sizeof(float2);
+// Block = 32 x 30 threads; thread (tx, ty) owns the cell pair (2 tx, 2 tx + 1)
+// of region row ty.  Region: 32 pairs (64 cells) x 30 rows = tile 56 x 24 plus
+// a 4-cell halo in x (keeps pairs 8-byte aligned in global memory) and a
+// 3-cell halo in y.  Values along z stay in each thread's registers; shared
+// memory holds only what x/y neighbours read: a (4 planes), x (2), the red z
+// of the residual stage (2) and the black z (2).
+constexpr int RP = 32, RW = 2 * RP, HX = 4, HY = 3, FTX = RW - 2 * HX, FTY = 24, RH = FTY + 2 * HY;
+constexpr int PPL = RP * RH;  // pairs per region plane = threads per block
+constexpr int NAS = 4, NXS = 2, NZS = 2;
+constexpr size_t FUSED_SMEM = (size_t)(NAS + NXS) * PPL * sizeof(float2) + (size_t)(2 * NZS) * PPL * sizeof(float);
 
 struct FusedArgs {
   Grid3 g;
@@ -62,281 +59,176 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 sc2(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float lane(float2 v, int i) { return i ? v.y : v.x; }
 
-// Neighbour sum N = sum_f (a_f/h^2) v_q of one cell (lane li of pair l) from
-// pair-packed planes: a (am/ac/ap) and v (vm/vc/vp).  mxl/mxr/mym/myp: face
-// masks (0 at a side wall); zlo/zhi: the plane below/above exists.
-__device__ __forceinline__ float nsum1(const Grid3& g, const float2* am, const float2* ac, const float2* ap,
-                                       const float2* vm, const float2* vc, const float2* vp, int l, int li,
-                                       float mxl, float mxr, float mym, float myp, bool zlo, bool zhi) {
-  const float2 a2 = ac[l], v2 = vc[l];
-  const float a0 = lane(a2, li);
-  float al, ar, vl, vr;
-  if (li == 0) {
-    al = ac[l - 1].y; vl = vc[l - 1].y; ar = a2.y; vr = v2.y;
-  } else {
-    al = a2.x; vl = v2.x; ar = ac[l + 1].x; vr = vc[l + 1].x;
-  }
-  float sx = (a0 + al) * mxl * vl;
-  sx = fmaf((a0 + ar) * mxr, vr, sx);
-  float sy = (a0 + lane(ac[l - RP], li)) * mym * lane(vc[l - RP], li);
-  sy = fmaf((a0 + lane(ac[l + RP], li)) * myp, lane(vc[l + RP], li), sy);
-  float sz = 0.f;
-  if (zlo) sz = (a0 + lane(am[l], li)) * lane(vm[l], li);
-  if (zhi) sz = fmaf(a0 + lane(ap[l], li), lane(vp[l], li), sz);
-  return fmaf(g.fx, sx, fmaf(g.fy, sy, g.fz * sz));
-}
-
-// Rows of a stage handled by one thread: region rows r0 + ty + BDY * m.
-template <int NROW>
-struct RowSet {
-  int l[NROW];      // pair index of the thread's pair in the row (-1: row unused)
-  int go[NROW];     // global offset (in cells) of the pair's first cell, plane excluded
-  float my0[NROW];  // 1 if the cell has a face to row - 1
-  float my1[NROW];  // 1 if the cell has a face to row + 1
-  int gy[NROW];
-};
-
-template <int NROW>
-__device__ __forceinline__ void make_rows(RowSet<NROW>& R, int r0, int rmax, int ty, int tx, int y0, int ny, int nx,
-                                          int gx0, bool colok) {
-#pragma unroll
-  for (int m = 0; m < NROW; ++m) {
-    const int ry = r0 + ty + BDY * m, gy = y0 + ry;
-    const bool ok = ry <= rmax && colok && gy >= 0 && gy < ny;
-    R.l[m] = ok ? ry * RP + tx : -1;
-    R.go[m] = gy * nx + gx0;
-    R.my0[m] = gy > 0 ? 1.f : 0.f;
-    R.my1[m] = gy < ny - 1 ? 1.f : 0.f;
-    R.gy[m] = gy;
-  }
-}
-
-__global__ void __launch_bounds__(FTHREADS, 2) k_cheb_sgs_fused(const FusedArgs P) {
-  extern __shared__ float2 sm2[];
-  float2* const xs = sm2;
-  float2* const as = xs + NXR * PSZ;
-  float2* const rs = as + NAR * PSZ;
-  float2* const zs = rs + NRR * PSZ;
-  float2* const ds = zs + NZR * PSZ;  // 1/D
+__global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
+  extern __shared__ float2 smf2[];
+  float2* const As = smf2;               // NAS planes of a
+  float2* const Xs = As + NAS * PPL;     // NXS planes of x_in
+  float* const Z1s = reinterpret_cast<float*>(Xs + NXS * PPL);  // red z of the residual stage
+  float* const ZBs = Z1s + NZS * PPL;                              // black z
   const Grid3& g = P.g;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const size_t pl = g.plane();
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int gx0 = blockIdx.x * FTX - HX + 2 * tx;  // first cell of this thread's pair
-  const int y0 = blockIdx.y * FTY - HY;            // region row 0
+  const int me = ty * RP + tx;
+  const int gx0 = blockIdx.x * FTX - HX + 2 * tx;
+  const int gy = blockIdx.y * FTY - HY + ty;
   const int k0 = blockIdx.z * P.kchunk;
   const int k1 = min(nz, k0 + P.kchunk);
   const bool xzero = P.xin == nullptr;
   const bool first = (P.flags & CHEB_FIRST) != 0;
-  const bool colin = gx0 >= 0 && gx0 < nx;  // nx even: both cells or neither
-  const float2 mxm = make_float2(gx0 > 0 ? 1.f : 0.f, 1.f);       // left faces of the two cells
-  const float2 mxp = make_float2(1.f, gx0 + 2 < nx ? 1.f : 0.f);  // right faces
-  const int rlo = max(0, k0 - 2), rhi = min(nz, k1 + 2);
-  const int blo = max(0, k0 - 1), bhi = min(nz, k1 + 1);
+  const bool in = gx0 >= 0 && gx0 < nx && gy >= 0 && gy < ny;  // nx even: both cells or neither
+  const bool rst = in && tx >= 1 && tx <= RP - 2 && ty >= 1 && ty <= RH - 2;            // residual: tile + 2
+  const bool bst = in && ty >= 2 && ty <= RH - 3;                                        // black: tile + 1
+  const bool fst = in && tx >= HX / 2 && tx < RP - HX / 2 && ty >= HY && ty < RH - HY;  // final: tile
+  const float mxl = gx0 > 0 ? 1.f : 0.f;       // face left of the first cell
+  const float mxr = gx0 + 2 < nx ? 1.f : 0.f;  // face right of the second cell
+  const float my0 = gy > 0 ? 1.f : 0.f, my1 = gy < ny - 1 ? 1.f : 0.f;
   const float2 fx2 = sc2(g.fx), fy2 = sc2(g.fy), fz2 = sc2(g.fz), fp2 = sc2(g.fp);
   const float2 zero2 = make_float2(0.f, 0.f);
+  const int rlo = max(0, k0 - 2), rhi = min(nz, k1 + 2);
+  const int blo = max(0, k0 - 1), bhi = min(nz, k1 + 1);
+  const size_t qo = in ? ((size_t)gy * nx + gx0) >> 1 : 0;  // pair offset in a plane
+  const float2* A2 = reinterpret_cast<const float2*>(P.a);
+  const float2* X2 = reinterpret_cast<const float2*>(P.xin);
+  const float2* B2 = reinterpret_cast<const float2*>(P.b);
+  const float2* D2 = reinterpret_cast<const float2*>(P.d);
+  const size_t pl2 = pl >> 1;
 
-  // r, z and 1/D rings start at zero: cells outside the domain stay zero
-  for (int t = ty * BDX + tx; t < (NRR + NZR + NDR) * PSZ; t += FTHREADS) rs[t] = zero2;
+  for (int s = 0; s < NZS; ++s) Z1s[s * PPL + me] = ZBs[s * PPL + me] = 0.f;
 
-  RowSet<NLROW> LD;  // plane loads: rows 0..21
-  make_rows(LD, 0, RH - 1, ty, tx, y0, ny, nx, gx0, colin);
-  RowSet<NRROW> RR;  // residual: rows 1..20, pairs 1..30
-  make_rows(RR, 1, RH - 2, ty, tx, y0, ny, nx, gx0, colin && tx >= 1 && tx <= RP - 2);
-  RowSet<NBROW> BR;  // black: rows 2..19, pairs 1..30
-  make_rows(BR, 2, RH - 3, ty, tx, y0, ny, nx, gx0, colin && tx >= 1 && tx <= RP - 2);
-  RowSet<NFROW> FR;  // final: rows 3..18, pairs 2..29
-  make_rows(FR, HY, HY + FTY - 1, ty, tx, y0, ny, nx, gx0, colin && tx >= HX / 2 && tx < RP - HX / 2);
-  // rows of the residual stage outside the domain (inside the region) get zeros
-  bool rzero[NRROW];
-#pragma unroll
-  for (int m = 0; m < NRROW; ++m) rzero[m] = RR.l[m] < 0 && 1 + ty + BDY * m <= RH - 2 && tx >= 1 && tx <= RP - 2;
-
-  float2 pa[NLROW], px[NLROW], pb[NRROW], pbn[NRROW], pd[NFROW], pdn[NFROW];
-#pragma unroll
-  for (int m = 0; m < NLROW; ++m) pa[m] = px[m] = zero2;
-#pragma unroll
-  for (int m = 0; m < NRROW; ++m) pb[m] = pbn[m] = zero2;
-#pragma unroll
-  for (int m = 0; m < NFROW; ++m) pd[m] = pdn[m] = zero2;
-  auto prefetch_ax = [&](int k) {
-#pragma unroll
-    for (int m = 0; m < NLROW; ++m) {
-      pa[m] = px[m] = zero2;
-      if (k >= 0 && k < nz && LD.l[m] >= 0) {
-        const size_t q = ((size_t)k * pl + LD.go[m]) >> 1;
-        pa[m] = __ldg(reinterpret_cast<const float2*>(P.a) + q);
-        if (!xzero) px[m] = __ldg(reinterpret_cast<const float2*>(P.xin) + q);
-      }
-    }
-  };
-  prefetch_ax(k0 - 3);
-
-  // ring slot offsets; a ring (depth 5): slot of planes kk-4 .. kk
-  int sa[5];
+  // register windows along z (plane t = current iteration)
+  float2 aw0 = zero2, aw1 = zero2, aw2 = zero2, aw3 = zero2, aw4 = zero2;  // a: t-4 .. t
+  float2 xw0 = zero2, xw1 = zero2, xw2 = zero2, xw3 = zero2;              // x_in: t-3 .. t
+  float2 rw0 = zero2, rw1 = zero2, rw2 = zero2;                           // r: t-3 .. t-1
+  float2 dw0 = zero2, dw1 = zero2, dw2 = zero2;                           // 1/D: t-3 .. t-1
+  float z1w0 = 0.f, z1w1 = 0.f, z1w2 = 0.f;                               // red z: t-3 .. t-1
+  float zbw0 = 0.f, zbw1 = 0.f, zbw2 = 0.f;                               // black z: t-4 .. t-2
+  float2 pa = zero2, px = zero2, pb = zero2, pbn = zero2, pd = zero2, pdn = zero2;
   {
-    int base = k0 - 3;
-#pragma unroll
-    for (int j = 0; j < 5; ++j) sa[j] = (((base - 4 + j) % NAR + NAR) % NAR) * PSZ;
+    const int k = k0 - 3;
+    if (in && k >= 0 && k < nz) {
+      pa = __ldg(A2 + (size_t)k * pl2 + qo);
+      if (!xzero) px = __ldg(X2 + (size_t)k * pl2 + qo);
+    }
   }
-  int sr[3], sd[3];  // r / 1-over-D rings (depth 3): planes kk-3 .. kk-1
-#pragma unroll
-  for (int j = 0; j < 3; ++j) sr[j] = sd[j] = ((((k0 - 3) - 3 + j) % 3 + 3) % 3) * PSZ;
 
-  for (int kk = k0 - 3; kk <= k1 + 2; ++kk) {
-    // slots: a(kk - 4 + j) at sa[j], r(kk - 3 + j) at sr[j], x/z(k) at (k & 3) * PSZ
-    if (kk >= 0 && kk < nz) {
-      float2* xd = xs + (kk & 3) * PSZ;
-      float2* ad = as + sa[4];
-#pragma unroll
-      for (int m = 0; m < NLROW; ++m) {
-        const int ry = ty + BDY * m;
-        if (ry < RH) {
-          ad[ry * RP + tx] = pa[m];
-          xd[ry * RP + tx] = px[m];
-        }
-      }
-    }
+  for (int t = k0 - 3; t <= k1 + 2; ++t) {
+    // One barrier per plane.  Every shared slot written below (a and x of plane
+    // t, red z of t-1, black z of t-2) is read by no one in this iteration, and
+    // every slot read below was written before this barrier.
     __syncthreads();
-    if (kk + 1 <= k1 + 2) prefetch_ax(kk + 1);
-    if (kk >= rlo && kk < rhi) {
-      const float2* b = reinterpret_cast<const float2*>(P.b) + (((size_t)kk * pl) >> 1);
-#pragma unroll
-      for (int m = 0; m < NRROW; ++m)
-        if (RR.l[m] >= 0) pbn[m] = __ldg(b + (RR.go[m] >> 1));
+    // ---- commit plane t (prefetched during the previous iteration) ----
+    aw0 = aw1; aw1 = aw2; aw2 = aw3; aw3 = aw4; aw4 = pa;
+    xw0 = xw1; xw1 = xw2; xw2 = xw3; xw3 = px;
+    As[(t & 3) * PPL + me] = pa;
+    Xs[(t & 1) * PPL + me] = px;
+    // ---- prefetch for the next iteration ----
+    pa = px = zero2;
+    if (in && t + 1 >= 0 && t + 1 < nz && t + 1 <= k1 + 2) {
+      pa = __ldg(A2 + (size_t)(t + 1) * pl2 + qo);
+      if (!xzero) px = __ldg(X2 + (size_t)(t + 1) * pl2 + qo);
     }
-    if (!first && kk - 2 >= k0 && kk - 2 < k1) {
-      const float2* d = reinterpret_cast<const float2*>(P.d) + (((size_t)(kk - 2) * pl) >> 1);
-#pragma unroll
-      for (int m = 0; m < NFROW; ++m)
-        if (FR.l[m] >= 0) pdn[m] = __ldg(d + (FR.go[m] >> 1));
-    }
+    if (rst && t >= rlo && t < rhi) pbn = __ldg(B2 + (size_t)t * pl2 + qo);
+    if (fst && !first && t - 2 >= k0 && t - 2 < k1) pdn = __ldg(D2 + (size_t)(t - 2) * pl2 + qo);
 
-    // ---- r, 1/D (both cells) and the red z on plane kr = kk - 1 ----
-    const int kr = kk - 1;
-    if (kr >= rlo && kr < rhi) {
-      const bool zlo = kr > 0, zhi = kr < nz - 1;
-      const float2* ac = as + sa[3];
-      const float2* am = as + sa[2];
-      const float2* ap = as + sa[4];
-      const float2* xc = xs + (kr & 3) * PSZ;
-      const float2* xm = xs + ((kr - 1) & 3) * PSZ;
-      const float2* xp = xs + ((kr + 1) & 3) * PSZ;
-      float2* rd = rs + sr[2];
-      float2* zd = zs + (kr & 3) * PSZ;
-      float2* dd = ds + sd[2];
-#pragma unroll
-      for (int m = 0; m < NRROW; ++m) {
-        const int l = RR.l[m];
-        if (l < 0) {
-          if (rzero[m]) {
-            const int lz = (1 + ty + BDY * m) * RP + tx;
-            rd[lz] = zero2;
-            zd[lz] = zero2;
-            dd[lz] = zero2;
-          }
-          continue;
-        }
-        const float2 my0 = sc2(RR.my0[m]), my1 = sc2(RR.my1[m]);
-        const float2 a2 = ac[l], al = ac[l - 1], ar = ac[l + 1];
+    // ---- residual stage, plane kr = t - 1: r, 1/D (both cells), red z ----
+    const int kr = t - 1;
+    {
+      float2 r = zero2, di = zero2;
+      float z1 = 0.f;
+      if (kr >= rlo && kr < rhi && rst) {
+        const bool zlo = kr > 0, zhi = kr < nz - 1;
+        const float2* ac = As + (kr & 3) * PPL;
+        const float2* xc = Xs + (kr & 1) * PPL;
+        const float2 a2 = aw3;  // plane kr
+        const float2 al = ac[me - 1], ar = ac[me + 1];
         const float2 aL = make_float2(al.y, a2.x), aR = make_float2(a2.y, ar.x);
-        const float2 fxm = mul2(add2(a2, aL), mxm), fxp = mul2(add2(a2, aR), mxp);
-        const float2 fym = mul2(add2(a2, ac[l - RP]), my0), fyp = mul2(add2(a2, ac[l + RP]), my1);
-        const float2 fzm = zlo ? add2(a2, am[l]) : zero2, fzp = zhi ? add2(a2, ap[l]) : zero2;
+        const float2 fxm = mul2(add2(a2, aL), make_float2(mxl, 1.f));
+        const float2 fxp = mul2(add2(a2, aR), make_float2(1.f, mxr));
+        const float2 fym = mul2(add2(a2, ac[me - RP]), sc2(my0)), fyp = mul2(add2(a2, ac[me + RP]), sc2(my1));
+        const float2 fzm = zlo ? add2(a2, aw2) : zero2, fzp = zhi ? add2(a2, aw4) : zero2;
         const float2 plate = add2(zlo ? zero2 : a2, zhi ? zero2 : a2);
         const float2 D =
             fma2(fx2, add2(fxm, fxp), fma2(fy2, add2(fym, fyp), fma2(fz2, add2(fzm, fzp), mul2(fp2, plate))));
-        float2 r = pb[m];
+        r = pb;
         if (!xzero) {
-          const float2 x2 = xc[l], xl = xc[l - 1], xr = xc[l + 1];
+          const float2 x2 = xw2;  // plane kr
+          const float2 xl = xc[me - 1], xr = xc[me + 1];
           const float2 xL = make_float2(xl.y, x2.x), xR = make_float2(x2.y, xr.x);
           float2 sx = mul2(fxm, sub2(x2, xL));
           sx = fma2(fxp, sub2(x2, xR), sx);
-          float2 sy = mul2(fym, sub2(x2, xc[l - RP]));
-          sy = fma2(fyp, sub2(x2, xc[l + RP]), sy);
+          float2 sy = mul2(fym, sub2(x2, xc[me - RP]));
+          sy = fma2(fyp, sub2(x2, xc[me + RP]), sy);
           float2 sz = mul2(fp2, mul2(plate, x2));
-          if (zlo) sz = fma2(fz2, mul2(fzm, sub2(x2, xm[l])), sz);
-          if (zhi) sz = fma2(fz2, mul2(fzp, sub2(x2, xp[l])), sz);
+          if (zlo) sz = fma2(fz2, mul2(fzm, sub2(x2, xw1)), sz);
+          if (zhi) sz = fma2(fz2, mul2(fzp, sub2(x2, xw3)), sz);
           r = sub2(r, fma2(fx2, sx, fma2(fy2, sy, sz)));
         }
-        const float2 di = make_float2(__frcp_rn(D.x), __frcp_rn(D.y));
-        rd[l] = r;
-        dd[l] = di;
-        const int red = (gx0 + RR.gy[m] + kr) & 1;  // 0: the first cell is red
-        zd[l] = red ? make_float2(0.f, r.y * di.y) : make_float2(r.x * di.x, 0.f);
+        di = make_float2(__fdividef(1.f, D.x), __fdividef(1.f, D.y));
+        const int lr = (gx0 + gy + kr) & 1;  // lane of the red cell
+        z1 = lane(r, lr) * lane(di, lr);
       }
+      rw0 = rw1; rw1 = rw2; rw2 = r;
+      dw0 = dw1; dw1 = dw2; dw2 = di;
+      z1w0 = z1w1; z1w1 = z1w2; z1w2 = z1;
+      Z1s[(kr & 1) * PPL + me] = z1;
     }
-    __syncthreads();
-    // ---- black z on plane kb = kk - 2 (tile + 1 halo) ----
-    const int kb = kk - 2;
-    if (kb >= blo && kb < bhi) {
-      const bool zlo = kb > 0, zhi = kb < nz - 1;
-      const float2* ac = as + sa[2];
-      const float2* am = as + sa[1];
-      const float2* ap = as + sa[3];
-      float2* zc = zs + (kb & 3) * PSZ;
-      const float2* zm = zs + ((kb - 1) & 3) * PSZ;
-      const float2* zp = zs + ((kb + 1) & 3) * PSZ;
-      const float2* rc = rs + sr[1];
-      const float2* dc = ds + sd[1];
-#pragma unroll
-      for (int m = 0; m < NBROW; ++m) {
-        const int l = BR.l[m];
-        if (l < 0) continue;
-        const int li = ((gx0 + BR.gy[m] + kb) & 1) ^ 1;  // lane of the black cell
-        const int col = 2 * tx + li;
-        if (col < HX - 1 || col > RW - HX) continue;     // region columns 3..60
-        const float N = nsum1(g, am, ac, ap, zm, zc, zp, l, li, li ? 1.f : mxm.x, li ? mxp.y : 1.f, BR.my0[m],
-                              BR.my1[m], zlo, zhi);
-        reinterpret_cast<float*>(zc)[2 * l + li] = (lane(rc[l], li) + N) * lane(dc[l], li);
+    // ---- black stage, plane kb = t - 2: z_B = (r + N z1) / D ----
+    const int kb = t - 2;
+    {
+      float zb = 0.f;
+      const int lb = ((gx0 + gy + kb) & 1) ^ 1;  // lane of the black cell
+      const int col = 2 * tx + lb;
+      if (kb >= blo && kb < bhi && bst && col >= HX - 1 && col <= RW - HX) {
+        const bool zlo = kb > 0, zhi = kb < nz - 1;
+        const float2* ac = As + (kb & 3) * PPL;
+        const float* zc = Z1s + (kb & 1) * PPL;
+        const float a0 = lane(aw2, lb);                 // plane kb
+        const float ain = lane(aw2, lb ^ 1);            // the red cell of the pair
+        const float aout = lb ? ac[me + 1].x : ac[me - 1].y;
+        const float mout = lb ? mxr : mxl;
+        float sx = (a0 + ain) * z1w1;                   // z1w1: red z of this pair, plane kb
+        sx = fmaf((a0 + aout) * mout, lb ? zc[me + 1] : zc[me - 1], sx);
+        float sy = (a0 + lane(ac[me - RP], lb)) * my0 * zc[me - RP];
+        sy = fmaf((a0 + lane(ac[me + RP], lb)) * my1, zc[me + RP], sy);
+        float sz = 0.f;
+        if (zlo) sz = (a0 + lane(aw1, lb)) * z1w0;
+        if (zhi) sz = fmaf(a0 + lane(aw3, lb), z1w2, sz);
+        const float N = fmaf(g.fx, sx, fmaf(g.fy, sy, g.fz * sz));
+        zb = (lane(rw1, lb) + N) * lane(dw1, lb);
       }
+      zbw0 = zbw1; zbw1 = zbw2; zbw2 = zb;
+      ZBs[(kb & 1) * PPL + me] = zb;
     }
-    __syncthreads();
-    // ---- final red z and the Chebyshev update on plane kf = kk - 3 (tile) ----
-    const int kf = kk - 3;
-    if (kf >= k0 && kf < k1) {
+    // ---- final stage, plane kf = t - 3: red z and the Chebyshev update ----
+    const int kf = t - 3;
+    if (kf >= k0 && kf < k1 && fst) {
       const bool zlo = kf > 0, zhi = kf < nz - 1;
-      const float2* ac = as + sa[1];
-      const float2* am = as + sa[0];
-      const float2* ap = as + sa[2];
-      const float2* zc = zs + (kf & 3) * PSZ;
-      const float2* zm = zs + ((kf - 1) & 3) * PSZ;
-      const float2* zp = zs + ((kf + 1) & 3) * PSZ;
-      const float2* rc = rs + sr[0];
-      const float2* dc = ds + sd[0];
-      const float2* xc = xs + (kf & 3) * PSZ;
-      float2* dg = reinterpret_cast<float2*>(P.d) + (((size_t)kf * pl) >> 1);
-      float2* xg = reinterpret_cast<float2*>(P.xout) + (((size_t)kf * pl) >> 1);
-      const float2 c2 = sc2(P.c2), c1 = sc2(P.c1);
-#pragma unroll
-      for (int m = 0; m < NFROW; ++m) {
-        const int l = FR.l[m];
-        if (l < 0) continue;
-        const int li = (gx0 + FR.gy[m] + kf) & 1;  // lane of the red cell
-        const float N = nsum1(g, am, ac, ap, zm, zc, zp, l, li, li ? 1.f : mxm.x, li ? mxp.y : 1.f, FR.my0[m],
-                              FR.my1[m], zlo, zhi);
-        const float zr = (lane(rc[l], li) + N) * lane(dc[l], li);
-        const float2 zb = zc[l];
-        const float2 z = li ? make_float2(zb.x, zr) : make_float2(zr, zb.y);
-        const float2 dv = first ? mul2(c2, z) : fma2(c1, pd[m], mul2(c2, z));
-        const int q = FR.go[m] >> 1;
-        dg[q] = dv;
-        xg[q] = xzero ? dv : add2(xc[l], dv);
-      }
+      const float2* ac = As + (kf & 3) * PPL;
+      const float* zc = ZBs + (kf & 1) * PPL;
+      const int lr = (gx0 + gy + kf) & 1;  // lane of the red cell
+      const float a0 = lane(aw1, lr);      // plane kf
+      const float ain = lane(aw1, lr ^ 1);
+      const float aout = lr ? ac[me + 1].x : ac[me - 1].y;
+      const float mout = lr ? mxr : mxl;
+      float sx = (a0 + ain) * zbw1;  // zbw1: black z of this pair, plane kf
+      sx = fmaf((a0 + aout) * mout, lr ? zc[me + 1] : zc[me - 1], sx);
+      float sy = (a0 + lane(ac[me - RP], lr)) * my0 * zc[me - RP];
+      sy = fmaf((a0 + lane(ac[me + RP], lr)) * my1, zc[me + RP], sy);
+      float sz = 0.f;
+      if (zlo) sz = (a0 + lane(aw0, lr)) * zbw0;
+      if (zhi) sz = fmaf(a0 + lane(aw2, lr), zbw2, sz);
+      const float N = fmaf(g.fx, sx, fmaf(g.fy, sy, g.fz * sz));
+      const float zr = (lane(rw0, lr) + N) * lane(dw0, lr);
+      const float2 z = lr ? make_float2(zbw1, zr) : make_float2(zr, zbw1);
+      const float2 c2 = sc2(P.c2);
+      const float2 dv = first ? mul2(c2, z) : fma2(sc2(P.c1), pd, mul2(c2, z));
+      const size_t q = (size_t)kf * pl2 + qo;
+      reinterpret_cast<float2*>(P.d)[q] = dv;
+      reinterpret_cast<float2*>(P.xout)[q] = xzero ? dv : add2(xw0, dv);
     }
-    __syncthreads();
-#pragma unroll
-    for (int m = 0; m < NRROW; ++m) pb[m] = pbn[m];
-#pragma unroll
-    for (int m = 0; m < NFROW; ++m) pd[m] = pdn[m];
-    // rotate the ring slots to the next plane
-    const int na = sa[0];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) sa[j] = sa[j + 1];
-    sa[4] = na;
-    const int nr = sr[0], nd = sd[0];
-    sr[0] = sr[1]; sr[1] = sr[2]; sr[2] = nr;
-    sd[0] = sd[1]; sd[1] = sd[2]; sd[2] = nd;
+    pb = pbn;
+    pd = pdn;
   }
 }
 
@@ -347,7 +239,7 @@ bool g_fused_attr_set = false;
 bool fused_smoother_eligible(const Grid3& g) { return g.nx >= 32 && g.nx % 2 == 0 && g.ny >= 16 && g.nz >= 8; }
 
 cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b, const float* xin, float* xout,
-                                  float* d, double c1, double c2, int flags, cudaStream_t s) {
+                                    float* d, double c1, double c2, int flags, cudaStream_t s) {
   if (!g_fused_attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_cheb_sgs_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)FUSED_SMEM);
@@ -355,14 +247,14 @@ cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b
     g_fused_attr_set = true;
   }
   const int tx = (g.nx + FTX - 1) / FTX, ty = (g.ny + FTY - 1) / FTY;
-  // enough z-chunks for ~8 blocks per SM, each chunk at least 8 planes
-  const int target = 152 * 8;
+  // about 4 waves of one block per SM, each z-chunk at least 8 planes
+  const int target = 152 * 4;
   int nzc = (target + tx * ty - 1) / (tx * ty);
   nzc = std::max(1, std::min(nzc, g.nz / 8));
   const int kchunk = (g.nz + nzc - 1) / nzc;
   nzc = (g.nz + kchunk - 1) / kchunk;
   FusedArgs P{g, a, b, xin, xout, d, (float)c1, (float)c2, flags, kchunk};
-  k_cheb_sgs_fused<<<dim3((unsigned)tx, (unsigned)ty, (unsigned)nzc), dim3(BDX, BDY), FUSED_SMEM, s>>>(P);
+  k_cheb_sgs_fused<<<dim3((unsigned)tx, (unsigned)ty, (unsigned)nzc), dim3(RP, RH), FUSED_SMEM, s>>>(P);
   return cudaGetLastError();
 }
 
