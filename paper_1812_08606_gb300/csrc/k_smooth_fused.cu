@@ -6,8 +6,13 @@
 //   z = B^{-1} r:  red  z = r / D,  black z = (r + N z)/D,  red z = (r + N z)/D
 //   d = c1 d + c2 z   (d = c2 z on the first step),   x_out = x_in + d
 //
-// Each thread block owns a 56 x 24 tile of the xy-plane (plus halos) and
-// marches through a range of z-planes; each thread owns one adjacent cell pair
+// The xy-plane is cut into 56 x 18 tiles; a work unit is one z-plane of one
+// tile.  The kernel is persistent: one block per resident slot, each taking an
+// equal share of the units (whole tile columns in rounds of one tile per
+// block, so that neighbouring tiles advance through z together and re-read
+// each other's halos from L2, then an even split of the leftover columns into
+// z-segments).  A block marches through each of its z-segments; each thread
+// owns one adjacent cell pair
 // (always one red and one black cell) of one region row.  With plane t just
 // committed, the block forms r, 1/D and the red z on plane t-1 over the tile +
 // 2 halo, the black z on plane t-2 over the tile + 1 halo, and the final red z
@@ -29,13 +34,13 @@ namespace gmg {
 
 namespace {
 
-// Block = 32 x 30 threads; thread (tx, ty) owns the cell pair (2 tx, 2 tx + 1)
-// of region row ty.  Region: 32 pairs (64 cells) x 30 rows = tile 56 x 24 plus
+// Block = 32 x 24 threads; thread (tx, ty) owns the cell pair (2 tx, 2 tx + 1)
+// of region row ty.  Region: 32 pairs (64 cells) x 24 rows = tile 56 x 18 plus
 // a 4-cell halo in x (keeps pairs 8-byte aligned in global memory) and a
 // 3-cell halo in y.  Values along z stay in each thread's registers; shared
 // memory holds only what x/y neighbours read: a (4 planes), x (2), the red z
 // of the residual stage (2) and the black z (2).
-constexpr int RP = 32, RW = 2 * RP, HX = 4, HY = 3, FTX = RW - 2 * HX, FTY = 24, RH = FTY + 2 * HY;
+constexpr int RP = 32, RW = 2 * RP, HX = 4, HY = 3, FTX = RW - 2 * HX, FTY = 18, RH = FTY + 2 * HY;
 constexpr int PPL = RP * RH;  // pairs per region plane = threads per block
 constexpr int NAS = 4, NXS = 2, NZS = 2;
 constexpr size_t FUSED_SMEM = (size_t)(NAS + NXS) * PPL * sizeof(float2) + (size_t)(2 * NZS) * PPL * sizeof(float);
@@ -49,7 +54,8 @@ struct FusedArgs {
   float* d;
   float c1, c2;
   int flags;
-  int kchunk;
+  int tiles_x;      // tiles along x
+  long long units;  // tiles x nz (one unit = one z-plane of one tile)
 };
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -59,8 +65,10 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 sc2(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float lane(float2 v, int i) { return i ? v.y : v.x; }
 
-__global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
-  extern __shared__ float2 smf2[];
+// Planes [k0, k1) of tile (bx, by).  Leaves shared memory in use: the caller
+// synchronises before the next segment.
+__device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, const int bx, const int by,
+                                              const int k0, const int k1) {
   float2* const As = smf2;               // NAS planes of a
   float2* const Xs = As + NAS * PPL;     // NXS planes of x_in
   float* const Z1s = reinterpret_cast<float*>(Xs + NXS * PPL);  // red z of the residual stage
@@ -70,10 +78,8 @@ __global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
   const size_t pl = g.plane();
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int me = ty * RP + tx;
-  const int gx0 = blockIdx.x * FTX - HX + 2 * tx;
-  const int gy = blockIdx.y * FTY - HY + ty;
-  const int k0 = blockIdx.z * P.kchunk;
-  const int k1 = min(nz, k0 + P.kchunk);
+  const int gx0 = bx * FTX - HX + 2 * tx;
+  const int gy = by * FTY - HY + ty;
   const bool xzero = P.xin == nullptr;
   const bool first = (P.flags & CHEB_FIRST) != 0;
   const bool in = gx0 >= 0 && gx0 < nx && gy >= 0 && gy < ny;  // nx even: both cells or neither
@@ -232,7 +238,33 @@ __global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
   }
 }
 
+__global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
+  extern __shared__ float2 smf2[];
+  const int nz = P.g.nz;
+  const long long G = gridDim.x, b = blockIdx.x;
+  // whole columns: tile r G + b in round r
+  const long long full = P.units / nz / G;
+  for (long long r = 0; r < full; ++r) {
+    const int tile = (int)(r * G + b);
+    fused_segment(P, smf2, tile % P.tiles_x, tile / P.tiles_x, 0, nz);
+    __syncthreads();
+  }
+  // leftover columns: an equal contiguous share of their (tile, plane) units
+  const long long base = full * G * nz, rest = P.units - base;
+  long long u = base + rest * b / G;
+  const long long end = base + rest * (b + 1) / G;
+  while (u < end) {
+    const int tile = (int)(u / nz);
+    const int k0 = (int)(u - (long long)tile * nz);
+    const int k1 = (int)min((long long)nz, k0 + (end - u));
+    fused_segment(P, smf2, tile % P.tiles_x, tile / P.tiles_x, k0, k1);
+    u += k1 - k0;
+    __syncthreads();
+  }
+}
+
 bool g_fused_attr_set = false;
+int g_fused_slots = 0;  // resident blocks of the kernel on the device (one device per process)
 
 }  // namespace
 
@@ -246,15 +278,20 @@ cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b
     if (e != cudaSuccess) return e;
     g_fused_attr_set = true;
   }
+  if (g_fused_slots == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cheb_sgs_fused, PPL, FUSED_SMEM);
+    if (e != cudaSuccess) return e;
+    g_fused_slots = std::max(1, sms * std::max(1, per));
+  }
   const int tx = (g.nx + FTX - 1) / FTX, ty = (g.ny + FTY - 1) / FTY;
-  // about 4 waves of one block per SM, each z-chunk at least 8 planes
-  const int target = 152 * 4;
-  int nzc = (target + tx * ty - 1) / (tx * ty);
-  nzc = std::max(1, std::min(nzc, g.nz / 8));
-  const int kchunk = (g.nz + nzc - 1) / nzc;
-  nzc = (g.nz + kchunk - 1) / kchunk;
-  FusedArgs P{g, a, b, xin, xout, d, (float)c1, (float)c2, flags, kchunk};
-  k_cheb_sgs_fused<<<dim3((unsigned)tx, (unsigned)ty, (unsigned)nzc), dim3(RP, RH), FUSED_SMEM, s>>>(P);
+  const long long units = (long long)tx * ty * g.nz;
+  // one block per resident slot, but at least 4 planes per block on small grids
+  const long long blocks = std::max(1LL, std::min((long long)g_fused_slots, units / 4));
+  FusedArgs P{g, a, b, xin, xout, d, (float)c1, (float)c2, flags, tx, units};
+  k_cheb_sgs_fused<<<(unsigned)blocks, dim3(RP, RH), FUSED_SMEM, s>>>(P);
   return cudaGetLastError();
 }
 
