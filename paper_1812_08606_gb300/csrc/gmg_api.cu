@@ -824,12 +824,20 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
   }
   {
     std::vector<double> R((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), col(m + 2), y(m);
+    // A zero initial guess (||x0|| = 0) gives r0 = b exactly: the first cycle
+    // then starts from b and ||b|| without the FP64 operator pass.
+    CKS(norm_dev(c, n, x, SL_NORM));
+    CKS(read_scalars(c, SL_NORM, 2));
+    bool r0_is_b = c->hpin[SL_NORM] == 0.0;
     for (;;) {
       // r0 = b - A x0, beta = ||r0||, v1 = r0 / beta (start of an Arnoldi cycle)
-      CKS(prof_residual<double>(c, F.g, F.a64, c->bvec, x, c->V, nullptr, PC_NONE, c->s));
-      CKS(norm_dev(c, n, c->V, SL_NORM));
-      CKS(read_scalars(c, SL_NORM, 2));
-      const double beta = c->hpin[SL_NORM];
+      double beta = bnorm;
+      if (!r0_is_b) {
+        CKS(prof_residual<double>(c, F.g, F.a64, c->bvec, x, c->V, nullptr, PC_NONE, c->s));
+        CKS(norm_dev(c, n, c->V, SL_NORM));
+        CKS(read_scalars(c, SL_NORM, 2));
+        beta = c->hpin[SL_NORM];
+      }
       if (!isfinite(beta)) {
         result = GMG_ERR_NONFINITE;
         break;
@@ -843,7 +851,8 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
         result = GMG_ERR_NOT_CONVERGED;
         break;
       }
-      CKS(prof_scale_value(c, n, c->V, c->V, 1.0 / beta, c->s));
+      CKS(prof_scale_value(c, n, r0_is_b ? c->bvec : c->V, c->V, 1.0 / beta, c->s));
+      r0_is_b = false;  // later cycles restart from x_k != 0
       std::fill(g.begin(), g.end(), 0.0);
       g[0] = beta;
       int k = 0;

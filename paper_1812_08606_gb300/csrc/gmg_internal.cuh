@@ -143,6 +143,13 @@ cudaError_t launch_residual_restrict(const Grid3& g, const T* a, const T* b, con
 template <typename T>
 cudaError_t launch_prolong_add(const Grid3& g_fine, const T* e, T* x, int mode, cudaStream_t s);
 
+// FP32 forms of the two transfers above with one thread per fine cell pair
+// (k_transfer.cu); the FP32 instantiations of launch_residual_restrict and
+// launch_prolong_add use them.  g is the fine grid (all dimensions even).
+cudaError_t launch_restrict_pairs(const Grid3& g, const float* a, const float* b, const float* x, float* coarse,
+                                  cudaStream_t s);
+cudaError_t launch_prolong_pairs(const Grid3& g, const float* e, float* x, int mode, cudaStream_t s);
+
 // coarse coefficient = mean of the 8 children (FP64), plus an FP32 copy if c32.
 cudaError_t launch_coarsen_coef(const Grid3& g_fine, const double* a, double* ac, float* ac32,
                                 cudaStream_t s);

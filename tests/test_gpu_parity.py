@@ -248,10 +248,12 @@ def test_eigen_bounds_match_oracle():
         assert info["lam_min"] == pytest.approx(hier.levels[lev].lam_min, rel=1e-11)
 
 
+# (8, 24, 144): 72 and 36 cell pairs per row on the two finest levels, so a row
+# spans 3 and 2 warps and the x-neighbours cross warp and block boundaries.
+@pytest.mark.parametrize("shape", [RAGGED, (8, 24, 144)])
 @pytest.mark.parametrize("prec", [gmg.GMG_PREC_FP64, gmg.GMG_PREC_MIXED])
 @pytest.mark.parametrize("mode", [gmg.GMG_PROLONG_TRILINEAR, gmg.GMG_PROLONG_CONSTANT])
-def test_transfers_and_coarse_solve(prec, mode):
-    shape = RAGGED
+def test_transfers_and_coarse_solve(prec, mode, shape):
     a = random_coefficient(150, shape, contrast=1e2)
     p = _params(shape, coarse_min=2, precision=prec, prolongation=mode)
     ctx = gmg.gmg_setup(p, _t(a))
