@@ -12,8 +12,8 @@
 // block, so that neighbouring tiles advance through z together and re-read
 // each other's halos from L2, then an even split of the leftover columns into
 // z-segments).  A block marches through each of its z-segments; each thread
-// owns one adjacent cell pair
-// (always one red and one black cell) of one region row.  With plane t just
+// owns one adjacent cell pair (always one red and one black cell) of one
+// region row.  With plane t just
 // committed, the block forms r, 1/D and the red z on plane t-1 over the tile +
 // 2 halo, the black z on plane t-2 over the tile + 1 halo, and the final red z
 // plus the update on plane t-3 over the tile.  Along z every value a thread
@@ -26,7 +26,15 @@
 // another block has already updated.  d is updated in place (each cell reads
 // only its own d).  Global traffic per cell: x_in, a, b, d read, x_out and d
 // written (6 words), plus the halo re-reads, which mostly hit L2.
+//
+// Away from the ends of a segment and from the plates a plane step needs no
+// range checks; those steady steps run two planes at a time.  A warp is one
+// region row and the two planes have opposite parity, so the lane holding the
+// cell each stage updates is fixed per warp and per plane of the pair: a
+// warp-uniform branch picks a copy of the step with that lane known at
+// compile time, which removes the lane selects from the stages.
 #include <algorithm>
+#include <type_traits>
 
 #include "gmg_internal.cuh"
 
@@ -86,6 +94,8 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
   const bool rst = in && tx >= 1 && tx <= RP - 2 && ty >= 1 && ty <= RH - 2;            // residual: tile + 2
   const bool bst = in && ty >= 2 && ty <= RH - 3;                                        // black: tile + 1
   const bool fst = in && tx >= HX / 2 && tx < RP - HX / 2 && ty >= HY && ty < RH - HY;  // final: tile
+  // the black stage covers the tile + 1 halo: cells of region columns HX - 1 .. RW - HX
+  const bool bcol0 = 2 * tx >= HX - 1 && 2 * tx <= RW - HX, bcol1 = 2 * tx + 1 >= HX - 1 && 2 * tx + 1 <= RW - HX;
   const float mxl = gx0 > 0 ? 1.f : 0.f;       // face left of the first cell
   const float mxr = gx0 + 2 < nx ? 1.f : 0.f;  // face right of the second cell
   const float my0 = gy > 0 ? 1.f : 0.f, my1 = gy < ny - 1 ? 1.f : 0.f;
@@ -118,32 +128,35 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
     }
   }
 
-  for (int t = k0 - 3; t <= k1 + 2; ++t) {
-    // One barrier per plane.  Every shared slot written below (a and x of plane
-    // t, red z of t-1, black z of t-2) is read by no one in this iteration, and
-    // every slot read below was written before this barrier.
-    __syncthreads();
-    // ---- commit plane t (prefetched during the previous iteration) ----
+  // One plane step.  LM = 0 or 1: the lane of the cell each stage updates (the
+  // red cell at t-1 and t-3, the black cell at t-2; the same lane for all
+  // three) is known at compile time; LM = 2: it is computed.  ST: steady state,
+  // every plane index of the step lies inside the segment and off the plates.
+  auto body = [&](auto LMT, auto STT, const int t) {
+    constexpr int LM = decltype(LMT)::value;
+    constexpr bool ST = decltype(STT)::value;
+    const int L = LM < 2 ? LM : (((gy + t) & 1) ^ 1);
+    // ---- commit plane t (prefetched during the previous step) ----
     aw0 = aw1; aw1 = aw2; aw2 = aw3; aw3 = aw4; aw4 = pa;
     xw0 = xw1; xw1 = xw2; xw2 = xw3; xw3 = px;
     As[(t & 3) * PPL + me] = pa;
     Xs[(t & 1) * PPL + me] = px;
-    // ---- prefetch for the next iteration ----
+    // ---- prefetch for the next step ----
     pa = px = zero2;
-    if (in && t + 1 >= 0 && t + 1 < nz && t + 1 <= k1 + 2) {
+    if (in && (ST || (t + 1 >= 0 && t + 1 < nz && t + 1 <= k1 + 2))) {
       pa = __ldg(A2 + (size_t)(t + 1) * pl2 + qo);
       if (!xzero) px = __ldg(X2 + (size_t)(t + 1) * pl2 + qo);
     }
-    if (rst && t >= rlo && t < rhi) pbn = __ldg(B2 + (size_t)t * pl2 + qo);
-    if (fst && !first && t - 2 >= k0 && t - 2 < k1) pdn = __ldg(D2 + (size_t)(t - 2) * pl2 + qo);
+    if (rst && (ST || (t >= rlo && t < rhi))) pbn = __ldg(B2 + (size_t)t * pl2 + qo);
+    if (fst && !first && (ST || (t - 2 >= k0 && t - 2 < k1))) pdn = __ldg(D2 + (size_t)(t - 2) * pl2 + qo);
 
     // ---- residual stage, plane kr = t - 1: r, 1/D (both cells), red z ----
     const int kr = t - 1;
     {
       float2 r = zero2, di = zero2;
       float z1 = 0.f;
-      if (kr >= rlo && kr < rhi && rst) {
-        const bool zlo = kr > 0, zhi = kr < nz - 1;
+      if (rst && (ST || (kr >= rlo && kr < rhi))) {
+        const bool zlo = ST || kr > 0, zhi = ST || kr < nz - 1;
         const float2* ac = As + (kr & 3) * PPL;
         const float2* xc = Xs + (kr & 1) * PPL;
         const float2 a2 = aw3;  // plane kr
@@ -153,9 +166,13 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
         const float2 fxp = mul2(add2(a2, aR), make_float2(1.f, mxr));
         const float2 fym = mul2(add2(a2, ac[me - RP]), sc2(my0)), fyp = mul2(add2(a2, ac[me + RP]), sc2(my1));
         const float2 fzm = zlo ? add2(a2, aw2) : zero2, fzp = zhi ? add2(a2, aw4) : zero2;
-        const float2 plate = add2(zlo ? zero2 : a2, zhi ? zero2 : a2);
-        const float2 D =
-            fma2(fx2, add2(fxm, fxp), fma2(fy2, add2(fym, fyp), fma2(fz2, add2(fzm, fzp), mul2(fp2, plate))));
+        float2 D;
+        if constexpr (ST) {
+          D = fma2(fx2, add2(fxm, fxp), fma2(fy2, add2(fym, fyp), mul2(fz2, add2(fzm, fzp))));
+        } else {
+          const float2 plate = add2(zlo ? zero2 : a2, zhi ? zero2 : a2);
+          D = fma2(fx2, add2(fxm, fxp), fma2(fy2, add2(fym, fyp), fma2(fz2, add2(fzm, fzp), mul2(fp2, plate))));
+        }
         r = pb;
         if (!xzero) {
           const float2 x2 = xw2;  // plane kr
@@ -165,14 +182,20 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
           sx = fma2(fxp, sub2(x2, xR), sx);
           float2 sy = mul2(fym, sub2(x2, xc[me - RP]));
           sy = fma2(fyp, sub2(x2, xc[me + RP]), sy);
-          float2 sz = mul2(fp2, mul2(plate, x2));
-          if (zlo) sz = fma2(fz2, mul2(fzm, sub2(x2, xw1)), sz);
-          if (zhi) sz = fma2(fz2, mul2(fzp, sub2(x2, xw3)), sz);
+          float2 sz;
+          if constexpr (ST) {
+            sz = mul2(fz2, mul2(fzm, sub2(x2, xw1)));
+            sz = fma2(fz2, mul2(fzp, sub2(x2, xw3)), sz);
+          } else {
+            const float2 plate = add2(zlo ? zero2 : a2, zhi ? zero2 : a2);
+            sz = mul2(fp2, mul2(plate, x2));
+            if (zlo) sz = fma2(fz2, mul2(fzm, sub2(x2, xw1)), sz);
+            if (zhi) sz = fma2(fz2, mul2(fzp, sub2(x2, xw3)), sz);
+          }
           r = sub2(r, fma2(fx2, sx, fma2(fy2, sy, sz)));
         }
         di = make_float2(__fdividef(1.f, D.x), __fdividef(1.f, D.y));
-        const int lr = (gx0 + gy + kr) & 1;  // lane of the red cell
-        z1 = lane(r, lr) * lane(di, lr);
+        z1 = lane(r, L) * lane(di, L);
       }
       rw0 = rw1; rw1 = rw2; rw2 = r;
       dw0 = dw1; dw1 = dw2; dw2 = di;
@@ -183,50 +206,48 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
     const int kb = t - 2;
     {
       float zb = 0.f;
-      const int lb = ((gx0 + gy + kb) & 1) ^ 1;  // lane of the black cell
-      const int col = 2 * tx + lb;
-      if (kb >= blo && kb < bhi && bst && col >= HX - 1 && col <= RW - HX) {
-        const bool zlo = kb > 0, zhi = kb < nz - 1;
+      const bool colok = L ? bcol1 : bcol0;
+      if (bst && colok && (ST || (kb >= blo && kb < bhi))) {
+        const bool zlo = ST || kb > 0, zhi = ST || kb < nz - 1;
         const float2* ac = As + (kb & 3) * PPL;
         const float* zc = Z1s + (kb & 1) * PPL;
-        const float a0 = lane(aw2, lb);                 // plane kb
-        const float ain = lane(aw2, lb ^ 1);            // the red cell of the pair
-        const float aout = lb ? ac[me + 1].x : ac[me - 1].y;
-        const float mout = lb ? mxr : mxl;
+        const float a0 = lane(aw2, L);                  // plane kb
+        const float ain = lane(aw2, L ^ 1);             // the red cell of the pair
+        const float aout = L ? ac[me + 1].x : ac[me - 1].y;
+        const float mout = L ? mxr : mxl;
         float sx = (a0 + ain) * z1w1;                   // z1w1: red z of this pair, plane kb
-        sx = fmaf((a0 + aout) * mout, lb ? zc[me + 1] : zc[me - 1], sx);
-        float sy = (a0 + lane(ac[me - RP], lb)) * my0 * zc[me - RP];
-        sy = fmaf((a0 + lane(ac[me + RP], lb)) * my1, zc[me + RP], sy);
+        sx = fmaf((a0 + aout) * mout, L ? zc[me + 1] : zc[me - 1], sx);
+        float sy = (a0 + lane(ac[me - RP], L)) * my0 * zc[me - RP];
+        sy = fmaf((a0 + lane(ac[me + RP], L)) * my1, zc[me + RP], sy);
         float sz = 0.f;
-        if (zlo) sz = (a0 + lane(aw1, lb)) * z1w0;
-        if (zhi) sz = fmaf(a0 + lane(aw3, lb), z1w2, sz);
+        if (zlo) sz = (a0 + lane(aw1, L)) * z1w0;
+        if (zhi) sz = fmaf(a0 + lane(aw3, L), z1w2, sz);
         const float N = fmaf(g.fx, sx, fmaf(g.fy, sy, g.fz * sz));
-        zb = (lane(rw1, lb) + N) * lane(dw1, lb);
+        zb = (lane(rw1, L) + N) * lane(dw1, L);
       }
       zbw0 = zbw1; zbw1 = zbw2; zbw2 = zb;
       ZBs[(kb & 1) * PPL + me] = zb;
     }
     // ---- final stage, plane kf = t - 3: red z and the Chebyshev update ----
     const int kf = t - 3;
-    if (kf >= k0 && kf < k1 && fst) {
-      const bool zlo = kf > 0, zhi = kf < nz - 1;
+    if (fst && (ST || (kf >= k0 && kf < k1))) {
+      const bool zlo = ST || kf > 0, zhi = ST || kf < nz - 1;
       const float2* ac = As + (kf & 3) * PPL;
       const float* zc = ZBs + (kf & 1) * PPL;
-      const int lr = (gx0 + gy + kf) & 1;  // lane of the red cell
-      const float a0 = lane(aw1, lr);      // plane kf
-      const float ain = lane(aw1, lr ^ 1);
-      const float aout = lr ? ac[me + 1].x : ac[me - 1].y;
-      const float mout = lr ? mxr : mxl;
+      const float a0 = lane(aw1, L);      // plane kf
+      const float ain = lane(aw1, L ^ 1);
+      const float aout = L ? ac[me + 1].x : ac[me - 1].y;
+      const float mout = L ? mxr : mxl;
       float sx = (a0 + ain) * zbw1;  // zbw1: black z of this pair, plane kf
-      sx = fmaf((a0 + aout) * mout, lr ? zc[me + 1] : zc[me - 1], sx);
-      float sy = (a0 + lane(ac[me - RP], lr)) * my0 * zc[me - RP];
-      sy = fmaf((a0 + lane(ac[me + RP], lr)) * my1, zc[me + RP], sy);
+      sx = fmaf((a0 + aout) * mout, L ? zc[me + 1] : zc[me - 1], sx);
+      float sy = (a0 + lane(ac[me - RP], L)) * my0 * zc[me - RP];
+      sy = fmaf((a0 + lane(ac[me + RP], L)) * my1, zc[me + RP], sy);
       float sz = 0.f;
-      if (zlo) sz = (a0 + lane(aw0, lr)) * zbw0;
-      if (zhi) sz = fmaf(a0 + lane(aw2, lr), zbw2, sz);
+      if (zlo) sz = (a0 + lane(aw0, L)) * zbw0;
+      if (zhi) sz = fmaf(a0 + lane(aw2, L), zbw2, sz);
       const float N = fmaf(g.fx, sx, fmaf(g.fy, sy, g.fz * sz));
-      const float zr = (lane(rw0, lr) + N) * lane(dw0, lr);
-      const float2 z = lr ? make_float2(zbw1, zr) : make_float2(zr, zbw1);
+      const float zr = (lane(rw0, L) + N) * lane(dw0, L);
+      const float2 z = L ? make_float2(zbw1, zr) : make_float2(zr, zbw1);
       const float2 c2 = sc2(P.c2);
       const float2 dv = first ? mul2(c2, z) : fma2(sc2(P.c1), pd, mul2(c2, z));
       const size_t q = (size_t)kf * pl2 + qo;
@@ -235,6 +256,35 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
     }
     pb = pbn;
     pd = pdn;
+  };
+
+  // One barrier per plane, at a block-uniform point before each step.  Every
+  // shared slot a step writes (a and x of plane t, red z of t-1, black z of
+  // t-2) is read by no one in the same step, and every slot it reads was
+  // written before the barrier.  Steady steps run in pairs (t even, t + 1);
+  // within a warp (one region row) the lane parity of the pair is fixed.
+  using I0 = std::integral_constant<int, 0>;
+  using I1 = std::integral_constant<int, 1>;
+  using IR = std::integral_constant<int, 2>;
+  using TS = std::integral_constant<bool, true>;
+  using TG = std::integral_constant<bool, false>;
+  const int tend = k1 + 2;
+  const int s0 = max(k0 + 3, 4), s1 = min(k1, nz - 2);  // steady steps
+  const bool godd = (gy & 1) != 0;
+  int t = k0 - 3;
+  while (t <= tend) {
+    if (!(t & 1) && t >= s0 && t + 1 <= s1) {
+      // t even: the lane is 1 - parity of gy at t, the parity of gy at t + 1
+      __syncthreads();
+      if (godd) body(I0{}, TS{}, t); else body(I1{}, TS{}, t);
+      __syncthreads();
+      if (godd) body(I1{}, TS{}, t + 1); else body(I0{}, TS{}, t + 1);
+      t += 2;
+    } else {
+      __syncthreads();
+      body(IR{}, TG{}, t);
+      ++t;
+    }
   }
 }
 
