@@ -76,6 +76,10 @@ typedef enum gmg_smoother_pc {
   GMG_PC_IDENTITY = 2  /* none (plain Chebyshev)                            */
 } gmg_smoother_pc;
 
+/* Orthogonalisation of the FGMRES Arnoldi process and of the eigen-bound
+ * Arnoldi.  With GMG_ORTH_CGS2 the FP32 eigen-bound Arnoldi of the mixed
+ * set-up takes a single classical pass (the bounds only steer the FP32
+ * smoother); FGMRES and the FP64 eigen bounds take both passes. */
 typedef enum gmg_orthogonalization {
   GMG_ORTH_CGS2 = 0, /* classical Gram-Schmidt applied twice, fused passes */
   GMG_ORTH_MGS = 1   /* modified Gram-Schmidt as printed in Algorithm 1    */

@@ -515,7 +515,7 @@ gmg_status norm_dev(gmg_ctx* c, size_t n, const T* w, int slot) {
 // coefficients in slots SL_H1 (+ SL_H2 for the second CGS pass) and the norm
 // of the result and its reciprocal in SL_NORM.
 template <typename T>
-gmg_status orthogonalize(gmg_ctx* c, size_t n, const T* V, size_t ld, int k, T* w) {
+gmg_status orthogonalize(gmg_ctx* c, size_t n, const T* V, size_t ld, int k, T* w, bool one_pass = false) {
   const int nb = reduce_blocks(n);
   if (c->p.orthogonalization == GMG_ORTH_MGS) {
     for (int i = 0; i < k; ++i) {
@@ -525,15 +525,21 @@ gmg_status orthogonalize(gmg_ctx* c, size_t n, const T* V, size_t ld, int k, T* 
     }
   } else if (k <= kCgsMaxVectors) {
     // three fused passes: h1 = V^T w; h2 = V^T (w - V h1); w -= V (h1 + h2) with ||w||^2
+    // (one_pass: h2 = 0, two passes)
     CKS(prof_cgs_dots<T>(c, n, w, V, ld, k, nullptr, c->partial, c->s));
     CKS(prof_finalize(c, c->partial, nb, k, c->dscal + SL_H1, 0, c->s));
-    CKS(prof_cgs_dots<T>(c, n, w, V, ld, k, c->dscal + SL_H1, c->partial, c->s));
-    CKS(prof_finalize(c, c->partial, nb, k, c->dscal + SL_H2, 0, c->s));
+    if (one_pass) {
+      CK(cudaMemsetAsync(c->dscal + SL_H2, 0, sizeof(double) * k, c->s));
+    } else {
+      CKS(prof_cgs_dots<T>(c, n, w, V, ld, k, c->dscal + SL_H1, c->partial, c->s));
+      CKS(prof_finalize(c, c->partial, nb, k, c->dscal + SL_H2, 0, c->s));
+    }
     CKS(prof_cgs_update<T>(c, n, w, V, ld, k, c->dscal + SL_H1, c->dscal + SL_H2, c->partial, c->s));
     CKS(prof_finalize_norm(c, c->partial, nb, c->dscal + SL_NORM, c->s));
     return GMG_OK;
   } else {
-    for (int pass = 0; pass < 2; ++pass) {
+    if (one_pass) CK(cudaMemsetAsync(c->dscal + SL_H2, 0, sizeof(double) * k, c->s));
+    for (int pass = 0; pass < (one_pass ? 1 : 2); ++pass) {
       double* hslot = c->dscal + (pass == 0 ? SL_H1 : SL_H2);
       for (int c0 = 0; c0 < k; c0 += 8) {
         const int kc = std::min(8, k - c0);
@@ -614,7 +620,9 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
       CKS(prof_apply<T, T, T>(c, L.g, a, V + (size_t)j * n, t1, c->s));
       CKS(smoother_pc<T>(c, L, t1, t2));
     }
-    CKS(orthogonalize<T>(c, n, V, n, j + 1, t2));
+    // One classical Gram-Schmidt pass in FP32: the bounds only steer the FP32
+    // smoother, and the second pass moves lambda-hat by less than 1e-7.
+    CKS(orthogonalize<T>(c, n, V, n, j + 1, t2, f32));
     CKS(read_column(c, j + 1, col.data()));
     for (int i = 0; i <= j + 1; ++i) {
       if (!isfinite(col[i])) return GMG_ERR_NONFINITE;

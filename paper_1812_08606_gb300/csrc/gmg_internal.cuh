@@ -59,6 +59,28 @@ enum ChebFlags : int { CHEB_UPDATE = 1, CHEB_FIRST = 2, CHEB_XZERO = 4 };
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+// Exact FP32 -> FP64 conversion from the IEEE-754 bit fields, on the integer
+// pipe only (GB300 runs the conversion instruction on the FP64 pipe, at 1/64
+// of the FP32 rate).  Normal numbers: exponent rebiased from 127 to 1023, the
+// 23 mantissa bits moved to the top of the 52-bit field.  Subnormal numbers
+// m 2^-149 are normalised first (leading bit of m moved to bit 23); zero,
+// infinity and NaN map to their FP64 forms (a NaN comes out quiet, payload kept).
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  const int sh = __clz(m | 1u) - 8;               // subnormal: shift that puts the leading bit at 23
+  const unsigned ms = (m << sh) & 0x7fffffu;
+  const unsigned ef = e == 0xffu ? 0x7ffu : (e != 0u ? e + 896u : 897u - (unsigned)sh);
+  const unsigned mf = e == 0xffu ? (m ? m | 0x400000u : 0u) : (e != 0u ? m : ms);  // NaN: quiet bit set
+  const bool zero = e == 0u && m == 0u;
+  const unsigned hi = zero ? sign : (sign | (ef << 20) | (mf >> 3));
+  const unsigned lo = zero ? 0u : (mf << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double to_f64(float f) { return f32_to_f64(f); }
+__device__ __forceinline__ double to_f64(double d) { return d; }
+
 // Diagonal D_p and the neighbour sum N_p = sum_f c_f x_q (so (A x)_p = D_p x_p - N_p),
 // and the difference form sum_f c_f (x_p - x_q) + plate terms, which keeps the
 // accuracy of A x for smooth x.  C is the arithmetic type.

@@ -31,9 +31,9 @@ __global__ void k_rhs(Grid3 g, const double* __restrict__ a, const double* __res
 }
 
 template <typename TE>
-__global__ void k_field(Grid3 g, double ihx2, double ihy2, double ihz2, const double* __restrict__ phi,
-                        TE* __restrict__ ex, TE* __restrict__ ey, TE* __restrict__ ez, double g_bot,
-                        double g_top) {
+__global__ void k_field(Grid3 g, double ihx2, double ihy2, double ihz2, float fhx, float fhy, float fhz,
+                        const double* __restrict__ phi, TE* __restrict__ ex, TE* __restrict__ ey,
+                        TE* __restrict__ ez, double g_bot, double g_top) {
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y;
   const int k = blockIdx.z;
@@ -47,9 +47,18 @@ __global__ void k_field(Grid3 g, double ihx2, double ihy2, double ihz2, const do
   const double yp = (j < g.ny - 1) ? phi[p + g.nx] : c;
   const double zm = (k > 0) ? phi[p - pl] : 2.0 * g_bot - c;  // plate ghost 2g - phi
   const double zp = (k < g.nz - 1) ? phi[p + pl] : 2.0 * g_top - c;
-  ex[p] = (TE)(-(xp - xm) * ihx2);
-  ey[p] = (TE)(-(yp - ym) * ihy2);
-  ez[p] = (TE)(-(zp - zm) * ihz2);
+  if constexpr (sizeof(TE) == 4) {
+    // FP32 output: the FP64 differences are rounded once to FP32 and scaled
+    // in FP32, which keeps the error at two FP32 roundings and takes three
+    // FP64-pipe instructions per cell fewer.
+    ex[p] = (float)(xm - xp) * fhx;
+    ey[p] = (float)(ym - yp) * fhy;
+    ez[p] = (float)(zm - zp) * fhz;
+  } else {
+    ex[p] = (TE)(-(xp - xm) * ihx2);
+    ey[p] = (TE)(-(yp - ym) * ihy2);
+    ez[p] = (TE)(-(zp - zm) * ihz2);
+  }
 }
 
 __global__ void k_adjoint_grad(Grid3 g, const double* __restrict__ phi, const double* __restrict__ lam,
@@ -178,11 +187,11 @@ cudaError_t launch_field(const Grid3& g, double hx, double hy, double hz, const 
   dim3 grid((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 7) / 8), (unsigned)g.nz);
   const double ix = 0.5 / hx, iy = 0.5 / hy, iz = 0.5 / hz;
   if (out_fp32)
-    k_field<float><<<grid, dim3(32, 8), 0, s>>>(g, ix, iy, iz, phi, (float*)ex, (float*)ey, (float*)ez, g_bot,
-                                                g_top);
+    k_field<float><<<grid, dim3(32, 8), 0, s>>>(g, ix, iy, iz, (float)ix, (float)iy, (float)iz, phi, (float*)ex,
+                                                (float*)ey, (float*)ez, g_bot, g_top);
   else
-    k_field<double><<<grid, dim3(32, 8), 0, s>>>(g, ix, iy, iz, phi, (double*)ex, (double*)ey, (double*)ez,
-                                                 g_bot, g_top);
+    k_field<double><<<grid, dim3(32, 8), 0, s>>>(g, ix, iy, iz, (float)ix, (float)iy, (float)iz, phi,
+                                                 (double*)ex, (double*)ey, (double*)ez, g_bot, g_top);
   return cudaGetLastError();
 }
 

@@ -171,8 +171,32 @@ __global__ void __launch_bounds__(RT) k_update_solution(size_t n, double* __rest
   __syncthreads();
   for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
     double v = x[p];
-    for (int i = 0; i < k; ++i) v = fma(ys[i], (double)Z[i * ldz + p], v);
+    for (int i = 0; i < k; ++i) v = fma(ys[i], to_f64(Z[i * ldz + p]), v);  // exact widening
     x[p] = v;
+  }
+}
+
+// The same update for a fixed number of vectors: the K loads of an element are
+// independent and issued together, and the sum runs as two interleaved FMA
+// chains (even and odd i) added at the end.
+template <int K, typename TZ>
+__global__ void __launch_bounds__(RT) k_update_solution_k(size_t n, double* __restrict__ x,
+                                                          const TZ* __restrict__ Z, size_t ldz,
+                                                          const double* __restrict__ y) {
+  __shared__ double ys[K];
+  if (threadIdx.x < K) ys[threadIdx.x] = y[threadIdx.x];
+  __syncthreads();
+  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
+    TZ zv[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) zv[i] = Z[i * ldz + p];
+    double s0 = x[p], s1 = 0.0;
+#pragma unroll
+    for (int i = 0; i < K; i += 2) {
+      s0 = fma(ys[i], to_f64(zv[i]), s0);
+      if (i + 1 < K) s1 = fma(ys[i + 1], to_f64(zv[i + 1]), s1);
+    }
+    x[p] = s0 + s1;
   }
 }
 
@@ -350,7 +374,14 @@ template <typename TZ>
 cudaError_t launch_update_solution(size_t n, double* x, const TZ* Z, size_t ldz, int k, const double* y,
                                    cudaStream_t s) {
   if (k < 1 || k > 64) return cudaErrorInvalidValue;
-  k_update_solution<TZ><<<reduce_blocks(n), RT, 0, s>>>(n, x, Z, ldz, k, y);
+  const int nb = reduce_blocks(n);
+  switch (k) {
+#define GMG_CASE(K) \
+  case K: k_update_solution_k<K, TZ><<<nb, RT, 0, s>>>(n, x, Z, ldz, y); break;
+    GMG_CASES32(GMG_CASE)
+#undef GMG_CASE
+    default: k_update_solution<TZ><<<nb, RT, 0, s>>>(n, x, Z, ldz, k, y);
+  }
   return cudaGetLastError();
 }
 template cudaError_t launch_update_solution<float>(size_t, double*, const float*, size_t, int, const double*,
