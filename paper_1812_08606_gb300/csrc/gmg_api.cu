@@ -1199,7 +1199,8 @@ gmg_status gmg_level_apply(gmg_ctx* c, int level, const void* x, void* y) {
 gmg_status gmg_level_smooth(gmg_ctx* c, int level, const void* b, void* x, int x_is_zero) {
   LevelData* L = level_ptr(c, level);
   if (!L || level == 0 || !b || !x || !L->r) return GMG_ERR_ARG;
-  if (c->mixed && L->fused) {
+  // the fused kernel reads b and x as float2: other alignments take the separate kernels
+  if (c->mixed && L->fused && pair_aligned(b) && pair_aligned(x)) {
     float* X = (float*)x;
     if (x_is_zero) return smooth_fused(c, level, (const float*)b, nullptr, X, L->x2);
     if (c->p.cheb_steps % 2 == 0) return smooth_fused(c, level, (const float*)b, X, X, L->x2);

@@ -165,9 +165,15 @@ cudaError_t launch_residual_restrict(const Grid3& g, const T* a, const T* b, con
 template <typename T>
 cudaError_t launch_prolong_add(const Grid3& g_fine, const T* e, T* x, int mode, cudaStream_t s);
 
+// The cell-pair kernels read and write FP32 arrays as float2: every such array
+// must start on an 8-byte boundary (their launchers refuse others with
+// cudaErrorMisalignedAddress and launch nothing).
+inline bool pair_aligned(const void* p) { return ((uintptr_t)p & 7) == 0; }
+
 // FP32 forms of the two transfers above with one thread per fine cell pair
 // (k_transfer.cu); the FP32 instantiations of launch_residual_restrict and
-// launch_prolong_add use them.  g is the fine grid (all dimensions even).
+// launch_prolong_add use them for 8-byte aligned arrays and fall back to the
+// one-cell kernels otherwise.  g is the fine grid (all dimensions even).
 cudaError_t launch_restrict_pairs(const Grid3& g, const float* a, const float* b, const float* x, float* coarse,
                                   cudaStream_t s);
 cudaError_t launch_prolong_pairs(const Grid3& g, const float* e, float* x, int mode, cudaStream_t s);

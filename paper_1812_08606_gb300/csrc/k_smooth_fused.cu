@@ -322,6 +322,8 @@ bool fused_smoother_eligible(const Grid3& g) { return g.nx >= 32 && g.nx % 2 == 
 
 cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b, const float* xin, float* xout,
                                     float* d, double c1, double c2, int flags, cudaStream_t s) {
+  if (!pair_aligned(a) || !pair_aligned(b) || (xin && !pair_aligned(xin)) || !pair_aligned(xout) || !pair_aligned(d))
+    return cudaErrorMisalignedAddress;
   if (!g_fused_attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_cheb_sgs_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)FUSED_SMEM);

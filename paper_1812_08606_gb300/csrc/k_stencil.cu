@@ -257,7 +257,9 @@ cudaError_t launch_cheb_update(size_t n, const T* z, T* d, T* x, double c1, doub
 template <typename T>
 cudaError_t launch_residual_restrict(const Grid3& g, const T* a, const T* b, const T* x, T* coarse,
                                      cudaStream_t s) {
-  if constexpr (std::is_same<T, float>::value) return launch_restrict_pairs(g, a, b, x, coarse, s);
+  if constexpr (std::is_same<T, float>::value) {
+    if (pair_aligned(a) && pair_aligned(b) && pair_aligned(x)) return launch_restrict_pairs(g, a, b, x, coarse, s);
+  }
   dim3 grid((unsigned)((g.nx / 2 + BX - 1) / BX), (unsigned)((g.ny / 2 + BY - 1) / BY), (unsigned)(g.nz / 2));
   k_residual_restrict<T><<<grid, dim3(BX, BY), 0, s>>>(g, a, b, x, coarse);
   return cudaGetLastError();
@@ -265,7 +267,9 @@ cudaError_t launch_residual_restrict(const Grid3& g, const T* a, const T* b, con
 
 template <typename T>
 cudaError_t launch_prolong_add(const Grid3& g, const T* e, T* x, int mode, cudaStream_t s) {
-  if constexpr (std::is_same<T, float>::value) return launch_prolong_pairs(g, e, x, mode, s);
+  if constexpr (std::is_same<T, float>::value) {
+    if (pair_aligned(x)) return launch_prolong_pairs(g, e, x, mode, s);
+  }
   k_prolong_add<T><<<grid_cells(g), dim3(BX, BY), 0, s>>>(g, e, x, mode);
   return cudaGetLastError();
 }

@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(TP* TR) k_prolong_pairs(Grid3 g, const float* 
 
 cudaError_t launch_restrict_pairs(const Grid3& g, const float* a, const float* b, const float* x, float* coarse,
                                   cudaStream_t s) {
+  if (!pair_aligned(a) || !pair_aligned(b) || !pair_aligned(x) || g.nx % 2) return cudaErrorMisalignedAddress;
   const int gx = (g.nx / 2 + TP - 1) / TP, gy = (g.ny + TR - 1) / TR;
   const int nzc = g.nz / 2;
   const int zc = z_chunks((long long)gx * gy, nzc, 4);
@@ -218,6 +219,7 @@ cudaError_t launch_restrict_pairs(const Grid3& g, const float* a, const float* b
 }
 
 cudaError_t launch_prolong_pairs(const Grid3& g, const float* e, float* x, int mode, cudaStream_t s) {
+  if (!pair_aligned(x) || g.nx % 2) return cudaErrorMisalignedAddress;
   const int gx = (g.nx / 2 + TP - 1) / TP, gy = (g.ny + TR - 1) / TR;
   const int nzc = g.nz / 2;
   const int zc = z_chunks((long long)gx * gy, nzc, 4);

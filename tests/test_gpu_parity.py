@@ -96,14 +96,14 @@ def test_apply_operator_and_rhs_fp64(shape, lengths):
 
 
 @pytest.mark.parametrize("arith,tol", [(gmg.GMG_OUTER_DOUBLE_FLOAT, 2e-14), (gmg.GMG_OUTER_FP64, 1e-15)])
-@pytest.mark.parametrize("shape", [RAGGED, (64, 64, 64), (10, 8, 8)])
+@pytest.mark.parametrize("shape", [RAGGED, (64, 64, 64), (10, 8, 8), (8, 24, 144)])
 def test_outer_arnoldi_product(arith, tol, shape):
     """w = A z_j for an FP32 z_j (the mixed-precision Arnoldi product) against
     the FP64 oracle operator on the same z; double-float arithmetic keeps a
     48-bit significand, so it agrees to ~1e-14."""
     a = make_inputs("twochannel512", shape=shape)["a"] if shape[0] >= 16 else random_coefficient(240, shape, 1e4)
     z = random_field(241, shape).astype(np.float32)
-    cm = 2 if shape == RAGGED else 4
+    cm = 2 if shape in (RAGGED, (8, 24, 144)) else 4
     p = _params(shape, coarse_min=cm, precision=gmg.GMG_PREC_MIXED, outer_arith=arith)
     ctx = gmg.gmg_setup(p, _t(a))
     w = torch.empty(shape, dtype=torch.float64, device=DEV)
@@ -111,6 +111,25 @@ def test_outer_arnoldi_product(arith, tol, shape):
     ref = O.apply_operator(_ogrid(shape), a, z.astype(np.float64))
     err = np.abs(_np(w) - ref).max() / np.abs(ref).max()
     assert err < tol, err
+
+
+def test_outer_product_pair_and_cell_kernels_agree_bitwise():
+    """The double-float product has a cell-pair kernel (even rows, 16-byte
+    aligned output) and a one-cell kernel (any other layout) doing the same
+    operations per cell; an output offset by one double takes the latter."""
+    shape = (8, 24, 144)
+    a = random_coefficient(243, shape, 1e4)
+    z = random_field(244, shape).astype(np.float32)
+    p = _params(shape, coarse_min=2, precision=gmg.GMG_PREC_MIXED, outer_arith=gmg.GMG_OUTER_DOUBLE_FLOAT)
+    ctx = gmg.gmg_setup(p, _t(a))
+    n = int(np.prod(shape))
+    w_pair = torch.empty(shape, dtype=torch.float64, device=DEV)
+    gmg.gmg_apply_outer(ctx, _t(z, torch.float32), w_pair)
+    buf = torch.empty(n + 1, dtype=torch.float64, device=DEV)
+    w_cell = buf[1:].view(shape)
+    assert w_cell.data_ptr() % 16 == 8
+    gmg.gmg_apply_outer(ctx, _t(z, torch.float32), w_cell)
+    assert torch.equal(w_pair, w_cell)
 
 
 def test_mixed_eigen_bounds_close_to_fp64():
@@ -285,6 +304,51 @@ def test_transfers_and_coarse_solve(prec, mode, shape):
     A = O.dense_operator(_ogrid(sc), oa)
     ref = np.linalg.solve(A, b.ravel()).reshape(sc)
     assert _rel(_np(x), ref) < (1e-5 if fp32 else 1e-12)
+
+
+def _offset_view(arr, dtype):
+    """A contiguous device copy of arr whose storage starts 4 bytes past an
+    8-byte boundary (as a sub-view of a larger allocation can)."""
+    n = arr.size
+    buf = torch.empty(n + 1, dtype=dtype, device=DEV)
+    v = buf[1:].view(arr.shape)
+    v.copy_(torch.from_numpy(np.ascontiguousarray(arr)).to(DEV))
+    assert v.data_ptr() % 8 == 4
+    return v
+
+
+def test_level_ops_accept_arrays_off_the_pair_alignment():
+    """The FP32 level kernels that move cell pairs as float2 need 8-byte
+    aligned arrays; arrays that are not take the one-cell kernels and give the
+    same results to FP32 rounding."""
+    shape = (8, 24, 144)
+    a = random_coefficient(320, shape, 1e3)
+    ctx = gmg.gmg_setup(_params(shape, coarse_min=2, precision=gmg.GMG_PREC_MIXED), _t(a))
+    lev = gmg.gmg_num_levels(ctx) - 1
+    s = gmg.gmg_level_info(ctx, lev)["shape"]
+    sc = gmg.gmg_level_info(ctx, lev - 1)["shape"]
+    b = random_field(321, s).astype(np.float32)
+    x0 = random_field(322, s).astype(np.float32)
+    e = random_field(323, sc).astype(np.float32)
+    # restriction
+    c1 = torch.empty(sc, dtype=torch.float32, device=DEV)
+    c2 = torch.empty(sc, dtype=torch.float32, device=DEV)
+    gmg.gmg_level_residual_restrict(ctx, lev, _t(b, torch.float32), _t(x0, torch.float32), c1)
+    gmg.gmg_level_residual_restrict(ctx, lev, _offset_view(b, torch.float32), _offset_view(x0, torch.float32), c2)
+    assert _rel(_np(c2), _np(c1)) < 1e-5
+    # prolongation
+    x1 = _t(x0, torch.float32)
+    x2 = _offset_view(x0, torch.float32)
+    gmg.gmg_level_prolong_add(ctx, lev, _t(e, torch.float32), x1)
+    gmg.gmg_level_prolong_add(ctx, lev, _t(e, torch.float32), x2)
+    assert _rel(_np(x2), _np(x1)) < 1e-6
+    # smoothing (fused kernel for aligned arrays, separate kernels otherwise)
+    for x_is_zero in (True, False):
+        x1 = _t(x0, torch.float32)
+        x2 = _offset_view(x0, torch.float32)
+        gmg.gmg_level_smooth(ctx, lev, _t(b, torch.float32), x1, x_is_zero)
+        gmg.gmg_level_smooth(ctx, lev, _offset_view(b, torch.float32), x2, x_is_zero)
+        assert _rel(_np(x2), _np(x1)) < 1e-5, x_is_zero
 
 
 @pytest.mark.parametrize("shape,cm", [(RAGGED, 2), ((32, 32, 32), 4), ((20, 16, 16), 4)])
