@@ -233,6 +233,10 @@ struct gmg_ctx {
   double *st_a = nullptr, *st_f = nullptr, *st_phi = nullptr;
   void *st_ex = nullptr, *st_ey = nullptr, *st_ez = nullptr;
   int st_fp32 = -1;  // element type of the field staging buffers (-1: none yet)
+  // copy stream of gmg_solve_host: input copies overlap the set-up, the
+  // potential's copy-out overlaps the field kernel
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_a = nullptr, ev_out = nullptr;
   float setup_ms = 0.f;
   // per-kernel profile
   bool prof_on = false;
@@ -984,6 +988,12 @@ void gmg_destroy(gmg_ctx* c) {
   if (c->s) cudaStreamSynchronize(c->s);
   prof_collect(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->cs) {
+    cudaStreamSynchronize(c->cs);
+    cudaStreamDestroy(c->cs);
+  }
+  for (cudaEvent_t e : {c->ev_in, c->ev_a, c->ev_out})
+    if (e) cudaEventDestroy(e);
   for (void* p : c->dev_allocs) cudaFree(p);
   for (void* p : c->host_allocs) cudaFreeHost(p);
   delete c;
@@ -1128,26 +1138,61 @@ gmg_status gmg_solve_host(gmg_ctx* c, const double* a_host, const double* f_host
     CKS(dev_alloc(c, &c->st_ez, n * esz));
     c->st_fp32 = field_fp32 ? 1 : 0;
   }
+  if (!c->cs) {
+    CK(cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+  }
+  // Every return waits for both streams, so no copy touches the host arrays
+  // after the call.
+  auto finish = [&](gmg_status st) {
+    const cudaError_t e1 = cudaStreamSynchronize(c->cs);
+    const cudaError_t e2 = cudaStreamSynchronize(c->s);
+    if (st == GMG_OK && (e1 != cudaSuccess || e2 != cudaSuccess)) return GMG_ERR_CUDA;
+    return st;
+  };
+#define CKF(...)                                       \
+  do {                                                 \
+    const cudaError_t e_ = (__VA_ARGS__);              \
+    if (e_ != cudaSuccess) return finish(map_err(e_)); \
+  } while (0)
+  // a on the compute stream (the set-up needs it); f and phi0 on the copy
+  // stream, after a, so they arrive while the set-up runs
+  CKF(cudaEventRecord(c->ev_a, c->s));  // orders the copies after earlier work on the compute stream
   if (a_host) {
-    CK(cudaMemcpyAsync(c->st_a, a_host, bytes, cudaMemcpyHostToDevice, c->s));
-    CKS(build(c, c->st_a));
+    CKF(cudaMemcpyAsync(c->st_a, a_host, bytes, cudaMemcpyHostToDevice, c->s));
+    CKF(cudaEventRecord(c->ev_a, c->s));
   }
-  CK(cudaMemcpyAsync(c->st_f, f_host, bytes, cudaMemcpyHostToDevice, c->s));
+  CKF(cudaStreamWaitEvent(c->cs, c->ev_a, 0));
+  CKF(cudaMemcpyAsync(c->st_f, f_host, bytes, cudaMemcpyHostToDevice, c->cs));
   if (phi0_host)
-    CK(cudaMemcpyAsync(c->st_phi, phi0_host, bytes, cudaMemcpyHostToDevice, c->s));
+    CKF(cudaMemcpyAsync(c->st_phi, phi0_host, bytes, cudaMemcpyHostToDevice, c->cs));
   else
-    CK(cudaMemsetAsync(c->st_phi, 0, bytes, c->s));
-  gmg_status st = solve_impl(c, c->st_f, c->st_phi, 0, info);
-  if (st != GMG_OK && st != GMG_ERR_NOT_CONVERGED) return st;
-  if (want_e) CKS(field_from_potential(c, c->st_phi, c->st_ex, c->st_ey, c->st_ez, field_fp32));
-  CK(cudaMemcpyAsync(phi_host, c->st_phi, bytes, cudaMemcpyDeviceToHost, c->s));
-  if (want_e) {
-    CK(cudaMemcpyAsync(ex_host, c->st_ex, n * esz, cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(ey_host, c->st_ey, n * esz, cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(ez_host, c->st_ez, n * esz, cudaMemcpyDeviceToHost, c->s));
+    CKF(cudaMemsetAsync(c->st_phi, 0, bytes, c->cs));
+  CKF(cudaEventRecord(c->ev_in, c->cs));
+  if (a_host) {
+    const gmg_status bs = build(c, c->st_a);
+    if (bs != GMG_OK) return finish(bs);
   }
-  CK(cudaStreamSynchronize(c->s));
-  return st;
+  CKF(cudaStreamWaitEvent(c->s, c->ev_in, 0));
+  gmg_status st = solve_impl(c, c->st_f, c->st_phi, 0, info);
+  if (st != GMG_OK && st != GMG_ERR_NOT_CONVERGED) return finish(st);
+  // phi leaves on the copy stream while the field kernel runs
+  CKF(cudaEventRecord(c->ev_out, c->s));
+  CKF(cudaStreamWaitEvent(c->cs, c->ev_out, 0));
+  CKF(cudaMemcpyAsync(phi_host, c->st_phi, bytes, cudaMemcpyDeviceToHost, c->cs));
+  if (want_e) {
+    const gmg_status fs = field_from_potential(c, c->st_phi, c->st_ex, c->st_ey, c->st_ez, field_fp32);
+    if (fs != GMG_OK) return finish(fs);
+    CKF(cudaEventRecord(c->ev_out, c->s));
+    CKF(cudaStreamWaitEvent(c->cs, c->ev_out, 0));
+    CKF(cudaMemcpyAsync(ex_host, c->st_ex, n * esz, cudaMemcpyDeviceToHost, c->cs));
+    CKF(cudaMemcpyAsync(ey_host, c->st_ey, n * esz, cudaMemcpyDeviceToHost, c->cs));
+    CKF(cudaMemcpyAsync(ez_host, c->st_ez, n * esz, cudaMemcpyDeviceToHost, c->cs));
+  }
+#undef CKF
+  return finish(st);
 }
 
 gmg_status gmg_set_stream(gmg_ctx* c, void* stream) {
