@@ -96,6 +96,19 @@ typedef enum gmg_outer_arith {
   GMG_OUTER_DOUBLE_FLOAT = 1 /* FP32 pairs (default)                         */
 } gmg_outer_arith;
 
+/* Multigrid cycle used as the FGMRES preconditioner (Sec. 3.2).  The paper
+ * preconditions the first time step, which has no previous potential and so
+ * starts from a zero guess, with full multigrid, and later steps with
+ * V-cycles. */
+typedef enum gmg_cycle {
+  GMG_CYCLE_V = 0,    /* one V-cycle from a zero guess (default)             */
+  GMG_CYCLE_FMG = 1,  /* full multigrid: the right-hand side is restricted to
+                         every level, the coarsest grid solved directly, and
+                         each finer level takes one V-cycle from the prolonged
+                         coarser result                                     */
+  GMG_CYCLE_AUTO = 2  /* FMG when the solve's initial guess is zero, else V  */
+} gmg_cycle;
+
 typedef struct gmg_params {
   int nx, ny, nz;              /* cells; halving all three must reach a grid
                                   whose smallest side equals coarse_min      */
@@ -119,6 +132,7 @@ typedef struct gmg_params {
                                   the level allows it (FP32, SGS, nx >= 32,
                                   ny >= 16, nz >= 8); 1: separate residual
                                   and half-sweep kernels everywhere          */
+  int cycle;                   /* gmg_cycle                                  */
 } gmg_params;
 
 typedef struct gmg_solve_info {
@@ -131,6 +145,7 @@ typedef struct gmg_solve_info {
   double res_history[GMG_MAX_HISTORY]; /* least-squares residual / ||b|| per iteration */
   float setup_ms;              /* last set-up (gmg_setup / update) time, ms    */
   float solve_ms;              /* this solve, ms (host wall clock incl. syncs) */
+  int fmg;                     /* 1 if this solve was preconditioned by FMG     */
 } gmg_solve_info;
 
 /* Fill *p with the paper's defaults for an nx x ny x nz unit-cube grid:
@@ -187,6 +202,32 @@ gmg_status field_from_potential(gmg_ctx* ctx, const double* phi_dev, void* ex_de
 gmg_status adjoint_coefficient_grad(gmg_ctx* ctx, const double* phi_dev, const double* lambda_dev,
                                     double* dlda_dev);
 
+/* Constants of the elliptic step of the semi-implicit scheme (Sec. 2.1). */
+typedef struct gmg_density_coef {
+  double tau;                  /* time step tau_n                             */
+  double mu_e, mu_p;           /* electron / ion mobility (magnitudes used:
+                                  the paper prints mu_e with both signs)      */
+  double diff_x, diff_y, diff_z; /* electron diffusion D_e = diag(...)        */
+  double e_over_eps0;          /* e / eps0 in the units of the densities,
+                                  mobilities and lengths (1.809514e-6 V cm for
+                                  cm^-3, cm^2/(V s) and cm)                   */
+} gmg_density_coef;
+
+/* Coefficient and right-hand side of the elliptic equation eq. (semi2) in its
+ * discrete form eq. (e18) (Sec. 2.2), from the electron and ion densities at
+ * t_n, divided through by eps0/e so that a = 1 in vacuum:
+ *   a = 1 + (e/eps0) (tau/2) (|mu_p| n_p + |mu_e| n_e)
+ *   f = (e/eps0) [n_p - n_e - (tau/2) sum_alpha D_alpha delta_alpha^2 n_e / h_alpha^2]
+ * where delta_alpha^2 is the second difference along alpha with the densities'
+ * homogeneous Neumann ghosts (ghost = interior cell).  The grid (nx, ny, nz,
+ * lx, ly, lz) is taken from p; no context is needed, so the first time step
+ * can assemble a before gmg_setup.  ne_dev, np_dev, a_dev, f_dev: FP64 device
+ * arrays of nx*ny*nz cells, caller-owned; a_dev / f_dev may not alias the
+ * densities.  stream: a cudaStream_t or NULL.  Errors: GMG_ERR_ARG (null
+ * pointer, bad grid, tau < 0 or non-finite constants), GMG_ERR_CUDA. */
+gmg_status assemble_coefficient_rhs(const gmg_params* p, const double* ne_dev, const double* np_dev,
+                                    const gmg_density_coef* dc, double* a_dev, double* f_dev, void* stream);
+
 /* End-to-end step with HOST buffers: copy a_host (may be NULL to keep the
  * current coefficient; else the set-up is renewed) and f_host to the device,
  * take the initial guess from phi0_host (NULL: zero, a cold start), solve,
@@ -217,9 +258,10 @@ gmg_status gmg_level_info(const gmg_ctx* ctx, int level, int* nx, int* ny, int* 
  * into out_dev (FP64, that level's size). */
 gmg_status gmg_level_coefficient(gmg_ctx* ctx, int level, double* out_dev);
 
-/* One V-cycle from a zero guess, z = M v (Appendix A): v_dev, z_dev FP64 of
- * the finest size.  In mixed mode v is rounded to FP32 and the V-cycle runs
- * in FP32; z is widened back to FP64. */
+/* One V-cycle from a zero guess, z = M v (Appendix A), or full multigrid if
+ * the context's cycle is GMG_CYCLE_FMG: v_dev, z_dev FP64 of the finest size.
+ * In mixed mode v is rounded to FP32 and the cycle runs in FP32; z is widened
+ * back to FP64. */
 gmg_status gmg_apply_preconditioner(gmg_ctx* ctx, const double* v_dev, double* z_dev);
 
 /* w = A z for an FP32 z of the finest size, as FGMRES forms its Arnoldi

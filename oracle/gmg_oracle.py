@@ -17,12 +17,15 @@ simulator for streamer discharges in three dimensions"):
   modified Gram-Schmidt, restarts and the stopping rule eq. (criterion) of
   Sec. 5.2;
 * one geometric-multigrid V-cycle from a zero guess as the preconditioner
-  (Sec. 3.2, eq. (eRichard), Appendix A);
+  (Sec. 3.2, eq. (eRichard), Appendix A), or full multigrid for a solve
+  without a previous potential (the first time step, Sec. 3.2);
 * the Chebyshev smoother eq. (smootheq)-(qntn)-(e19) with a one-step SSOR
   preconditioner and eigen bounds 1.1 / 0.1 times the largest Ritz value of a
   10-step Arnoldi run (Sec. 3.2);
 * a direct (Cholesky) solve on the coarsest grid (Sec. 3.2);
 * E = -grad(phi) by central differences (Sec. 2.2);
+* the coefficient and right-hand side of eq. (semi2) / (e18) from the
+  electron and ion densities (Sec. 2.1, 2.2);
 * the discrete adjoint of the solve (not in the paper; derived from e18).
 
 Readings of points the paper leaves open (each is listed with its reason in
@@ -41,7 +44,12 @@ R6 "quadratic-polynomial" Chebyshev: the smoother is defined by p_n in
 R7 the 10-step Arnoldi for the eigen bounds runs on the smoother's operator
    B^{-1} A_l from a splitmix64-hash start vector;
 R8 after FGMRES's own stopping test, the true residual ||b - A x|| / ||b|| is
-   also required to be below the tolerance, else the method restarts.
+   also required to be below the tolerance, else the method restarts;
+R14 full multigrid carries the right-hand side down by the same 8-child mean
+   as the residuals, prolongs each level's result with the V-cycle's
+   prolongation and takes one V-cycle per level;
+R15 the densities take homogeneous Neumann ghosts in the diffusion term of
+   eq. (e18), and the mobilities enter with their magnitudes.
 
 Array layout: ``(nz, ny, nx)`` float64, x fastest.
 """
@@ -76,6 +84,7 @@ class OracleParams:
     eig_lo: float = 0.1          # Sec. 3.2
     prolongation: str = "trilinear"   # R4; or "constant"
     smoother_pc: str = "sgs"          # R5; or "jacobi", "identity"
+    cycle: str = "v"             # preconditioner: "v", "fmg", or "auto" (FMG for a zero guess, Sec. 3.2)
 
 
 @dataclass
@@ -472,6 +481,42 @@ def vcycle(hier: Hierarchy, b: np.ndarray, level: int | None = None) -> np.ndarr
     return x
 
 
+def vcycle_from(hier: Hierarchy, b: np.ndarray, x: np.ndarray, level: int | None = None) -> np.ndarray:
+    """One V-cycle for A_l x = b starting from the guess x: pre-smoothing
+    starts from x, the coarse-grid correction and post-smoothing are those of
+    ``vcycle``.  The result is x + M_l (b - A_l x)."""
+    p = hier.params
+    if level is None:
+        level = len(hier.levels) - 1
+    if level == 0:
+        return coarse_solve(hier, b)
+    lev = hier.levels[level]
+    x = chebyshev_smooth(lev.grid, lev.a, b, x, lev.lam_max, lev.lam_min, p.cheb_steps, p.smoother_pc)
+    r = b - apply_operator(lev.grid, lev.a, x)
+    e = vcycle(hier, restrict(r), level - 1)
+    x = x + prolong(e, p.prolongation)
+    x = chebyshev_smooth(lev.grid, lev.a, b, x, lev.lam_max, lev.lam_min, p.cheb_steps, p.smoother_pc)
+    return x
+
+
+def fmg(hier: Hierarchy, b: np.ndarray) -> np.ndarray:
+    """Full multigrid, the preconditioner of the first time step (Sec. 3.2):
+    the right-hand side is carried down to every level by the same 8-child
+    mean as the residuals; the coarsest equation is solved directly; going
+    up, each level starts from the prolonged solution of the level below and
+    takes one V-cycle."""
+    p = hier.params
+    top = len(hier.levels) - 1
+    rhs = [None] * (top + 1)
+    rhs[top] = b
+    for level in range(top, 0, -1):
+        rhs[level - 1] = restrict(rhs[level])
+    x = coarse_solve(hier, rhs[0])
+    for level in range(1, top + 1):
+        x = vcycle_from(hier, rhs[level], prolong(x, p.prolongation), level)
+    return x
+
+
 # ---------------------------------------------------------------------------
 # FGMRES, Algorithm 1 (Sec. 3.1) with the stopping rule eq. (criterion)
 # ---------------------------------------------------------------------------
@@ -559,8 +604,48 @@ def solve(params: OracleParams, a: np.ndarray, f: np.ndarray, phi0: np.ndarray |
         b = np.array(f, dtype=np.float64, copy=True)
     else:
         b = assemble_rhs(grid, a, f, params.phi_bottom, params.phi_top)
-    phi, info = fgmres(grid, a, b, phi0, lambda v: vcycle(hier, v), params)
+    cycle = params.cycle
+    if cycle == "auto":   # Sec. 3.2: FMG when there is no previous potential, V-cycles after
+        cycle = "fmg" if phi0 is None or not np.any(phi0) else "v"
+    precond = (lambda v: fmg(hier, v)) if cycle == "fmg" else (lambda v: vcycle(hier, v))
+    phi, info = fgmres(grid, a, b, phi0, precond, params)
     return phi, info, hier
+
+
+# ---------------------------------------------------------------------------
+# Coefficient and right-hand side of the elliptic step from the densities
+# ---------------------------------------------------------------------------
+
+ELEMENTARY_CHARGE = 1.602176634e-19          # C (exact in the SI)
+VACUUM_PERMITTIVITY_CM = 8.8541878128e-14   # F/cm (CODATA 2018)
+
+
+def neumann_second_difference(u: np.ndarray, axis: int) -> np.ndarray:
+    """delta^2 u = u_{i+1} - 2 u_i + u_{i-1} along ``axis`` with the
+    homogeneous Neumann condition of the densities (ghost = interior cell),
+    Sec. 2.2."""
+    u = np.moveaxis(u, axis, 0)
+    ext = np.concatenate([u[:1], u, u[-1:]], axis=0)
+    return np.moveaxis(ext[2:] - 2.0 * u + ext[:-2], 0, axis)
+
+
+def assemble_coefficient_rhs(grid: Grid, n_e: np.ndarray, n_p: np.ndarray, tau: float, mu_e: float,
+                             mu_p: float, diffusion: tuple, e_over_eps0: float):
+    """a and f of the elliptic equation eq. (semi2) in its discrete form
+    eq. (e18), divided through by eps0/e so that a = 1 in vacuum:
+
+        P = eps0/e + (tau/2)(mu_p n_p + mu_e n_e),   a = (e/eps0) P,
+        f = (e/eps0) [n_p - n_e - (tau/2) sum_alpha D_alpha delta_alpha^2 n_e / h_alpha^2].
+
+    The mobility enters with its magnitude (R11: the sign of mu_e differs
+    between Sec. 2 and Sec. 5.2)."""
+    a = 1.0 + e_over_eps0 * 0.5 * tau * (abs(mu_p) * n_p + abs(mu_e) * n_e)
+    dx, dy, dz = diffusion
+    lap = (dx / grid.hx ** 2 * neumann_second_difference(n_e, 2)
+           + dy / grid.hy ** 2 * neumann_second_difference(n_e, 1)
+           + dz / grid.hz ** 2 * neumann_second_difference(n_e, 0))
+    f = e_over_eps0 * (n_p - n_e - 0.5 * tau * lap)
+    return a, f
 
 
 # ---------------------------------------------------------------------------

@@ -233,6 +233,7 @@ struct gmg_ctx {
   double *st_a = nullptr, *st_f = nullptr, *st_phi = nullptr;
   void *st_ex = nullptr, *st_ey = nullptr, *st_ez = nullptr;
   int st_fp32 = -1;  // element type of the field staging buffers (-1: none yet)
+  bool fmg_now = false;  // the preconditioner of the current solve is full multigrid
   // copy stream of gmg_solve_host: input copies overlap the set-up, the
   // potential's copy-out overlaps the field kernel
   cudaStream_t cs = nullptr;
@@ -484,6 +485,7 @@ gmg_status validate(const gmg_params* p, int* nlevels) {
   if (p->orthogonalization != 0 && p->orthogonalization != 1) return GMG_ERR_ARG;
   if (p->outer_arith != GMG_OUTER_FP64 && p->outer_arith != GMG_OUTER_DOUBLE_FLOAT) return GMG_ERR_ARG;
   if (p->smoother_kernel != 0 && p->smoother_kernel != 1) return GMG_ERR_ARG;
+  if (p->cycle < GMG_CYCLE_V || p->cycle > GMG_CYCLE_AUTO) return GMG_ERR_ARG;
   if ((double)p->nx * p->ny * p->nz > 4.0e9) return GMG_ERR_ARG;
   int nx = p->nx, ny = p->ny, nz = p->nz, L = 1;
   while (std::min(nx, std::min(ny, nz)) > p->coarse_min) {
@@ -762,7 +764,7 @@ gmg_status smooth_fused(gmg_ctx* c, int l, const float* b, const float* xin, flo
 }
 
 template <typename T>
-gmg_status vcycle(gmg_ctx* c, int l, const T* b, T* x) {
+gmg_status vcycle(gmg_ctx* c, int l, const T* b, T* x, bool from_guess = false) {
   if (l == 0) return (prof_coarse_apply<T>(c, c->nc, coarse_inv<T>(c), b, x, c->s));
   const LevelData& L = c->lev[l];
   const LevelData& Lc = c->lev[l - 1];
@@ -773,14 +775,14 @@ gmg_status vcycle(gmg_ctx* c, int l, const T* b, T* x) {
       float* U = L.x2;
       float* pre = (c->p.cheb_steps % 2) ? U : x;
       float* pre_alt = (pre == U) ? x : U;
-      CKS(smooth_fused(c, l, b, nullptr, pre, pre_alt));
+      CKS(smooth_fused(c, l, b, from_guess ? x : nullptr, pre, pre_alt));
       CKS(prof_residual_restrict<float>(c, L.g, a, b, pre, (float*)Lc.b, c->s));
       CKS(vcycle<float>(c, l - 1, (const float*)Lc.b, (float*)Lc.x));
       CKS(prof_prolong_add<float>(c, L.g, (const float*)Lc.x, pre, c->p.prolongation, c->s));
       return smooth_fused(c, l, b, pre, x, U);
     }
   }
-  CKS(smooth<T>(c, l, b, x, true));
+  CKS(smooth<T>(c, l, b, x, !from_guess));
   CKS(prof_residual_restrict<T>(c, L.g, a, b, x, (T*)Lc.b, c->s));
   CKS(vcycle<T>(c, l - 1, (const T*)Lc.b, (T*)Lc.x));
   CKS(prof_prolong_add<T>(c, L.g, (const T*)Lc.x, x, c->p.prolongation, c->s));
@@ -789,13 +791,40 @@ gmg_status vcycle(gmg_ctx* c, int l, const T* b, T* x) {
 }
 
 // z (level precision, finest size) = M v, v FP64.
+// Full multigrid (Sec. 3.2): b is carried down by the 8-child mean, the
+// coarsest grid is solved directly, and each finer level starts from the
+// prolonged coarser result and takes one V-cycle.  Level l < top keeps its
+// right-hand side in lev[l].b and its result in lev[l].x; the V-cycle of
+// level l then reuses the buffers of the levels below, which are done.
+template <typename T>
+gmg_status fmg(gmg_ctx* c, int top, const T* b, T* z) {
+  const T* bl = b;
+  for (int l = top; l >= 1; --l) {
+    CKS(prof_residual_restrict<T>(c, c->lev[l].g, level_a<T>(c->lev[l]), bl, (const T*)nullptr,
+                                  (T*)c->lev[l - 1].b, c->s));
+    bl = (const T*)c->lev[l - 1].b;
+  }
+  CKS(prof_coarse_apply<T>(c, c->nc, coarse_inv<T>(c), (const T*)c->lev[0].b, (T*)c->lev[0].x, c->s));
+  for (int l = 1; l <= top; ++l) {
+    const LevelData& L = c->lev[l];
+    T* xl = l == top ? z : (T*)L.x;
+    const T* blv = l == top ? b : (const T*)L.b;
+    CK(cudaMemsetAsync(xl, 0, L.n * sizeof(T), c->s));
+    CKS(prof_prolong_add<T>(c, L.g, (const T*)c->lev[l - 1].x, xl, c->p.prolongation, c->s));
+    CKS(vcycle<T>(c, l, blv, xl, true));
+  }
+  return GMG_OK;
+}
+
 gmg_status precondition(gmg_ctx* c, const double* v, void* z) {
   const int top = (int)c->lev.size() - 1;
   if (c->mixed) {
     float* bf = (float*)c->lev[top].b;
     CKS(prof_cast_d2f(c, c->N(), v, bf, c->s));
+    if (c->fmg_now && top > 0) return fmg<float>(c, top, bf, (float*)z);
     return vcycle<float>(c, top, bf, (float*)z);
   }
+  if (c->fmg_now && top > 0) return fmg<double>(c, top, v, (double*)z);
   return vcycle<double>(c, top, v, (double*)z);
 }
 
@@ -841,6 +870,9 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
     CKS(norm_dev(c, n, x, SL_NORM));
     CKS(read_scalars(c, SL_NORM, 2));
     bool r0_is_b = c->hpin[SL_NORM] == 0.0;
+    // Sec. 3.2: full multigrid for a solve without a previous potential
+    c->fmg_now = c->p.cycle == GMG_CYCLE_FMG || (c->p.cycle == GMG_CYCLE_AUTO && r0_is_b);
+    loc.fmg = c->fmg_now ? 1 : 0;
     for (;;) {
       // r0 = b - A x0, beta = ||r0||, v1 = r0 / beta (start of an Arnoldi cycle)
       double beta = bnorm;
@@ -968,6 +1000,7 @@ void gmg_default_params(gmg_params* p, int nx, int ny, int nz) {
   p->orthogonalization = GMG_ORTH_CGS2;
   p->outer_arith = GMG_OUTER_DOUBLE_FLOAT;
   p->smoother_kernel = 0;
+  p->cycle = GMG_CYCLE_V;
 }
 
 const char* gmg_status_string(gmg_status s) {
@@ -1195,6 +1228,30 @@ gmg_status gmg_solve_host(gmg_ctx* c, const double* a_host, const double* f_host
   return finish(st);
 }
 
+gmg_status assemble_coefficient_rhs(const gmg_params* p, const double* ne_dev, const double* np_dev,
+                                    const gmg_density_coef* dc, double* a_dev, double* f_dev, void* stream) {
+  if (!p || !ne_dev || !np_dev || !dc || !a_dev || !f_dev) return GMG_ERR_ARG;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || !(p->lx > 0) || !(p->ly > 0) || !(p->lz > 0)) return GMG_ERR_ARG;
+  if (a_dev == ne_dev || a_dev == np_dev || f_dev == ne_dev || f_dev == np_dev || a_dev == f_dev)
+    return GMG_ERR_ARG;
+  const double k[] = {dc->tau, dc->mu_e, dc->mu_p, dc->diff_x, dc->diff_y, dc->diff_z, dc->e_over_eps0};
+  for (double v : k)
+    if (!std::isfinite(v)) return GMG_ERR_ARG;
+  if (dc->tau < 0) return GMG_ERR_ARG;
+  const Grid3 g = make_grid(p->nx, p->ny, p->nz, p->lx, p->ly, p->lz);
+  const double hx = p->lx / p->nx, hy = p->ly / p->ny, hz = p->lz / p->nz;
+  DensityCoef d;
+  d.half_tau_e_eps0_mu_e = dc->e_over_eps0 * 0.5 * dc->tau * std::fabs(dc->mu_e);
+  d.half_tau_e_eps0_mu_p = dc->e_over_eps0 * 0.5 * dc->tau * std::fabs(dc->mu_p);
+  d.e_over_eps0 = dc->e_over_eps0;
+  d.half_tau = 0.5 * dc->tau;
+  d.dx_ih2 = dc->diff_x / (hx * hx);
+  d.dy_ih2 = dc->diff_y / (hy * hy);
+  d.dz_ih2 = dc->diff_z / (hz * hz);
+  const cudaError_t e = launch_assemble(g, d, ne_dev, np_dev, a_dev, f_dev, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GMG_OK : map_err(e);
+}
+
 gmg_status gmg_set_stream(gmg_ctx* c, void* stream) {
   if (!c) return GMG_ERR_ARG;
   CK(cudaStreamSynchronize(c->s));
@@ -1224,6 +1281,7 @@ gmg_status gmg_level_coefficient(gmg_ctx* c, int level, double* out_dev) {
 
 gmg_status gmg_apply_preconditioner(gmg_ctx* c, const double* v_dev, double* z_dev) {
   if (!c || !v_dev || !z_dev) return GMG_ERR_ARG;
+  c->fmg_now = c->p.cycle == GMG_CYCLE_FMG;
   CKS(precondition(c, v_dev, c->Z));
   if (c->mixed) return (prof_cast_f2d(c, c->N(), (const float*)c->Z, z_dev, c->s));
   return (prof_copy_d(c, c->N(), (const double*)c->Z, z_dev, c->s));

@@ -156,7 +156,8 @@ template <typename T>
 cudaError_t launch_cheb_update(size_t n, const T* z, T* d, T* x, double c1, double c2, int flags,
                                cudaStream_t s);
 
-// coarse = mean over the 8 children of (b - A x) on the fine grid g.
+// coarse = mean over the 8 children of (b - A x) on the fine grid g (x null:
+// of b itself).
 template <typename T>
 cudaError_t launch_residual_restrict(const Grid3& g, const T* a, const T* b, const T* x, T* coarse,
                                      cudaStream_t s);
@@ -195,6 +196,14 @@ cudaError_t launch_field(const Grid3& g, double hx, double hy, double hz, const 
                          cudaStream_t s);
 
 // dL/da from phi and lambda.
+// a and f of the elliptic step from the densities (eqs. (semi2), (e18)).
+struct DensityCoef {
+  double half_tau_e_eps0_mu_e, half_tau_e_eps0_mu_p;  // (e/eps0)(tau/2)|mu|
+  double e_over_eps0, half_tau;
+  double dx_ih2, dy_ih2, dz_ih2;                      // D_alpha / h_alpha^2
+};
+cudaError_t launch_assemble(const Grid3& g, const DensityCoef& dc, const double* ne, const double* np, double* a,
+                            double* f, cudaStream_t s);
 cudaError_t launch_adjoint_grad(const Grid3& g, const double* phi, const double* lam, double* out,
                                 double g_bot, double g_top, cudaStream_t s);
 

@@ -61,6 +61,26 @@ __global__ void k_field(Grid3 g, double ihx2, double ihy2, double ihz2, float fh
   }
 }
 
+// a and f of eq. (e18) from the densities, one thread per cell; the second
+// differences of n_e take the densities' zero-flux ghosts (ghost = cell).
+__global__ void k_assemble(Grid3 g, DensityCoef dc, const double* __restrict__ ne, const double* __restrict__ np,
+                           double* __restrict__ a, double* __restrict__ f) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const size_t pl = g.plane();
+  const size_t p = ((size_t)k * g.ny + j) * g.nx + i;
+  const double c = ne[p], ni = np[p];
+  const double xm = i > 0 ? ne[p - 1] : c, xp = i < g.nx - 1 ? ne[p + 1] : c;
+  const double ym = j > 0 ? ne[p - g.nx] : c, yp = j < g.ny - 1 ? ne[p + g.nx] : c;
+  const double zm = k > 0 ? ne[p - pl] : c, zp = k < g.nz - 1 ? ne[p + pl] : c;
+  const double lap = dc.dx_ih2 * ((xp - 2.0 * c) + xm) + dc.dy_ih2 * ((yp - 2.0 * c) + ym) +
+                     dc.dz_ih2 * ((zp - 2.0 * c) + zm);
+  a[p] = 1.0 + (dc.half_tau_e_eps0_mu_p * ni + dc.half_tau_e_eps0_mu_e * c);
+  f[p] = dc.e_over_eps0 * ((ni - c) - dc.half_tau * lap);
+}
+
 __global__ void k_adjoint_grad(Grid3 g, const double* __restrict__ phi, const double* __restrict__ lam,
                                double* __restrict__ out, double g_bot, double g_top) {
   const int i = blockIdx.x * 32 + threadIdx.x;
@@ -192,6 +212,13 @@ cudaError_t launch_field(const Grid3& g, double hx, double hy, double hz, const 
   else
     k_field<double><<<grid, dim3(32, 8), 0, s>>>(g, ix, iy, iz, (float)ix, (float)iy, (float)iz, phi,
                                                  (double*)ex, (double*)ey, (double*)ez, g_bot, g_top);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const Grid3& g, const DensityCoef& dc, const double* ne, const double* np, double* a,
+                            double* f, cudaStream_t s) {
+  dim3 grid((unsigned)((g.nx + 31) / 32), (unsigned)((g.ny + 7) / 8), (unsigned)g.nz);
+  k_assemble<<<grid, dim3(32, 8), 0, s>>>(g, dc, ne, np, a, f);
   return cudaGetLastError();
 }
 

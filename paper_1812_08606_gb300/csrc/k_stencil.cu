@@ -123,6 +123,24 @@ __global__ void __launch_bounds__(BX* BY) k_residual_restrict(Grid3 g, const T* 
   coarse[((size_t)kc * nyc + jc) * nxc + ic] = sum * (T)0.125;
 }
 
+// b_c = mean of the 8 children of b (full multigrid carries the right-hand
+// side down with the residuals' restriction).
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_restrict_only(Grid3 g, const T* __restrict__ b, T* __restrict__ coarse) {
+  const int nxc = g.nx / 2, nyc = g.ny / 2;
+  const int ic = blockIdx.x * BX + threadIdx.x;
+  const int jc = blockIdx.y * BY + threadIdx.y;
+  const int kc = blockIdx.z;
+  if (ic >= nxc || jc >= nyc) return;
+  T sum = (T)0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int i = 2 * ic + (c & 1), j = 2 * jc + ((c >> 1) & 1), k = 2 * kc + (c >> 2);
+    sum += ldg(b + ((size_t)k * g.ny + j) * g.nx + i);
+  }
+  coarse[((size_t)kc * nyc + jc) * nxc + ic] = sum * (T)0.125;
+}
+
 // ---------------------------------------------------------------------------
 // x_fine += P e_coarse.  Trilinear: per axis the child takes 3/4 of its
 // parent and 1/4 of the neighbour on its side; beyond the domain the
@@ -257,10 +275,14 @@ cudaError_t launch_cheb_update(size_t n, const T* z, T* d, T* x, double c1, doub
 template <typename T>
 cudaError_t launch_residual_restrict(const Grid3& g, const T* a, const T* b, const T* x, T* coarse,
                                      cudaStream_t s) {
+  dim3 grid((unsigned)((g.nx / 2 + BX - 1) / BX), (unsigned)((g.ny / 2 + BY - 1) / BY), (unsigned)(g.nz / 2));
+  if (!x) {  // x = 0: b itself
+    k_restrict_only<T><<<grid, dim3(BX, BY), 0, s>>>(g, b, coarse);
+    return cudaGetLastError();
+  }
   if constexpr (std::is_same<T, float>::value) {
     if (pair_aligned(a) && pair_aligned(b) && pair_aligned(x)) return launch_restrict_pairs(g, a, b, x, coarse, s);
   }
-  dim3 grid((unsigned)((g.nx / 2 + BX - 1) / BX), (unsigned)((g.ny / 2 + BY - 1) / BY), (unsigned)(g.nz / 2));
   k_residual_restrict<T><<<grid, dim3(BX, BY), 0, s>>>(g, a, b, x, coarse);
   return cudaGetLastError();
 }

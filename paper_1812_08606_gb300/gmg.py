@@ -36,6 +36,12 @@ GMG_ORTH_CGS2 = 0
 GMG_ORTH_MGS = 1
 GMG_OUTER_FP64 = 0
 GMG_OUTER_DOUBLE_FLOAT = 1
+GMG_CYCLE_V = 0
+GMG_CYCLE_FMG = 1
+GMG_CYCLE_AUTO = 2
+
+# e / eps0 in V cm (densities in cm^-3, mobilities in cm^2/(V s), lengths in cm)
+E_OVER_EPS0_CM = 1.602176634e-19 / 8.8541878128e-14
 
 
 class gmg_params(ctypes.Structure):
@@ -47,7 +53,7 @@ class gmg_params(ctypes.Structure):
         ("max_iters", ctypes.c_int), ("rtol", ctypes.c_double), ("eig_steps", ctypes.c_int),
         ("eig_hi", ctypes.c_double), ("eig_lo", ctypes.c_double), ("precision", ctypes.c_int),
         ("prolongation", ctypes.c_int), ("smoother_pc", ctypes.c_int), ("orthogonalization", ctypes.c_int),
-        ("outer_arith", ctypes.c_int), ("smoother_kernel", ctypes.c_int),
+        ("outer_arith", ctypes.c_int), ("smoother_kernel", ctypes.c_int), ("cycle", ctypes.c_int),
     ]
 
 
@@ -56,12 +62,20 @@ class gmg_solve_info(ctypes.Structure):
         ("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
         ("true_rel_residual", ctypes.c_double), ("bnorm", ctypes.c_double), ("n_history", ctypes.c_int),
         ("res_history", ctypes.c_double * GMG_MAX_HISTORY), ("setup_ms", ctypes.c_float),
-        ("solve_ms", ctypes.c_float),
+        ("solve_ms", ctypes.c_float), ("fmg", ctypes.c_int),
     ]
 
     @property
     def history(self):
         return [self.res_history[i] for i in range(self.n_history)]
+
+
+class gmg_density_coef(ctypes.Structure):
+    _fields_ = [
+        ("tau", ctypes.c_double), ("mu_e", ctypes.c_double), ("mu_p", ctypes.c_double),
+        ("diff_x", ctypes.c_double), ("diff_y", ctypes.c_double), ("diff_z", ctypes.c_double),
+        ("e_over_eps0", ctypes.c_double),
+    ]
 
 
 class GMGError(RuntimeError):
@@ -104,6 +118,8 @@ _SIGS = {
     "gmg_hessenberg_max_real_eig": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gmg_test_fail_allocation_after": (None, [ctypes.c_int]),
     "gmg_coarse_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(gmg_params), _P, _P, _P, _P]),
+    "assemble_coefficient_rhs": (ctypes.c_int, [ctypes.POINTER(gmg_params), _P, _P, ctypes.POINTER(gmg_density_coef),
+                                                _P, _P, _P]),
     "gmg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "gmg_profile_reset": (ctypes.c_int, [_P]),
     "gmg_profile_num_kernels": (ctypes.c_int, []),
@@ -411,3 +427,17 @@ def gmg_coarse_solve_noalloc(params: gmg_params, a: torch.Tensor, b: torch.Tenso
     _check(load().gmg_coarse_solve_noalloc(ctypes.byref(params), _dev(a, numel=n, name="a"),
                                            _dev(b, numel=n, name="b"), _dev(x, numel=n, name="x"),
                                            _stream_ptr(stream)), "gmg_coarse_solve_noalloc")
+
+
+def assemble_coefficient_rhs(params: gmg_params, n_e: torch.Tensor, n_p: torch.Tensor, a: torch.Tensor,
+                             f: torch.Tensor, tau: float, mu_e: float, mu_p: float, diffusion=(0.0, 0.0, 0.0),
+                             e_over_eps0: float = E_OVER_EPS0_CM, stream=None):
+    """a and f of the elliptic step (eqs. (semi2), (e18)) from the densities,
+    on the grid of ``params``; all tensors FP64 on the device."""
+    n = params.nx * params.ny * params.nz
+    dc = gmg_density_coef(float(tau), float(mu_e), float(mu_p), float(diffusion[0]), float(diffusion[1]),
+                          float(diffusion[2]), float(e_over_eps0))
+    _check(load().assemble_coefficient_rhs(ctypes.byref(params), _dev(n_e, numel=n, name="n_e"),
+                                           _dev(n_p, numel=n, name="n_p"), ctypes.byref(dc),
+                                           _dev(a, numel=n, name="a"), _dev(f, numel=n, name="f"),
+                                           _stream_ptr(stream)), "assemble_coefficient_rhs")

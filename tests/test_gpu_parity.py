@@ -67,7 +67,8 @@ def _oracle_hierarchy(a, p):
                         coarse_min=p.coarse_min, cheb_steps=p.cheb_steps, restart=p.restart,
                         max_iters=p.max_iters, rtol=p.rtol, eig_steps=p.eig_steps, eig_hi=p.eig_hi,
                         eig_lo=p.eig_lo, prolongation=["trilinear", "constant"][p.prolongation],
-                        smoother_pc=["sgs", "jacobi", "identity"][p.smoother_pc])
+                        smoother_pc=["sgs", "jacobi", "identity"][p.smoother_pc],
+                        cycle=["v", "fmg", "auto"][p.cycle])
     return op
 
 
@@ -608,3 +609,147 @@ def test_autograd_matches_cpu_adjoint_64():
     ef, ea = _rel(_np(f.grad), lam), _rel(_np(a.grad), ga)
     print(f"adjoint vs CPU at 64^3: dL/df {ef:.2e}, dL/da {ea:.2e}")
     assert ef < 1e-7 and ea < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Full multigrid (first time step) and the assembly from the densities
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("shape,cm", [(RAGGED, 2), ((32, 32, 32), 4), ((8, 24, 144), 2)])
+def test_fmg_preconditioner_fp64_matches_oracle(shape, cm):
+    a = make_inputs("channel128", shape=shape)["a"] if shape[0] >= 16 else random_coefficient(330, shape, 1e3)
+    p = _params(shape, coarse_min=cm, precision=gmg.GMG_PREC_FP64, cycle=gmg.GMG_CYCLE_FMG)
+    ctx = gmg.gmg_setup(p, _t(a))
+    hier = O.build_hierarchy(_ogrid(shape), a, _oracle_hierarchy(a, p))
+    v = random_field(331, shape)
+    z = torch.empty(shape, dtype=torch.float64, device=DEV)
+    gmg.gmg_apply_preconditioner(ctx, _t(v), z)
+    assert _rel(_np(z), O.fmg(hier, v)) < 1e-12
+
+
+def test_fmg_preconditioner_mixed_close_to_oracle():
+    shape = (32, 32, 32)
+    a = make_inputs("twochannel512", shape=shape)["a"]
+    p = _params(shape, precision=gmg.GMG_PREC_MIXED, cycle=gmg.GMG_CYCLE_FMG)
+    ctx = gmg.gmg_setup(p, _t(a))
+    hier = O.build_hierarchy(_ogrid(shape), a, _oracle_hierarchy(a, p))
+    v = random_field(332, shape)
+    z = torch.empty(shape, dtype=torch.float64, device=DEV)
+    gmg.gmg_apply_preconditioner(ctx, _t(v), z)
+    assert _rel(_np(z), O.fmg(hier, v)) < 1e-4
+
+
+@pytest.mark.parametrize("workload,n", [("channel128", 32), ("twochannel512", 32)])
+def test_fmg_solve_fp64_matches_oracle(workload, n):
+    inp = make_inputs(workload, n=n)
+    shape = inp["a"].shape
+    p = _params(shape, precision=gmg.GMG_PREC_FP64, orthogonalization=gmg.GMG_ORTH_MGS, cycle=gmg.GMG_CYCLE_FMG)
+    ref, rinfo, _ = O.solve(_oracle_hierarchy(inp["a"], p), inp["a"], inp["f"])
+    ctx = gmg.gmg_setup(p, _t(inp["a"]))
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    info = gmg.fgmres_solve(ctx, _t(inp["f"]), phi)
+    assert info.fmg == 1
+    assert info.iterations == rinfo.iterations
+    assert _rel(_np(phi), ref) < 1e-10
+    assert info.true_rel_residual < 1e-8
+
+
+def test_auto_cycle_takes_fmg_only_from_a_zero_guess():
+    """Sec. 3.2: full multigrid for the first step (no previous potential),
+    V-cycles once a previous potential is the initial guess."""
+    inp = make_inputs("twochannel512", n=64)
+    shape = inp["a"].shape
+    res = {}
+    for cyc in (gmg.GMG_CYCLE_V, gmg.GMG_CYCLE_AUTO):
+        p = _params(shape, precision=gmg.GMG_PREC_MIXED, cycle=cyc)
+        ctx = gmg.gmg_setup(p, _t(inp["a"]))
+        phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+        first = gmg.fgmres_solve(ctx, _t(inp["f"]), phi)
+        assert first.true_rel_residual < 1e-8
+        # the next "time step": slightly changed coefficient, warm start from phi
+        gmg.gmg_update_coefficient(ctx, _t(inp["a"] * 1.001))
+        second = gmg.fgmres_solve(ctx, _t(inp["f"]), phi)
+        assert second.true_rel_residual < 1e-8
+        res[cyc] = (first, second)
+    v1, v2 = res[gmg.GMG_CYCLE_V]
+    a1, a2 = res[gmg.GMG_CYCLE_AUTO]
+    assert (v1.fmg, v2.fmg, a1.fmg, a2.fmg) == (0, 0, 1, 0)
+    assert a1.iterations <= v1.iterations
+    assert a2.iterations == v2.iterations
+    assert v2.iterations < v1.iterations          # the warm start pays
+
+
+def _densities(shape, seed):
+    """Smooth positive densities of streamer magnitude (cm^-3): a channel
+    profile plus seeded smooth noise, electrons and ions different."""
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) / nz, (np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx,
+                          indexing="ij")
+    prof = np.exp(-((x - 0.5) ** 2 + (y - 0.5) ** 2) / 0.05 ** 2 - (z - 0.5) ** 2 / 0.1 ** 2)
+    ne = 1e8 + 1e14 * prof * (1.0 + 0.1 * random_field(seed, shape))
+    npos = 1e8 + 1e14 * prof * (1.0 + 0.1 * random_field(seed + 1, shape))
+    return ne, npos
+
+
+@pytest.mark.parametrize("shape,lengths", [(RAGGED, (1.0, 1.0, 1.0)), ((8, 24, 144), (2.0, 1.0, 0.5))])
+def test_assembly_matches_oracle(shape, lengths):
+    ne, npos = _densities(shape, 340)
+    p = _params(shape, lx=lengths[0], ly=lengths[1], lz=lengths[2])
+    nz, ny, nx = shape
+    grid = O.Grid(nx, ny, nz, *lengths)
+    kw = dict(tau=2e-12, mu_e=-2.9e5 / 760, mu_p=2.6e3 / 760, diffusion=(2190.0, 2190.0, 1800.0))
+    a_ref, f_ref = O.assemble_coefficient_rhs(grid, ne, npos, kw["tau"], kw["mu_e"], kw["mu_p"], kw["diffusion"],
+                                              gmg.E_OVER_EPS0_CM)
+    a = torch.empty(shape, dtype=torch.float64, device=DEV)
+    f = torch.empty(shape, dtype=torch.float64, device=DEV)
+    gmg.assemble_coefficient_rhs(p, _t(ne), _t(npos), a, f, **kw)
+    np.testing.assert_allclose(_np(a), a_ref, rtol=1e-14, atol=0)
+    assert np.abs(_np(f) - f_ref).max() <= 1e-13 * np.abs(f_ref).max()
+
+
+def test_assembly_rejects_bad_arguments():
+    shape = (8, 8, 8)
+    p = _params(shape)
+    ne = torch.ones(shape, dtype=torch.float64, device=DEV)
+    a = torch.empty_like(ne)
+    f = torch.empty_like(ne)
+    with pytest.raises(gmg.GMGError) as e:
+        gmg.assemble_coefficient_rhs(p, ne, ne, a, f, tau=-1.0, mu_e=1.0, mu_p=1.0)
+    assert e.value.status == gmg.GMG_ERR_ARG
+    with pytest.raises(gmg.GMGError):
+        gmg.assemble_coefficient_rhs(p, ne, ne, ne, f, tau=1.0, mu_e=1.0, mu_p=1.0)      # a aliases n_e
+    with pytest.raises(gmg.GMGError):
+        gmg.assemble_coefficient_rhs(p, ne, ne, a, f, tau=1.0, mu_e=float("nan"), mu_p=1.0)
+
+
+def test_time_steps_from_assembled_densities_converge_with_few_iterations():
+    """The f-1 loop on a 64^3 streamer (eq. (51) densities, Sec. 5.2 mobilities,
+    52 kV): assemble a and f, renew the set-up, solve warm-started from the
+    previous potential; the first step uses FMG (cycle = auto)."""
+    shape = (64, 64, 64)
+    nz, ny, nx = shape
+    p = _params(shape, precision=gmg.GMG_PREC_MIXED, cycle=gmg.GMG_CYCLE_AUTO, phi_top=52e3)
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) / nz, (np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx,
+                          indexing="ij")
+    ctx = None
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    a = torch.empty(shape, dtype=torch.float64, device=DEV)
+    f = torch.empty(shape, dtype=torch.float64, device=DEV)
+    iters = []
+    for step in range(4):
+        zc = 0.5 + 0.01 * step            # the head drifts by 0.01 cm a step
+        n = 1e8 + 1e14 * np.exp(-((z - zc) / 0.027) ** 2 - ((x - 1.0) ** 2 + (y - 1.0) ** 2) / 0.021 ** 2)
+        ne, npos = _t(n), _t(n * (1.0 + 0.05 * step))
+        gmg.assemble_coefficient_rhs(p, ne, npos, a, f, tau=2e-12, mu_e=-2.9e5 / 760, mu_p=2.6e3 / 760,
+                                     diffusion=(2190.0, 2190.0, 1800.0))
+        if ctx is None:
+            ctx = gmg.gmg_setup(p, a)
+        else:
+            gmg.gmg_update_coefficient(ctx, a)
+        info = gmg.fgmres_solve(ctx, f, phi)
+        assert info.true_rel_residual < 1e-8
+        assert info.fmg == (1 if step == 0 else 0)
+        iters.append(info.iterations)
+    assert max(iters[1:]) <= 4, iters
+

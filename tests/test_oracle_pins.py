@@ -536,3 +536,123 @@ def test_adjoint_dot_product_identity():
     lhs = np.dot(inp["w"].ravel(), phi.ravel())
     rhs = np.dot(inp["f"].ravel(), lam.ravel())
     assert lhs == pytest.approx(rhs, rel=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Full multigrid (the first time step's preconditioner, Sec. 3.2)
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("coarse_min,prolongation", [(4, "trilinear"), (2, "trilinear"), (2, "constant")])
+def test_fmg_equals_dense_recursion(coarse_min, prolongation):
+    """A V-cycle from a guess x0 is the consistent iteration x0 + M_l (b - A_l x0),
+    so full multigrid is the matrix F_l = P F_{l-1} R + M_l (I - A_l P F_{l-1} R)
+    with F_1 = A_1^{-1}; M_l is read off the zero-guess V-cycle as a dense matrix."""
+    shape = (8, 8, 8)
+    grid = _grid(shape)
+    a = random_coefficient(41, shape, contrast=30.0)
+    params = O.OracleParams(coarse_min=coarse_min, prolongation=prolongation)
+    hier = O.build_hierarchy(grid, a, params)
+    F = None
+    for li, lev in enumerate(hier.levels):
+        n = lev.grid.size
+        A = O.dense_operator(lev.grid, lev.a)
+        if li == 0:
+            F = np.linalg.inv(A)
+            continue
+        M = _dense_from_map(lambda e: O.vcycle(hier, e, li), n, lev.grid.shape)
+        cshape = hier.levels[li - 1].grid.shape
+        nc = hier.levels[li - 1].grid.size
+        R = np.array([O.restrict(e.reshape(lev.grid.shape)).ravel() for e in np.eye(n)]).T
+        Pr = np.array([O.prolong(e.reshape(cshape), prolongation).ravel() for e in np.eye(nc)]).T
+        X0 = Pr @ F @ R
+        F = X0 + M @ (np.eye(n) - A @ X0)
+    v = random_field(42, shape)
+    np.testing.assert_allclose(O.fmg(hier, v).ravel(), F @ v.ravel(), rtol=1e-10, atol=1e-12)
+
+
+def test_vcycle_from_a_zero_guess_is_the_vcycle():
+    shape = (16, 16, 16)
+    grid = _grid(shape)
+    a = random_coefficient(43, shape, contrast=100.0)
+    hier = O.build_hierarchy(grid, a, O.OracleParams(coarse_min=4))
+    b = random_field(44, shape)
+    np.testing.assert_allclose(O.vcycle_from(hier, b, np.zeros(shape)), O.vcycle(hier, b), rtol=0, atol=1e-14)
+    # from the exact solution nothing changes (the cycle is a consistent iteration)
+    x = random_field(45, shape)
+    xb = O.apply_operator(grid, a, x)
+    np.testing.assert_allclose(O.vcycle_from(hier, xb, x), x, rtol=1e-11, atol=1e-11)
+
+
+def test_fmg_preconditioned_fgmres_converges_no_slower():
+    shape = (32, 32, 32)
+    inp = make_inputs("channel128", shape=shape)
+    pv = O.OracleParams(coarse_min=4, cycle="v")
+    pf = O.OracleParams(coarse_min=4, cycle="fmg")
+    pa = O.OracleParams(coarse_min=4, cycle="auto")
+    _, iv, _ = O.solve(pv, inp["a"], inp["f"])
+    _, i_f, _ = O.solve(pf, inp["a"], inp["f"])
+    _, ia, _ = O.solve(pa, inp["a"], inp["f"])       # zero guess: FMG
+    assert iv.converged and i_f.converged and ia.converged
+    assert i_f.iterations <= iv.iterations
+    assert ia.iterations == i_f.iterations
+    assert i_f.true_rel_residual < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# Coefficient and right-hand side from the densities, eq. (semi2) / (e18)
+# ---------------------------------------------------------------------------
+
+E_OVER_EPS0 = O.ELEMENTARY_CHARGE / O.VACUUM_PERMITTIVITY_CM
+
+
+def test_assembly_constant_densities_closed_form():
+    shape = (6, 5, 4)
+    grid = _grid(shape, (2.0, 1.0, 0.5))
+    ne = np.full(shape, 3.0e13)
+    npos = np.full(shape, 5.0e13)
+    a, f = O.assemble_coefficient_rhs(grid, ne, npos, 2e-12, -381.6, 3.42, (2190.0, 2190.0, 1800.0), E_OVER_EPS0)
+    np.testing.assert_allclose(a, 1.0 + E_OVER_EPS0 * 1e-12 * (3.42 * 5.0e13 + 381.6 * 3.0e13), rtol=1e-15)
+    # no diffusion term for uniform densities
+    np.testing.assert_allclose(f, E_OVER_EPS0 * 2.0e13, rtol=1e-14)
+
+
+def test_assembly_vacuum_coefficient_matches_the_papers_magnitude():
+    """At n_e = n_p = 1e14 cm^-3, tau = 2 ps and the mobilities of Sec. 5.2
+    (|mu_e| = 2.9e5/760, mu_p = 2.6e3/760 cm^2/(V s)) the coefficient is about
+    1.07: the mild contrast of the paper's own runs."""
+    shape = (4, 4, 4)
+    grid = _grid(shape)
+    n = np.full(shape, 1e14)
+    a, _ = O.assemble_coefficient_rhs(grid, n, n, 2e-12, -2.9e5 / 760, 2.6e3 / 760, (2190.0, 2190.0, 1800.0),
+                                      E_OVER_EPS0)
+    assert a[0, 0, 0] == pytest.approx(1.0697, abs=5e-4)
+
+
+def test_assembly_diffusion_term_on_a_quadratic_profile():
+    """n_e = i^2 along x: delta^2 = 2 inside; the Neumann ghosts give
+    n_1 - n_0 = 1 at the first cell and n_{m-2} - n_{m-1} = -(2m - 3) at the last."""
+    m = 7
+    shape = (3, 4, m)
+    grid = _grid(shape, (float(m), 1.0, 1.0))          # hx = 1
+    i = np.arange(m, dtype=np.float64)
+    ne = np.broadcast_to(i ** 2, shape).copy()
+    zero = np.zeros(shape)
+    tau, dx = 1.0, 1.0
+    a, f = O.assemble_coefficient_rhs(grid, ne, zero, tau, 0.0, 0.0, (dx, 5.0, 7.0), 1.0)
+    d2 = np.full(m, 2.0)
+    d2[0] = 1.0
+    d2[-1] = -(2 * m - 3)
+    np.testing.assert_allclose(f, np.broadcast_to(-ne[0, 0] - 0.5 * tau * dx * d2, shape), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(a, 1.0, rtol=0, atol=0)
+
+
+def test_assembly_diffusion_term_conserves_charge():
+    """With zero-flux ghosts the second differences telescope: the diffusion
+    term sums to zero, so sum(f) = (e/eps0) sum(n_p - n_e) for any densities."""
+    shape = (8, 6, 10)
+    grid = _grid(shape, (1.0, 0.7, 1.3))
+    ne = 1e12 * (1.0 + random_field(46, shape) ** 2)
+    npos = 1e12 * (1.0 + random_field(47, shape) ** 2)
+    _, f = O.assemble_coefficient_rhs(grid, ne, npos, 3e-12, 381.6, 3.42, (2190.0, 2190.0, 1800.0), E_OVER_EPS0)
+    assert f.sum() == pytest.approx(E_OVER_EPS0 * (npos - ne).sum(), rel=1e-9)
