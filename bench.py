@@ -65,6 +65,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-regimes", action="store_true",
+                    help="skip the first-step (FMG) and warm-started time-step measurements")
+    ap.add_argument("--regime-steps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -327,6 +330,12 @@ def run_ours(args, dist):
     if not args.no_fp64:
         out["fp64"] = fp64_arm(args, gmg, a, f, phi, ex, ey, ez, N, n, stream)
 
+    # the paper's two other regimes: FMG for a zero-guess first step, and
+    # warm-started time steps assembled from the densities
+    if not args.no_regimes:
+        out["first_step_fmg"] = fmg_arm(args, gmg, a, f, phi, ex, ey, ez, N, n, stream)
+        out["time_steps"] = time_step_arm(args, gmg, N, n, stream)
+
     # end to end through the host-buffer C ABI call
     if not args.no_e2e:
         out["e2e"] = e2e_arm(args, gmg, ctx, inp, n, N, stream, dist)
@@ -361,6 +370,79 @@ def fp64_arm(args, gmg, a, f, phi, ex, ey, ez, N, n, stream):
     return {"ms_per_step": round(ms, 3), "value": round(N / (ms / 1e3) / 1e6, 2), "unit": "Mcells/s",
             "solve_ms": round(statistics.mean(i.solve_ms for i in infos), 3), "iterations": last.iterations,
             "true_rel_residual": last.true_rel_residual, "steps": args.fp64_steps}
+
+
+def fmg_arm(args, gmg, a, f, phi, ex, ey, ez, N, n, stream):
+    """The headline step with full multigrid as the preconditioner (the
+    paper's choice for a solve without a previous potential, Sec. 3.2)."""
+    import torch
+    p = gmg.gmg_default_params(n, n, n, precision=gmg.GMG_PREC_MIXED, cycle=gmg.GMG_CYCLE_FMG)
+    ctx = gmg.gmg_setup(p, a, stream)
+    infos = []
+    for i in range(args.regime_steps + 1):
+        if i == 1:
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.clear()
+        gmg.gmg_update_coefficient(ctx, a)
+        phi.zero_()
+        infos.append(gmg.fgmres_solve(ctx, f, phi))
+        gmg.field_from_potential(ctx, phi, ex, ey, ez)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.regime_steps
+    ctx.close()
+    last = infos[-1]
+    return {"ms_per_step": round(ms, 3), "value": round(N / (ms / 1e3) / 1e6, 2), "unit": "Mcells/s",
+            "iterations": last.iterations, "true_rel_residual": last.true_rel_residual,
+            "solve_ms": round(statistics.mean(i.solve_ms for i in infos), 3), "steps": args.regime_steps,
+            "preconditioner": "FMG (FP32), zero initial guess"}
+
+
+def time_step_arm(args, gmg, N, n, stream):
+    """Time steps of the elliptic part of the semi-implicit scheme on the
+    paper's double-headed streamer (eq. (51) densities, Sec. 5.2 constants,
+    52 kV, tau = 2 ps): each step assembles a and f from the densities on the
+    GPU, renews the set-up, solves warm-started from the previous potential
+    (cycle = auto: FMG on the first step only) and forms E.  The density
+    sequence (a drifting head, growing ions) is built on the device before the
+    timed region; the first step is untimed."""
+    import torch
+    from streamer_inputs import streamer_densities, MU_E, MU_P, DIFFUSION, PHI0
+    dev = torch.device("cuda", torch.cuda.current_device())
+    K = args.regime_steps
+    dens = [streamer_densities((n, n, n), k, xp=torch, device=dev) for k in range(K + 1)]
+    p = gmg.gmg_default_params(n, n, n, precision=gmg.GMG_PREC_MIXED, cycle=gmg.GMG_CYCLE_AUTO, phi_top=PHI0)
+    a = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+    f = torch.empty_like(a)
+    phi = torch.zeros_like(a)
+    ex, ey, ez = (torch.empty((n, n, n), dtype=torch.float32, device=dev) for _ in range(3))
+    kw = dict(tau=2e-12, mu_e=MU_E, mu_p=MU_P, diffusion=DIFFUSION, stream=stream)
+    gmg.assemble_coefficient_rhs(p, dens[0][0], dens[0][1], a, f, **kw)
+    ctx = gmg.gmg_setup(p, a, stream)
+    first = gmg.fgmres_solve(ctx, f, phi)
+    gmg.field_from_potential(ctx, phi, ex, ey, ez)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for k in range(1, K + 1):
+        gmg.assemble_coefficient_rhs(p, dens[k][0], dens[k][1], a, f, **kw)
+        gmg.gmg_update_coefficient(ctx, a)
+        infos.append(gmg.fgmres_solve(ctx, f, phi))
+        gmg.field_from_potential(ctx, phi, ex, ey, ez)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    ctx.close()
+    del dens
+    return {"ms_per_step": round(ms, 3), "value": round(N / (ms / 1e3) / 1e6, 2), "unit": "Mcells/s",
+            "iterations": [i.iterations for i in infos], "first_step_iterations": first.iterations,
+            "first_step_fmg": first.fmg, "true_rel_residual": max(i.true_rel_residual for i in infos),
+            "steps": K, "step": "assemble a, f from n_e, n_p + set-up + warm-started solve + E (FP32)",
+            "workload": f"double-headed streamer eq. (51), {n}^3, tau = 2 ps, 52 kV"}
 
 
 def e2e_arm(args, gmg, ctx, inp, n, N, stream, dist):

@@ -83,6 +83,40 @@ def gaussian_head(shape, centre, width=HEAD_WIDTH) -> np.ndarray:
     return gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
 
 
+# Double-headed streamer of the paper's tests (eq. (51), Sec. 5.2): densities in
+# cm^-3 on a cm domain, the channel axis at x = y = 1 (on the unit cube: the
+# corner, a symmetric quarter of the streamer between zero-flux walls).
+STREAMER_SIGMA_Z = 0.027
+STREAMER_SIGMA_R = 0.021
+STREAMER_BACKGROUND = 1.0e8
+STREAMER_PEAK = 1.0e14
+# Sec. 5.2 constants at 760 Torr (cm^2/(V s), cm^2/s, V)
+MU_E = 2.9e5 / 760.0
+MU_P = 2.6e3 / 760.0
+DIFFUSION = (2190.0, 2190.0, 1800.0)
+PHI0 = 52.0e3
+
+
+def streamer_densities(shape, step: int = 0, drift: float = 0.01, ion_growth: float = 0.05, xp=np, device=None):
+    """(n_e, n_p) for step ``step`` of a synthetic time-step sequence: the
+    eq. (51) profile with its centre at z = 0.5 + drift * step, and the ion
+    density scaled by (1 + ion_growth * step) (a stand-in for the charge
+    separation the transport would produce).  ``xp`` is numpy (default) or
+    torch (then the arrays are built on ``device``); both evaluate the same
+    separable product."""
+    x, y, z = _grid(shape)
+    gz = np.exp(-(((z - (0.5 + drift * step)) / STREAMER_SIGMA_Z) ** 2))
+    gy = np.exp(-((y - 1.0) ** 2) / STREAMER_SIGMA_R ** 2)
+    gx = np.exp(-((x - 1.0) ** 2) / STREAMER_SIGMA_R ** 2)
+    if xp is np:
+        prof = gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    else:
+        t = lambda v: xp.from_numpy(v).to(device)   # noqa: E731
+        prof = t(gz)[:, None, None] * t(gy)[None, :, None] * t(gx)[None, None, :]
+    ne = STREAMER_BACKGROUND + STREAMER_PEAK * prof
+    return ne, ne * (1.0 + ion_growth * step)
+
+
 def _noise(rng, shape):
     return rng.uniform(-1.0, 1.0, size=shape)
 

@@ -17,7 +17,8 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from oracle import gmg_oracle as O  # noqa: E402
-from streamer_inputs import make_inputs, random_coefficient, random_field  # noqa: E402
+from streamer_inputs import (make_inputs, random_coefficient, random_field, streamer_densities,  # noqa: E402
+                             MU_E, MU_P, DIFFUSION, PHI0)
 
 pytestmark = pytest.mark.gpu
 
@@ -726,23 +727,18 @@ def test_assembly_rejects_bad_arguments():
 def test_time_steps_from_assembled_densities_converge_with_few_iterations():
     """The f-1 loop on a 64^3 streamer (eq. (51) densities, Sec. 5.2 mobilities,
     52 kV): assemble a and f, renew the set-up, solve warm-started from the
-    previous potential; the first step uses FMG (cycle = auto)."""
+    previous potential; the first step uses FMG (cycle = auto).  The oracle
+    takes 3-4 iterations on the warm steps of this sequence."""
     shape = (64, 64, 64)
-    nz, ny, nx = shape
-    p = _params(shape, precision=gmg.GMG_PREC_MIXED, cycle=gmg.GMG_CYCLE_AUTO, phi_top=52e3)
-    z, y, x = np.meshgrid((np.arange(nz) + 0.5) / nz, (np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx,
-                          indexing="ij")
+    p = _params(shape, precision=gmg.GMG_PREC_MIXED, cycle=gmg.GMG_CYCLE_AUTO, phi_top=PHI0)
     ctx = None
     phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
     a = torch.empty(shape, dtype=torch.float64, device=DEV)
     f = torch.empty(shape, dtype=torch.float64, device=DEV)
     iters = []
     for step in range(4):
-        zc = 0.5 + 0.01 * step            # the head drifts by 0.01 cm a step
-        n = 1e8 + 1e14 * np.exp(-((z - zc) / 0.027) ** 2 - ((x - 1.0) ** 2 + (y - 1.0) ** 2) / 0.021 ** 2)
-        ne, npos = _t(n), _t(n * (1.0 + 0.05 * step))
-        gmg.assemble_coefficient_rhs(p, ne, npos, a, f, tau=2e-12, mu_e=-2.9e5 / 760, mu_p=2.6e3 / 760,
-                                     diffusion=(2190.0, 2190.0, 1800.0))
+        ne, npos = streamer_densities(shape, step, xp=torch, device=DEV)
+        gmg.assemble_coefficient_rhs(p, ne, npos, a, f, tau=2e-12, mu_e=MU_E, mu_p=MU_P, diffusion=DIFFUSION)
         if ctx is None:
             ctx = gmg.gmg_setup(p, a)
         else:
@@ -752,4 +748,3 @@ def test_time_steps_from_assembled_densities_converge_with_few_iterations():
         assert info.fmg == (1 if step == 0 else 0)
         iters.append(info.iterations)
     assert max(iters[1:]) <= 4, iters
-
