@@ -334,7 +334,15 @@ def run_ours(args, dist):
     # warm-started time steps assembled from the densities
     if not args.no_regimes:
         out["first_step_fmg"] = fmg_arm(args, gmg, a, f, phi, ex, ey, ez, N, n, stream)
-        out["time_steps"] = time_step_arm(args, gmg, N, n, stream)
+        out["time_steps"] = time_step_arm(args, gmg, (n, n, n), stream)
+        # the paper's own mesh for its solver comparison: 256 x 256 x 320 cells (coarsest 4 x 4 x 5)
+        tp = time_step_arm(args, gmg, (320, 256, 256), stream)
+        # context: the paper's FGMRES on this mesh, Table t1 (640 Xeon cores, 50 solves in 10.589 s,
+        # assembly included; its own streamer run, tau = 3.28 ps)
+        tp["paper_table_t1"] = {"value": round(256 * 256 * 320 * 50 / 10.589 / 1e6, 1), "unit": "Mcells/s",
+                                "hardware": "640 Xeon E5-2660 v3 cores", "ratio": round(
+                                    tp["value"] / (256 * 256 * 320 * 50 / 10.589 / 1e6), 2)}
+        out["time_steps_paper_mesh"] = tp
 
     # end to end through the host-buffer C ABI call
     if not args.no_e2e:
@@ -401,7 +409,7 @@ def fmg_arm(args, gmg, a, f, phi, ex, ey, ez, N, n, stream):
             "preconditioner": "FMG (FP32), zero initial guess"}
 
 
-def time_step_arm(args, gmg, N, n, stream):
+def time_step_arm(args, gmg, shape, stream):
     """Time steps of the elliptic part of the semi-implicit scheme on the
     paper's double-headed streamer (eq. (51) densities, Sec. 5.2 constants,
     52 kV, tau = 2 ps): each step assembles a and f from the densities on the
@@ -413,12 +421,14 @@ def time_step_arm(args, gmg, N, n, stream):
     from streamer_inputs import streamer_densities, MU_E, MU_P, DIFFUSION, PHI0
     dev = torch.device("cuda", torch.cuda.current_device())
     K = args.regime_steps
-    dens = [streamer_densities((n, n, n), k, xp=torch, device=dev) for k in range(K + 1)]
-    p = gmg.gmg_default_params(n, n, n, precision=gmg.GMG_PREC_MIXED, cycle=gmg.GMG_CYCLE_AUTO, phi_top=PHI0)
-    a = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+    nz, ny, nx = shape
+    N = nx * ny * nz
+    dens = [streamer_densities(shape, k, xp=torch, device=dev) for k in range(K + 1)]
+    p = gmg.gmg_default_params(nx, ny, nz, precision=gmg.GMG_PREC_MIXED, cycle=gmg.GMG_CYCLE_AUTO, phi_top=PHI0)
+    a = torch.empty(shape, dtype=torch.float64, device=dev)
     f = torch.empty_like(a)
     phi = torch.zeros_like(a)
-    ex, ey, ez = (torch.empty((n, n, n), dtype=torch.float32, device=dev) for _ in range(3))
+    ex, ey, ez = (torch.empty(shape, dtype=torch.float32, device=dev) for _ in range(3))
     kw = dict(tau=2e-12, mu_e=MU_E, mu_p=MU_P, diffusion=DIFFUSION, stream=stream)
     gmg.assemble_coefficient_rhs(p, dens[0][0], dens[0][1], a, f, **kw)
     ctx = gmg.gmg_setup(p, a, stream)
@@ -436,13 +446,15 @@ def time_step_arm(args, gmg, N, n, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / K
+    levels = gmg.gmg_num_levels(ctx)
     ctx.close()
     del dens
     return {"ms_per_step": round(ms, 3), "value": round(N / (ms / 1e3) / 1e6, 2), "unit": "Mcells/s",
             "iterations": [i.iterations for i in infos], "first_step_iterations": first.iterations,
             "first_step_fmg": first.fmg, "true_rel_residual": max(i.true_rel_residual for i in infos),
             "steps": K, "step": "assemble a, f from n_e, n_p + set-up + warm-started solve + E (FP32)",
-            "workload": f"double-headed streamer eq. (51), {n}^3, tau = 2 ps, 52 kV"}
+            "workload": f"double-headed streamer eq. (51), {nx} x {ny} x {nz} cells on the unit cube, "
+                        f"tau = 2 ps, 52 kV", "levels": levels}
 
 
 def e2e_arm(args, gmg, ctx, inp, n, N, stream, dist):

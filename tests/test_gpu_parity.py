@@ -748,3 +748,43 @@ def test_time_steps_from_assembled_densities_converge_with_few_iterations():
         assert info.fmg == (1 if step == 0 else 0)
         iters.append(info.iterations)
     assert max(iters[1:]) <= 4, iters
+
+
+# ---------------------------------------------------------------------------
+# The paper's anisotropic meshes (nz = 1.25 nx on the unit cube, coarsest 4 x 4 x 5)
+# ---------------------------------------------------------------------------
+
+
+def _streamer_problem(shape):
+    nz, ny, nx = shape
+    ne, npos = streamer_densities(shape, 0)
+    a, f = O.assemble_coefficient_rhs(O.Grid(nx, ny, nz), ne, npos, 2e-12, MU_E, MU_P, DIFFUSION,
+                                      gmg.E_OVER_EPS0_CM)
+    return a, f
+
+
+@pytest.mark.parametrize("cycle", [gmg.GMG_CYCLE_V, gmg.GMG_CYCLE_FMG])
+def test_anisotropic_fp64_solve_matches_oracle(cycle):
+    shape = (20, 16, 16)                      # 16 x 16 x 20 -> 8 x 8 x 10 -> 4 x 4 x 5
+    a, f = _streamer_problem(shape)
+    p = _params(shape, precision=gmg.GMG_PREC_FP64, orthogonalization=gmg.GMG_ORTH_MGS, cycle=cycle, phi_top=PHI0)
+    ref, rinfo, _ = O.solve(_oracle_hierarchy(a, p), a, f)
+    ctx = gmg.gmg_setup(p, _t(a))
+    assert gmg.gmg_level_info(ctx, 0)["shape"] == (5, 4, 4)
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    info = gmg.fgmres_solve(ctx, _t(f), phi)
+    assert info.iterations == rinfo.iterations
+    assert _rel(_np(phi), ref) < 1e-10
+
+
+@pytest.mark.parametrize("shape", [(40, 32, 32), (80, 64, 64)])
+def test_anisotropic_mixed_solve_meets_tolerance(shape):
+    a, f = _streamer_problem(shape)
+    p = _params(shape, precision=gmg.GMG_PREC_MIXED, cycle=gmg.GMG_CYCLE_AUTO, phi_top=PHI0)
+    ctx = gmg.gmg_setup(p, _t(a))
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    info = gmg.fgmres_solve(ctx, _t(f), phi)
+    assert info.fmg == 1 and info.true_rel_residual < 1e-8
+    assert _true_residual(shape, _oracle_hierarchy(a, p), a, f, _np(phi)) < 1e-8
+    ref, _, _ = O.solve(O.OracleParams(coarse_min=4, phi_top=PHI0, rtol=1e-11), a, f)
+    assert _rel(_np(phi), ref) < 1e-6
