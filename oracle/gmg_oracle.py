@@ -593,8 +593,189 @@ def fgmres(grid: Grid, a: np.ndarray, b: np.ndarray, x0: np.ndarray | None, prec
         info.restarts += 1
 
 
+# ---------------------------------------------------------------------------
+# The other preconditioned Krylov methods of the paper's comparison (Sec. 5.4,
+# Tables t1 and t2): GMRES, CG, FCG, CGS and BiCGSTAB with the same multigrid
+# preconditioner, all right-preconditioned.  Each stops when its recurrence
+# residual falls below rtol ||b||, then checks the true residual and, if that
+# is not below the tolerance, starts again from the current iterate (R8).
+# ---------------------------------------------------------------------------
+
+KRYLOV_METHODS = ("fgmres", "gmres", "cg", "fcg", "cgs", "bicgstab")
+
+
+def gmres(grid: Grid, a: np.ndarray, b: np.ndarray, x0: np.ndarray | None, precond,
+          params: OracleParams) -> tuple[np.ndarray, SolveInfo]:
+    """Restarted right-preconditioned GMRES: Arnoldi (modified Gram-Schmidt)
+    on A M stores only V; after k steps x = x_0 + M (V_k y_k)."""
+    info = SolveInfo()
+    m = params.restart
+    x = np.zeros(grid.shape) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    bnorm = float(np.linalg.norm(b))
+    if bnorm == 0.0:
+        info.converged, info.true_rel_residual = True, 0.0
+        return np.zeros(grid.shape), info
+    while True:
+        r = b - apply_operator(grid, a, x)
+        beta = float(np.linalg.norm(r))
+        info.true_rel_residual = beta / bnorm
+        if info.true_rel_residual < params.rtol:
+            info.converged = True
+            return x, info
+        if info.iterations >= params.max_iters or beta == 0.0:
+            return x, info
+        V = [r.ravel() / beta]
+        H = np.zeros((m + 1, m))
+        k = 0
+        y = np.zeros(0)
+        for j in range(m):
+            w = apply_operator(grid, a, precond(V[j].reshape(grid.shape))).ravel()
+            for i in range(j + 1):
+                H[i, j] = np.dot(w, V[i])
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            k = j + 1
+            info.iterations += 1
+            y, res = _least_squares_residual(H[: j + 2, : j + 1], beta)
+            info.history.append(res / bnorm)
+            if H[j + 1, j] == 0.0:
+                break
+            V.append(w / H[j + 1, j])
+            if res / bnorm < params.rtol or info.iterations >= params.max_iters:
+                break
+        u = sum(y[i] * V[i] for i in range(k))
+        x = x + precond(u.reshape(grid.shape))
+        info.restarts += 1
+
+
+def _restarting(method_step):
+    """Wrap a short-recurrence method: run it from the current x until its
+    recurrence residual meets rtol ||b|| (or the iteration cap), then check the
+    true residual and start it again from x if needed (R8)."""
+    def run(grid, a, b, x0, precond, params):
+        info = SolveInfo()
+        x = np.zeros(grid.shape) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+        bnorm = float(np.linalg.norm(b))
+        if bnorm == 0.0:
+            info.converged, info.true_rel_residual = True, 0.0
+            return np.zeros(grid.shape), info
+        while True:
+            r = b - apply_operator(grid, a, x)
+            info.true_rel_residual = float(np.linalg.norm(r)) / bnorm
+            if info.true_rel_residual < params.rtol:
+                info.converged = True
+                return x, info
+            if info.iterations >= params.max_iters:
+                return x, info
+            x = method_step(grid, a, x, r, precond, params, bnorm, info)
+            info.restarts += 1
+    return run
+
+
+def _stop(info, params, rnorm, bnorm):
+    info.iterations += 1
+    info.history.append(rnorm / bnorm)
+    return rnorm / bnorm < params.rtol or info.iterations >= params.max_iters
+
+
+@_restarting
+def cg(grid, a, x, r, precond, params, bnorm, info):
+    """Preconditioned conjugate gradients (Saad, Algorithm 9.1)."""
+    z = precond(r)
+    p = z.copy()
+    rho = float(np.vdot(r, z))
+    while True:
+        q = apply_operator(grid, a, p)
+        alpha = rho / float(np.vdot(p, q))
+        x = x + alpha * p
+        r = r - alpha * q
+        if _stop(info, params, float(np.linalg.norm(r)), bnorm):
+            return x
+        z = precond(r)
+        rho_new = float(np.vdot(r, z))
+        p = z + (rho_new / rho) * p
+        rho = rho_new
+
+
+@_restarting
+def fcg(grid, a, x, r, precond, params, bnorm, info):
+    """Flexible conjugate gradients with one stored direction (Notay's FCG(1)):
+    p_k = z_k - ((z_k, q_{k-1}) / (p_{k-1}, q_{k-1})) p_{k-1}, q = A p,
+    alpha_k = (p_k, r_k) / (p_k, q_k)."""
+    p_prev = q_prev = None
+    pq_prev = 0.0
+    while True:
+        z = precond(r)
+        p = z if p_prev is None else z - (float(np.vdot(z, q_prev)) / pq_prev) * p_prev
+        q = apply_operator(grid, a, p)
+        pq = float(np.vdot(p, q))
+        alpha = float(np.vdot(p, r)) / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        if _stop(info, params, float(np.linalg.norm(r)), bnorm):
+            return x
+        p_prev, q_prev, pq_prev = p, q, pq
+
+
+@_restarting
+def cgs(grid, a, x, r, precond, params, bnorm, info):
+    """Conjugate gradient squared (Saad, Algorithm 7.6), right-preconditioned:
+    the search directions p and u + q are preconditioned before A acts."""
+    rt = r.copy()
+    rho_old = 1.0
+    u = q = p = np.zeros(grid.shape)
+    first = True
+    while True:
+        rho = float(np.vdot(rt, r))
+        beta = 0.0 if first else rho / rho_old
+        u = r + beta * q
+        p = u + beta * (q + beta * p)
+        first = False
+        ph = precond(p)
+        vh = apply_operator(grid, a, ph)
+        alpha = rho / float(np.vdot(rt, vh))
+        q = u - alpha * vh
+        uh = precond(u + q)
+        x = x + alpha * uh
+        r = r - alpha * apply_operator(grid, a, uh)
+        rho_old = rho
+        if _stop(info, params, float(np.linalg.norm(r)), bnorm):
+            return x
+
+
+@_restarting
+def bicgstab(grid, a, x, r, precond, params, bnorm, info):
+    """BiCGSTAB (Saad, Algorithm 7.7), right-preconditioned."""
+    rt = r.copy()
+    p = r.copy()
+    rho = float(np.vdot(rt, r))
+    while True:
+        ph = precond(p)
+        v = apply_operator(grid, a, ph)
+        alpha = rho / float(np.vdot(rt, v))
+        s = r - alpha * v
+        sh = precond(s)
+        t = apply_operator(grid, a, sh)
+        tt = float(np.vdot(t, t))
+        omega = float(np.vdot(t, s)) / tt if tt > 0.0 else 0.0
+        x = x + alpha * ph + omega * sh
+        r = s - omega * t
+        if _stop(info, params, float(np.linalg.norm(r)), bnorm):
+            return x
+        rho_new = float(np.vdot(rt, r))
+        beta = (rho_new / rho) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        rho = rho_new
+
+
+def krylov(method: str, grid: Grid, a: np.ndarray, b: np.ndarray, x0, precond, params: OracleParams):
+    """Dispatch to one of the methods of the paper's comparison."""
+    fn = {"fgmres": fgmres, "gmres": gmres, "cg": cg, "fcg": fcg, "cgs": cgs, "bicgstab": bicgstab}[method]
+    return fn(grid, a, b, x0, precond, params)
+
+
 def solve(params: OracleParams, a: np.ndarray, f: np.ndarray, phi0: np.ndarray | None = None,
-          homogeneous: bool = False, hierarchy: Hierarchy | None = None):
+          homogeneous: bool = False, hierarchy: Hierarchy | None = None, method: str = "fgmres"):
     """phi solving -div(a grad phi) = f with the plate data of ``params``
     (or zero plate data if ``homogeneous``), by GMG-preconditioned FGMRES."""
     nz, ny, nx = a.shape
@@ -608,7 +789,7 @@ def solve(params: OracleParams, a: np.ndarray, f: np.ndarray, phi0: np.ndarray |
     if cycle == "auto":   # Sec. 3.2: FMG when there is no previous potential, V-cycles after
         cycle = "fmg" if phi0 is None or not np.any(phi0) else "v"
     precond = (lambda v: fmg(hier, v)) if cycle == "fmg" else (lambda v: vcycle(hier, v))
-    phi, info = fgmres(grid, a, b, phi0, precond, params)
+    phi, info = krylov(method, grid, a, b, phi0, precond, params)
     return phi, info, hier
 
 

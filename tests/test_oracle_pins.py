@@ -656,3 +656,78 @@ def test_assembly_diffusion_term_conserves_charge():
     npos = 1e12 * (1.0 + random_field(47, shape) ** 2)
     _, f = O.assemble_coefficient_rhs(grid, ne, npos, 3e-12, 381.6, 3.42, (2190.0, 2190.0, 1800.0), E_OVER_EPS0)
     assert f.sum() == pytest.approx(E_OVER_EPS0 * (npos - ne).sum(), rel=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# The other Krylov methods of the paper's comparison (Tables t1, t2)
+# ---------------------------------------------------------------------------
+
+
+def _dense_problem(seed=50, contrast=20.0):
+    shape = (8, 8, 8)
+    grid = _grid(shape)
+    a = random_coefficient(seed, shape, contrast=contrast)
+    A = O.dense_operator(grid, a)
+    b = random_field(seed + 1, shape)
+    return grid, a, A, b
+
+
+@pytest.mark.parametrize("method", O.KRYLOV_METHODS)
+def test_krylov_with_the_exact_preconditioner_takes_one_iteration(method):
+    grid, a, A, b = _dense_problem()
+    Ainv = np.linalg.inv(A)
+    x, info = O.krylov(method, grid, a, b, None, lambda v: (Ainv @ v.ravel()).reshape(grid.shape),
+                       O.OracleParams(rtol=1e-10))
+    assert info.converged and info.iterations == 1
+    np.testing.assert_allclose(A @ x.ravel(), b.ravel(), rtol=0, atol=1e-10 * np.linalg.norm(b))
+
+
+def test_gmres_equals_fgmres_for_a_fixed_preconditioner():
+    grid, a, A, b = _dense_problem(52)
+    hier = O.build_hierarchy(grid, a, O.OracleParams(coarse_min=2))
+    pc = lambda v: O.vcycle(hier, v)   # noqa: E731  (a fixed linear map)
+    params = O.OracleParams(rtol=1e-11, restart=5)
+    x1, i1 = O.krylov("fgmres", grid, a, b, None, pc, params)
+    x2, i2 = O.krylov("gmres", grid, a, b, None, pc, params)
+    assert i1.iterations == i2.iterations and i1.restarts == i2.restarts
+    np.testing.assert_allclose(x2, x1, rtol=1e-9, atol=1e-12)
+
+
+def test_fcg_equals_pcg_for_a_symmetric_preconditioner():
+    grid, a, A, b = _dense_problem(54)
+    dinv = 1.0 / np.diag(A)
+    pc = lambda v: (dinv * v.ravel()).reshape(grid.shape)   # noqa: E731  (Jacobi: SPD)
+    params = O.OracleParams(rtol=1e-10, max_iters=500)
+    x1, i1 = O.krylov("cg", grid, a, b, None, pc, params)
+    x2, i2 = O.krylov("fcg", grid, a, b, None, pc, params)
+    assert i1.iterations == i2.iterations
+    np.testing.assert_allclose(x2, x1, rtol=1e-8, atol=1e-12)
+
+
+@pytest.mark.parametrize("method", ["cg", "cgs", "bicgstab"])
+def test_short_recurrences_match_scipy(method):
+    """The same textbook algorithms in SciPy (Jacobi-preconditioned, relative
+    tolerance on ||r||/||b||): the same iteration count within one step and
+    the same solution."""
+    import scipy.sparse.linalg as sla
+    grid, a, A, b = _dense_problem(56)
+    dinv = 1.0 / np.diag(A)
+    M = sla.LinearOperator(A.shape, matvec=lambda v: dinv * v)
+    count = [0]
+
+    def cb(_):
+        count[0] += 1
+    fn = {"cg": sla.cg, "cgs": sla.cgs, "bicgstab": sla.bicgstab}[method]
+    xs, flag = fn(A, b.ravel(), rtol=1e-9, atol=0.0, maxiter=1000, M=M, callback=cb)
+    assert flag == 0
+    x, info = O.krylov(method, grid, a, b, None, lambda v: (dinv * v.ravel()).reshape(grid.shape),
+                       O.OracleParams(rtol=1e-9, max_iters=1000))
+    assert abs(info.iterations - count[0]) <= 1, (info.iterations, count[0])
+    np.testing.assert_allclose(x.ravel(), xs, rtol=1e-6, atol=1e-9 * np.abs(xs).max())
+
+
+@pytest.mark.parametrize("method", O.KRYLOV_METHODS)
+def test_krylov_methods_reach_the_true_residual_with_multigrid(method):
+    inp = make_inputs("channel128", shape=(16, 16, 16))
+    phi, info, _ = O.solve(O.OracleParams(coarse_min=4), inp["a"], inp["f"], method=method)
+    assert info.converged and info.true_rel_residual < 1e-8
