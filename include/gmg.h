@@ -109,6 +109,18 @@ typedef enum gmg_cycle {
   GMG_CYCLE_AUTO = 2  /* FMG when the solve's initial guess is zero, else V  */
 } gmg_cycle;
 
+/* Krylov method of gmg_krylov_solve: the paper's solver and the other
+ * multigrid-preconditioned methods of its comparison (Sec. 5.4, Tables t1
+ * and t2), all right-preconditioned with the same cycle. */
+typedef enum gmg_krylov {
+  GMG_KRYLOV_FGMRES = 0,   /* Algorithm 1 (fgmres_solve)                      */
+  GMG_KRYLOV_GMRES = 1,    /* restarted GMRES, stores only V, x += M (V y)    */
+  GMG_KRYLOV_CG = 2,       /* preconditioned conjugate gradients             */
+  GMG_KRYLOV_FCG = 3,      /* flexible CG with one stored direction          */
+  GMG_KRYLOV_CGS = 4,      /* conjugate gradient squared                     */
+  GMG_KRYLOV_BICGSTAB = 5  /* BiCGSTAB                                       */
+} gmg_krylov;
+
 typedef struct gmg_params {
   int nx, ny, nz;              /* cells; halving all three must reach a grid
                                   whose smallest side equals coarse_min      */
@@ -146,6 +158,7 @@ typedef struct gmg_solve_info {
   float setup_ms;              /* last set-up (gmg_setup / update) time, ms    */
   float solve_ms;              /* this solve, ms (host wall clock incl. syncs) */
   int fmg;                     /* 1 if this solve was preconditioned by FMG     */
+  int precond_calls;           /* preconditioner applications in this solve     */
 } gmg_solve_info;
 
 /* Fill *p with the paper's defaults for an nx x ny x nz unit-cube grid:
@@ -178,6 +191,17 @@ gmg_status gmg_update_coefficient(gmg_ctx* ctx, const double* a_dev);
  * Returns GMG_OK, GMG_ERR_NOT_CONVERGED, GMG_ERR_NONFINITE or a CUDA error. */
 gmg_status fgmres_solve(gmg_ctx* ctx, const double* f_dev, double* phi_dev, int homogeneous_bc,
                         gmg_solve_info* info);
+
+/* Solve like fgmres_solve with another Krylov method (gmg_krylov).  Each
+ * method stops when its own residual estimate falls below rtol ||b||, then
+ * checks the true residual and restarts from phi if that is not below rtol.
+ * info->iterations counts the method's iterations (CGS and BiCGSTAB apply
+ * the preconditioner twice per iteration: see info->precond_calls).  The
+ * short-recurrence methods keep their vectors in the Krylov basis storage and
+ * need restart >= 7.  Errors as fgmres_solve; GMG_ERR_ARG for an unknown
+ * method; GMG_ERR_BREAKDOWN if a method breaks down before any progress. */
+gmg_status gmg_krylov_solve(gmg_ctx* ctx, int method, const double* f_dev, double* phi_dev, int homogeneous_bc,
+                            gmg_solve_info* info);
 
 /* y = A x (the operator of eq. (e18) with zero Dirichlet data), FP64. */
 gmg_status apply_operator(gmg_ctx* ctx, const double* x_dev, double* y_dev);

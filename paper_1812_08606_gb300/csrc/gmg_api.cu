@@ -180,7 +180,7 @@ enum KernelClass : int {
   K_CHEB_F64, K_CHEB_F32, K_RESTRICT_F64, K_RESTRICT_F32, K_PROLONG_F64, K_PROLONG_F32, K_COARSE_F64,
   K_COARSE_F32, K_DOT, K_FINALIZE, K_AXPY, K_SCALE, K_UPDATE_X, K_CAST, K_COPY, K_RHS, K_FIELD, K_ADJOINT,
   K_COARSEN, K_COEF_CHECK, K_HASH, K_COARSE_ASSEMBLE, K_COARSE_FACTOR, K_DOT_F32, K_AXPY_F32, K_APPLY_DF64,
-  K_SPLIT, K_CHEB_FUSED, K_CGS_DOTS, K_CGS_DOTS_F32, K_CGS_UPDATE, K_CGS_UPDATE_F32, NK
+  K_SPLIT, K_CHEB_FUSED, K_CGS_DOTS, K_CGS_DOTS_F32, K_CGS_UPDATE, K_CGS_UPDATE_F32, K_LIN3, NK
 };
 static const char* const kKernelNames[NK] = {
     "apply_f64", "apply_outer_f64a_f32x", "apply_f32", "residual_f64", "residual_f32", "sgs_half_f64",
@@ -189,7 +189,7 @@ static const char* const kKernelNames[NK] = {
     "multi_axpy", "scale", "update_solution", "cast", "copy", "rhs", "field", "adjoint_grad", "coarsen_coef",
     "coef_check", "hash_vector", "coarse_assemble", "coarse_factor", "multi_dot_f32", "multi_axpy_f32",
     "apply_outer_df64", "split_coef", "cheb_sgs_fused_f32", "cgs_dots", "cgs_dots_f32", "cgs_update",
-    "cgs_update_f32"};
+    "cgs_update_f32", "vector_lin3"};
 
 struct ProfPending {
   int cls;
@@ -234,6 +234,7 @@ struct gmg_ctx {
   void *st_ex = nullptr, *st_ey = nullptr, *st_ez = nullptr;
   int st_fp32 = -1;  // element type of the field staging buffers (-1: none yet)
   bool fmg_now = false;  // the preconditioner of the current solve is full multigrid
+  long long precond_calls = 0;  // preconditioner applications (reported per solve)
   // copy stream of gmg_solve_host: input copies overlap the set-up, the
   // potential's copy-out overlaps the field kernel
   cudaStream_t cs = nullptr;
@@ -414,6 +415,13 @@ template <typename TZ>
 gmg_status prof_update_solution(gmg_ctx* c, size_t n, double* x, const TZ* Z, size_t ldz, int k, const double* y,
                                 cudaStream_t s) {
   GMG_RUN(K_UPDATE_X, (double)n * (16.0 + k * sizeof(TZ)), launch_update_solution<TZ>(n, x, Z, ldz, k, y, s));
+}
+template <typename T1, typename T2>
+gmg_status prof_lin3(gmg_ctx* c, size_t n, double a1, const T1* v1, double a2, const T2* v2, double a3,
+                     const double* v3, double* out) {
+  const double bytes = (double)n * (8.0 + (v1 ? sizeof(T1) : 0) + (v2 ? sizeof(T2) : 0) + (v3 ? 8.0 : 0.0));
+  cudaStream_t s = c->s;
+  GMG_RUN(K_LIN3, bytes, launch_lin3<T1, T2>(n, a1, v1, a2, v2, a3, v3, out, s));
 }
 gmg_status prof_cast_d2f(gmg_ctx* c, size_t n, const double* src, float* dst, cudaStream_t s) {
   GMG_RUN(K_CAST, 12.0 * n, launch_cast_d2f(n, src, dst, s));
@@ -818,6 +826,7 @@ gmg_status fmg(gmg_ctx* c, int top, const T* b, T* z) {
 
 gmg_status precondition(gmg_ctx* c, const double* v, void* z) {
   const int top = (int)c->lev.size() - 1;
+  ++c->precond_calls;
   if (c->mixed) {
     float* bf = (float*)c->lev[top].b;
     CKS(prof_cast_d2f(c, c->N(), v, bf, c->s));
@@ -838,8 +847,12 @@ gmg_status apply_outer(gmg_ctx* c, const void* z, double* w) {
 
 void* zvec(gmg_ctx* c, int j) { return (char*)c->Z + (size_t)j * c->N() * c->esz; }
 
-gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, gmg_solve_info* info) {
+// FGMRES (flexible = true, Algorithm 1) or right-preconditioned GMRES, which
+// keeps only V and forms x += M (V y) at the end of each cycle.
+gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, gmg_solve_info* info,
+                      bool flexible = true) {
   const double t0 = now_ms();
+  c->precond_calls = 0;
   const LevelData& F = c->fine();
   const size_t n = F.n;
   const int m = c->p.restart;
@@ -903,8 +916,9 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
       bool fail = false;
       for (int j = 0; j < m; ++j) {
         double* vj = c->V + (size_t)j * n;
-        CKS(precondition(c, vj, zvec(c, j)));           // z_j = M v_j (one V-cycle)
-        CKS(apply_outer(c, zvec(c, j), c->w));            // w = A z_j
+        void* zj = zvec(c, flexible ? j : 0);            // GMRES needs no stored z
+        CKS(precondition(c, vj, zj));                    // z_j = M v_j (one V-cycle)
+        CKS(apply_outer(c, zj, c->w));                   // w = A z_j
         CKS(orthogonalize(c, n, c->V, n, j + 1, c->w));   // Gram-Schmidt: h_{i,j}
         CKS(read_column(c, j + 1, col.data()));          // h_{j+1,j} = ||w||
         for (int i = 0; i <= j + 1; ++i)
@@ -949,10 +963,20 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
       }
       for (int i = 0; i < k; ++i) c->hpin[SL_Y + i] = y[i];
       CK(cudaMemcpyAsync(c->dscal + SL_Y, c->hpin + SL_Y, sizeof(double) * k, cudaMemcpyHostToDevice, c->s));
-      if (c->mixed)
+      if (!flexible) {
+        // GMRES: u = V y, then x += M u
+        CK(cudaMemsetAsync(c->w, 0, n * sizeof(double), c->s));
+        CKS(prof_update_solution<double>(c, n, c->w, c->V, n, k, c->dscal + SL_Y, c->s));
+        CKS(precondition(c, c->w, zvec(c, 0)));
+        if (c->mixed)
+          CKS(prof_lin3<float, double>(c, n, 1.0, (const float*)zvec(c, 0), 0.0, nullptr, 1.0, x, x));
+        else
+          CKS(prof_lin3<double, double>(c, n, 1.0, (const double*)zvec(c, 0), 0.0, nullptr, 1.0, x, x));
+      } else if (c->mixed) {
         CKS(prof_update_solution<float>(c, n, x, (const float*)c->Z, n, k, c->dscal + SL_Y, c->s));
-      else
+      } else {
         CKS(prof_update_solution<double>(c, n, x, (const double*)c->Z, n, k, c->dscal + SL_Y, c->s));
+      }
       loc.restarts++;  // restart from x_k (the true residual is checked at the loop top)
     }
   }
@@ -960,6 +984,252 @@ done:
   CK(cudaStreamSynchronize(c->s));
   prof_collect(c);
   loc.solve_ms = (float)(now_ms() - t0);
+  loc.precond_calls = (int)c->precond_calls;
+  if (info) *info = loc;
+  return result;
+}
+
+// ---------------------------------------------------------------------------
+// Short-recurrence Krylov methods with the same preconditioner (the paper's
+// comparison of elliptic solvers, Tables t1 and t2): preconditioned CG,
+// flexible CG with one stored direction, CGS and BiCGSTAB, right-
+// preconditioned.  FP64 vectors; the preconditioner output z is FP32 in mixed
+// mode and A z takes the double-float Arnoldi product; A p for a combination
+// p = z + beta p' is formed as A z + beta A p' so no FP64 stencil runs inside
+// the iteration.  Each method stops when its recurrence residual falls below
+// rtol ||b||; the true residual is then checked and the method starts again
+// from x if needed (as for FGMRES).  Work vectors live in the Krylov basis
+// storage: V[0] r, V[1] p, V[2] q, V[3] the shadow residual, V[4..6] method
+// temporaries; Z[0], Z[1] hold preconditioner outputs.
+// ---------------------------------------------------------------------------
+
+gmg_status dot64(gmg_ctx* c, const double* x, const double* y, double* out) {
+  const size_t n = c->N();
+  CKS(prof_multi_dot<double>(c, n, x, y, 0, 1, c->partial, c->s));
+  CKS(prof_finalize(c, c->partial, reduce_blocks(n), 1, c->dscal + SL_H1, 0, c->s));
+  CKS(read_scalars(c, SL_H1, 1));
+  *out = c->hpin[SL_H1];
+  return GMG_OK;
+}
+
+gmg_status norm64(gmg_ctx* c, const double* x, double* out) {
+  CKS(norm_dev<double>(c, c->N(), x, SL_NORM));
+  CKS(read_scalars(c, SL_NORM, 2));
+  *out = c->hpin[SL_NORM];
+  return GMG_OK;
+}
+
+template <typename TZ>
+gmg_status short_cycle(gmg_ctx* c, int method, double* x, double bnorm, gmg_solve_info& loc, bool& breakdown) {
+  const size_t n = c->N();
+  double* V = c->V;
+  double *r = V, *p = V + n, *q = V + 2 * n, *rt = V + 3 * n, *t4 = V + 4 * n, *t5 = V + 5 * n, *t6 = V + 6 * n;
+  TZ* z0 = (TZ*)zvec(c, 0);
+  TZ* z1 = (TZ*)zvec(c, 1);
+  double* w = c->w;
+  const bool widen = sizeof(TZ) == 4;
+  const int cap = c->p.max_iters;
+  auto record = [&](double rnorm) {
+    ++loc.iterations;
+    if (loc.n_history < GMG_MAX_HISTORY) loc.res_history[loc.n_history++] = rnorm / bnorm;
+    return rnorm / bnorm < c->p.rtol || loc.iterations >= cap || !isfinite(rnorm);
+  };
+  // z = M r, zd = z in FP64 (a copy only in mixed mode), w = A z
+  auto pc_op = [&](const double* rv, TZ* z, const double** zd) -> gmg_status {
+    CKS(precondition(c, rv, z));
+    if (widen) {
+      CKS(prof_lin3<TZ, double>(c, n, 1.0, z, 0.0, nullptr, 0.0, nullptr, t6));
+      *zd = t6;
+    } else {
+      *zd = (const double*)z;
+    }
+    return apply_outer(c, z, w);
+  };
+  breakdown = false;
+  double rnorm = 0.0;
+  if (method == GMG_KRYLOV_CG || method == GMG_KRYLOV_FCG) {
+    const bool flexible = method == GMG_KRYLOV_FCG;
+    double rho = 0.0, pq_prev = 0.0;
+    for (int it = 0;; ++it) {
+      const double* zd = nullptr;
+      CKS(pc_op(r, z0, &zd));
+      if (it == 0) {
+        CKS(prof_lin3<double, double>(c, n, 1.0, zd, 0.0, nullptr, 0.0, nullptr, p));
+        CKS(prof_lin3<double, double>(c, n, 1.0, w, 0.0, nullptr, 0.0, nullptr, q));
+        if (!flexible) CKS(dot64(c, r, zd, &rho));
+      } else {
+        double beta;
+        if (flexible) {  // Notay: beta = -(z, q') / (p', q')
+          double zq;
+          CKS(dot64(c, zd, q, &zq));
+          beta = -zq / pq_prev;
+        } else {         // Fletcher-Reeves form of PCG
+          double rho_new;
+          CKS(dot64(c, r, zd, &rho_new));
+          beta = rho_new / rho;
+          rho = rho_new;
+        }
+        if (!isfinite(beta)) {
+          breakdown = true;
+          return GMG_OK;
+        }
+        CKS(prof_lin3<double, double>(c, n, 1.0, zd, 0.0, nullptr, beta, p, p));  // p = z + beta p
+        CKS(prof_lin3<double, double>(c, n, 1.0, w, 0.0, nullptr, beta, q, q));   // q = A z + beta q
+      }
+      double pq, num;
+      CKS(dot64(c, p, q, &pq));
+      if (flexible) CKS(dot64(c, p, r, &num));
+      else num = rho;
+      const double alpha = num / pq;
+      if (!isfinite(alpha) || pq == 0.0) {
+        breakdown = true;
+        return GMG_OK;
+      }
+      CKS(prof_lin3<double, double>(c, n, alpha, p, 0.0, nullptr, 1.0, x, x));    // x += alpha p
+      CKS(prof_lin3<double, double>(c, n, -alpha, q, 0.0, nullptr, 1.0, r, r));   // r -= alpha q
+      CKS(norm64(c, r, &rnorm));
+      if (record(rnorm)) return GMG_OK;
+      pq_prev = pq;
+    }
+  }
+  if (method == GMG_KRYLOV_CGS) {
+    CKS(prof_lin3<double, double>(c, n, 1.0, r, 0.0, nullptr, 0.0, nullptr, rt));
+    CK(cudaMemsetAsync(p, 0, n * sizeof(double), c->s));
+    CK(cudaMemsetAsync(q, 0, n * sizeof(double), c->s));
+    double rho_old = 1.0;
+    for (int it = 0;; ++it) {
+      double rho;
+      CKS(dot64(c, rt, r, &rho));
+      const double beta = it == 0 ? 0.0 : rho / rho_old;
+      if (!isfinite(beta) || rho == 0.0) {
+        breakdown = true;
+        return GMG_OK;
+      }
+      double* u = t4;
+      CKS(prof_lin3<double, double>(c, n, 1.0, r, beta, q, 0.0, nullptr, u));           // u = r + beta q
+      CKS(prof_lin3<double, double>(c, n, 1.0, u, beta, q, beta * beta, p, p));         // p = u + beta (q + beta p)
+      CKS(precondition(c, p, z0));                                                      // p^ = M p
+      CKS(apply_outer(c, z0, w));                                                       // v^ = A p^
+      double rv;
+      CKS(dot64(c, rt, w, &rv));
+      const double alpha = rho / rv;
+      if (!isfinite(alpha)) {
+        breakdown = true;
+        return GMG_OK;
+      }
+      CKS(prof_lin3<double, double>(c, n, 1.0, u, -alpha, w, 0.0, nullptr, q));         // q = u - alpha v^
+      CKS(prof_lin3<double, double>(c, n, 1.0, u, 1.0, q, 0.0, nullptr, t5));           // u + q
+      CKS(precondition(c, t5, z1));                                                     // u^ = M (u + q)
+      CKS(prof_lin3<TZ, double>(c, n, alpha, z1, 0.0, nullptr, 1.0, x, x));              // x += alpha u^
+      CKS(apply_outer(c, z1, w));                                                       // A u^
+      CKS(prof_lin3<double, double>(c, n, -alpha, w, 0.0, nullptr, 1.0, r, r));          // r -= alpha A u^
+      rho_old = rho;
+      CKS(norm64(c, r, &rnorm));
+      if (record(rnorm)) return GMG_OK;
+    }
+  }
+  // BiCGSTAB
+  CKS(prof_lin3<double, double>(c, n, 1.0, r, 0.0, nullptr, 0.0, nullptr, rt));
+  CKS(prof_lin3<double, double>(c, n, 1.0, r, 0.0, nullptr, 0.0, nullptr, p));
+  double rho;
+  CKS(dot64(c, rt, r, &rho));
+  double* v = t4;
+  double* sv = t5;
+  double* tv = t6;
+  for (;;) {
+    CKS(precondition(c, p, z0));                                                        // p^ = M p
+    CKS(apply_outer(c, z0, v));                                                         // v = A p^
+    double rv;
+    CKS(dot64(c, rt, v, &rv));
+    const double alpha = rho / rv;
+    if (!isfinite(alpha)) {
+      breakdown = true;
+      return GMG_OK;
+    }
+    CKS(prof_lin3<double, double>(c, n, 1.0, r, -alpha, v, 0.0, nullptr, sv));           // s = r - alpha v
+    CKS(precondition(c, sv, z1));                                                       // s^ = M s
+    CKS(apply_outer(c, z1, tv));                                                        // t = A s^
+    double tt, ts;
+    CKS(dot64(c, tv, tv, &tt));
+    CKS(dot64(c, tv, sv, &ts));
+    const double omega = tt > 0.0 ? ts / tt : 0.0;
+    CKS(prof_lin3<TZ, TZ>(c, n, alpha, z0, omega, z1, 1.0, x, x));                       // x += alpha p^ + omega s^
+    CKS(prof_lin3<double, double>(c, n, 1.0, sv, -omega, tv, 0.0, nullptr, r));         // r = s - omega t
+    CKS(norm64(c, r, &rnorm));
+    if (record(rnorm)) return GMG_OK;
+    double rho_new;
+    CKS(dot64(c, rt, r, &rho_new));
+    const double beta = (rho_new / rho) * (alpha / omega);
+    if (!isfinite(beta) || rho_new == 0.0) {
+      breakdown = true;
+      return GMG_OK;
+    }
+    CKS(prof_lin3<double, double>(c, n, 1.0, r, -beta * omega, v, beta, p, p));          // p = r + beta (p - omega v)
+    rho = rho_new;
+  }
+}
+
+gmg_status solve_short(gmg_ctx* c, int method, const double* f, double* x, int homogeneous, gmg_solve_info* info) {
+  const double t0 = now_ms();
+  c->precond_calls = 0;
+  const LevelData& F = c->fine();
+  const size_t n = F.n;
+  gmg_solve_info loc;
+  memset(&loc, 0, sizeof(loc));
+  loc.setup_ms = c->setup_ms;
+  gmg_status result = GMG_OK;
+  if (c->p.restart < 7) return GMG_ERR_ARG;  // the work vectors live in V[0..6]
+  CKS(prof_rhs(c, F.g, F.a64, f, c->bvec, c->p.phi_bottom, c->p.phi_top, homogeneous, c->s));
+  double bnorm;
+  CKS(norm64(c, c->bvec, &bnorm));
+  loc.bnorm = bnorm;
+  double xnorm;
+  CKS(norm64(c, x, &xnorm));
+  c->fmg_now = c->p.cycle == GMG_CYCLE_FMG || (c->p.cycle == GMG_CYCLE_AUTO && xnorm == 0.0);
+  loc.fmg = c->fmg_now ? 1 : 0;
+  if (!isfinite(bnorm)) {
+    result = GMG_ERR_NONFINITE;
+  } else if (bnorm == 0.0) {
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), c->s));
+    loc.converged = 1;
+  } else {
+    bool r_is_b = xnorm == 0.0;  // zero guess: r = b exactly
+    for (;;) {
+      if (r_is_b)
+        CKS(prof_lin3<double, double>(c, n, 1.0, c->bvec, 0.0, nullptr, 0.0, nullptr, c->V));
+      else
+        CKS(prof_residual<double>(c, F.g, F.a64, c->bvec, x, c->V, nullptr, PC_NONE, c->s));  // r = b - A x
+      r_is_b = false;
+      double rn;
+      CKS(norm64(c, c->V, &rn));
+      if (!isfinite(rn)) {
+        result = GMG_ERR_NONFINITE;
+        break;
+      }
+      loc.true_rel_residual = rn / bnorm;
+      if (loc.true_rel_residual < c->p.rtol) {
+        loc.converged = 1;
+        break;
+      }
+      if (loc.iterations >= c->p.max_iters) {
+        result = GMG_ERR_NOT_CONVERGED;
+        break;
+      }
+      bool breakdown = false;
+      const int before = loc.iterations;
+      CKS(c->mixed ? short_cycle<float>(c, method, x, bnorm, loc, breakdown)
+                   : short_cycle<double>(c, method, x, bnorm, loc, breakdown));
+      if (breakdown && loc.iterations == before) {  // no progress: a breakdown at the first step
+        result = GMG_ERR_BREAKDOWN;
+        break;
+      }
+      loc.restarts++;
+    }
+  }
+  CK(cudaStreamSynchronize(c->s));
+  prof_collect(c);
+  loc.solve_ms = (float)(now_ms() - t0);
+  loc.precond_calls = (int)c->precond_calls;
   if (info) *info = loc;
   return result;
 }
@@ -1285,6 +1555,20 @@ gmg_status gmg_apply_preconditioner(gmg_ctx* c, const double* v_dev, double* z_d
   CKS(precondition(c, v_dev, c->Z));
   if (c->mixed) return (prof_cast_f2d(c, c->N(), (const float*)c->Z, z_dev, c->s));
   return (prof_copy_d(c, c->N(), (const double*)c->Z, z_dev, c->s));
+}
+
+gmg_status gmg_krylov_solve(gmg_ctx* c, int method, const double* f_dev, double* phi_dev, int homogeneous_bc,
+                            gmg_solve_info* info) {
+  if (!c || !f_dev || !phi_dev) return GMG_ERR_ARG;
+  switch (method) {
+    case GMG_KRYLOV_FGMRES: return solve_impl(c, f_dev, phi_dev, homogeneous_bc, info, true);
+    case GMG_KRYLOV_GMRES: return solve_impl(c, f_dev, phi_dev, homogeneous_bc, info, false);
+    case GMG_KRYLOV_CG:
+    case GMG_KRYLOV_FCG:
+    case GMG_KRYLOV_CGS:
+    case GMG_KRYLOV_BICGSTAB: return solve_short(c, method, f_dev, phi_dev, homogeneous_bc, info);
+    default: return GMG_ERR_ARG;
+  }
 }
 
 gmg_status gmg_apply_outer(gmg_ctx* c, const float* z, double* w) {

@@ -246,6 +246,10 @@ template <typename TZ>
 cudaError_t launch_update_solution(size_t n, double* x, const TZ* Z, size_t ldz, int k,
                                    const double* y, cudaStream_t s);
 // partial[b*2 + 0] = min over block of a; partial[b*2+1] = count of non-finite / non-positive.
+// out = a1 v1 + a2 v2 + a3 v3 (FP64 out; null vectors drop their terms; out may alias v3).
+template <typename T1, typename T2>
+cudaError_t launch_lin3(size_t n, double a1, const T1* v1, double a2, const T2* v2, double a3, const double* v3,
+                        double* out, cudaStream_t s);
 cudaError_t launch_coef_check(size_t n, const double* a, double* partial, cudaStream_t s);
 cudaError_t launch_finalize_check(const double* partial, int nblocks, double* out, cudaStream_t s);
 

@@ -200,6 +200,21 @@ __global__ void __launch_bounds__(RT) k_update_solution_k(size_t n, double* __re
   }
 }
 
+// out = a1 v1 + a2 v2 + a3 v3 in FP64 (the vector updates of CG, FCG, CGS and
+// BiCGSTAB); FP32 terms are widened exactly, a null vector drops its term, and
+// out may be v3 or a double v1 / v2 (each element is read before it is written).
+template <typename T1, typename T2>
+__global__ void __launch_bounds__(RT) k_lin3(size_t n, double a1, const T1* v1, double a2, const T2* v2, double a3,
+                                             const double* v3, double* out) {
+  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
+    double s = 0.0;
+    if (v1) s = a1 * to_f64(v1[p]);
+    if (v2) s = fma(a2, to_f64(v2[p]), s);
+    if (v3) s = fma(a3, v3[p], s);
+    out[p] = s;
+  }
+}
+
 __global__ void __launch_bounds__(RT) k_coef_check(size_t n, const double* __restrict__ a,
                                                    double* __restrict__ partial) {
   __shared__ double sh[RT / 32];
@@ -388,6 +403,19 @@ template cudaError_t launch_update_solution<float>(size_t, double*, const float*
                                                    cudaStream_t);
 template cudaError_t launch_update_solution<double>(size_t, double*, const double*, size_t, int, const double*,
                                                     cudaStream_t);
+
+template <typename T1, typename T2>
+cudaError_t launch_lin3(size_t n, double a1, const T1* v1, double a2, const T2* v2, double a3, const double* v3,
+                        double* out, cudaStream_t s) {
+  k_lin3<T1, T2><<<flat_blocks(n), RT, 0, s>>>(n, a1, v1, a2, v2, a3, v3, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_lin3<double, double>(size_t, double, const double*, double, const double*, double,
+                                                 const double*, double*, cudaStream_t);
+template cudaError_t launch_lin3<float, double>(size_t, double, const float*, double, const double*, double,
+                                                const double*, double*, cudaStream_t);
+template cudaError_t launch_lin3<float, float>(size_t, double, const float*, double, const float*, double,
+                                               const double*, double*, cudaStream_t);
 
 cudaError_t launch_coef_check(size_t n, const double* a, double* partial, cudaStream_t s) {
   k_coef_check<<<reduce_blocks(n), RT, 0, s>>>(n, a, partial);

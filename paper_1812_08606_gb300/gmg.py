@@ -39,6 +39,13 @@ GMG_OUTER_DOUBLE_FLOAT = 1
 GMG_CYCLE_V = 0
 GMG_CYCLE_FMG = 1
 GMG_CYCLE_AUTO = 2
+GMG_KRYLOV_FGMRES = 0
+GMG_KRYLOV_GMRES = 1
+GMG_KRYLOV_CG = 2
+GMG_KRYLOV_FCG = 3
+GMG_KRYLOV_CGS = 4
+GMG_KRYLOV_BICGSTAB = 5
+KRYLOV_NAMES = {"fgmres": 0, "gmres": 1, "cg": 2, "fcg": 3, "cgs": 4, "bicgstab": 5}
 
 # e / eps0 in V cm (densities in cm^-3, mobilities in cm^2/(V s), lengths in cm)
 E_OVER_EPS0_CM = 1.602176634e-19 / 8.8541878128e-14
@@ -62,7 +69,7 @@ class gmg_solve_info(ctypes.Structure):
         ("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
         ("true_rel_residual", ctypes.c_double), ("bnorm", ctypes.c_double), ("n_history", ctypes.c_int),
         ("res_history", ctypes.c_double * GMG_MAX_HISTORY), ("setup_ms", ctypes.c_float),
-        ("solve_ms", ctypes.c_float), ("fmg", ctypes.c_int),
+        ("solve_ms", ctypes.c_float), ("fmg", ctypes.c_int), ("precond_calls", ctypes.c_int),
     ]
 
     @property
@@ -93,6 +100,7 @@ _SIGS = {
     "gmg_setup": (ctypes.c_int, [ctypes.POINTER(gmg_params), _P, _P, ctypes.POINTER(_P)]),
     "gmg_update_coefficient": (ctypes.c_int, [_P, _P]),
     "fgmres_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(gmg_solve_info)]),
+    "gmg_krylov_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.POINTER(gmg_solve_info)]),
     "apply_operator": (ctypes.c_int, [_P, _P, _P]),
     "assemble_rhs": (ctypes.c_int, [_P, _P, _P]),
     "field_from_potential": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
@@ -248,6 +256,18 @@ def fgmres_solve(ctx: Context, f: torch.Tensor, phi: torch.Tensor, homogeneous_b
     st = load().fgmres_solve(ctx.handle, _dev(f, numel=ctx.n, name="f"), _dev(phi, numel=ctx.n, name="phi"),
                              int(bool(homogeneous_bc)), ctypes.byref(info))
     _check(st, "fgmres_solve", allow=(GMG_OK, GMG_ERR_NOT_CONVERGED))
+    return info
+
+
+def gmg_krylov_solve(ctx: Context, method, f: torch.Tensor, phi: torch.Tensor,
+                     homogeneous_bc: bool = False) -> gmg_solve_info:
+    """Like fgmres_solve with the Krylov method ``method`` (a GMG_KRYLOV_*
+    value or one of "fgmres", "gmres", "cg", "fcg", "cgs", "bicgstab")."""
+    m = KRYLOV_NAMES[method] if isinstance(method, str) else int(method)
+    info = gmg_solve_info()
+    st = load().gmg_krylov_solve(ctx.handle, m, _dev(f, numel=ctx.n, name="f"), _dev(phi, numel=ctx.n, name="phi"),
+                                 int(bool(homogeneous_bc)), ctypes.byref(info))
+    _check(st, "gmg_krylov_solve", allow=(GMG_OK, GMG_ERR_NOT_CONVERGED))
     return info
 
 

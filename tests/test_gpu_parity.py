@@ -788,3 +788,53 @@ def test_anisotropic_mixed_solve_meets_tolerance(shape):
     assert _true_residual(shape, _oracle_hierarchy(a, p), a, f, _np(phi)) < 1e-8
     ref, _, _ = O.solve(O.OracleParams(coarse_min=4, phi_top=PHI0, rtol=1e-11), a, f)
     assert _rel(_np(phi), ref) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# The other Krylov methods of the paper's comparison (Tables t1, t2)
+# ---------------------------------------------------------------------------
+
+KRYLOV = ["fgmres", "gmres", "cg", "fcg", "cgs", "bicgstab"]
+
+
+@pytest.mark.parametrize("method", KRYLOV)
+def test_krylov_fp64_matches_oracle(method):
+    inp = make_inputs("channel128", n=32)
+    shape = inp["a"].shape
+    p = _params(shape, precision=gmg.GMG_PREC_FP64, orthogonalization=gmg.GMG_ORTH_MGS)
+    ref, rinfo, _ = O.solve(_oracle_hierarchy(inp["a"], p), inp["a"], inp["f"], method=method)
+    ctx = gmg.gmg_setup(p, _t(inp["a"]))
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    info = gmg.gmg_krylov_solve(ctx, method, _t(inp["f"]), phi)
+    assert info.converged and info.true_rel_residual < 1e-8
+    assert info.iterations == rinfo.iterations, (info.iterations, rinfo.iterations)
+    assert _rel(_np(phi), ref) < 1e-9
+
+
+@pytest.mark.parametrize("method", KRYLOV)
+def test_krylov_mixed_meets_the_true_residual(method):
+    inp = make_inputs("twochannel512", n=64)
+    shape = inp["a"].shape
+    p = _params(shape, precision=gmg.GMG_PREC_MIXED)
+    ctx = gmg.gmg_setup(p, _t(inp["a"]))
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    info = gmg.gmg_krylov_solve(ctx, method, _t(inp["f"]), phi)
+    assert info.converged and info.true_rel_residual < 1e-8
+    assert _true_residual(shape, _oracle_hierarchy(inp["a"], p), inp["a"], inp["f"], _np(phi)) < 1e-8
+    per_iter = 2 if method in ("cgs", "bicgstab") else 1
+    extra = info.restarts if method == "gmres" else 0      # GMRES: one more M per cycle for x
+    assert info.precond_calls == per_iter * info.iterations + extra
+
+
+def test_krylov_rejects_unknown_method_and_short_restart():
+    shape = (16, 16, 16)
+    inp = make_inputs("channel128", shape=shape)
+    ctx = gmg.gmg_setup(_params(shape, restart=5), _t(inp["a"]))
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    with pytest.raises(gmg.GMGError) as e:
+        gmg.gmg_krylov_solve(ctx, 17, _t(inp["f"]), phi)
+    assert e.value.status == gmg.GMG_ERR_ARG
+    with pytest.raises(gmg.GMGError):
+        gmg.gmg_krylov_solve(ctx, "bicgstab", _t(inp["f"]), phi)     # needs restart >= 7
+    info = gmg.gmg_krylov_solve(ctx, "gmres", _t(inp["f"]), phi)     # GMRES works with any restart
+    assert info.true_rel_residual < 1e-8
