@@ -343,6 +343,17 @@ def run_ours(args, dist):
                                 "hardware": "640 Xeon E5-2660 v3 cores", "ratio": round(
                                     tp["value"] / (256 * 256 * 320 * 50 / 10.589 / 1e6), 2)}
         out["time_steps_paper_mesh"] = tp
+        # Table t1's comparison: the same time steps with each Krylov method and the same preconditioner
+        cmp = {}
+        for m in ("fgmres", "gmres", "cg", "fcg", "cgs", "bicgstab"):
+            r = tp if m == "fgmres" else time_step_arm(args, gmg, (320, 256, 256), stream, method=m)
+            cmp[m] = {"ms_per_step": r["ms_per_step"], "iterations": r["iterations"],
+                      "precond_calls": r["precond_calls"]}
+        for m in cmp:
+            cmp[m]["ratio_to_fgmres"] = round(cmp[m]["ms_per_step"] / cmp["fgmres"]["ms_per_step"], 3)
+        cmp["paper_table_t1_ratio"] = {"fgmres": 1.0, "gmres": 1.1888, "cg": 1.1884, "fcg": 1.1724, "cgs": 1.3301,
+                                       "bicgstab": 1.3263}
+        out["krylov_comparison_paper_mesh"] = cmp
 
     # end to end through the host-buffer C ABI call
     if not args.no_e2e:
@@ -409,7 +420,7 @@ def fmg_arm(args, gmg, a, f, phi, ex, ey, ez, N, n, stream):
             "preconditioner": "FMG (FP32), zero initial guess"}
 
 
-def time_step_arm(args, gmg, shape, stream):
+def time_step_arm(args, gmg, shape, stream, method="fgmres"):
     """Time steps of the elliptic part of the semi-implicit scheme on the
     paper's double-headed streamer (eq. (51) densities, Sec. 5.2 constants,
     52 kV, tau = 2 ps): each step assembles a and f from the densities on the
@@ -432,7 +443,7 @@ def time_step_arm(args, gmg, shape, stream):
     kw = dict(tau=2e-12, mu_e=MU_E, mu_p=MU_P, diffusion=DIFFUSION, stream=stream)
     gmg.assemble_coefficient_rhs(p, dens[0][0], dens[0][1], a, f, **kw)
     ctx = gmg.gmg_setup(p, a, stream)
-    first = gmg.fgmres_solve(ctx, f, phi)
+    first = gmg.gmg_krylov_solve(ctx, method, f, phi)
     gmg.field_from_potential(ctx, phi, ex, ey, ez)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -441,7 +452,7 @@ def time_step_arm(args, gmg, shape, stream):
     for k in range(1, K + 1):
         gmg.assemble_coefficient_rhs(p, dens[k][0], dens[k][1], a, f, **kw)
         gmg.gmg_update_coefficient(ctx, a)
-        infos.append(gmg.fgmres_solve(ctx, f, phi))
+        infos.append(gmg.gmg_krylov_solve(ctx, method, f, phi))
         gmg.field_from_potential(ctx, phi, ex, ey, ez)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -451,6 +462,7 @@ def time_step_arm(args, gmg, shape, stream):
     del dens
     return {"ms_per_step": round(ms, 3), "value": round(N / (ms / 1e3) / 1e6, 2), "unit": "Mcells/s",
             "iterations": [i.iterations for i in infos], "first_step_iterations": first.iterations,
+            "precond_calls": [i.precond_calls for i in infos], "method": method,
             "first_step_fmg": first.fmg, "true_rel_residual": max(i.true_rel_residual for i in infos),
             "steps": K, "step": "assemble a, f from n_e, n_p + set-up + warm-started solve + E (FP32)",
             "workload": f"double-headed streamer eq. (51), {nx} x {ny} x {nz} cells on the unit cube, "
