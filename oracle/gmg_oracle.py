@@ -26,6 +26,8 @@ simulator for streamer discharges in three dimensions"):
 * E = -grad(phi) by central differences (Sec. 2.2);
 * the coefficient and right-hand side of eq. (semi2) / (e18) from the
   electron and ion densities (Sec. 2.1, 2.2);
+* the second-order semi-implicit step eqs. (e1)-(e2) with the MUSCL / Koren
+  finite-volume transport of Sec. 2.2;
 * the discrete adjoint of the solve (not in the paper; derived from e18).
 
 Readings of points the paper leaves open (each is listed with its reason in
@@ -49,7 +51,12 @@ R14 full multigrid carries the right-hand side down by the same 8-child mean
    as the residuals, prolongs each level's result with the V-cycle's
    prolongation and takes one V-cycle per level;
 R15 the densities take homogeneous Neumann ghosts in the diffusion term of
-   eq. (e18), and the mobilities enter with their magnitudes.
+   eq. (e18), and the mobilities enter with their magnitudes;
+R19 transport: face values by MUSCL with the Koren limiter
+   phi(r) = max(0, min(2r, (1+2r)/3, 2)), densities with two layers of
+   Neumann ghosts, face fields from phi with the solve's ghosts (mirror on the
+   side walls, 2 g - phi on the plates), |E| of the source from the
+   cell-centred central differences.
 
 Array layout: ``(nz, ny, nx)`` float64, x fastest.
 """
@@ -827,6 +834,110 @@ def assemble_coefficient_rhs(grid: Grid, n_e: np.ndarray, n_p: np.ndarray, tau: 
            + dz / grid.hz ** 2 * neumann_second_difference(n_e, 0))
     f = e_over_eps0 * (n_p - n_e - 0.5 * tau * lap)
     return a, f
+
+
+# ---------------------------------------------------------------------------
+# The semi-implicit time step around the solve (eqs. (e1)-(e2), Sec. 2.1) with
+# the finite-volume transport of Sec. 2.2 (MUSCL with the Koren limiter)
+# ---------------------------------------------------------------------------
+
+PRESSURE_TORR = 760.0
+IONIZATION_A = 5.7      # alpha(|E|) = A P exp(-B P / |E|) cm^-1, Sec. 5.2
+IONIZATION_B = 260.0
+
+
+def ionization_coefficient(e_abs: np.ndarray, pressure: float = PRESSURE_TORR) -> np.ndarray:
+    """alpha(|E|) = 5.7 P exp(-260 P / |E|) cm^-1 (|E| in V/cm, P in Torr), Sec. 5.2; 0 where |E| = 0."""
+    e_abs = np.asarray(e_abs, dtype=np.float64)
+    out = np.zeros_like(e_abs)
+    nz = e_abs > 0
+    out[nz] = IONIZATION_A * pressure * np.exp(-IONIZATION_B * pressure / e_abs[nz])
+    return out
+
+
+def koren_slope(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Limited slope phi(r) b of the Koren limiter phi(r) = max(0, min(2r, (1+2r)/3, 2)),
+    r = a / b (a: the downwind difference, b: the upwind one), written without
+    the division: 0 if a b <= 0, else sign(b) min(2|a|, (|b| + 2|a|)/3, 2|b|)."""
+    aa, ab = np.abs(a), np.abs(b)
+    s = np.sign(b) * np.minimum(np.minimum(2.0 * aa, (ab + 2.0 * aa) / 3.0), 2.0 * ab)
+    return np.where(a * b > 0.0, s, 0.0)
+
+
+def face_fields(grid: Grid, phi: np.ndarray, g_bottom: float, g_top: float):
+    """Face-normal fields E_f = -(phi_q - phi_p)/h on every face of every axis,
+    boundary faces included (arrays one longer than the grid along the axis):
+    zero on the side walls (mirror ghosts), -2 (phi_0 - g)/hz-type values on
+    the plates (ghost 2 g - phi)."""
+    out = []
+    for axis, h in ((2, grid.hx), (1, grid.hy), (0, grid.hz)):
+        u = np.moveaxis(phi, axis, 0)
+        if axis == 0:
+            lo, hi = 2.0 * g_bottom - u[:1], 2.0 * g_top - u[-1:]
+        else:
+            lo, hi = u[:1], u[-1:]
+        ext = np.concatenate([lo, u, hi], axis=0)
+        out.append(np.moveaxis(-(ext[1:] - ext[:-1]) / h, 0, axis))
+    return out   # (E_x faces, E_y faces, E_z faces)
+
+
+def _drift_divergence(n: np.ndarray, velocity_faces, grid: Grid) -> np.ndarray:
+    """div(v n) by the finite-volume MUSCL scheme: on each face the upwind
+    cell's value extrapolated with the Koren-limited slope, times the face
+    velocity; densities take homogeneous Neumann ghosts (two layers)."""
+    div = np.zeros_like(n)
+    for (axis, h), v in zip(((2, grid.hx), (1, grid.hy), (0, grid.hz)), velocity_faces):
+        u = np.moveaxis(n, axis, 0)
+        vv = np.moveaxis(v, axis, 0)
+        m = u.shape[0]
+        ext = np.concatenate([u[1:2] if m > 1 else u[:1], u[:1], u, u[-1:], u[-2:-1] if m > 1 else u[-1:]], axis=0)
+        # face k between cells k-1 and k (k = 0..m), padded index of cell i is i + 2
+        left = ext[1:m + 2] + 0.5 * koren_slope(ext[2:m + 3] - ext[1:m + 2], ext[1:m + 2] - ext[0:m + 1])
+        right = ext[2:m + 3] + 0.5 * koren_slope(ext[1:m + 2] - ext[2:m + 3], ext[2:m + 3] - ext[3:m + 4])
+        flux = np.where(vv > 0.0, vv * left, vv * right)
+        div += np.moveaxis((flux[1:] - flux[:-1]) / h, 0, axis)
+    return div
+
+
+def transport_rhs(grid: Grid, n_e: np.ndarray, n_p: np.ndarray, phi: np.ndarray, g_bottom: float, g_top: float,
+                  mu_e: float, mu_p: float, diffusion: tuple):
+    """Right-hand sides of the transport equations of eq. (eM) for the field
+    E = -grad(phi):  dn_e/dt = div(mu_e E n_e) + div(D_e grad n_e) + S,
+    dn_p/dt = -div(mu_p E n_p) + S,  S = alpha(|E|) mu_e |E| n_e, with |E| at
+    the cell centres from the central differences of Sec. 2.2 (R19)."""
+    ef = face_fields(grid, phi, g_bottom, g_top)
+    ve = [-abs(mu_e) * e for e in ef]              # electrons drift against E
+    vp = [abs(mu_p) * e for e in ef]
+    ex, ey, ez = field_from_potential(grid, phi, g_bottom, g_top)
+    eabs = np.sqrt(ex * ex + ey * ey + ez * ez)
+    src = ionization_coefficient(eabs) * abs(mu_e) * eabs * n_e
+    dx, dy, dz = diffusion
+    diff = (dx / grid.hx ** 2 * neumann_second_difference(n_e, 2)
+            + dy / grid.hy ** 2 * neumann_second_difference(n_e, 1)
+            + dz / grid.hz ** 2 * neumann_second_difference(n_e, 0))
+    return -_drift_divergence(n_e, ve, grid) + diff + src, -_drift_divergence(n_p, vp, grid) + src
+
+
+def transport_stage(grid, base_e, base_p, eval_e, eval_p, phi, g_bottom, g_top, mu_e, mu_p, diffusion, c):
+    """One explicit stage: base + c * (transport right-hand side at eval)."""
+    re, rp = transport_rhs(grid, eval_e, eval_p, phi, g_bottom, g_top, mu_e, mu_p, diffusion)
+    return base_e + c * re, base_p + c * rp
+
+
+def semi_implicit_step(params: OracleParams, n_e: np.ndarray, n_p: np.ndarray, tau: float, mu_e: float,
+                       mu_p: float, diffusion: tuple, e_over_eps0: float, phi_prev: np.ndarray | None = None):
+    """The second-order semi-implicit step, eqs. (e1)-(e2): the elliptic
+    equation eq. (semi2) gives phi^{n+1/2} (assembled from n^n); the predictor
+    n^{n+1/2} = n^n + (tau/2) R(n^n) and the corrector n^{n+1} = n^n +
+    tau R(n^{n+1/2}) both use E^{n+1/2}."""
+    nz, ny, nx = n_e.shape
+    grid = Grid(nx, ny, nz, params.lx, params.ly, params.lz)
+    a, f = assemble_coefficient_rhs(grid, n_e, n_p, tau, mu_e, mu_p, diffusion, e_over_eps0)
+    phi, info, _ = solve(params, a, f, phi0=phi_prev)
+    args = (phi, params.phi_bottom, params.phi_top, mu_e, mu_p, diffusion)
+    he, hp = transport_stage(grid, n_e, n_p, n_e, n_p, *args, 0.5 * tau)
+    ne1, np1 = transport_stage(grid, n_e, n_p, he, hp, *args, tau)
+    return ne1, np1, phi, info
 
 
 # ---------------------------------------------------------------------------

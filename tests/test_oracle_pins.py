@@ -731,3 +731,117 @@ def test_krylov_methods_reach_the_true_residual_with_multigrid(method):
     inp = make_inputs("channel128", shape=(16, 16, 16))
     phi, info, _ = O.solve(O.OracleParams(coarse_min=4), inp["a"], inp["f"], method=method)
     assert info.converged and info.true_rel_residual < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# Transport and the semi-implicit time step, eqs. (e1)-(e2) (Sec. 2.1, 2.2)
+# ---------------------------------------------------------------------------
+
+
+def test_koren_limiter_closed_form():
+    r = np.array([-3.0, -0.1, 0.0, 0.1, 0.25, 0.5, 1.0, 2.0, 2.5, 4.0, 100.0])
+    phi = np.maximum(0.0, np.minimum(np.minimum(2 * r, (1 + 2 * r) / 3), 2.0))
+    # phi(r) b with b = 1 and b = -2 (a = r b)
+    np.testing.assert_allclose(O.koren_slope(r * 1.0, np.ones_like(r)), phi, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(O.koren_slope(r * -2.0, np.full_like(r, -2.0)), -2.0 * phi, rtol=0, atol=1e-15)
+    assert O.koren_slope(np.array([1.0]), np.array([0.0]))[0] == 0.0      # flat upwind side
+
+
+def test_ionization_coefficient_values():
+    e = np.array([0.0, 1e4, 2.08e5])
+    a = O.ionization_coefficient(e)
+    assert a[0] == 0.0
+    assert a[1] == pytest.approx(5.7 * 760 * np.exp(-260 * 760 / 1e4), rel=1e-14)
+    assert a[2] == pytest.approx(5.7 * 760 * np.exp(-260 * 760 / 2.08e5), rel=1e-14)
+
+
+def _uniform_field_case(m=12, e0=1.5e5):
+    """phi = -e0 x on a unit cube of m^3 cells with both plates at 0 V:
+    interior x-faces carry E_x = e0, y- and z-faces carry no field inside."""
+    shape = (m, m, m)
+    grid = _grid(shape)
+    x = (np.arange(m) + 0.5) / m
+    phi = np.broadcast_to(-e0 * x, shape).copy()
+    return grid, phi, e0
+
+
+def test_transport_rhs_linear_density_in_a_uniform_field():
+    grid, phi, e0 = _uniform_field_case()
+    m = grid.nx
+    idx = np.arange(m, dtype=np.float64)
+    ne = np.broadcast_to(1e12 + 1e10 * idx, grid.shape).copy()       # linear in x: the slopes are exact
+    npos = np.broadcast_to(2e12 - 3e9 * idx, grid.shape).copy()
+    mu_e, mu_p = 380.0, 3.4
+    re, rp = O.transport_rhs(grid, ne, npos, phi, 0.0, 0.0, mu_e, mu_p, (1.0e3, 2.0e3, 3.0e3))
+    g_e, g_p = 1e10 / grid.hx, -3e9 / grid.hx
+    lam = O.ionization_coefficient(np.array([e0]))[0] * mu_e * e0
+    inner = (slice(3, m - 3),) * 3
+    # electrons drift at -mu_e E: -div(v n) = mu_e e0 dn/dx; no diffusion of a linear profile
+    np.testing.assert_allclose(re[inner], mu_e * e0 * g_e + lam * ne[inner], rtol=1e-11)
+    np.testing.assert_allclose(rp[inner], -mu_p * e0 * g_p + lam * ne[inner], rtol=1e-11)
+
+
+def test_two_stage_step_is_the_explicit_midpoint_rule():
+    """Uniform densities in a uniform field grow by the ionization source only:
+    the predictor-corrector of eqs. (e1)-(e2) gives n (1 + tau l + (tau l)^2 / 2)."""
+    grid, phi, e0 = _uniform_field_case(m=14)
+    ne = np.full(grid.shape, 1e12)
+    npos = np.full(grid.shape, 1.2e12)
+    mu_e, mu_p, tau = 380.0, 3.4, 2e-12
+    lam = O.ionization_coefficient(np.array([e0]))[0] * mu_e * e0
+    args = (phi, 0.0, 0.0, mu_e, mu_p, (0.0, 0.0, 0.0))
+    he, hp = O.transport_stage(grid, ne, npos, ne, npos, *args, 0.5 * tau)
+    e1, p1 = O.transport_stage(grid, ne, npos, he, hp, *args, tau)
+    inner = (slice(5, 9),) * 3
+    np.testing.assert_allclose(e1[inner], 1e12 * (1 + tau * lam + 0.5 * (tau * lam) ** 2), rtol=1e-13)
+    np.testing.assert_allclose(p1[inner], 1.2e12 + tau * lam * 1e12 * (1 + 0.5 * tau * lam), rtol=1e-13)
+
+
+def test_drift_divergence_second_order_on_a_smooth_monotone_profile():
+    errs = []
+    for m in (32, 64):
+        grid, phi, e0 = _uniform_field_case(m=m, e0=1e5)
+        x = (np.arange(m) + 0.5) / m
+        prof = np.exp(-((x - 0.3) / 0.25) ** 2)                     # decreasing for x > 0.3
+        ne = np.broadcast_to(1e12 * prof, grid.shape).copy()
+        re, _ = O.transport_rhs(grid, ne, ne, phi, 0.0, 0.0, 380.0, 0.0, (0.0, 0.0, 0.0))
+        lam = O.ionization_coefficient(np.array([e0]))[0] * 380.0 * e0
+        exact = 380.0 * e0 * 1e12 * prof * (-2 * (x - 0.3) / 0.25 ** 2)   # mu_e E dn/dx
+        sel = (x > 0.45) & (x < 0.85)
+        k = m // 2
+        errs.append(np.abs(re[k, k, sel] - lam * ne[k, k, sel] - exact[sel]).max() / np.abs(exact[sel]).max())
+    assert np.log2(errs[0] / errs[1]) > 1.8, errs
+
+
+def test_stable_step_keeps_densities_non_negative():
+    shape = (10, 12, 14)
+    grid = _grid(shape)
+    rng = np.random.default_rng(7)
+    ne = np.where(rng.uniform(size=shape) > 0.7, 1e13, 0.0)         # sharp, non-negative
+    npos = ne[::-1].copy()
+    phi = 2e4 * random_field(60, shape)
+    mu_e, mu_p, dd = 380.0, 3.4, (2190.0, 2190.0, 1800.0)
+    ef = O.face_fields(grid, phi, 0.0, 2e4)
+    rate = sum(mu_e * np.abs(e).max() / h + 2 * d / h ** 2 for e, h, d in zip(ef, (grid.hx, grid.hy, grid.hz), dd))
+    tau = 0.4 / rate
+    args = (phi, 0.0, 2e4, mu_e, mu_p, dd)
+    he, hp = O.transport_stage(grid, ne, npos, ne, npos, *args, 0.5 * tau)
+    e1, p1 = O.transport_stage(grid, ne, npos, he, hp, *args, tau)
+    assert e1.min() >= -1e-6 * ne.max() and p1.min() >= -1e-6 * npos.max()
+
+
+def test_semi_implicit_step_runs_the_solve_and_both_stages():
+    shape = (16, 16, 16)
+    from streamer_inputs import streamer_densities, MU_E, MU_P, DIFFUSION, PHI0
+    ne, npos = streamer_densities(shape, 0)
+    params = O.OracleParams(coarse_min=4, phi_top=PHI0, cycle="auto")
+    e_over = O.ELEMENTARY_CHARGE / O.VACUUM_PERMITTIVITY_CM
+    ne1, np1, phi, info = O.semi_implicit_step(params, ne, npos, 2e-12, MU_E, MU_P, DIFFUSION, e_over)
+    assert info.converged and info.true_rel_residual < 1e-8
+    grid = _grid(shape)
+    args = (phi, 0.0, PHI0, MU_E, MU_P, DIFFUSION)
+    he, hp = O.transport_stage(grid, ne, npos, ne, npos, *args, 1e-12)
+    e_ref, p_ref = O.transport_stage(grid, ne, npos, he, hp, *args, 2e-12)
+    np.testing.assert_array_equal(ne1, e_ref)
+    np.testing.assert_array_equal(np1, p_ref)
+    assert np.all(np.isfinite(ne1)) and not np.array_equal(ne1, ne)
