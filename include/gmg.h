@@ -192,6 +192,34 @@ gmg_status gmg_update_coefficient(gmg_ctx* ctx, const double* a_dev);
 gmg_status fgmres_solve(gmg_ctx* ctx, const double* f_dev, double* phi_dev, int homogeneous_bc,
                         gmg_solve_info* info);
 
+/* Transport constants of eq. (eM) (Sec. 2.1, 5.2), in the units of the grid
+ * lengths, potentials and densities (cm, V, cm^-3 in the paper). */
+typedef struct gmg_transport_coef {
+  double mu_e, mu_p;             /* mobilities (magnitudes used)              */
+  double diff_x, diff_y, diff_z; /* electron diffusion D_e = diag(...)        */
+  double ion_a, ion_b;           /* alpha(|E|) = ion_a P exp(-ion_b P / |E|)  */
+  double pressure;               /* P (the paper: 5.7, 260, 760 Torr)         */
+} gmg_transport_coef;
+
+/* One explicit stage of the transport equations of eq. (eM) in the field
+ * E = -grad(phi), the building block of the second-order semi-implicit step
+ * eqs. (e1)-(e2) (predictor: c = tau/2, eval = base = n^n; corrector: c = tau,
+ * base = n^n, eval = n^{n+1/2}):
+ *   out_e = base_e + c [ div(mu_e E n_e) + div(D_e grad n_e) + alpha(|E|) mu_e |E| n_e ]
+ *   out_p = base_p + c [ -div(mu_p E n_p) + alpha(|E|) mu_e |E| n_e ]
+ * with n and E at the eval state.  Finite volumes on the grid of p (Sec. 2.2):
+ * MUSCL face values with the Koren limiter phi(r) = max(0, min(2r, (1+2r)/3, 2)),
+ * upwinded by the face velocity (-mu_e E_f for electrons, mu_p E_f for ions,
+ * E_f from phi with mirror ghosts on the side walls and 2 g - phi on the plates,
+ * g = p->phi_bottom / phi_top); densities take two layers of zero-flux ghosts;
+ * |E| of the source is the cell-centred central difference field.  All arrays
+ * FP64 device arrays of nx*ny*nz cells; out_e / out_p may be base_e / base_p
+ * but not eval_e, eval_p or phi.  No context is needed.  Errors: GMG_ERR_ARG
+ * (null or aliased pointers, bad grid, non-finite constants), GMG_ERR_CUDA. */
+gmg_status transport_stage(const gmg_params* p, const double* base_e, const double* base_p,
+                           const double* eval_e, const double* eval_p, const double* phi,
+                           const gmg_transport_coef* tc, double c, double* out_e, double* out_p, void* stream);
+
 /* Solve like fgmres_solve with another Krylov method (gmg_krylov).  Each
  * method stops when its own residual estimate falls below rtol ||b||, then
  * checks the true residual and restarts from phi if that is not below rtol.

@@ -1522,6 +1522,38 @@ gmg_status assemble_coefficient_rhs(const gmg_params* p, const double* ne_dev, c
   return e == cudaSuccess ? GMG_OK : map_err(e);
 }
 
+gmg_status transport_stage(const gmg_params* p, const double* base_e, const double* base_p,
+                           const double* eval_e, const double* eval_p, const double* phi,
+                           const gmg_transport_coef* tc, double cstage, double* out_e, double* out_p, void* stream) {
+  if (!p || !base_e || !base_p || !eval_e || !eval_p || !phi || !tc || !out_e || !out_p) return GMG_ERR_ARG;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || !(p->lx > 0) || !(p->ly > 0) || !(p->lz > 0)) return GMG_ERR_ARG;
+  const void* ins[] = {eval_e, eval_p, phi};
+  for (const void* q : ins)
+    if (q == out_e || q == out_p) return GMG_ERR_ARG;
+  if (out_e == out_p || base_e == out_p || base_p == out_e) return GMG_ERR_ARG;
+  const double k[] = {tc->mu_e, tc->mu_p, tc->diff_x, tc->diff_y, tc->diff_z, tc->ion_a, tc->ion_b, tc->pressure,
+                      cstage, p->phi_bottom, p->phi_top};
+  for (double v : k)
+    if (!std::isfinite(v)) return GMG_ERR_ARG;
+  const Grid3 g = make_grid(p->nx, p->ny, p->nz, p->lx, p->ly, p->lz);
+  TransportCoef t;
+  t.mu_e = std::fabs(tc->mu_e);
+  t.mu_p = std::fabs(tc->mu_p);
+  t.diff_x = tc->diff_x;
+  t.diff_y = tc->diff_y;
+  t.diff_z = tc->diff_z;
+  t.ion_ap = tc->ion_a * tc->pressure;
+  t.ion_bp = tc->ion_b * tc->pressure;
+  t.g_bottom = p->phi_bottom;
+  t.g_top = p->phi_top;
+  t.hx = p->lx / p->nx;
+  t.hy = p->ly / p->ny;
+  t.hz = p->lz / p->nz;
+  const cudaError_t e = launch_transport(g, t, base_e, base_p, eval_e, eval_p, phi, cstage, out_e, out_p,
+                                         static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GMG_OK : map_err(e);
+}
+
 gmg_status gmg_set_stream(gmg_ctx* c, void* stream) {
   if (!c) return GMG_ERR_ARG;
   CK(cudaStreamSynchronize(c->s));

@@ -204,6 +204,17 @@ struct DensityCoef {
 };
 cudaError_t launch_assemble(const Grid3& g, const DensityCoef& dc, const double* ne, const double* np, double* a,
                             double* f, cudaStream_t s);
+// One explicit transport stage (k_transport.cu): constants in the grid's units.
+struct TransportCoef {
+  double mu_e, mu_p;              // mobility magnitudes
+  double diff_x, diff_y, diff_z;  // electron diffusion
+  double ion_ap, ion_bp;          // alpha(|E|) = ion_ap exp(-ion_bp / |E|)
+  double g_bottom, g_top;         // plate potentials (the field's ghosts)
+  double hx, hy, hz;
+};
+cudaError_t launch_transport(const Grid3& g, const TransportCoef& tc, const double* base_e, const double* base_p,
+                             const double* ev_e, const double* ev_p, const double* phi, double c, double* out_e,
+                             double* out_p, cudaStream_t s);
 cudaError_t launch_adjoint_grad(const Grid3& g, const double* phi, const double* lam, double* out,
                                 double g_bot, double g_top, cudaStream_t s);
 

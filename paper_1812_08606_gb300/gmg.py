@@ -85,6 +85,14 @@ class gmg_density_coef(ctypes.Structure):
     ]
 
 
+class gmg_transport_coef(ctypes.Structure):
+    _fields_ = [
+        ("mu_e", ctypes.c_double), ("mu_p", ctypes.c_double), ("diff_x", ctypes.c_double),
+        ("diff_y", ctypes.c_double), ("diff_z", ctypes.c_double), ("ion_a", ctypes.c_double),
+        ("ion_b", ctypes.c_double), ("pressure", ctypes.c_double),
+    ]
+
+
 class GMGError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -128,6 +136,8 @@ _SIGS = {
     "gmg_coarse_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(gmg_params), _P, _P, _P, _P]),
     "assemble_coefficient_rhs": (ctypes.c_int, [ctypes.POINTER(gmg_params), _P, _P, ctypes.POINTER(gmg_density_coef),
                                                 _P, _P, _P]),
+    "transport_stage": (ctypes.c_int, [ctypes.POINTER(gmg_params), _P, _P, _P, _P, _P,
+                                       ctypes.POINTER(gmg_transport_coef), ctypes.c_double, _P, _P, _P]),
     "gmg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "gmg_profile_reset": (ctypes.c_int, [_P]),
     "gmg_profile_num_kernels": (ctypes.c_int, []),
@@ -461,3 +471,19 @@ def assemble_coefficient_rhs(params: gmg_params, n_e: torch.Tensor, n_p: torch.T
                                            _dev(n_p, numel=n, name="n_p"), ctypes.byref(dc),
                                            _dev(a, numel=n, name="a"), _dev(f, numel=n, name="f"),
                                            _stream_ptr(stream)), "assemble_coefficient_rhs")
+
+
+def transport_stage(params: gmg_params, base_e: torch.Tensor, base_p: torch.Tensor, eval_e: torch.Tensor,
+                    eval_p: torch.Tensor, phi: torch.Tensor, c: float, out_e: torch.Tensor, out_p: torch.Tensor,
+                    mu_e: float, mu_p: float, diffusion=(0.0, 0.0, 0.0), ion_a: float = 5.7, ion_b: float = 260.0,
+                    pressure: float = 760.0, stream=None):
+    """One explicit transport stage out = base + c R(eval) (eqs. (e1)-(e2)); FP64 device tensors."""
+    n = params.nx * params.ny * params.nz
+    tc = gmg_transport_coef(float(mu_e), float(mu_p), float(diffusion[0]), float(diffusion[1]), float(diffusion[2]),
+                            float(ion_a), float(ion_b), float(pressure))
+    _check(load().transport_stage(ctypes.byref(params), _dev(base_e, numel=n, name="base_e"),
+                                  _dev(base_p, numel=n, name="base_p"), _dev(eval_e, numel=n, name="eval_e"),
+                                  _dev(eval_p, numel=n, name="eval_p"), _dev(phi, numel=n, name="phi"),
+                                  ctypes.byref(tc), float(c), _dev(out_e, numel=n, name="out_e"),
+                                  _dev(out_p, numel=n, name="out_p"), _stream_ptr(stream)), "transport_stage")
+

@@ -838,3 +838,82 @@ def test_krylov_rejects_unknown_method_and_short_restart():
         gmg.gmg_krylov_solve(ctx, "bicgstab", _t(inp["f"]), phi)     # needs restart >= 7
     info = gmg.gmg_krylov_solve(ctx, "gmres", _t(inp["f"]), phi)     # GMRES works with any restart
     assert info.true_rel_residual < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# The semi-implicit time step: MUSCL/Koren transport stages, eqs. (e1)-(e2)
+# ---------------------------------------------------------------------------
+
+from paper_1812_08606_gb300.streamer import SemiImplicitStepper  # noqa: E402
+
+
+@pytest.mark.parametrize("shape,lengths", [(RAGGED, (1.0, 1.0, 1.0)), ((8, 24, 144), (2.0, 1.0, 0.5)),
+                                           ((4, 2, 34), (1.0, 1.0, 1.0))])
+def test_transport_stage_matches_oracle(shape, lengths):
+    nz, ny, nx = shape
+    grid = O.Grid(nx, ny, nz, *lengths)
+    ne, npos = _densities(shape, 350)
+    he, hp = ne * (1 + 0.1 * random_field(352, shape)), npos * (1 + 0.1 * random_field(353, shape))
+    phi = 3e4 * random_field(351, shape) + 1e4
+    p = _params(shape, lx=lengths[0], ly=lengths[1], lz=lengths[2], phi_bottom=-2e3, phi_top=5e4)
+    kw = dict(mu_e=MU_E, mu_p=MU_P, diffusion=DIFFUSION)
+    ref_e, ref_p = O.transport_stage(grid, ne, npos, he, hp, phi, -2e3, 5e4, MU_E, MU_P, DIFFUSION, 3e-12)
+    oe = torch.empty(shape, dtype=torch.float64, device=DEV)
+    op = torch.empty_like(oe)
+    gmg.transport_stage(p, _t(ne), _t(npos), _t(he), _t(hp), _t(phi), 3e-12, oe, op, **kw)
+    assert np.abs(_np(oe) - ref_e).max() <= 1e-12 * np.abs(ref_e).max()
+    assert np.abs(_np(op) - ref_p).max() <= 1e-12 * np.abs(ref_p).max()
+    # in place on the base arrays gives the same
+    be, bp = _t(ne), _t(npos)
+    gmg.transport_stage(p, be, bp, _t(he), _t(hp), _t(phi), 3e-12, be, bp, **kw)
+    assert torch.equal(be, oe) and torch.equal(bp, op)
+
+
+def test_transport_stage_rejects_aliasing():
+    shape = (8, 8, 8)
+    p = _params(shape)
+    x = [torch.ones(shape, dtype=torch.float64, device=DEV) for _ in range(4)]
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    with pytest.raises(gmg.GMGError):
+        gmg.transport_stage(p, x[0], x[1], x[2], x[3], phi, 1.0, x[2], x[1], mu_e=1.0, mu_p=1.0)   # out = eval
+    with pytest.raises(gmg.GMGError):
+        gmg.transport_stage(p, x[0], x[1], x[2], x[3], phi, 1.0, x[0], x[0], mu_e=1.0, mu_p=1.0)   # out_e = out_p
+
+
+def test_semi_implicit_step_fp64_matches_oracle():
+    shape = (16, 16, 16)
+    ne, npos = streamer_densities(shape, 0)
+    p = _params(shape, precision=gmg.GMG_PREC_FP64, orthogonalization=gmg.GMG_ORTH_MGS, cycle=gmg.GMG_CYCLE_AUTO,
+                phi_top=PHI0)
+    ref_e, ref_p, ref_phi, rinfo = O.semi_implicit_step(_oracle_hierarchy(ne, p), ne, npos, 2e-12, MU_E, MU_P,
+                                                        DIFFUSION, gmg.E_OVER_EPS0_CM)
+    st = SemiImplicitStepper(p, 2e-12, MU_E, MU_P, DIFFUSION)
+    oe = torch.empty(shape, dtype=torch.float64, device=DEV)
+    op = torch.empty_like(oe)
+    info = st.step(_t(ne), _t(npos), oe, op)
+    assert info.iterations == rinfo.iterations and info.fmg == 1
+    assert _rel(_np(st.phi), ref_phi) < 1e-10
+    assert np.abs(_np(oe) - ref_e).max() <= 1e-9 * np.abs(ref_e).max()
+    assert np.abs(_np(op) - ref_p).max() <= 1e-9 * np.abs(ref_p).max()
+    st.close()
+
+
+def test_semi_implicit_steps_mixed_stay_positive_and_warm():
+    """Five 2 ps steps of the eq. (51) streamer at 64^3 in 52 kV: the densities
+    stay finite and non-negative, the first step takes FMG and later steps
+    need few iterations from the previous potential."""
+    shape = (64, 64, 64)
+    ne0, np0 = streamer_densities(shape, 0, xp=torch, device=DEV)
+    p = _params(shape, precision=gmg.GMG_PREC_MIXED, cycle=gmg.GMG_CYCLE_AUTO, phi_top=PHI0)
+    st = SemiImplicitStepper(p, 2e-12, MU_E, MU_P, DIFFUSION)
+    ne, npos = ne0.clone(), np0.clone()
+    iters = []
+    for _ in range(5):
+        info = st.step(ne, npos, ne, npos)
+        assert info.true_rel_residual < 1e-8
+        iters.append(info.iterations)
+    assert torch.isfinite(ne).all() and torch.isfinite(npos).all()
+    assert ne.min().item() >= -1e-6 * ne0.max().item() and npos.min().item() >= -1e-6 * np0.max().item()
+    assert not torch.equal(ne, ne0)
+    assert max(iters[1:]) <= 5, iters
+    st.close()
