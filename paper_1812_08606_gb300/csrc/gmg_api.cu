@@ -1537,6 +1537,7 @@ gmg_status transport_stage(const gmg_params* p, const double* base_e, const doub
     if (!std::isfinite(v)) return GMG_ERR_ARG;
   const Grid3 g = make_grid(p->nx, p->ny, p->nz, p->lx, p->ly, p->lz);
   TransportCoef t;
+  const double hx = p->lx / p->nx, hy = p->ly / p->ny, hz = p->lz / p->nz;
   t.mu_e = std::fabs(tc->mu_e);
   t.mu_p = std::fabs(tc->mu_p);
   t.diff_x = tc->diff_x;
@@ -1546,9 +1547,15 @@ gmg_status transport_stage(const gmg_params* p, const double* base_e, const doub
   t.ion_bp = tc->ion_b * tc->pressure;
   t.g_bottom = p->phi_bottom;
   t.g_top = p->phi_top;
-  t.hx = p->lx / p->nx;
-  t.hy = p->ly / p->ny;
-  t.hz = p->lz / p->nz;
+  t.ihx = 1.0 / hx;
+  t.ihy = 1.0 / hy;
+  t.ihz = 1.0 / hz;
+  t.ih2x = 0.5 / hx;
+  t.ih2y = 0.5 / hy;
+  t.ih2z = 0.5 / hz;
+  t.dih2x = tc->diff_x / (hx * hx);
+  t.dih2y = tc->diff_y / (hy * hy);
+  t.dih2z = tc->diff_z / (hz * hz);
   const cudaError_t e = launch_transport(g, t, base_e, base_p, eval_e, eval_p, phi, cstage, out_e, out_p,
                                          static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GMG_OK : map_err(e);

@@ -210,7 +210,9 @@ struct TransportCoef {
   double diff_x, diff_y, diff_z;  // electron diffusion
   double ion_ap, ion_bp;          // alpha(|E|) = ion_ap exp(-ion_bp / |E|)
   double g_bottom, g_top;         // plate potentials (the field's ghosts)
-  double hx, hy, hz;
+  double ihx, ihy, ihz;           // 1/h
+  double ih2x, ih2y, ih2z;        // 1/(2h): the central-difference field
+  double dih2x, dih2y, dih2z;     // D_alpha / h_alpha^2
 };
 cudaError_t launch_transport(const Grid3& g, const TransportCoef& tc, const double* base_e, const double* base_p,
                              const double* ev_e, const double* ev_p, const double* phi, double c, double* out_e,

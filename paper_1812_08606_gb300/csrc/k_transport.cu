@@ -18,11 +18,12 @@ namespace gmg {
 
 namespace {
 
-// Koren-limited slope phi(r) b, r = a / b, without the division.
+// Koren-limited slope phi(r) b, r = a / b, without the division (GB300 runs an
+// FP64 divide as a multi-instruction sequence; 1/3 is a multiplication).
 __device__ __forceinline__ double koren(double a, double b) {
   if (!(a * b > 0.0)) return 0.0;
   const double aa = fabs(a), ab = fabs(b);
-  const double s = fmin(fmin(2.0 * aa, (ab + 2.0 * aa) / 3.0), 2.0 * ab);
+  const double s = fmin(fmin(2.0 * aa, (ab + 2.0 * aa) * (1.0 / 3.0)), 2.0 * ab);
   return copysign(s, b);
 }
 
@@ -57,19 +58,18 @@ __global__ void __launch_bounds__(256) k_transport(Grid3 g, TransportCoef tc, co
   const double fzm = k > 0 ? phi[p - pl] : 2.0 * tc.g_bottom - fc;
   const double fzp = k < nz - 1 ? phi[p + pl] : 2.0 * tc.g_top - fc;
   // |E| at the centre (central differences) and the ionization source rate
-  const double ex = -(fxp - fxm) / (2.0 * tc.hx), ey = -(fyp - fym) / (2.0 * tc.hy),
-               ez = -(fzp - fzm) / (2.0 * tc.hz);
+  const double ex = (fxm - fxp) * tc.ih2x, ey = (fym - fyp) * tc.ih2y, ez = (fzm - fzp) * tc.ih2z;
   const double eabs = sqrt(ex * ex + ey * ey + ez * ez);
   const double alpha = eabs > 0.0 ? tc.ion_ap * exp(-tc.ion_bp / eabs) : 0.0;
   const double src = alpha * tc.mu_e * eabs * ev_e[p];
   // face fields: low and high face along each axis
-  const double E[3][2] = {{-(fc - fxm) / tc.hx, -(fxp - fc) / tc.hx},
-                          {-(fc - fym) / tc.hy, -(fyp - fc) / tc.hy},
-                          {-(fc - fzm) / tc.hz, -(fzp - fc) / tc.hz}};
+  const double E[3][2] = {{(fxm - fc) * tc.ihx, (fc - fxp) * tc.ihx},
+                          {(fym - fc) * tc.ihy, (fc - fyp) * tc.ihy},
+                          {(fzm - fc) * tc.ihz, (fc - fzp) * tc.ihz}};
   const int pos[3] = {i, j, k}, len[3] = {nx, ny, nz};
   const size_t stride[3] = {1, (size_t)nx, pl};
-  const double h[3] = {tc.hx, tc.hy, tc.hz};
-  const double dd[3] = {tc.diff_x, tc.diff_y, tc.diff_z};
+  const double ih[3] = {tc.ihx, tc.ihy, tc.ihz};
+  const double dd[3] = {tc.dih2x, tc.dih2y, tc.dih2z};  // D_alpha / h_alpha^2
   double div_e = 0.0, div_p = 0.0, diff = 0.0;
   const double ce = ev_e[p];
 #pragma unroll
@@ -87,10 +87,10 @@ __global__ void __launch_bounds__(256) k_transport(Grid3 g, TransportCoef tc, co
     const double vlo_p = tc.mu_p * E[ax][0], vhi_p = tc.mu_p * E[ax][1];
     const double flo_e = vlo_e * face_value(vlo_e, ue), fhi_e = vhi_e * face_value(vhi_e, ue + 1);
     const double flo_p = vlo_p * face_value(vlo_p, up), fhi_p = vhi_p * face_value(vhi_p, up + 1);
-    div_e += (fhi_e - flo_e) / h[ax];
-    div_p += (fhi_p - flo_p) / h[ax];
+    div_e += (fhi_e - flo_e) * ih[ax];
+    div_p += (fhi_p - flo_p) * ih[ax];
     // electron diffusion with one mirrored layer (ue[1], ue[3] are the neighbours)
-    diff += dd[ax] / (h[ax] * h[ax]) * ((ue[3] - 2.0 * ce) + ue[1]);
+    diff += dd[ax] * ((ue[3] - 2.0 * ce) + ue[1]);
   }
   out_e[p] = base_e[p] + c * ((-div_e + diff) + src);
   out_p[p] = base_p[p] + c * (-div_p + src);
