@@ -354,6 +354,9 @@ def run_ours(args, dist):
         cmp["paper_table_t1_ratio"] = {"fgmres": 1.0, "gmres": 1.1888, "cg": 1.1884, "fcg": 1.1724, "cgs": 1.3301,
                                        "bicgstab": 1.3263}
         out["krylov_comparison_paper_mesh"] = cmp
+        # the whole second-order semi-implicit step (eqs. (e1)-(e2)): solve + MUSCL/Koren transport
+        out["streamer_steps_paper_mesh"] = streamer_arm(args, gmg, (320, 256, 256), stream)
+        out["streamer_steps"] = streamer_arm(args, gmg, (n, n, n), stream)
 
     # end to end through the host-buffer C ABI call
     if not args.no_e2e:
@@ -467,6 +470,46 @@ def time_step_arm(args, gmg, shape, stream, method="fgmres"):
             "steps": K, "step": "assemble a, f from n_e, n_p + set-up + warm-started solve + E (FP32)",
             "workload": f"double-headed streamer eq. (51), {nx} x {ny} x {nz} cells on the unit cube, "
                         f"tau = 2 ps, 52 kV", "levels": levels}
+
+
+def streamer_arm(args, gmg, shape, stream):
+    """Full steps of the second-order semi-implicit scheme on the eq. (51)
+    streamer (52 kV, tau = 2 ps, Sec. 5.2 constants): assembly, set-up,
+    warm-started solve for phi^{n+1/2}, predictor and corrector transport
+    stages.  One untimed first step (FMG), then the timed steps."""
+    import torch
+    from streamer_inputs import streamer_densities, MU_E, MU_P, DIFFUSION, PHI0
+    from paper_1812_08606_gb300.streamer import SemiImplicitStepper
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nz, ny, nx = shape
+    N = nx * ny * nz
+    ne, npos = streamer_densities(shape, 0, xp=torch, device=dev)
+    p = gmg.gmg_default_params(nx, ny, nz, precision=gmg.GMG_PREC_MIXED, cycle=gmg.GMG_CYCLE_AUTO, phi_top=PHI0)
+    st = SemiImplicitStepper(p, 2e-12, MU_E, MU_P, DIFFUSION, device=dev, stream=stream)
+    first = st.step(ne, npos, ne, npos)
+    K = args.regime_steps
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [st.step(ne, npos, ne, npos) for _ in range(K)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    # the two transport stages alone, timed on the same state
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kw = dict(mu_e=MU_E, mu_p=MU_P, diffusion=DIFFUSION, stream=stream)
+    t0.record(stream)
+    gmg.transport_stage(p, ne, npos, ne, npos, st.phi, 1e-12, st.half_e, st.half_p, **kw)
+    gmg.transport_stage(p, ne, npos, st.half_e, st.half_p, st.phi, 2e-12, st.a, st.f, **kw)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    st.close()
+    return {"ms_per_step": round(ms, 3), "value": round(N / (ms / 1e3) / 1e6, 2), "unit": "Mcells/s",
+            "transport_ms_per_step": round(t0.elapsed_time(t1), 3), "iterations": [i.iterations for i in infos],
+            "first_step_iterations": first.iterations, "true_rel_residual": max(i.true_rel_residual for i in infos),
+            "steps": K, "step": "eqs. (e1)-(e2): assemble + set-up + solve phi^{n+1/2} + predictor + corrector (FP64 "
+                                "MUSCL/Koren transport)",
+            "workload": f"eq. (51) double-headed streamer, {nx} x {ny} x {nz} cells, tau = 2 ps, 52 kV"}
 
 
 def e2e_arm(args, gmg, ctx, inp, n, N, stream, dist):
