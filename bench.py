@@ -45,7 +45,8 @@ L2_BYTES = 129 * 2**20
 NCU_TRAFFIC = {
     "cheb_sgs_fused_f32": {
         "source": "paper_1812_08606_gb300/csrc/k_smooth_fused.cu",
-        "sha": "a67a9381bb515a39516c462b6f9fce1306ec078d",
+        "sha": "a1638834959259fb4d927d1bba7f14d70e825d94",
+        # (captured with the same device code; the later edit made the launch set-up per device)
         # twochannel 256^3, finest-level step with x_in and d: 396,786,176 DRAM bytes / 402,653,184 algorithmic
         "dram_over_algorithmic": 396786176 / 402653184,
     },

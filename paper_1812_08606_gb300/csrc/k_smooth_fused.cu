@@ -34,6 +34,7 @@
 // warp-uniform branch picks a copy of the step with that lane known at
 // compile time, which removes the lane selects from the stages.
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "gmg_internal.cuh"
@@ -313,8 +314,29 @@ __global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
   }
 }
 
-bool g_fused_attr_set = false;
-int g_fused_slots = 0;  // resident blocks of the kernel on the device (one device per process)
+// Per device: the kernel's shared-memory attribute is set and its resident
+// block count known (0 = not yet).  Guarded by a mutex for host threads.
+constexpr int kMaxDevices = 64;
+int g_fused_slots[kMaxDevices] = {};
+std::mutex g_fused_mutex;
+
+cudaError_t fused_slots(int* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_fused_mutex);
+  if (g_fused_slots[dev] == 0) {
+    e = cudaFuncSetAttribute(k_cheb_sgs_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM);
+    int sms = 0, per = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cheb_sgs_fused, PPL, FUSED_SMEM);
+    if (e != cudaSuccess) return e;
+    g_fused_slots[dev] = std::max(1, sms * std::max(1, per));
+  }
+  *out = g_fused_slots[dev];
+  return cudaSuccess;
+}
 
 }  // namespace
 
@@ -324,24 +346,13 @@ cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b
                                     float* d, double c1, double c2, int flags, cudaStream_t s) {
   if (!pair_aligned(a) || !pair_aligned(b) || (xin && !pair_aligned(xin)) || !pair_aligned(xout) || !pair_aligned(d))
     return cudaErrorMisalignedAddress;
-  if (!g_fused_attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_cheb_sgs_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)FUSED_SMEM);
-    if (e != cudaSuccess) return e;
-    g_fused_attr_set = true;
-  }
-  if (g_fused_slots == 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cheb_sgs_fused, PPL, FUSED_SMEM);
-    if (e != cudaSuccess) return e;
-    g_fused_slots = std::max(1, sms * std::max(1, per));
-  }
+  int slots = 0;
+  const cudaError_t e = fused_slots(&slots);
+  if (e != cudaSuccess) return e;
   const int tx = (g.nx + FTX - 1) / FTX, ty = (g.ny + FTY - 1) / FTY;
   const long long units = (long long)tx * ty * g.nz;
   // one block per resident slot, but at least 4 planes per block on small grids
-  const long long blocks = std::max(1LL, std::min((long long)g_fused_slots, units / 4));
+  const long long blocks = std::max(1LL, std::min((long long)slots, units / 4));
   FusedArgs P{g, a, b, xin, xout, d, (float)c1, (float)c2, flags, tx, units};
   k_cheb_sgs_fused<<<(unsigned)blocks, dim3(RP, RH), FUSED_SMEM, s>>>(P);
   return cudaGetLastError();

@@ -917,3 +917,53 @@ def test_semi_implicit_steps_mixed_stay_positive_and_warm():
     assert not torch.equal(ne, ne0)
     assert max(iters[1:]) <= 5, iters
     st.close()
+
+
+# ---------------------------------------------------------------------------
+# Edge cases of the first-step, Krylov and transport entry points
+# ---------------------------------------------------------------------------
+
+
+def test_fmg_on_a_single_level_is_the_direct_solve():
+    shape = (4, 4, 6)                      # coarse_min 4: one level, the dense Cholesky
+    a = random_coefficient(360, shape, 1e2)
+    f = random_field(361, shape)
+    p = _params(shape, coarse_min=4, precision=gmg.GMG_PREC_FP64, cycle=gmg.GMG_CYCLE_FMG)
+    ctx = gmg.gmg_setup(p, _t(a))
+    assert gmg.gmg_num_levels(ctx) == 1
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    info = gmg.fgmres_solve(ctx, _t(f), phi)
+    assert info.iterations == 1 and info.true_rel_residual < 1e-12
+
+
+@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres"])
+def test_krylov_iteration_cap_reports_not_converged(method):
+    inp = make_inputs("twochannel512", n=32)
+    shape = inp["a"].shape
+    ctx = gmg.gmg_setup(_params(shape, max_iters=2), _t(inp["a"]))
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    info = gmg.gmg_krylov_solve(ctx, method, _t(inp["f"]), phi)
+    assert info.converged == 0 and info.iterations == 2
+    assert np.isfinite(_np(phi)).all()
+
+
+@pytest.mark.parametrize("shape", [(1, 5, 6), (3, 1, 8), (5, 6, 2)])
+def test_transport_and_assembly_on_thin_grids(shape):
+    nz, ny, nx = shape
+    grid = O.Grid(nx, ny, nz)
+    ne, npos = _densities(shape, 370)
+    phi = 1e4 * random_field(371, shape)
+    p = _params(shape, phi_top=3e3)
+    ref_e, ref_p = O.transport_stage(grid, ne, npos, ne, npos, phi, 0.0, 3e3, MU_E, MU_P, DIFFUSION, 2e-12)
+    oe = torch.empty(shape, dtype=torch.float64, device=DEV)
+    op = torch.empty_like(oe)
+    gmg.transport_stage(p, _t(ne), _t(npos), _t(ne), _t(npos), _t(phi), 2e-12, oe, op, mu_e=MU_E, mu_p=MU_P,
+                        diffusion=DIFFUSION)
+    assert np.abs(_np(oe) - ref_e).max() <= 1e-12 * np.abs(ref_e).max()
+    assert np.abs(_np(op) - ref_p).max() <= 1e-12 * np.abs(ref_p).max()
+    a_ref, f_ref = O.assemble_coefficient_rhs(grid, ne, npos, 2e-12, MU_E, MU_P, DIFFUSION, gmg.E_OVER_EPS0_CM)
+    a = torch.empty_like(oe)
+    f = torch.empty_like(oe)
+    gmg.assemble_coefficient_rhs(p, _t(ne), _t(npos), a, f, tau=2e-12, mu_e=MU_E, mu_p=MU_P, diffusion=DIFFUSION)
+    np.testing.assert_allclose(_np(a), a_ref, rtol=1e-14)
+    assert np.abs(_np(f) - f_ref).max() <= 1e-13 * np.abs(f_ref).max()
