@@ -310,6 +310,7 @@ def run_ours(args, dist):
         "data": "synthetic (seeded streamer-shaped a and f)",
         "config": {"workload": f"{args.workload} {n}^3", "cells": N, "kappa": inp["kappa"],
                    "precision": "mixed: FP32 V-cycle inside FP64 FGMRES", "restart": params.restart,
+                   "orthogonalization": ["CGS2", "MGS (Algorithm 1, fused passes)"][params.orthogonalization],
                    "rtol": params.rtol, "cheb_steps": params.cheb_steps, "levels": gmg.gmg_num_levels(ctx),
                    "l2": "inputs larger than L2 (1 FP64 field = %.2f GB > 129 MB)" % (8 * N / 1e9) if 8 * N > L2_BYTES
                    else "inputs smaller than L2", "parallelism": "replicas" if dist.world > 1 else "single GPU"},

@@ -76,13 +76,16 @@ typedef enum gmg_smoother_pc {
   GMG_PC_IDENTITY = 2  /* none (plain Chebyshev)                            */
 } gmg_smoother_pc;
 
-/* Orthogonalisation of the FGMRES Arnoldi process and of the eigen-bound
- * Arnoldi.  With GMG_ORTH_CGS2 the FP32 eigen-bound Arnoldi of the mixed
- * set-up takes a single classical pass (the bounds only steer the FP32
- * smoother); FGMRES and the FP64 eigen bounds take both passes. */
+/* Orthogonalisation of the FGMRES Arnoldi process and of the FP64 eigen-bound
+ * Arnoldi.  The FP32 eigen-bound Arnoldi of the mixed set-up always takes a
+ * single classical pass (the bounds only steer the FP32 smoother).  MGS runs
+ * one fused pass per basis vector (about 2 FMA and 32 bytes per element per
+ * vector); CGS2 runs three fused passes (about 4 FMA per element per vector),
+ * which on GB300's 1/64-rate FP64 pipe is the slower of the two. */
 typedef enum gmg_orthogonalization {
   GMG_ORTH_CGS2 = 0, /* classical Gram-Schmidt applied twice, fused passes */
-  GMG_ORTH_MGS = 1   /* modified Gram-Schmidt as printed in Algorithm 1    */
+  GMG_ORTH_MGS = 1   /* modified Gram-Schmidt as printed in Algorithm 1
+                        (default)                                          */
 } gmg_orthogonalization;
 
 /* Arithmetic of the FGMRES matrix-vector product w = A z_j when z_j is the
@@ -165,7 +168,7 @@ typedef struct gmg_solve_info {
  * plate data 0 / 1, coarse_min 4, 3 Chebyshev steps (a quadratic p_n, Sec.
  * 3.2), restart 20 (the paper uses 30, Sec. 3.1), rtol 1e-8 (Sec. 5.2),
  * 10 Arnoldi steps with factors 1.1 / 0.1 (Sec. 3.2), mixed precision,
- * trilinear prolongation, SGS smoother preconditioner, CGS2, double-float
+ * trilinear prolongation, SGS smoother preconditioner, MGS, double-float
  * Arnoldi product in mixed precision. */
 void gmg_default_params(gmg_params* p, int nx, int ny, int nz);
 

@@ -180,7 +180,7 @@ enum KernelClass : int {
   K_CHEB_F64, K_CHEB_F32, K_RESTRICT_F64, K_RESTRICT_F32, K_PROLONG_F64, K_PROLONG_F32, K_COARSE_F64,
   K_COARSE_F32, K_DOT, K_FINALIZE, K_AXPY, K_SCALE, K_UPDATE_X, K_CAST, K_COPY, K_RHS, K_FIELD, K_ADJOINT,
   K_COARSEN, K_COEF_CHECK, K_HASH, K_COARSE_ASSEMBLE, K_COARSE_FACTOR, K_DOT_F32, K_AXPY_F32, K_APPLY_DF64,
-  K_SPLIT, K_CHEB_FUSED, K_CGS_DOTS, K_CGS_DOTS_F32, K_CGS_UPDATE, K_CGS_UPDATE_F32, K_LIN3, NK
+  K_SPLIT, K_CHEB_FUSED, K_CGS_DOTS, K_CGS_DOTS_F32, K_CGS_UPDATE, K_CGS_UPDATE_F32, K_LIN3, K_MGS, K_MGS_F32, NK
 };
 static const char* const kKernelNames[NK] = {
     "apply_f64", "apply_outer_f64a_f32x", "apply_f32", "residual_f64", "residual_f32", "sgs_half_f64",
@@ -189,7 +189,7 @@ static const char* const kKernelNames[NK] = {
     "multi_axpy", "scale", "update_solution", "cast", "copy", "rhs", "field", "adjoint_grad", "coarsen_coef",
     "coef_check", "hash_vector", "coarse_assemble", "coarse_factor", "multi_dot_f32", "multi_axpy_f32",
     "apply_outer_df64", "split_coef", "cheb_sgs_fused_f32", "cgs_dots", "cgs_dots_f32", "cgs_update",
-    "cgs_update_f32", "vector_lin3"};
+    "cgs_update_f32", "vector_lin3", "mgs_pass", "mgs_pass_f32"};
 
 struct ProfPending {
   int cls;
@@ -416,6 +416,12 @@ gmg_status prof_update_solution(gmg_ctx* c, size_t n, double* x, const TZ* Z, si
                                 cudaStream_t s) {
   GMG_RUN(K_UPDATE_X, (double)n * (16.0 + k * sizeof(TZ)), launch_update_solution<TZ>(n, x, Z, ldz, k, y, s));
 }
+template <typename T>
+gmg_status prof_mgs_step(gmg_ctx* c, size_t n, T* w, const T* vi, const T* vnext, const double* hi, double* partial) {
+  const double bytes = (double)sizeof(T) * n * (1.0 + (vi ? 2.0 : 0.0) + (vnext ? 1.0 : 0.0));
+  cudaStream_t s = c->s;
+  GMG_RUN(is_f32<T>() ? K_MGS_F32 : K_MGS, bytes, launch_mgs_step<T>(n, w, vi, vnext, hi, partial, s));
+}
 template <typename T1, typename T2>
 gmg_status prof_lin3(gmg_ctx* c, size_t n, double a1, const T1* v1, double a2, const T2* v2, double a3,
                      const double* v3, double* out) {
@@ -531,12 +537,20 @@ gmg_status norm_dev(gmg_ctx* c, size_t n, const T* w, int slot) {
 template <typename T>
 gmg_status orthogonalize(gmg_ctx* c, size_t n, const T* V, size_t ld, int k, T* w, bool one_pass = false) {
   const int nb = reduce_blocks(n);
-  if (c->p.orthogonalization == GMG_ORTH_MGS) {
+  if (c->p.orthogonalization == GMG_ORTH_MGS && !one_pass) {
+    // Algorithm 1's modified Gram-Schmidt, one fused pass per basis vector:
+    // pass i applies h_{i} v_i to w and forms (w, v_{i+1}); the last forms ||w||.
+    CKS(prof_mgs_step<T>(c, n, w, (const T*)nullptr, V, nullptr, c->partial));
+    CKS(prof_finalize(c, c->partial, nb, 1, c->dscal + SL_H1, 0, c->s));
     for (int i = 0; i < k; ++i) {
-      CKS(prof_multi_dot<T>(c, n, w, V + (size_t)i * ld, ld, 1, c->partial, c->s));
-      CKS(prof_finalize(c, c->partial, nb, 1, c->dscal + SL_H1 + i, 0, c->s));
-      CKS(prof_multi_axpy<T>(c, n, w, V + (size_t)i * ld, ld, 1, c->dscal + SL_H1 + i, c->s));
+      const T* vnext = i + 1 < k ? V + (size_t)(i + 1) * ld : nullptr;
+      CKS(prof_mgs_step<T>(c, n, w, V + (size_t)i * ld, vnext, c->dscal + SL_H1 + i, c->partial));
+      if (vnext)
+        CKS(prof_finalize(c, c->partial, nb, 1, c->dscal + SL_H1 + i + 1, 0, c->s));
+      else
+        CKS(prof_finalize_norm(c, c->partial, nb, c->dscal + SL_NORM, c->s));
     }
+    return GMG_OK;
   } else if (k <= kCgsMaxVectors) {
     // three fused passes: h1 = V^T w; h2 = V^T (w - V h1); w -= V (h1 + h2) with ||w||^2
     // (one_pass: h2 = 0, two passes)
@@ -1267,7 +1281,7 @@ void gmg_default_params(gmg_params* p, int nx, int ny, int nz) {
   p->precision = GMG_PREC_MIXED;
   p->prolongation = GMG_PROLONG_TRILINEAR;
   p->smoother_pc = GMG_PC_SGS;
-  p->orthogonalization = GMG_ORTH_CGS2;
+  p->orthogonalization = GMG_ORTH_MGS;
   p->outer_arith = GMG_OUTER_DOUBLE_FLOAT;
   p->smoother_kernel = 0;
   p->cycle = GMG_CYCLE_V;

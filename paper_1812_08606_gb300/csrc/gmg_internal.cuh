@@ -259,6 +259,11 @@ template <typename TZ>
 cudaError_t launch_update_solution(size_t n, double* x, const TZ* Z, size_t ldz, int k,
                                    const double* y, cudaStream_t s);
 // partial[b*2 + 0] = min over block of a; partial[b*2+1] = count of non-finite / non-positive.
+// One fused modified Gram-Schmidt pass: w -= (*hi) vi (vi null: none), then the
+// partial sums of (w, vnext) (vnext null: ||w||^2), one per reduce block.
+template <typename T>
+cudaError_t launch_mgs_step(size_t n, T* w, const T* vi, const T* vnext, const double* hi, double* partial,
+                            cudaStream_t s);
 // out = a1 v1 + a2 v2 + a3 v3 (FP64 out; null vectors drop their terms; out may alias v3).
 template <typename T1, typename T2>
 cudaError_t launch_lin3(size_t n, double a1, const T1* v1, double a2, const T2* v2, double a3, const double* v3,

@@ -57,6 +57,31 @@ __global__ void __launch_bounds__(RT) k_multi_dot(size_t n, const T* __restrict_
   }
 }
 
+// ---- Modified Gram-Schmidt, one fused pass per basis vector ----
+// w -= h_i v_i (h_i read from device memory; vi null: no update) and the
+// partial sums of (w, v_next) with the updated w (vnext null: ||w||^2).  Each
+// pass reads w, v_i and v_next once and writes w, so MGS moves about 32 bytes
+// per element per basis vector and takes 2 FMA: on GB300, whose FP64 rate is
+// 1/64 of FP32, that is cheaper than the 4 FMA per element per vector of CGS2.
+template <typename T>
+__global__ void __launch_bounds__(RT) k_mgs_step(size_t n, T* __restrict__ w, const T* __restrict__ vi,
+                                                 const T* __restrict__ vnext, const double* __restrict__ hi,
+                                                 double* __restrict__ partial) {
+  __shared__ double sh[RT / 32];
+  const T h = vi ? (T)*hi : (T)0;
+  T acc = (T)0;
+  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
+    T wp = w[p];
+    if (vi) {
+      wp = fma(-h, vi[p], wp);
+      w[p] = wp;
+    }
+    acc = fma(wp, vnext ? vnext[p] : wp, acc);
+  }
+  const double t = block_sum<RT>((double)acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
 // ---- Fused classical Gram-Schmidt passes (K <= CGS_KMAX vectors) ----
 // K is a template parameter: a loop over a runtime count would issue every
 // unrolled (predicated-off) load and FMA, which on GB300's 1/64-rate FP64 pipe
@@ -416,6 +441,17 @@ template cudaError_t launch_lin3<float, double>(size_t, double, const float*, do
                                                 const double*, double*, cudaStream_t);
 template cudaError_t launch_lin3<float, float>(size_t, double, const float*, double, const float*, double,
                                                const double*, double*, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_mgs_step(size_t n, T* w, const T* vi, const T* vnext, const double* hi, double* partial,
+                            cudaStream_t s) {
+  k_mgs_step<T><<<reduce_blocks(n), RT, 0, s>>>(n, w, vi, vnext, hi, partial);
+  return cudaGetLastError();
+}
+template cudaError_t launch_mgs_step<double>(size_t, double*, const double*, const double*, const double*, double*,
+                                             cudaStream_t);
+template cudaError_t launch_mgs_step<float>(size_t, float*, const float*, const float*, const double*, double*,
+                                            cudaStream_t);
 
 cudaError_t launch_coef_check(size_t n, const double* a, double* partial, cudaStream_t s) {
   k_coef_check<<<reduce_blocks(n), RT, 0, s>>>(n, a, partial);
