@@ -965,8 +965,8 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
         const double est = fabs(g[j + 1]) / bnorm;
         if (loc.n_history < GMG_MAX_HISTORY) loc.res_history[loc.n_history++] = est;
         if (hnext == 0.0) break;  // lucky breakdown: the solution is in K_j
-        CKS(prof_scale(c, n, c->w, c->V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));
         if (est < c->p.rtol || loc.iterations >= c->p.max_iters) break;  // stopping test
+        CKS(prof_scale(c, n, c->w, c->V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));  // v_{j+1}
       }
       if (fail) break;
       // y_k from the triangular system, x_k = x_0 + Z_k y_k
