@@ -358,8 +358,12 @@ gmg_status gmg_hessenberg_max_real_eig(const double* h_host, int m, double* out)
  * is bracketed by CUDA events on the context's stream, and each launch's
  * algorithmic bytes (every array the kernel must touch, read or written
  * once) are accumulated per kernel class.  Timing adds two event records per
- * launch and no synchronisation beyond the solver's own. */
+ * launch and no synchronisation beyond the solver's own.  Launches that move
+ * fewer algorithmic bytes than gmg_profile_min_bytes (default 0) are counted
+ * but not timed, which keeps the host from falling behind the GPU on the
+ * coarse levels' many small launches. */
 gmg_status gmg_profile_enable(gmg_ctx* ctx, int on);
+gmg_status gmg_profile_min_bytes(gmg_ctx* ctx, double min_bytes);
 gmg_status gmg_profile_reset(gmg_ctx* ctx);
 int gmg_profile_num_kernels(void);
 /* Totals of kernel class k (0 <= k < gmg_profile_num_kernels()): its name

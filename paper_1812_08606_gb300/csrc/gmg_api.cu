@@ -242,6 +242,7 @@ struct gmg_ctx {
   float setup_ms = 0.f;
   // per-kernel profile
   bool prof_on = false;
+  double prof_min_bytes = 0.0;  // launches below this are counted, not timed
   std::vector<cudaEvent_t> ev_pool;
   std::vector<ProfPending> pend;
   double k_ms[NK] = {};
@@ -307,7 +308,7 @@ void prof_collect(gmg_ctx* c) {
 template <typename F>
 gmg_status run_kernel(gmg_ctx* c, int cls, double bytes, F&& launch) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c->prof_on && (e0 = prof_event(c)) != nullptr) cudaEventRecord(e0, c->s);
+  if (c->prof_on && bytes >= c->prof_min_bytes && (e0 = prof_event(c)) != nullptr) cudaEventRecord(e0, c->s);
   const cudaError_t e = launch();
   c->k_launch[cls] += 1;
   if (e != cudaSuccess) {
@@ -1698,6 +1699,12 @@ gmg_status gmg_profile_enable(gmg_ctx* c, int on) {
   CK(cudaStreamSynchronize(c->s));
   prof_collect(c);
   c->prof_on = on != 0;
+  return GMG_OK;
+}
+
+gmg_status gmg_profile_min_bytes(gmg_ctx* c, double min_bytes) {
+  if (!c || !(min_bytes >= 0.0)) return GMG_ERR_ARG;
+  c->prof_min_bytes = min_bytes;
   return GMG_OK;
 }
 

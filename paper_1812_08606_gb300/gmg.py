@@ -140,6 +140,7 @@ _SIGS = {
                                        ctypes.POINTER(gmg_transport_coef), ctypes.c_double, _P, _P, _P]),
     "gmg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "gmg_profile_reset": (ctypes.c_int, [_P]),
+    "gmg_profile_min_bytes": (ctypes.c_int, [_P, ctypes.c_double]),
     "gmg_profile_num_kernels": (ctypes.c_int, []),
     "gmg_profile_get": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                        ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
@@ -421,6 +422,10 @@ def gmg_test_fail_allocation_after(n: int):
 
 def gmg_profile_enable(ctx: Context, on: bool = True):
     _check(load().gmg_profile_enable(ctx.handle, int(bool(on))), "gmg_profile_enable")
+
+
+def gmg_profile_min_bytes(ctx: Context, min_bytes: float):
+    _check(load().gmg_profile_min_bytes(ctx.handle, float(min_bytes)), "gmg_profile_min_bytes")
 
 
 def gmg_profile_reset(ctx: Context):
