@@ -218,10 +218,26 @@ typedef struct gmg_transport_coef {
  * |E| of the source is the cell-centred central difference field.  All arrays
  * FP64 device arrays of nx*ny*nz cells; out_e / out_p may be base_e / base_p
  * but not eval_e, eval_p or phi.  No context is needed.  Errors: GMG_ERR_ARG
- * (null or aliased pointers, bad grid, non-finite constants), GMG_ERR_CUDA. */
+ * (null or aliased pointers, bad grid or a plane nx*ny of 2^31 cells or more,
+ * non-finite constants), GMG_ERR_CUDA. */
 gmg_status transport_stage(const gmg_params* p, const double* base_e, const double* base_p,
                            const double* eval_e, const double* eval_p, const double* phi,
                            const gmg_transport_coef* tc, double c, double* out_e, double* out_p, void* stream);
+
+/* Both transport stages of one second-order semi-implicit step, eqs. (e1)-(e2),
+ * in the field of one phi (phi^{n+1/2}):
+ *   predictor  half = n + (tau/2) R(n),   corrector  out = n + tau R(half),
+ * R the right-hand side of transport_stage.  The ionization rate
+ * alpha(|E|) mu_e |E| depends on phi only: the predictor writes it to rate[] and
+ * the corrector reads it there, so the result is bit-identical to the two
+ * transport_stage calls.  All arrays FP64 device arrays of nx*ny*nz cells;
+ * out_e / out_p may be n_e / n_p (in place); half_e, half_p and rate are
+ * scratch owned by the caller and alias nothing else.  Errors: GMG_ERR_ARG
+ * (null or aliased pointers, bad grid as in transport_stage, non-finite
+ * constants or tau), GMG_ERR_CUDA. */
+gmg_status transport_step(const gmg_params* p, const double* n_e, const double* n_p, const double* phi,
+                          const gmg_transport_coef* tc, double tau, double* half_e, double* half_p, double* out_e,
+                          double* out_p, double* rate, void* stream);
 
 /* Solve like fgmres_solve with another Krylov method (gmg_krylov).  Each
  * method stops when its own residual estimate falls below rtol ||b||, then

@@ -1537,42 +1537,82 @@ gmg_status assemble_coefficient_rhs(const gmg_params* p, const double* ne_dev, c
   return e == cudaSuccess ? GMG_OK : map_err(e);
 }
 
-gmg_status transport_stage(const gmg_params* p, const double* base_e, const double* base_p,
-                           const double* eval_e, const double* eval_p, const double* phi,
-                           const gmg_transport_coef* tc, double cstage, double* out_e, double* out_p, void* stream) {
-  if (!p || !base_e || !base_p || !eval_e || !eval_p || !phi || !tc || !out_e || !out_p) return GMG_ERR_ARG;
+namespace {
+
+// Validates the grid and constants of a transport call and fills the kernel's
+// coefficients (mobility magnitudes, alpha's constants times the pressure,
+// 1/h^2, 1/(2h), D/h^2).
+gmg_status transport_coef(const gmg_params* p, const gmg_transport_coef* tc, double cstage, Grid3* g,
+                          TransportCoef* t) {
   if (p->nx < 1 || p->ny < 1 || p->nz < 1 || !(p->lx > 0) || !(p->ly > 0) || !(p->lz > 0)) return GMG_ERR_ARG;
-  const void* ins[] = {eval_e, eval_p, phi};
-  for (const void* q : ins)
-    if (q == out_e || q == out_p) return GMG_ERR_ARG;
-  if (out_e == out_p || base_e == out_p || base_p == out_e) return GMG_ERR_ARG;
+  if ((size_t)p->nx * (size_t)p->ny >= (size_t)1 << 31) return GMG_ERR_ARG;  // one plane indexed in 32 bits
   const double k[] = {tc->mu_e, tc->mu_p, tc->diff_x, tc->diff_y, tc->diff_z, tc->ion_a, tc->ion_b, tc->pressure,
                       cstage, p->phi_bottom, p->phi_top};
   for (double v : k)
     if (!std::isfinite(v)) return GMG_ERR_ARG;
-  const Grid3 g = make_grid(p->nx, p->ny, p->nz, p->lx, p->ly, p->lz);
-  TransportCoef t;
+  *g = make_grid(p->nx, p->ny, p->nz, p->lx, p->ly, p->lz);
   const double hx = p->lx / p->nx, hy = p->ly / p->ny, hz = p->lz / p->nz;
-  t.mu_e = std::fabs(tc->mu_e);
-  t.mu_p = std::fabs(tc->mu_p);
-  t.diff_x = tc->diff_x;
-  t.diff_y = tc->diff_y;
-  t.diff_z = tc->diff_z;
-  t.ion_ap = tc->ion_a * tc->pressure;
-  t.ion_bp = tc->ion_b * tc->pressure;
-  t.g_bottom = p->phi_bottom;
-  t.g_top = p->phi_top;
-  t.ihx = 1.0 / hx;
-  t.ihy = 1.0 / hy;
-  t.ihz = 1.0 / hz;
-  t.ih2x = 0.5 / hx;
-  t.ih2y = 0.5 / hy;
-  t.ih2z = 0.5 / hz;
-  t.dih2x = tc->diff_x / (hx * hx);
-  t.dih2y = tc->diff_y / (hy * hy);
-  t.dih2z = tc->diff_z / (hz * hz);
-  const cudaError_t e = launch_transport(g, t, base_e, base_p, eval_e, eval_p, phi, cstage, out_e, out_p,
+  t->mu_e = std::fabs(tc->mu_e);
+  t->mu_p = std::fabs(tc->mu_p);
+  t->diff_x = tc->diff_x;
+  t->diff_y = tc->diff_y;
+  t->diff_z = tc->diff_z;
+  t->ion_ap = tc->ion_a * tc->pressure;
+  t->ion_bp = tc->ion_b * tc->pressure;
+  t->g_bottom = p->phi_bottom;
+  t->g_top = p->phi_top;
+  t->kx = 1.0 / (hx * hx);
+  t->ky = 1.0 / (hy * hy);
+  t->kz = 1.0 / (hz * hz);
+  t->ih2x = 0.5 / hx;
+  t->ih2y = 0.5 / hy;
+  t->ih2z = 0.5 / hz;
+  t->dih2x = tc->diff_x / (hx * hx);
+  t->dih2y = tc->diff_y / (hy * hy);
+  t->dih2z = tc->diff_z / (hz * hz);
+  return GMG_OK;
+}
+
+}  // namespace
+
+gmg_status transport_stage(const gmg_params* p, const double* base_e, const double* base_p,
+                           const double* eval_e, const double* eval_p, const double* phi,
+                           const gmg_transport_coef* tc, double cstage, double* out_e, double* out_p, void* stream) {
+  if (!p || !base_e || !base_p || !eval_e || !eval_p || !phi || !tc || !out_e || !out_p) return GMG_ERR_ARG;
+  const void* ins[] = {eval_e, eval_p, phi};
+  for (const void* q : ins)
+    if (q == out_e || q == out_p) return GMG_ERR_ARG;
+  if (out_e == out_p || base_e == out_p || base_p == out_e) return GMG_ERR_ARG;
+  Grid3 g;
+  TransportCoef t;
+  const gmg_status st = transport_coef(p, tc, cstage, &g, &t);
+  if (st != GMG_OK) return st;
+  const cudaError_t e = launch_transport(g, t, base_e, base_p, eval_e, eval_p, phi, cstage, out_e, out_p, nullptr, 0,
                                          static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GMG_OK : map_err(e);
+}
+
+gmg_status transport_step(const gmg_params* p, const double* n_e, const double* n_p, const double* phi,
+                          const gmg_transport_coef* tc, double tau, double* half_e, double* half_p, double* out_e,
+                          double* out_p, double* rate, void* stream) {
+  if (!p || !n_e || !n_p || !phi || !tc || !half_e || !half_p || !out_e || !out_p || !rate) return GMG_ERR_ARG;
+  // half_* and rate are written while n_*, phi (and half_* in the corrector) are read
+  const void* w[] = {half_e, half_p, rate};
+  const void* r[] = {n_e, n_p, phi, out_e, out_p};
+  for (int a = 0; a < 3; ++a) {
+    for (const void* q : r)
+      if (q == w[a]) return GMG_ERR_ARG;
+    for (int b = a + 1; b < 3; ++b)
+      if (w[a] == w[b]) return GMG_ERR_ARG;
+  }
+  if (out_e == out_p || out_e == phi || out_p == phi || out_e == n_p || out_p == n_e) return GMG_ERR_ARG;
+  Grid3 g;
+  TransportCoef t;
+  gmg_status st = transport_coef(p, tc, tau, &g, &t);
+  if (st != GMG_OK) return st;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_transport(g, t, n_e, n_p, n_e, n_p, phi, 0.5 * tau, half_e, half_p, rate, 1, s);
+  if (e == cudaSuccess) e = launch_transport(g, t, n_e, n_p, half_e, half_p, phi, tau, out_e, out_p, rate, 2, s);
   return e == cudaSuccess ? GMG_OK : map_err(e);
 }
 

@@ -210,13 +210,15 @@ struct TransportCoef {
   double diff_x, diff_y, diff_z;  // electron diffusion
   double ion_ap, ion_bp;          // alpha(|E|) = ion_ap exp(-ion_bp / |E|)
   double g_bottom, g_top;         // plate potentials (the field's ghosts)
-  double ihx, ihy, ihz;           // 1/h
+  double kx, ky, kz;              // 1/h^2: the drift divergence of the scaled face fluxes
   double ih2x, ih2y, ih2z;        // 1/(2h): the central-difference field
   double dih2x, dih2y, dih2z;     // D_alpha / h_alpha^2
 };
+// rate_mode 0: the ionization rate computed in place; 1: also stored to rate[];
+// 2: read from rate[] (written by a mode-1 stage with the same phi).
 cudaError_t launch_transport(const Grid3& g, const TransportCoef& tc, const double* base_e, const double* base_p,
                              const double* ev_e, const double* ev_p, const double* phi, double c, double* out_e,
-                             double* out_p, cudaStream_t s);
+                             double* out_p, double* rate, int rate_mode, cudaStream_t s);
 cudaError_t launch_adjoint_grad(const Grid3& g, const double* phi, const double* lam, double* out,
                                 double g_bot, double g_top, cudaStream_t s);
 

@@ -138,6 +138,8 @@ _SIGS = {
                                                 _P, _P, _P]),
     "transport_stage": (ctypes.c_int, [ctypes.POINTER(gmg_params), _P, _P, _P, _P, _P,
                                        ctypes.POINTER(gmg_transport_coef), ctypes.c_double, _P, _P, _P]),
+    "transport_step": (ctypes.c_int, [ctypes.POINTER(gmg_params), _P, _P, _P, ctypes.POINTER(gmg_transport_coef),
+                                      ctypes.c_double, _P, _P, _P, _P, _P, _P]),
     "gmg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "gmg_profile_reset": (ctypes.c_int, [_P]),
     "gmg_profile_min_bytes": (ctypes.c_int, [_P, ctypes.c_double]),
@@ -491,4 +493,20 @@ def transport_stage(params: gmg_params, base_e: torch.Tensor, base_p: torch.Tens
                                   _dev(eval_p, numel=n, name="eval_p"), _dev(phi, numel=n, name="phi"),
                                   ctypes.byref(tc), float(c), _dev(out_e, numel=n, name="out_e"),
                                   _dev(out_p, numel=n, name="out_p"), _stream_ptr(stream)), "transport_stage")
+
+
+def transport_step(params: gmg_params, n_e: torch.Tensor, n_p: torch.Tensor, phi: torch.Tensor, tau: float,
+                   half_e: torch.Tensor, half_p: torch.Tensor, out_e: torch.Tensor, out_p: torch.Tensor,
+                   rate: torch.Tensor, mu_e: float, mu_p: float, diffusion=(0.0, 0.0, 0.0), ion_a: float = 5.7,
+                   ion_b: float = 260.0, pressure: float = 760.0, stream=None):
+    """Predictor and corrector of eqs. (e1)-(e2) in the field of phi: half = n + (tau/2) R(n),
+    out = n + tau R(half); half_*, rate are scratch; FP64 device tensors; out may be n."""
+    n = params.nx * params.ny * params.nz
+    tc = gmg_transport_coef(float(mu_e), float(mu_p), float(diffusion[0]), float(diffusion[1]), float(diffusion[2]),
+                            float(ion_a), float(ion_b), float(pressure))
+    _check(load().transport_step(ctypes.byref(params), _dev(n_e, numel=n, name="n_e"), _dev(n_p, numel=n, name="n_p"),
+                                 _dev(phi, numel=n, name="phi"), ctypes.byref(tc), float(tau),
+                                 _dev(half_e, numel=n, name="half_e"), _dev(half_p, numel=n, name="half_p"),
+                                 _dev(out_e, numel=n, name="out_e"), _dev(out_p, numel=n, name="out_p"),
+                                 _dev(rate, numel=n, name="rate"), _stream_ptr(stream)), "transport_step")
 

@@ -6,8 +6,8 @@ coefficient and right-hand side from the densities at t_n
 solve for phi^{n+1/2} warm-started from the previous step's potential (the
 first step, with a zero guess, takes full multigrid when ``params.cycle`` is
 GMG_CYCLE_AUTO), then the predictor n^{n+1/2} = n^n + (tau/2) R(n^n) and the
-corrector n^{n+1} = n^n + tau R(n^{n+1/2}) (``transport_stage``), both in the
-field E^{n+1/2}.
+corrector n^{n+1} = n^n + tau R(n^{n+1/2}) (``transport_step``), both in the
+field E^{n+1/2}, which share the ionization rate alpha(|E|) mu_e |E|.
 """
 from __future__ import annotations
 
@@ -33,7 +33,7 @@ class SemiImplicitStepper:
         shape = (params.nz, params.ny, params.nx)
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         z = lambda: torch.zeros(shape, dtype=torch.float64, device=dev)   # noqa: E731
-        self.a, self.f, self.phi, self.half_e, self.half_p = z(), z(), z(), z(), z()
+        self.a, self.f, self.phi, self.half_e, self.half_p, self.rate = z(), z(), z(), z(), z(), z()
         self.ctx = None
         self.last_info = None
 
@@ -51,8 +51,7 @@ class SemiImplicitStepper:
         info = gmg.fgmres_solve(self.ctx, self.f, self.phi)
         ion_a, ion_b, pres = self.ion
         kw = dict(mu_e=mu_e, mu_p=mu_p, diffusion=self.diffusion, ion_a=ion_a, ion_b=ion_b, pressure=pres, stream=s)
-        gmg.transport_stage(p, n_e, n_p, n_e, n_p, self.phi, 0.5 * tau, self.half_e, self.half_p, **kw)
-        gmg.transport_stage(p, n_e, n_p, self.half_e, self.half_p, self.phi, tau, out_e, out_p, **kw)
+        gmg.transport_step(p, n_e, n_p, self.phi, tau, self.half_e, self.half_p, out_e, out_p, self.rate, **kw)
         self.last_info = info
         return info
 

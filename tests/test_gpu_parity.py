@@ -848,7 +848,7 @@ from paper_1812_08606_gb300.streamer import SemiImplicitStepper  # noqa: E402
 
 
 @pytest.mark.parametrize("shape,lengths", [(RAGGED, (1.0, 1.0, 1.0)), ((8, 24, 144), (2.0, 1.0, 0.5)),
-                                           ((4, 2, 34), (1.0, 1.0, 1.0))])
+                                           ((4, 2, 34), (1.0, 1.0, 1.0)), ((64, 75, 100), (1.0, 0.7, 0.6))])
 def test_transport_stage_matches_oracle(shape, lengths):
     nz, ny, nx = shape
     grid = O.Grid(nx, ny, nz, *lengths)
@@ -878,6 +878,57 @@ def test_transport_stage_rejects_aliasing():
         gmg.transport_stage(p, x[0], x[1], x[2], x[3], phi, 1.0, x[2], x[1], mu_e=1.0, mu_p=1.0)   # out = eval
     with pytest.raises(gmg.GMGError):
         gmg.transport_stage(p, x[0], x[1], x[2], x[3], phi, 1.0, x[0], x[0], mu_e=1.0, mu_p=1.0)   # out_e = out_p
+
+
+@pytest.mark.parametrize("shape,lengths", [(RAGGED, (1.0, 1.0, 1.0)), ((48, 20, 72), (1.0, 0.5, 1.5))])
+def test_transport_step_matches_two_stages_and_oracle(shape, lengths):
+    """Predictor + corrector with the shared ionization rate: bit-identical to
+    the two transport_stage calls, and to the oracle's stages within 1e-12."""
+    nz, ny, nx = shape
+    grid = O.Grid(nx, ny, nz, *lengths)
+    ne, npos = _densities(shape, 380)
+    phi = 3e4 * random_field(381, shape) + 1e4
+    p = _params(shape, lx=lengths[0], ly=lengths[1], lz=lengths[2], phi_bottom=-1e3, phi_top=4e4)
+    kw = dict(mu_e=MU_E, mu_p=MU_P, diffusion=DIFFUSION)
+    tau = 2e-12
+    args = (phi, -1e3, 4e4, MU_E, MU_P, DIFFUSION)
+    he_ref, hp_ref = O.transport_stage(grid, ne, npos, ne, npos, *args, 0.5 * tau)
+    ref_e, ref_p = O.transport_stage(grid, ne, npos, he_ref, hp_ref, *args, tau)
+    z = lambda: torch.empty(shape, dtype=torch.float64, device=DEV)   # noqa: E731
+    he, hp, oe, op, rate = z(), z(), z(), z(), z()
+    gmg.transport_step(p, _t(ne), _t(npos), _t(phi), tau, he, hp, oe, op, rate, **kw)
+    assert np.abs(_np(oe) - ref_e).max() <= 1e-12 * np.abs(ref_e).max()
+    assert np.abs(_np(op) - ref_p).max() <= 1e-12 * np.abs(ref_p).max()
+    assert np.abs(_np(he) - he_ref).max() <= 1e-12 * np.abs(he_ref).max()
+    # the same two stages through transport_stage (the rate computed in place)
+    se, sp, te, tp = z(), z(), z(), z()
+    gmg.transport_stage(p, _t(ne), _t(npos), _t(ne), _t(npos), _t(phi), 0.5 * tau, se, sp, **kw)
+    gmg.transport_stage(p, _t(ne), _t(npos), se, sp, _t(phi), tau, te, tp, **kw)
+    assert torch.equal(se, he) and torch.equal(sp, hp) and torch.equal(te, oe) and torch.equal(tp, op)
+    # the rate is alpha(|E|) mu_e |E| of the central-difference field
+    ex, ey, ez = O.field_from_potential(grid, phi, -1e3, 4e4)
+    eabs = np.sqrt(ex * ex + ey * ey + ez * ez)
+    np.testing.assert_allclose(_np(rate), O.ionization_coefficient(eabs) * MU_E * eabs, rtol=1e-12, atol=0)
+    # in place on n
+    be, bp = _t(ne), _t(npos)
+    gmg.transport_step(p, be, bp, _t(phi), tau, he, hp, be, bp, rate, **kw)
+    assert torch.equal(be, oe) and torch.equal(bp, op)
+
+
+def test_transport_step_rejects_aliasing():
+    shape = (8, 8, 8)
+    p = _params(shape)
+    x = [torch.ones(shape, dtype=torch.float64, device=DEV) for _ in range(7)]
+    ne, np_, phi, he, hp, rate, oe = x
+    kw = dict(mu_e=1.0, mu_p=1.0)
+    for args in [(ne, np_, phi, 1.0, ne, hp, oe, oe.clone(), rate),      # half = n
+                 (ne, np_, phi, 1.0, he, hp, oe, oe.clone(), oe),        # rate = out
+                 (ne, np_, phi, 1.0, he, he, oe, oe.clone(), rate),      # half_e = half_p
+                 (ne, np_, phi, 1.0, he, hp, phi, oe, rate),              # out = phi
+                 (ne, np_, phi, 1.0, he, hp, np_, ne, rate),              # out swapped with n
+                 (ne, np_, phi, float("nan"), he, hp, oe, oe.clone(), rate)]:
+        with pytest.raises(gmg.GMGError):
+            gmg.transport_step(p, *args, **kw)
 
 
 def test_semi_implicit_step_fp64_matches_oracle():
