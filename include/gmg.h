@@ -224,6 +224,14 @@ gmg_status transport_stage(const gmg_params* p, const double* base_e, const doub
                            const double* eval_e, const double* eval_p, const double* phi,
                            const gmg_transport_coef* tc, double c, double* out_e, double* out_p, void* stream);
 
+/* dst[i] = src[i] rounded to FP32 (round to nearest, ties to even; overflow to
+ * infinity; NaN stays NaN): the rounding the mixed-precision preconditioner
+ * applies to its FP64 input v_j before the FP32 V-cycle (Sec. 3.1), done on the
+ * integer pipe.  src: n FP64 device values, dst: n FP32 device values (no
+ * overlap), both owned by the caller; enqueued on stream.  Errors: GMG_ERR_ARG
+ * (null or identical pointers with n > 0), GMG_ERR_CUDA. */
+gmg_status gmg_round_to_f32(const double* src, float* dst, size_t n, void* stream);
+
 /* Both transport stages of one second-order semi-implicit step, eqs. (e1)-(e2),
  * in the field of one phi (phi^{n+1/2}):
  *   predictor  half = n + (tau/2) R(n),   corrector  out = n + tau R(half),

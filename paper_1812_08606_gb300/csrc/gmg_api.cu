@@ -180,7 +180,8 @@ enum KernelClass : int {
   K_CHEB_F64, K_CHEB_F32, K_RESTRICT_F64, K_RESTRICT_F32, K_PROLONG_F64, K_PROLONG_F32, K_COARSE_F64,
   K_COARSE_F32, K_DOT, K_FINALIZE, K_AXPY, K_SCALE, K_UPDATE_X, K_CAST, K_COPY, K_RHS, K_FIELD, K_ADJOINT,
   K_COARSEN, K_COEF_CHECK, K_HASH, K_COARSE_ASSEMBLE, K_COARSE_FACTOR, K_DOT_F32, K_AXPY_F32, K_APPLY_DF64,
-  K_SPLIT, K_CHEB_FUSED, K_CGS_DOTS, K_CGS_DOTS_F32, K_CGS_UPDATE, K_CGS_UPDATE_F32, K_LIN3, K_MGS, K_MGS_F32, NK
+  K_SPLIT, K_CHEB_FUSED, K_CGS_DOTS, K_CGS_DOTS_F32, K_CGS_UPDATE, K_CGS_UPDATE_F32, K_LIN3, K_MGS, K_MGS_F32,
+  K_SCALE_ROUND, NK
 };
 static const char* const kKernelNames[NK] = {
     "apply_f64", "apply_outer_f64a_f32x", "apply_f32", "residual_f64", "residual_f32", "sgs_half_f64",
@@ -189,7 +190,7 @@ static const char* const kKernelNames[NK] = {
     "multi_axpy", "scale", "update_solution", "cast", "copy", "rhs", "field", "adjoint_grad", "coarsen_coef",
     "coef_check", "hash_vector", "coarse_assemble", "coarse_factor", "multi_dot_f32", "multi_axpy_f32",
     "apply_outer_df64", "split_coef", "cheb_sgs_fused_f32", "cgs_dots", "cgs_dots_f32", "cgs_update",
-    "cgs_update_f32", "vector_lin3", "mgs_pass", "mgs_pass_f32"};
+    "cgs_update_f32", "vector_lin3", "mgs_pass", "mgs_pass_f32", "scale_round"};
 
 struct ProfPending {
   int cls;
@@ -235,6 +236,9 @@ struct gmg_ctx {
   int st_fp32 = -1;  // element type of the field staging buffers (-1: none yet)
   bool fmg_now = false;  // the preconditioner of the current solve is full multigrid
   long long precond_calls = 0;  // preconditioner applications (reported per solve)
+  // mixed precision: the finest level's FP32 right-hand side already holds the
+  // rounding of this FP64 vector (written with it by prof_scale_round)
+  const double* b32_of = nullptr;
   // copy stream of gmg_solve_host: input copies overlap the set-up, the
   // potential's copy-out overlaps the field kernel
   cudaStream_t cs = nullptr;
@@ -411,6 +415,10 @@ gmg_status prof_scale(gmg_ctx* c, size_t n, const T* src, T* dst, const double* 
 }
 gmg_status prof_scale_value(gmg_ctx* c, size_t n, const double* src, double* dst, double alpha, cudaStream_t s) {
   GMG_RUN(K_SCALE, 16.0 * n, launch_scale_value(n, src, dst, alpha, s));
+}
+gmg_status prof_scale_round(gmg_ctx* c, size_t n, const double* src, double* dst, float* dst32, const double* sc,
+                            double alpha, cudaStream_t s) {
+  GMG_RUN(K_SCALE_ROUND, 20.0 * n, launch_scale_round(n, src, dst, dst32, sc, alpha, s));
 }
 template <typename TZ>
 gmg_status prof_update_solution(gmg_ctx* c, size_t n, double* x, const TZ* Z, size_t ldz, int k, const double* y,
@@ -844,7 +852,8 @@ gmg_status precondition(gmg_ctx* c, const double* v, void* z) {
   ++c->precond_calls;
   if (c->mixed) {
     float* bf = (float*)c->lev[top].b;
-    CKS(prof_cast_d2f(c, c->N(), v, bf, c->s));
+    if (c->b32_of != v) CKS(prof_cast_d2f(c, c->N(), v, bf, c->s));
+    c->b32_of = nullptr;  // the cycle may overwrite it
     if (c->fmg_now && top > 0) return fmg<float>(c, top, bf, (float*)z);
     return vcycle<float>(c, top, bf, (float*)z);
   }
@@ -868,6 +877,7 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
                       bool flexible = true) {
   const double t0 = now_ms();
   c->precond_calls = 0;
+  c->b32_of = nullptr;
   const LevelData& F = c->fine();
   const size_t n = F.n;
   const int m = c->p.restart;
@@ -923,7 +933,13 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
         result = GMG_ERR_NOT_CONVERGED;
         break;
       }
-      CKS(prof_scale_value(c, n, r0_is_b ? c->bvec : c->V, c->V, 1.0 / beta, c->s));
+      if (c->mixed) {  // v_1 and its FP32 rounding (the first preconditioner input) in one pass
+        CKS(prof_scale_round(c, n, r0_is_b ? c->bvec : c->V, c->V, (float*)c->lev.back().b, nullptr, 1.0 / beta,
+                             c->s));
+        c->b32_of = c->V;
+      } else {
+        CKS(prof_scale_value(c, n, r0_is_b ? c->bvec : c->V, c->V, 1.0 / beta, c->s));
+      }
       r0_is_b = false;  // later cycles restart from x_k != 0
       std::fill(g.begin(), g.end(), 0.0);
       g[0] = beta;
@@ -967,7 +983,13 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
         if (loc.n_history < GMG_MAX_HISTORY) loc.res_history[loc.n_history++] = est;
         if (hnext == 0.0) break;  // lucky breakdown: the solution is in K_j
         if (est < c->p.rtol || loc.iterations >= c->p.max_iters) break;  // stopping test
-        CKS(prof_scale(c, n, c->w, c->V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));  // v_{j+1}
+        double* vnext = c->V + (size_t)(j + 1) * n;
+        if (c->mixed) {  // v_{j+1} = w / h_{j+1,j} and its FP32 rounding for the next V-cycle
+          CKS(prof_scale_round(c, n, c->w, vnext, (float*)c->lev.back().b, c->dscal + SL_NORM + 1, 0.0, c->s));
+          c->b32_of = vnext;
+        } else {
+          CKS(prof_scale(c, n, c->w, vnext, c->dscal + SL_NORM + 1, c->s));
+        }
       }
       if (fail) break;
       // y_k from the triangular system, x_k = x_0 + Z_k y_k
@@ -1187,6 +1209,7 @@ gmg_status short_cycle(gmg_ctx* c, int method, double* x, double bnorm, gmg_solv
 gmg_status solve_short(gmg_ctx* c, int method, const double* f, double* x, int homogeneous, gmg_solve_info* info) {
   const double t0 = now_ms();
   c->precond_calls = 0;
+  c->b32_of = nullptr;
   const LevelData& F = c->fine();
   const size_t n = F.n;
   gmg_solve_info loc;
@@ -1613,6 +1636,13 @@ gmg_status transport_step(const gmg_params* p, const double* n_e, const double* 
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = launch_transport(g, t, n_e, n_p, n_e, n_p, phi, 0.5 * tau, half_e, half_p, rate, 1, s);
   if (e == cudaSuccess) e = launch_transport(g, t, n_e, n_p, half_e, half_p, phi, tau, out_e, out_p, rate, 2, s);
+  return e == cudaSuccess ? GMG_OK : map_err(e);
+}
+
+gmg_status gmg_round_to_f32(const double* src, float* dst, size_t n, void* stream) {
+  if (n == 0) return GMG_OK;
+  if (!src || !dst || (const void*)src == (const void*)dst) return GMG_ERR_ARG;
+  const cudaError_t e = launch_cast_d2f(n, src, dst, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GMG_OK : map_err(e);
 }
 

@@ -78,6 +78,38 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   const unsigned lo = zero ? 0u : (mf << 29);
   return __hiloint2double((int)hi, (int)lo);
 }
+
+// FP64 -> FP32 with round to nearest, ties to even, from the IEEE-754 bit
+// fields on the integer pipe only; bit-identical to the conversion instruction
+// (which GB300 runs on the FP64 pipe).  The 53-bit significand M (implicit bit
+// included) is shifted right to the FP32 grid: by 29 bits for a normal FP32
+// result (exponent rebiased from 1023 to 127), by more for a subnormal one
+// (units of 2^-149); the dropped bits decide the rounding, and a carry out of
+// the mantissa moves into the exponent (the largest finite FP32 rounds up to
+// infinity that way).  Infinity and NaN keep their class (a NaN comes out
+// quiet, the top 22 payload bits kept); FP64 subnormals round to a signed zero.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const int ef = e - 896;  // FP32 biased exponent of a normal result
+  if (ef >= 1 && ef <= 254) {
+    // the common case in 32-bit words: kept = top 23 of the 52 mantissa bits,
+    // rest = the 29 dropped ones; round up when rest + (kept odd) > half
+    const unsigned kept = ((hi & 0xfffffu) << 3) | (lo >> 29), rest = lo & 0x1fffffffu;
+    const unsigned up = rest + (kept & 1u) > 0x10000000u ? 1u : 0u;
+    return __uint_as_float(sign | (((unsigned)ef << 23) + kept + up));
+  }
+  const unsigned long long m = ((unsigned long long)(hi & 0xfffffu) << 32) | lo;
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x400000u | (unsigned)(m >> 29) : 0u));
+  if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);  // beyond FP32: infinity
+  const int sh = 926 - e;                                    // subnormal result: 30 or more
+  if (e == 0 || sh > 54) return __uint_as_float(sign);       // below half the smallest subnormal
+  const unsigned long long sig = m | (1ULL << 52);
+  const unsigned long long kept = sig >> sh, rest = sig & ((1ULL << sh) - 1ULL), half = 1ULL << (sh - 1);
+  const unsigned up = (rest > half || (rest == half && (kept & 1ULL))) ? 1u : 0u;
+  return __uint_as_float(sign | ((unsigned)kept + up));
+}
 __device__ __forceinline__ double to_f64(float f) { return f32_to_f64(f); }
 __device__ __forceinline__ double to_f64(double d) { return d; }
 
@@ -256,6 +288,10 @@ template <typename T>
 cudaError_t launch_scale(size_t n, const T* src, T* dst, const double* scale, cudaStream_t s);
 // dst = src * alpha (alpha by value).
 cudaError_t launch_scale_value(size_t n, const double* src, double* dst, double alpha, cudaStream_t s);
+// dst = src * s, dst32 = FP32 rounding of dst; s = *scale (device) or alpha when
+// scale is null; dst may be src.
+cudaError_t launch_scale_round(size_t n, const double* src, double* dst, float* dst32, const double* scale,
+                               double alpha, cudaStream_t s);
 // x += sum_i y[i] z_i, Z row stride ldz, k <= 64, y on the device.
 template <typename TZ>
 cudaError_t launch_update_solution(size_t n, double* x, const TZ* Z, size_t ldz, int k,

@@ -187,6 +187,19 @@ __global__ void k_scale_value(size_t n, const double* __restrict__ src, double* 
     dst[p] = src[p] * s;
 }
 
+// dst = src * s (s = *scale, or alpha when scale is null) and dst32 = dst rounded
+// to FP32: the new Arnoldi vector and the mixed-precision preconditioner's
+// input in one pass (dst may be src).
+__global__ void k_scale_round(size_t n, const double* src, double* dst, float* __restrict__ dst32,
+                              const double* __restrict__ scale, double alpha) {
+  const double s = scale ? scale[0] : alpha;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+    const double v = src[p] * s;
+    dst[p] = v;
+    dst32[p] = f64_to_f32(v);
+  }
+}
+
 template <typename TZ>
 __global__ void __launch_bounds__(RT) k_update_solution(size_t n, double* __restrict__ x,
                                                         const TZ* __restrict__ Z, size_t ldz, int k,
@@ -407,6 +420,12 @@ GMG_INST(double)
 
 cudaError_t launch_scale_value(size_t n, const double* src, double* dst, double alpha, cudaStream_t s) {
   k_scale_value<<<flat_blocks(n), 256, 0, s>>>(n, src, dst, alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_round(size_t n, const double* src, double* dst, float* dst32, const double* scale,
+                               double alpha, cudaStream_t s) {
+  k_scale_round<<<flat_blocks(n), 256, 0, s>>>(n, src, dst, dst32, scale, alpha);
   return cudaGetLastError();
 }
 

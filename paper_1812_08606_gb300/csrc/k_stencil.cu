@@ -198,9 +198,12 @@ __global__ void k_coarsen_coef(Grid3 g, const double* __restrict__ a, double* __
   }
 }
 
+// FP64 -> FP32 (round to nearest even) on the integer pipe: the copy is then
+// bound by HBM alone, not by GB300's FP64 pipe, which runs the conversion
+// instruction.
 __global__ void k_cast_d2f(size_t n, const double* __restrict__ s, float* __restrict__ d) {
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
-    d[p] = (float)s[p];
+    d[p] = f64_to_f32(s[p]);
 }
 __global__ void k_cast_f2d(size_t n, const float* __restrict__ s, double* __restrict__ d) {
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)

@@ -138,6 +138,7 @@ _SIGS = {
                                                 _P, _P, _P]),
     "transport_stage": (ctypes.c_int, [ctypes.POINTER(gmg_params), _P, _P, _P, _P, _P,
                                        ctypes.POINTER(gmg_transport_coef), ctypes.c_double, _P, _P, _P]),
+    "gmg_round_to_f32": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
     "transport_step": (ctypes.c_int, [ctypes.POINTER(gmg_params), _P, _P, _P, ctypes.POINTER(gmg_transport_coef),
                                       ctypes.c_double, _P, _P, _P, _P, _P, _P]),
     "gmg_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -493,6 +494,15 @@ def transport_stage(params: gmg_params, base_e: torch.Tensor, base_p: torch.Tens
                                   _dev(eval_p, numel=n, name="eval_p"), _dev(phi, numel=n, name="phi"),
                                   ctypes.byref(tc), float(c), _dev(out_e, numel=n, name="out_e"),
                                   _dev(out_p, numel=n, name="out_p"), _stream_ptr(stream)), "transport_stage")
+
+
+def gmg_round_to_f32(src: torch.Tensor, dst: torch.Tensor, stream=None):
+    """dst = src rounded to FP32 (nearest even); FP64 / FP32 device tensors of one size."""
+    n = src.numel()
+    if dst.numel() != n:
+        raise ValueError("gmg_round_to_f32: src and dst sizes differ")
+    _check(load().gmg_round_to_f32(_dev(src, numel=n, name="src"), _dev(dst, numel=n, name="dst", dtype=torch.float32),
+                                   ctypes.c_size_t(n), _stream_ptr(stream)), "gmg_round_to_f32")
 
 
 def transport_step(params: gmg_params, n_e: torch.Tensor, n_p: torch.Tensor, phi: torch.Tensor, tau: float,

@@ -931,6 +931,40 @@ def test_transport_step_rejects_aliasing():
             gmg.transport_step(p, *args, **kw)
 
 
+def test_round_to_f32_matches_the_conversion_instruction():
+    """The integer-pipe FP64 -> FP32 rounding equals the hardware conversion
+    bit for bit: random bit patterns over the whole FP64 range, values near
+    the FP32 limits and subnormals, exact ties (both parities), overflow,
+    zeros, infinities; NaN stays NaN."""
+    rng = np.random.default_rng(390)
+    bits = rng.integers(0, 2 ** 63, size=1 << 20, dtype=np.int64).astype(np.uint64)
+    bits[::2] |= np.uint64(1) << np.uint64(63)
+    rnd = bits.view(np.float64)
+    # values around the FP32 grid: FP32 values plus offsets of about half an FP32 ulp
+    f = rng.standard_normal(1 << 18).astype(np.float32)
+    g = f.astype(np.float64)
+    ulp = np.spacing(np.abs(f)).astype(np.float64)
+    ties = np.concatenate([g + 0.5 * ulp, g - 0.5 * ulp, g + 0.5 * ulp * (1 + 2.0 ** -30), g + 0.5 * ulp * (1 - 2.0 ** -30)])
+    fmax, tiny = float(np.finfo(np.float32).max), float(np.finfo(np.float32).smallest_subnormal)
+    edge = np.array([0.0, -0.0, np.inf, -np.inf, fmax, -fmax, fmax * (1 + 2.0 ** -25), fmax * (1 + 2.0 ** -24),
+                     fmax * 2, 1e300, -1e300, tiny, tiny / 2, tiny * 0.5000001, tiny * 1.5, tiny * 2.5, tiny / 3,
+                     float(np.finfo(np.float32).tiny), float(np.finfo(np.float32).tiny) * (1 - 2.0 ** -25),
+                     5e-324, -5e-324, 1e-310, 2.0 ** -149, 2.0 ** -150, 2.0 ** -150 * (1 + 2.0 ** -40),
+                     2.0 ** -126 - 2.0 ** -150, 1.0, -1.0, 1 + 2.0 ** -24, 1 + 3 * 2.0 ** -24, 3.0 ** 40])
+    sub = rng.uniform(-1, 1, 1 << 16) * 2.0 ** rng.uniform(-160, -120, 1 << 16)
+    x = np.concatenate([rnd, ties, edge, sub])
+    src = torch.from_numpy(x).to(DEV)
+    dst = torch.empty(x.size, dtype=torch.float32, device=DEV)
+    gmg.gmg_round_to_f32(src, dst)
+    ref = src.float()   # the hardware conversion, round to nearest even
+    torch.cuda.synchronize()
+    nan = torch.isnan(src)
+    assert torch.isnan(dst[nan]).all()
+    got, want = dst[~nan].view(torch.int32), ref[~nan].view(torch.int32)
+    bad = (got != want).nonzero()
+    assert bad.numel() == 0, (x[~nan.cpu().numpy()][bad[:5].cpu().numpy().ravel()], got[bad[:5]].cpu(), want[bad[:5]].cpu())
+
+
 def test_semi_implicit_step_fp64_matches_oracle():
     shape = (16, 16, 16)
     ne, npos = streamer_densities(shape, 0)
