@@ -71,6 +71,9 @@ def parse_args():
     ap.add_argument("--no-regimes", action="store_true",
                     help="skip the first-step (FMG) and warm-started time-step measurements")
     ap.add_argument("--regime-steps", type=int, default=3)
+    ap.add_argument("--streamer-only", metavar="NZxNYxNX", default=None,
+                    help="run only the semi-implicit streamer steps on this mesh (e.g. 320x256x256) and print "
+                         "their line; for profiling the transport kernel")
     return ap.parse_args()
 
 
@@ -235,6 +238,14 @@ def run_ours(args, dist):
     gmg.load()
     torch.cuda.set_device(dist.local)
     dev = torch.device("cuda", dist.local)
+    if args.streamer_only:
+        shape = tuple(int(v) for v in args.streamer_only.lower().split("x"))
+        if len(shape) != 3 or min(shape) < 1:
+            raise SystemExit("--streamer-only wants NZxNYxNX")
+        r = streamer_arm(args, gmg, shape, torch.cuda.current_stream())
+        return {"metric": "Mcells/s per semi-implicit streamer step (eqs. (e1)-(e2))", "value": r["value"],
+                "unit": "Mcells/s", "n_gpus": dist.world, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "data": "synthetic (eq. (51) streamer densities)", "streamer": r}
     inp, n = make_workload(args)
     N = n**3
     a = torch.from_numpy(inp["a"]).to(dev)
