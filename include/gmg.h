@@ -319,6 +319,23 @@ gmg_status gmg_solve_host(gmg_ctx* ctx, const double* a_host, const double* f_ho
                           double* phi_host, void* ex_host, void* ey_host, void* ez_host, int field_fp32,
                           gmg_solve_info* info);
 
+/* gmg_solve_host, pipelined: returns once the solve has finished (info filled)
+ * with the copy-out of phi (and E) still in flight on the context's copy-out
+ * stream.  phi_host and ex/ey/ez_host must stay valid and unread until
+ * gmg_host_wait(ctx) returns; a_host, f_host and phi0_host have been consumed
+ * only when the next call, or gmg_host_wait, returns.  A following call may be
+ * made at once: its uploads and set-up overlap this copy-out (the link carries
+ * both directions at once), and its own staging writes wait for it.  Errors
+ * return like gmg_solve_host, with every copy completed. */
+gmg_status gmg_solve_host_async(gmg_ctx* ctx, const double* a_host, const double* f_host, const double* phi0_host,
+                                double* phi_host, void* ex_host, void* ey_host, void* ez_host, int field_fp32,
+                                gmg_solve_info* info);
+
+/* Waits for every copy and kernel of the context's host-array solves (the
+ * copy-out of gmg_solve_host_async included).  Errors: GMG_ERR_ARG (null ctx),
+ * GMG_ERR_CUDA (a failed copy or kernel). */
+gmg_status gmg_host_wait(gmg_ctx* ctx);
+
 gmg_status gmg_set_stream(gmg_ctx* ctx, void* stream);
 void gmg_destroy(gmg_ctx* ctx);
 const char* gmg_status_string(gmg_status s);

@@ -229,8 +229,10 @@ struct gmg_ctx {
   double* bvec = nullptr;
   double* partial = nullptr;
   double* dscal = nullptr;
-  double* hpin = nullptr;
+  double* hpin = nullptr;      // mapped pinned host scalars ...
+  double* hpin_dev = nullptr;  // ... and their device address
   int* hstat = nullptr;
+  int* hstat_dev = nullptr;
   double *st_a = nullptr, *st_f = nullptr, *st_phi = nullptr;
   void *st_ex = nullptr, *st_ey = nullptr, *st_ez = nullptr;
   int st_fp32 = -1;  // element type of the field staging buffers (-1: none yet)
@@ -241,8 +243,8 @@ struct gmg_ctx {
   const double* b32_of = nullptr;
   // copy stream of gmg_solve_host: input copies overlap the set-up, the
   // potential's copy-out overlaps the field kernel
-  cudaStream_t cs = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_a = nullptr, ev_out = nullptr;
+  cudaStream_t cs = nullptr, cso = nullptr;  // input and copy-out streams
+  cudaEvent_t ev_in = nullptr, ev_a = nullptr, ev_out = nullptr, ev_done = nullptr;
   float setup_ms = 0.f;
   // per-kernel profile
   bool prof_on = false;
@@ -526,7 +528,7 @@ gmg_status validate(const gmg_params* p, int* nlevels) {
 
 // Read `count` device scalars from slot `slot` into ctx->hpin[slot...]; synchronises.
 gmg_status read_scalars(gmg_ctx* c, int slot, int count) {
-  CK(cudaMemcpyAsync(c->hpin + slot, c->dscal + slot, sizeof(double) * count, cudaMemcpyDeviceToHost, c->s));
+  CK(launch_words_to_host(c->dscal + slot, c->hpin_dev + slot, sizeof(double) * count, c->s));
   CK(cudaStreamSynchronize(c->s));
   prof_collect(c);
   return GMG_OK;
@@ -704,7 +706,7 @@ gmg_status build(gmg_ctx* c, const double* a_dev) {
   const LevelData& C0 = c->lev[0];
   CKS(prof_coarse_assemble(c, C0.g, C0.a64, c->cA, c->s));
   CKS(prof_coarse_factor(c, c->nc, c->cA, c->cW, c->cinv64, c->cinv32, c->cstatus, c->s));
-  CK(cudaMemcpyAsync(c->hstat, c->cstatus, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+  CK(launch_words_to_host(c->cstatus, c->hstat_dev, sizeof(int), c->s));
   CK(cudaStreamSynchronize(c->s));
   if (c->hstat[0] != 0) return GMG_ERR_BREAKDOWN;
   c->setup_ms = (float)(now_ms() - t0);
@@ -1329,11 +1331,12 @@ void gmg_destroy(gmg_ctx* c) {
   if (c->s) cudaStreamSynchronize(c->s);
   prof_collect(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-  if (c->cs) {
-    cudaStreamSynchronize(c->cs);
-    cudaStreamDestroy(c->cs);
-  }
-  for (cudaEvent_t e : {c->ev_in, c->ev_a, c->ev_out})
+  for (cudaStream_t q : {c->cs, c->cso})
+    if (q) {
+      cudaStreamSynchronize(q);
+      cudaStreamDestroy(q);
+    }
+  for (cudaEvent_t e : {c->ev_in, c->ev_a, c->ev_out, c->ev_done})
     if (e) cudaEventDestroy(e);
   for (void* p : c->dev_allocs) cudaFree(p);
   for (void* p : c->host_allocs) cudaFreeHost(p);
@@ -1408,13 +1411,18 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
   if ((st = dalloc(c, &c->cinv32, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->cstatus, 4)) != GMG_OK) return fail(st);
   {
-    void* h = nullptr;
-    if (cudaMallocHost(&h, sizeof(double) * N_SCAL) != cudaSuccess) return fail(GMG_ERR_ALLOC);
+    // mapped, so that kernels write the scalars the host reads (read_scalars)
+    void *h = nullptr, *hd = nullptr;
+    if (cudaHostAlloc(&h, sizeof(double) * N_SCAL, cudaHostAllocMapped) != cudaSuccess) return fail(GMG_ERR_ALLOC);
     c->host_allocs.push_back(h);
+    if (cudaHostGetDevicePointer(&hd, h, 0) != cudaSuccess) return fail(GMG_ERR_CUDA);
     c->hpin = (double*)h;
-    if (cudaMallocHost(&h, sizeof(int) * 4) != cudaSuccess) return fail(GMG_ERR_ALLOC);
+    c->hpin_dev = (double*)hd;
+    if (cudaHostAlloc(&h, sizeof(int) * 4, cudaHostAllocMapped) != cudaSuccess) return fail(GMG_ERR_ALLOC);
     c->host_allocs.push_back(h);
+    if (cudaHostGetDevicePointer(&hd, h, 0) != cudaSuccess) return fail(GMG_ERR_CUDA);
     c->hstat = (int*)h;
+    c->hstat_dev = (int*)hd;
   }
   if ((st = build(c, a_dev)) != GMG_OK) return fail(st);
   *out = c;
@@ -1459,9 +1467,16 @@ gmg_status adjoint_coefficient_grad(gmg_ctx* c, const double* phi_dev, const dou
   return (prof_adjoint_grad(c, F.g, phi_dev, lambda_dev, dlda_dev, c->p.phi_bottom, c->p.phi_top, c->s));
 }
 
-gmg_status gmg_solve_host(gmg_ctx* c, const double* a_host, const double* f_host, const double* phi0_host,
-                          double* phi_host, void* ex_host, void* ey_host, void* ez_host, int field_fp32,
-                          gmg_solve_info* info) {
+namespace {
+
+// The host-array solve.  wait = true: returns with every copy done.  wait =
+// false (pipelined): returns once the solve has finished and the copy-out of
+// phi and E is enqueued on the copy-out stream; gmg_host_wait completes it, and
+// the next call's uploads and set-up overlap it (the staging arrays of phi and E
+// are rewritten only after it, through the event ev_done).
+gmg_status solve_host_impl(gmg_ctx* c, const double* a_host, const double* f_host, const double* phi0_host,
+                           double* phi_host, void* ex_host, void* ey_host, void* ez_host, int field_fp32,
+                           gmg_solve_info* info, bool wait) {
   if (!c || !f_host || !phi_host) return GMG_ERR_ARG;
   const bool want_e = ex_host && ey_host && ez_host;
   if ((ex_host || ey_host || ez_host) && !want_e) return GMG_ERR_ARG;
@@ -1481,16 +1496,21 @@ gmg_status gmg_solve_host(gmg_ctx* c, const double* a_host, const double* f_host
   }
   if (!c->cs) {
     CK(cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->cso, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming));
+    CK(cudaEventRecord(c->ev_done, c->cso));
   }
-  // Every return waits for both streams, so no copy touches the host arrays
-  // after the call.
+  // The synchronous form and every error wait for all three streams, so no copy
+  // touches the host arrays after the call.
   auto finish = [&](gmg_status st) {
+    if (!wait && (st == GMG_OK || st == GMG_ERR_NOT_CONVERGED)) return st;
     const cudaError_t e1 = cudaStreamSynchronize(c->cs);
-    const cudaError_t e2 = cudaStreamSynchronize(c->s);
-    if (st == GMG_OK && (e1 != cudaSuccess || e2 != cudaSuccess)) return GMG_ERR_CUDA;
+    const cudaError_t e2 = cudaStreamSynchronize(c->cso);
+    const cudaError_t e3 = cudaStreamSynchronize(c->s);
+    if (st == GMG_OK && (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)) return GMG_ERR_CUDA;
     return st;
   };
 #define CKF(...)                                       \
@@ -1498,15 +1518,19 @@ gmg_status gmg_solve_host(gmg_ctx* c, const double* a_host, const double* f_host
     const cudaError_t e_ = (__VA_ARGS__);              \
     if (e_ != cudaSuccess) return finish(map_err(e_)); \
   } while (0)
-  // a on the compute stream (the set-up needs it); f and phi0 on the copy
-  // stream, after a, so they arrive while the set-up runs
-  CKF(cudaEventRecord(c->ev_a, c->s));  // orders the copies after earlier work on the compute stream
-  if (a_host) {
-    CKF(cudaMemcpyAsync(c->st_a, a_host, bytes, cudaMemcpyHostToDevice, c->s));
-    CKF(cudaEventRecord(c->ev_a, c->s));
-  }
+  // Inputs on the input copy stream, after earlier work on the compute stream
+  // that may still read them (ev_a): a first (the set-up needs it), then f and
+  // phi0, which arrive while the set-up runs.  phi's staging array is rewritten
+  // only after the previous call's copy-out of it (ev_done).
+  CKF(cudaEventRecord(c->ev_a, c->s));
   CKF(cudaStreamWaitEvent(c->cs, c->ev_a, 0));
+  if (a_host) {
+    CKF(cudaMemcpyAsync(c->st_a, a_host, bytes, cudaMemcpyHostToDevice, c->cs));
+    CKF(cudaEventRecord(c->ev_a, c->cs));
+    CKF(cudaStreamWaitEvent(c->s, c->ev_a, 0));
+  }
   CKF(cudaMemcpyAsync(c->st_f, f_host, bytes, cudaMemcpyHostToDevice, c->cs));
+  CKF(cudaStreamWaitEvent(c->cs, c->ev_done, 0));
   if (phi0_host)
     CKF(cudaMemcpyAsync(c->st_phi, phi0_host, bytes, cudaMemcpyHostToDevice, c->cs));
   else
@@ -1519,21 +1543,50 @@ gmg_status gmg_solve_host(gmg_ctx* c, const double* a_host, const double* f_host
   CKF(cudaStreamWaitEvent(c->s, c->ev_in, 0));
   gmg_status st = solve_impl(c, c->st_f, c->st_phi, 0, info);
   if (st != GMG_OK && st != GMG_ERR_NOT_CONVERGED) return finish(st);
-  // phi leaves on the copy stream while the field kernel runs
+  // phi leaves on the copy-out stream while the field kernel runs
   CKF(cudaEventRecord(c->ev_out, c->s));
-  CKF(cudaStreamWaitEvent(c->cs, c->ev_out, 0));
-  CKF(cudaMemcpyAsync(phi_host, c->st_phi, bytes, cudaMemcpyDeviceToHost, c->cs));
+  CKF(cudaStreamWaitEvent(c->cso, c->ev_out, 0));
+  CKF(cudaMemcpyAsync(phi_host, c->st_phi, bytes, cudaMemcpyDeviceToHost, c->cso));
   if (want_e) {
     const gmg_status fs = field_from_potential(c, c->st_phi, c->st_ex, c->st_ey, c->st_ez, field_fp32);
     if (fs != GMG_OK) return finish(fs);
     CKF(cudaEventRecord(c->ev_out, c->s));
-    CKF(cudaStreamWaitEvent(c->cs, c->ev_out, 0));
-    CKF(cudaMemcpyAsync(ex_host, c->st_ex, n * esz, cudaMemcpyDeviceToHost, c->cs));
-    CKF(cudaMemcpyAsync(ey_host, c->st_ey, n * esz, cudaMemcpyDeviceToHost, c->cs));
-    CKF(cudaMemcpyAsync(ez_host, c->st_ez, n * esz, cudaMemcpyDeviceToHost, c->cs));
+    CKF(cudaStreamWaitEvent(c->cso, c->ev_out, 0));
+    CKF(cudaMemcpyAsync(ex_host, c->st_ex, n * esz, cudaMemcpyDeviceToHost, c->cso));
+    CKF(cudaMemcpyAsync(ey_host, c->st_ey, n * esz, cudaMemcpyDeviceToHost, c->cso));
+    CKF(cudaMemcpyAsync(ez_host, c->st_ez, n * esz, cudaMemcpyDeviceToHost, c->cso));
   }
+  // the next call rewrites phi's staging array (and, after its solve, E's) only
+  // once this copy-out is done: its input stream waits on ev_done
+  CKF(cudaEventRecord(c->ev_done, c->cso));
 #undef CKF
   return finish(st);
+}
+
+}  // namespace
+
+gmg_status gmg_solve_host(gmg_ctx* c, const double* a_host, const double* f_host, const double* phi0_host,
+                          double* phi_host, void* ex_host, void* ey_host, void* ez_host, int field_fp32,
+                          gmg_solve_info* info) {
+  return solve_host_impl(c, a_host, f_host, phi0_host, phi_host, ex_host, ey_host, ez_host, field_fp32, info, true);
+}
+
+gmg_status gmg_solve_host_async(gmg_ctx* c, const double* a_host, const double* f_host, const double* phi0_host,
+                                double* phi_host, void* ex_host, void* ey_host, void* ez_host, int field_fp32,
+                                gmg_solve_info* info) {
+  return solve_host_impl(c, a_host, f_host, phi0_host, phi_host, ex_host, ey_host, ez_host, field_fp32, info,
+                         false);
+}
+
+gmg_status gmg_host_wait(gmg_ctx* c) {
+  if (!c) return GMG_ERR_ARG;
+  if (!c->cs) return GMG_OK;  // no host-array solve yet
+  const cudaError_t e1 = cudaStreamSynchronize(c->cs);
+  const cudaError_t e2 = cudaStreamSynchronize(c->cso);
+  const cudaError_t e3 = cudaStreamSynchronize(c->s);
+  if (e1 != cudaSuccess) return map_err(e1);
+  if (e2 != cudaSuccess) return map_err(e2);
+  return e3 == cudaSuccess ? GMG_OK : map_err(e3);
 }
 
 gmg_status assemble_coefficient_rhs(const gmg_params* p, const double* ne_dev, const double* np_dev,

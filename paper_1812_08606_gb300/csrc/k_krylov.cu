@@ -423,6 +423,21 @@ cudaError_t launch_scale_value(size_t n, const double* src, double* dst, double 
   return cudaGetLastError();
 }
 
+// A few words from device memory into mapped pinned host memory, written by
+// the kernel itself: the copy engines may be busy with large transfers of
+// another stream, and a small copy queued behind them would stall the host
+// for their whole duration.
+__global__ void k_words_to_host(const unsigned* __restrict__ src, unsigned* dst, int words) {
+  for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+
+cudaError_t launch_words_to_host(const void* src, void* dst_mapped, size_t bytes, cudaStream_t s) {
+  if (bytes % 4 != 0 || bytes > (size_t)1 << 20) return cudaErrorInvalidValue;
+  if (bytes == 0) return cudaSuccess;
+  k_words_to_host<<<1, 256, 0, s>>>((const unsigned*)src, (unsigned*)dst_mapped, (int)(bytes / 4));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scale_round(size_t n, const double* src, double* dst, float* dst32, const double* scale,
                                double alpha, cudaStream_t s) {
   k_scale_round<<<flat_blocks(n), 256, 0, s>>>(n, src, dst, dst32, scale, alpha);

@@ -115,6 +115,9 @@ _SIGS = {
     "adjoint_coefficient_grad": (ctypes.c_int, [_P, _P, _P, _P]),
     "gmg_solve_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int,
                                       ctypes.POINTER(gmg_solve_info)]),
+    "gmg_solve_host_async": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int,
+                                            ctypes.POINTER(gmg_solve_info)]),
+    "gmg_host_wait": (ctypes.c_int, [_P]),
     "gmg_set_stream": (ctypes.c_int, [_P, _P]),
     "gmg_destroy": (None, [_P]),
     "gmg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -311,10 +314,7 @@ def adjoint_coefficient_grad(ctx: Context, phi: torch.Tensor, lam: torch.Tensor,
                                            _dev(dlda, numel=ctx.n, name="dlda")), "adjoint_coefficient_grad")
 
 
-def gmg_solve_host(ctx: Context, a_host, f_host, phi_host, phi0_host=None, ex_host=None, ey_host=None,
-                   ez_host=None):
-    """End-to-end solve on host tensors (pinned for full bandwidth): the
-    result lands in phi_host; phi0_host=None means a zero initial guess."""
+def _solve_host(fn: str, ctx: Context, a_host, f_host, phi_host, phi0_host, ex_host, ey_host, ez_host):
     info = gmg_solve_info()
     a_ptr = _host(a_host, numel=ctx.n, name="a") if a_host is not None else None
     x0_ptr = _host(phi0_host, numel=ctx.n, name="phi0") if phi0_host is not None else None
@@ -324,11 +324,30 @@ def gmg_solve_host(ctx: Context, a_host, f_host, phi_host, phi0_host=None, ex_ho
         fp32 = int(ex_host.dtype == torch.float32)
         dt = torch.float32 if fp32 else torch.float64
         eptrs = [_host(t, dt, ctx.n, nm) for t, nm in ((ex_host, "ex"), (ey_host, "ey"), (ez_host, "ez"))]
-    st = load().gmg_solve_host(ctx.handle, a_ptr, _host(f_host, numel=ctx.n, name="f"), x0_ptr,
-                               _host(phi_host, numel=ctx.n, name="phi"), eptrs[0], eptrs[1], eptrs[2], fp32,
-                               ctypes.byref(info))
-    _check(st, "gmg_solve_host", allow=(GMG_OK, GMG_ERR_NOT_CONVERGED))
+    st = getattr(load(), fn)(ctx.handle, a_ptr, _host(f_host, numel=ctx.n, name="f"), x0_ptr,
+                             _host(phi_host, numel=ctx.n, name="phi"), eptrs[0], eptrs[1], eptrs[2], fp32,
+                             ctypes.byref(info))
+    _check(st, fn, allow=(GMG_OK, GMG_ERR_NOT_CONVERGED))
     return info
+
+
+def gmg_solve_host(ctx: Context, a_host, f_host, phi_host, phi0_host=None, ex_host=None, ey_host=None,
+                   ez_host=None):
+    """End-to-end solve on host tensors (pinned for full bandwidth): the
+    result lands in phi_host; phi0_host=None means a zero initial guess."""
+    return _solve_host("gmg_solve_host", ctx, a_host, f_host, phi_host, phi0_host, ex_host, ey_host, ez_host)
+
+
+def gmg_solve_host_async(ctx: Context, a_host, f_host, phi_host, phi0_host=None, ex_host=None, ey_host=None,
+                         ez_host=None):
+    """gmg_solve_host, pipelined: returns with the copy-out of phi (and E) in
+    flight; gmg_host_wait(ctx) completes it before the host arrays are read."""
+    return _solve_host("gmg_solve_host_async", ctx, a_host, f_host, phi_host, phi0_host, ex_host, ey_host, ez_host)
+
+
+def gmg_host_wait(ctx: Context):
+    """Waits for every copy and kernel of the context's host-array solves."""
+    _check(load().gmg_host_wait(ctx.handle), "gmg_host_wait")
 
 
 def gmg_set_stream(ctx: Context, stream):
