@@ -379,6 +379,8 @@ def run_ours(args, dist):
                                        "bicgstab": 1.3263}
         out["krylov_comparison_paper_mesh"] = cmp
         # the whole second-order semi-implicit step (eqs. (e1)-(e2)): solve + MUSCL/Koren transport
+        out["adjoint_fwd_bwd"] = adjoint_arm(args, gmg, stream, 256)
+        out["kappa_sweep_256"] = kappa_sweep_arm(args, gmg, stream, 256)
         out["streamer_steps_paper_mesh"] = streamer_arm(args, gmg, (320, 256, 256), stream)
         out["streamer_steps"] = streamer_arm(args, gmg, (n, n, n), stream)
 
@@ -490,6 +492,96 @@ def time_step_arm(args, gmg, shape, stream, method="fgmres"):
             "steps": K, "step": "assemble a, f from n_e, n_p + set-up + warm-started solve + E (FP32)",
             "workload": f"double-headed streamer eq. (51), {nx} x {ny} x {nz} cells on the unit cube, "
                         f"tau = 2 ps, 52 kV", "levels": levels}
+
+
+def kappa_sweep_arm(args, gmg, stream, n):
+    """The variable-coefficient channel problem at n^3 for kappa in {1e1, 1e3,
+    1e4}: the mixed solve (FP32 V-cycle in FP64 FGMRES) timed beside the plain
+    FP64 solve on the same inputs (set-up + solve each), with iterations, true
+    residuals and the mixed phi's relative error against the FP64 phi (which
+    equals the FP64 oracle's to 1e-10 in the parity tests)."""
+    import torch
+    from streamer_inputs import make_inputs
+    dev = torch.device("cuda", torch.cuda.current_device())
+    N = n ** 3
+    rows = {}
+    for kappa in (1e1, 1e3, 1e4):
+        inp = make_inputs("channel256", n=n, kappa=kappa)
+        a = torch.from_numpy(inp["a"]).to(dev)
+        f = torch.from_numpy(inp["f"]).to(dev)
+        res = {}
+        for name, prec, K in (("mixed", gmg.GMG_PREC_MIXED, args.regime_steps), ("fp64", gmg.GMG_PREC_FP64, 1)):
+            ctx = gmg.gmg_setup(gmg.gmg_default_params(n, n, n, precision=prec), a, stream)
+            phi = torch.zeros_like(f)
+            for i in range(K + 1):
+                if i == 1:
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                gmg.gmg_update_coefficient(ctx, a)
+                phi.zero_()
+                info = gmg.fgmres_solve(ctx, f, phi)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ctx.close()
+            ms = e0.elapsed_time(e1) / K
+            res[name] = (ms, info, phi)
+        (mm, mi, mp), (fm, fi, fp) = res["mixed"], res["fp64"]
+        rel = (torch.linalg.vector_norm(mp - fp) / torch.linalg.vector_norm(fp)).item()
+        rel_max = ((mp - fp).abs().max() / fp.abs().max()).item()
+        rows[f"{kappa:g}"] = {
+            "mixed": {"ms_per_step": round(mm, 3), "value": round(N / (mm / 1e3) / 1e6, 2),
+                      "iterations": mi.iterations, "true_rel_residual": mi.true_rel_residual},
+            "fp64": {"ms_per_step": round(fm, 3), "value": round(N / (fm / 1e3) / 1e6, 2),
+                     "iterations": fi.iterations, "true_rel_residual": fi.true_rel_residual},
+            "speedup": round(fm / mm, 2), "phi_rel_err_l2": rel, "phi_rel_err_max": rel_max}
+        del a, f, res, mp, fp
+    return {"unit": "Mcells/s", "step": "set-up + solve to a 1e-8 true residual (no field)",
+            "workload": f"channel problem, {n}^3, a = 1 + kappa n", "kappa": rows}
+
+
+def adjoint_arm(args, gmg, stream, n):
+    """Forward and backward through torch.autograd on the adjoint workload (the
+    channel problem with a smoothed N(0,1) loss weight w, L = sum w phi): the
+    forward solve renews the set-up (a new coefficient each step), the backward
+    pass is the adjoint solve A lambda = w plus the dL/da face kernel."""
+    import torch
+    from streamer_inputs import make_inputs
+    from paper_1812_08606_gb300.autograd import PoissonSolver
+    dev = torch.device("cuda", torch.cuda.current_device())
+    inp = make_inputs("adjoint", n=n)
+    shape = inp["a"].shape
+    N = n ** 3
+    a = torch.from_numpy(inp["a"]).to(dev).requires_grad_(True)
+    f = torch.from_numpy(inp["f"]).to(dev).requires_grad_(True)
+    w = torch.from_numpy(inp["w"]).to(dev)
+    solver = PoissonSolver(shape, stream=stream, precision=gmg.GMG_PREC_MIXED)
+
+    def step():
+        with torch.no_grad():
+            a.mul_(1.0)   # a new version of the coefficient: the set-up is renewed, as in a training step
+        phi = solver.solve(a, f)
+        return torch.autograd.grad((w * phi).sum(), (a, f))
+
+    step()
+    K = args.regime_steps
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    fi, bi = solver.last_info, solver.last_adjoint_info
+    solver.close()
+    return {"ms_per_step": round(ms, 3), "value": round(N / (ms / 1e3) / 1e6, 2), "unit": "Mcells/s",
+            "forward_iterations": fi.iterations, "adjoint_iterations": bi.iterations,
+            "forward_true_rel_residual": fi.true_rel_residual, "adjoint_true_rel_residual": bi.true_rel_residual,
+            "steps": K, "step": "forward (set-up + GMG-FGMRES) and backward (adjoint GMG-FGMRES + dL/da, dL/df) "
+                                "through torch.autograd, mixed precision",
+            "workload": f"adjoint loss L = sum w phi on the channel problem, {n}^3"}
 
 
 def streamer_arm(args, gmg, shape, stream):

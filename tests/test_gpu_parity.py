@@ -408,6 +408,7 @@ def test_fp64_solve_matches_oracle(workload, n, orth):
 
 
 @pytest.mark.parametrize("workload,n,kappa,arith", [("const32", 32, None, 1), ("channel128", 64, None, 1),
+                                                    ("channel256", 64, 1e1, 1), ("channel256", 64, 1e3, 1),
                                                     ("channel256", 64, 1e4, 1), ("twochannel512", 64, None, 1),
                                                     ("twochannel512", 64, None, 0)])
 def test_mixed_solve_residual_and_error(workload, n, kappa, arith):
