@@ -47,6 +47,8 @@ constexpr int MAX_COARSE = 1024;  // unknowns of the dense coarsest grid
 constexpr int MAXV = 64;          // Krylov vectors
 // device scalar slots
 constexpr int SL_H1 = 0, SL_H2 = 64, SL_NORM = 128, SL_Y = 136, SL_CHECK = 200, N_SCAL = 256;
+// one eigen-estimate column: h1[0..k), h2[0..k), ||w|| with k <= 32 (eig_steps <= 32)
+constexpr int EIG_STRIDE = 65, EIG_MAX_STEPS = 32;
 
 double now_ms() {
   using namespace std::chrono;
@@ -231,6 +233,9 @@ struct gmg_ctx {
   double* dscal = nullptr;
   double* hpin = nullptr;      // mapped pinned host scalars ...
   double* hpin_dev = nullptr;  // ... and their device address
+  double* eigH = nullptr;      // the eigen estimate's Hessenberg columns (device) ...
+  double* heig = nullptr;      // ... their mapped pinned host copy ...
+  double* heig_dev = nullptr;  // ... and its device address
   int* hstat = nullptr;
   int* hstat_dev = nullptr;
   double *st_a = nullptr, *st_f = nullptr, *st_phi = nullptr;
@@ -502,7 +507,7 @@ gmg_status validate(const gmg_params* p, int* nlevels) {
   if (p->coarse_min < 1 || p->cheb_steps < 1 || p->cheb_steps > 8) return GMG_ERR_ARG;
   if (p->restart < 1 || p->restart > MAXV - 1 || p->max_iters < 1) return GMG_ERR_ARG;
   if (!(p->rtol > 0) || !isfinite(p->rtol)) return GMG_ERR_ARG;
-  if (p->eig_steps < 1 || p->eig_steps > 32) return GMG_ERR_ARG;
+  if (p->eig_steps < 1 || p->eig_steps > EIG_MAX_STEPS) return GMG_ERR_ARG;
   if (!(p->eig_hi > p->eig_lo) || !(p->eig_lo > 0) || !isfinite(p->eig_hi)) return GMG_ERR_ARG;
   if (p->precision != GMG_PREC_FP64 && p->precision != GMG_PREC_MIXED) return GMG_ERR_ARG;
   if (p->prolongation != 0 && p->prolongation != 1) return GMG_ERR_ARG;
@@ -644,12 +649,13 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
   CKS(prof_hash_vector<T>(c, n, V, c->s));
   CKS(norm_dev<T>(c, n, V, SL_NORM));
   CKS(prof_scale<T>(c, n, V, V, c->dscal + SL_NORM + 1, c->s));
-  std::vector<double> H((size_t)(steps + 1) * steps, 0.0);
-  int m = steps;
-  std::vector<double> col(steps + 2);
+  // The columns of H stay on the device (the normalisation reads 1/||w|| there)
+  // and come to the host once, after the last step: one host sync per level.
+  // After a breakdown (||w|| = 0) the later vectors are zero and their columns
+  // are dropped on the host.
+  const bool fused_mv = sizeof(T) == 4 && L.fused;
   // On levels with the fused smoother, one fused step forms the product:
   // with b = 0, x_in = v and c2 = -1 its direction d equals B^{-1}(A v).
-  const bool fused_mv = sizeof(T) == 4 && L.fused;
   if (fused_mv) CK(cudaMemsetAsync(L.b, 0, n * sizeof(float), c->s));
   for (int j = 0; j < steps; ++j) {
     if (fused_mv) {
@@ -662,16 +668,31 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
     // One classical Gram-Schmidt pass in FP32: the bounds only steer the FP32
     // smoother, and the second pass moves lambda-hat by less than 1e-7.
     CKS(orthogonalize<T>(c, n, V, n, j + 1, t2, f32));
-    CKS(read_column(c, j + 1, col.data()));
-    for (int i = 0; i <= j + 1; ++i) {
-      if (!isfinite(col[i])) return GMG_ERR_NONFINITE;
-      H[(size_t)i * steps + j] = col[i];
+    CK(launch_gather_column(c->dscal + SL_H1, c->dscal + SL_H2, c->dscal + SL_NORM, j + 1,
+                            c->eigH + (size_t)j * EIG_STRIDE, c->s));
+    if (j + 1 < steps)  // v_{j+1}; the last one is never used
+      CKS(prof_scale<T>(c, n, t2, V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));
+  }
+  CK(launch_words_to_host(c->eigH, c->heig_dev, sizeof(double) * (size_t)steps * EIG_STRIDE, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  prof_collect(c);
+  std::vector<double> H((size_t)(steps + 1) * steps, 0.0);
+  int m = steps;
+  const bool cgs2 = c->p.orthogonalization == GMG_ORTH_CGS2;
+  for (int j = 0; j < steps; ++j) {
+    const double* col = c->heig + (size_t)j * EIG_STRIDE;
+    const int k = j + 1;
+    for (int i = 0; i < k; ++i) {
+      const double h = col[i] + (cgs2 ? col[k + i] : 0.0);
+      if (!isfinite(h)) return GMG_ERR_NONFINITE;
+      H[(size_t)i * steps + j] = h;
     }
-    if (col[j + 1] == 0.0) {
-      m = j + 1;
+    if (!isfinite(col[2 * k])) return GMG_ERR_NONFINITE;
+    H[(size_t)k * steps + j] = col[2 * k];
+    if (col[2 * k] == 0.0) {
+      m = k;
       break;
     }
-    CKS(prof_scale<T>(c, n, t2, V + (size_t)(j + 1) * n, c->dscal + SL_NORM + 1, c->s));
   }
   std::vector<double> Hm((size_t)m * m);
   for (int r = 0; r < m; ++r)
@@ -1410,6 +1431,7 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
   if ((st = dalloc(c, &c->cinv64, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->cinv32, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->cstatus, 4)) != GMG_OK) return fail(st);
+  if ((st = dalloc(c, &c->eigH, (size_t)EIG_STRIDE * EIG_MAX_STEPS)) != GMG_OK) return fail(st);
   {
     // mapped, so that kernels write the scalars the host reads (read_scalars)
     void *h = nullptr, *hd = nullptr;
@@ -1423,6 +1445,12 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
     if (cudaHostGetDevicePointer(&hd, h, 0) != cudaSuccess) return fail(GMG_ERR_CUDA);
     c->hstat = (int*)h;
     c->hstat_dev = (int*)hd;
+    if (cudaHostAlloc(&h, sizeof(double) * EIG_STRIDE * EIG_MAX_STEPS, cudaHostAllocMapped) != cudaSuccess)
+      return fail(GMG_ERR_ALLOC);
+    c->host_allocs.push_back(h);
+    if (cudaHostGetDevicePointer(&hd, h, 0) != cudaSuccess) return fail(GMG_ERR_CUDA);
+    c->heig = (double*)h;
+    c->heig_dev = (double*)hd;
   }
   if ((st = build(c, a_dev)) != GMG_OK) return fail(st);
   *out = c;

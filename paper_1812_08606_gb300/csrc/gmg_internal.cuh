@@ -288,6 +288,9 @@ template <typename T>
 cudaError_t launch_scale(size_t n, const T* src, T* dst, const double* scale, cudaStream_t s);
 // dst = src * alpha (alpha by value).
 cudaError_t launch_scale_value(size_t n, const double* src, double* dst, double alpha, cudaStream_t s);
+// out[0..2k] = h1[0..k), h2[0..k), *nrm (device to device; k <= 64).
+cudaError_t launch_gather_column(const double* h1, const double* h2, const double* nrm, int k, double* out,
+                                 cudaStream_t s);
 // bytes (a multiple of 4, at most 1 MB) from device memory to mapped pinned
 // host memory (its device address), by a one-block kernel instead of a copy engine.
 cudaError_t launch_words_to_host(const void* src, void* dst_mapped, size_t bytes, cudaStream_t s);

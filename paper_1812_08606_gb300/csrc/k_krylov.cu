@@ -423,6 +423,19 @@ cudaError_t launch_scale_value(size_t n, const double* src, double* dst, double 
   return cudaGetLastError();
 }
 
+// out = [h1[0..k), h2[0..k), *nrm]: one Hessenberg column kept on the device.
+__global__ void k_gather_column(const double* __restrict__ h1, const double* __restrict__ h2,
+                                const double* __restrict__ nrm, int k, double* __restrict__ out) {
+  for (int i = threadIdx.x; i <= 2 * k; i += blockDim.x) out[i] = i < k ? h1[i] : (i < 2 * k ? h2[i - k] : nrm[0]);
+}
+
+cudaError_t launch_gather_column(const double* h1, const double* h2, const double* nrm, int k, double* out,
+                                 cudaStream_t s) {
+  if (k < 1 || k > 64) return cudaErrorInvalidValue;
+  k_gather_column<<<1, 128, 0, s>>>(h1, h2, nrm, k, out);
+  return cudaGetLastError();
+}
+
 // A few words from device memory into mapped pinned host memory, written by
 // the kernel itself: the copy engines may be busy with large transfers of
 // another stream, and a small copy queued behind them would stall the host
