@@ -104,12 +104,13 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
   const float2 zero2 = make_float2(0.f, 0.f);
   const int rlo = max(0, k0 - 2), rhi = min(nz, k1 + 2);
   const int blo = max(0, k0 - 1), bhi = min(nz, k1 + 1);
-  const size_t qo = in ? ((size_t)gy * nx + gx0) >> 1 : 0;  // pair offset in a plane
+  // pair offsets in 32 bits (fused_smoother_eligible keeps (nz + 4) planes of pairs below 2^31)
+  const int qo = in ? (gy * nx + gx0) >> 1 : 0;  // pair offset in a plane
   const float2* A2 = reinterpret_cast<const float2*>(P.a);
   const float2* X2 = reinterpret_cast<const float2*>(P.xin);
   const float2* B2 = reinterpret_cast<const float2*>(P.b);
   const float2* D2 = reinterpret_cast<const float2*>(P.d);
-  const size_t pl2 = pl >> 1;
+  const int pl2 = (int)(pl >> 1);
 
   for (int s = 0; s < NZS; ++s) Z1s[s * PPL + me] = ZBs[s * PPL + me] = 0.f;
 
@@ -124,8 +125,8 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
   {
     const int k = k0 - 3;
     if (in && k >= 0 && k < nz) {
-      pa = __ldg(A2 + (size_t)k * pl2 + qo);
-      if (!xzero) px = __ldg(X2 + (size_t)k * pl2 + qo);
+      pa = __ldg(A2 + (k * pl2 + qo));
+      if (!xzero) px = __ldg(X2 + (k * pl2 + qo));
     }
   }
 
@@ -144,12 +145,13 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
     Xs[(t & 1) * PPL + me] = px;
     // ---- prefetch for the next step ----
     pa = px = zero2;
+    const int ot = t * pl2 + qo;  // pair offset of plane t
     if (in && (ST || (t + 1 >= 0 && t + 1 < nz && t + 1 <= k1 + 2))) {
-      pa = __ldg(A2 + (size_t)(t + 1) * pl2 + qo);
-      if (!xzero) px = __ldg(X2 + (size_t)(t + 1) * pl2 + qo);
+      pa = __ldg(A2 + (ot + pl2));
+      if (!xzero) px = __ldg(X2 + (ot + pl2));
     }
-    if (rst && (ST || (t >= rlo && t < rhi))) pbn = __ldg(B2 + (size_t)t * pl2 + qo);
-    if (fst && !first && (ST || (t - 2 >= k0 && t - 2 < k1))) pdn = __ldg(D2 + (size_t)(t - 2) * pl2 + qo);
+    if (rst && (ST || (t >= rlo && t < rhi))) pbn = __ldg(B2 + ot);
+    if (fst && !first && (ST || (t - 2 >= k0 && t - 2 < k1))) pdn = __ldg(D2 + (ot - 2 * pl2));
 
     // ---- residual stage, plane kr = t - 1: r, 1/D (both cells), red z ----
     const int kr = t - 1;
@@ -251,7 +253,7 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
       const float2 z = L ? make_float2(zbw1, zr) : make_float2(zr, zbw1);
       const float2 c2 = sc2(P.c2);
       const float2 dv = first ? mul2(c2, z) : fma2(sc2(P.c1), pd, mul2(c2, z));
-      const size_t q = (size_t)kf * pl2 + qo;
+      const int q = kf * pl2 + qo;
       reinterpret_cast<float2*>(P.d)[q] = dv;
       reinterpret_cast<float2*>(P.xout)[q] = xzero ? dv : add2(xw0, dv);
     }
@@ -340,7 +342,10 @@ cudaError_t fused_slots(int* out) {
 
 }  // namespace
 
-bool fused_smoother_eligible(const Grid3& g) { return g.nx >= 32 && g.nx % 2 == 0 && g.ny >= 16 && g.nz >= 8; }
+bool fused_smoother_eligible(const Grid3& g) {
+  return g.nx >= 32 && g.nx % 2 == 0 && g.ny >= 16 && g.nz >= 8 &&
+         (size_t)(g.nz + 4) * (g.plane() / 2) < ((size_t)1 << 31);  // 32-bit pair offsets
+}
 
 cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b, const float* xin, float* xout,
                                     float* d, double c1, double c2, int flags, cudaStream_t s) {
