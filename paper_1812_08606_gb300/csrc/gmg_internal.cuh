@@ -58,6 +58,10 @@ enum ChebFlags : int { CHEB_UPDATE = 1, CHEB_FIRST = 2, CHEB_XZERO = 4 };
 
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+// The grid's cells, with four planes to spare, index in 32 bits: the pair and
+// transfer kernels then form offsets with 32-bit arithmetic.
+inline bool cells_fit_int32(const Grid3& g) { return (size_t)(g.nz + 4) * g.plane() < ((size_t)1 << 31); }
+
 
 // Exact FP32 -> FP64 conversion from the IEEE-754 bit fields, on the integer
 // pipe only (GB300 runs the conversion instruction on the FP64 pipe, at 1/64

@@ -148,15 +148,16 @@ __global__ void __launch_bounds__(256) k_apply_df64_pairs(Grid3 g, DfCoef c, con
   const int ip = blockIdx.x * 32 + tx, j = blockIdx.y * 8 + threadIdx.y;
   const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
   const bool act = ip < np && j < ny;
-  const size_t pp = (size_t)ny * np;  // pairs per plane
-  const size_t q = act ? (size_t)j * np + ip : 0;
+  // pair offsets in 32 bits: the launcher keeps (nz + 2) planes of pairs below 2^31
+  const int pp = ny * np;  // pairs per plane
+  const int q = act ? j * np + ip : 0;
   const bool lds = act && j > 0, ldn = act && j < ny - 1;
   const bool ldl = act && tx == 0 && ip > 0, ldr = act && tx == 31 && ip + 1 < np;
   const bool wl = ip > 0, wr = ip + 1 < np;  // the row continues left of / right of the pair
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   const float2 zz = f2(0.f, 0.f);
-  auto la = [&](int k) { return (act && k >= 0 && k < nz) ? __ldg(a4 + (size_t)k * pp + q) : z4; };
-  auto lz = [&](int k) { return (act && k >= 0 && k < nz) ? __ldg(z2 + (size_t)k * pp + q) : zz; };
+  auto la = [&](int k) { return (act && k >= 0 && k < nz) ? __ldg(a4 + (k * pp + q)) : z4; };
+  auto lz = [&](int k) { return (act && k >= 0 && k < nz) ? __ldg(z2 + (k * pp + q)) : zz; };
   const float2 cxh = f2(c.xh, c.xh), cxl = f2(c.xl, c.xl), cyh = f2(c.yh, c.yh), cyl = f2(c.yl, c.yl);
   const float2 czh = f2(c.zh, c.zh), czl = f2(c.zl, c.zl), cph = f2(c.ph, c.ph), cpl = f2(c.pl, c.pl);
   float4 am = la(k0 - 1), ac = la(k0);
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(256) k_apply_df64_pairs(Grid3 g, DfCoef c, con
   for (int k = k0; k < k1; ++k) {
     const float4 ap = la(k + 1);
     const float2 zp = lz(k + 1);
-    const size_t o = (size_t)k * pp + q;
+    const int o = k * pp + q;
     const float4 as = lds ? __ldg(a4 + o - np) : z4, an = ldn ? __ldg(a4 + o + np) : z4;
     const float2 zs = lds ? __ldg(z2 + o - np) : zz, zn = ldn ? __ldg(z2 + o + np) : zz;
     // the left pair's second cell and the right pair's first cell
@@ -249,8 +250,11 @@ DfCoef make_df_coef(const Grid3& g) {
 
 cudaError_t launch_apply_df64(const Grid3& g, const DfCoef& c, const float2* a2, const float* z, double* w,
                               cudaStream_t s) {
-  // pair kernel: even rows and 16-byte (a, w) / 8-byte (z) alignment of the pair arrays
-  if (g.nx % 2 == 0 && ((uintptr_t)a2 & 15) == 0 && ((uintptr_t)z & 7) == 0 && ((uintptr_t)w & 15) == 0) {
+  // pair kernel: even rows, 16-byte (a, w) / 8-byte (z) alignment of the pair arrays, and fewer than 2^31
+  // cell pairs in nz + 2 planes (32-bit offsets)
+  const bool pairs_fit = (size_t)(g.nz + 2) * (g.plane() / 2) < ((size_t)1 << 31);
+  if (g.nx % 2 == 0 && pairs_fit && ((uintptr_t)a2 & 15) == 0 && ((uintptr_t)z & 7) == 0 &&
+      ((uintptr_t)w & 15) == 0) {
     const int gx = (g.nx / 2 + 31) / 32, gy = (g.ny + 7) / 8;
     const long long xy = (long long)gx * gy, target = 152LL * 8 * 2;
     int zc = (int)std::max(1LL, std::min((target + xy - 1) / xy, (long long)std::max(1, g.nz / 4)));

@@ -284,7 +284,8 @@ cudaError_t launch_residual_restrict(const Grid3& g, const T* a, const T* b, con
     return cudaGetLastError();
   }
   if constexpr (std::is_same<T, float>::value) {
-    if (pair_aligned(a) && pair_aligned(b) && pair_aligned(x)) return launch_restrict_pairs(g, a, b, x, coarse, s);
+    if (pair_aligned(a) && pair_aligned(b) && pair_aligned(x) && cells_fit_int32(g))
+      return launch_restrict_pairs(g, a, b, x, coarse, s);
   }
   k_residual_restrict<T><<<grid, dim3(BX, BY), 0, s>>>(g, a, b, x, coarse);
   return cudaGetLastError();
@@ -293,7 +294,7 @@ cudaError_t launch_residual_restrict(const Grid3& g, const T* a, const T* b, con
 template <typename T>
 cudaError_t launch_prolong_add(const Grid3& g, const T* e, T* x, int mode, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
-    if (pair_aligned(x)) return launch_prolong_pairs(g, e, x, mode, s);
+    if (pair_aligned(x) && cells_fit_int32(g)) return launch_prolong_pairs(g, e, x, mode, s);
   }
   k_prolong_add<T><<<grid_cells(g), dim3(BX, BY), 0, s>>>(g, e, x, mode);
   return cudaGetLastError();

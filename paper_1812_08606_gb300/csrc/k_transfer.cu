@@ -58,8 +58,9 @@ __global__ void __launch_bounds__(TP* TR, 4) k_restrict_pairs(Grid3 g, const flo
   const int kc0 = blockIdx.z * kchunk, kc1 = min(nzc, kc0 + kchunk);
   const bool act = ip < nxc && j < ny;
   const int i0 = 2 * ip;
-  const size_t pl2 = g.plane() >> 1;
-  const size_t q = act ? ((size_t)j * nx + i0) >> 1 : 0;  // pair offset in a plane
+  // offsets in 32 bits: the launcher keeps nz + 4 planes of cells below 2^31
+  const int pl2 = (int)(g.plane() >> 1);
+  const int q = act ? (j * nx + i0) >> 1 : 0;  // pair offset in a plane
   const float2* A2 = reinterpret_cast<const float2*>(a);
   const float2* X2 = reinterpret_cast<const float2*>(x);
   const float2* B2 = reinterpret_cast<const float2*>(b);
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(TP* TR, 4) k_restrict_pairs(Grid3 g, const flo
   const bool lds = act && j > 0, ldn = act && j < ny - 1;
   const float2 fx2 = f2(g.fx, g.fx), fy2 = f2(g.fy, g.fy), fz2 = f2(g.fz, g.fz), fp2 = f2(g.fp, g.fp);
   const float2 z2 = f2(0.f, 0.f);
-  auto load = [&](const float2* P, int k) { return (act && k >= 0 && k < nz) ? __ldg(P + (size_t)k * pl2 + q) : z2; };
+  auto load = [&](const float2* P, int k) { return (act && k >= 0 && k < nz) ? __ldg(P + (k * pl2 + q)) : z2; };
 
   const int k0 = 2 * kc0, k1 = 2 * kc1;
   float2 xm = load(X2, k0 - 1), xc = load(X2, k0), xp = load(X2, k0 + 1);
@@ -79,15 +80,15 @@ __global__ void __launch_bounds__(TP* TR, 4) k_restrict_pairs(Grid3 g, const flo
   int slot = 0;
   for (int k = k0; k < k1; ++k) {
     const float2 xq = load(X2, k + 2), aq = load(A2, k + 2);
-    const size_t o = (size_t)k * pl2 + q;
+    const int o = k * pl2 + q;
     const float2 bb = act ? __ldg(B2 + o) : z2;
     const float2 xs = lds ? __ldg(X2 + o - nx / 2) : z2, as = lds ? __ldg(A2 + o - nx / 2) : z2;
     const float2 xn = ldn ? __ldg(X2 + o + nx / 2) : z2, an = ldn ? __ldg(A2 + o + nx / 2) : z2;
     // x-neighbours: lane - 1 holds cell i0 - 1 in .y, lane + 1 holds i0 + 2 in .x
     float xl = __shfl_up_sync(FULL, xc.y, 1), al = __shfl_up_sync(FULL, ac.y, 1);
     float xr = __shfl_down_sync(FULL, xc.x, 1), ar = __shfl_down_sync(FULL, ac.x, 1);
-    const float* xs1 = x + (size_t)k * g.plane() + (size_t)j * nx + i0;
-    const float* as1 = a + (size_t)k * g.plane() + (size_t)j * nx + i0;
+    const float* xs1 = x + 2 * o;  // the pair's first cell
+    const float* as1 = a + 2 * o;
     if (tx == 0) {
       xl = ldl ? __ldg(xs1 - 1) : 0.f;
       al = ldl ? __ldg(as1 - 1) : 0.f;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(TP* TR, 4) k_restrict_pairs(Grid3 g, const flo
       __syncthreads();
       if (!(ty & 1) && act) {
         const int kc = k >> 1;
-        coarse[((size_t)kc * nyc + (j >> 1)) * nxc + ip] = 0.125f * (s + hand[slot][ty >> 1][tx]);
+        coarse[(kc * nyc + (j >> 1)) * nxc + ip] = 0.125f * (s + hand[slot][ty >> 1][tx]);
       }
       s = 0.f;
       slot ^= 1;
@@ -152,10 +153,11 @@ __global__ void __launch_bounds__(TP* TR) k_prolong_pairs(Grid3 g, const float* 
   // the halo column of the edge lanes
   const int ih = tx == 0 ? ip - 1 : (tx == TP - 1 ? ip + 1 : -1);
   const bool hact = act && ih >= 0 && ih < nxc;
-  const size_t pc = (size_t)nyc * nxc;
-  const size_t rc = act ? (size_t)jc * nxc : 0, rn = act ? (size_t)jn * nxc : 0;
-  auto ld = [&](bool on, int kc, size_t row, int col) {
-    return (on && kc >= 0 && kc < nzc) ? __ldg(e + (size_t)kc * pc + row + col) : 0.f;
+  // offsets in 32 bits: the launcher keeps nz + 4 planes of fine cells below 2^31
+  const int pc = nyc * nxc;
+  const int rc = act ? jc * nxc : 0, rn = act ? jn * nxc : 0;
+  auto ld = [&](bool on, int kc, int row, int col) {
+    return (on && kc >= 0 && kc < nzc) ? __ldg(e + (kc * pc + row + col)) : 0.f;
   };
   // window of coarse planes kc - 1, kc, kc + 1: rows (jc, jn), own column and halo column
   float c0m = ld(act, kc0 - 1, rc, ip), n0m = ld(act, kc0 - 1, rn, ip);
@@ -164,8 +166,8 @@ __global__ void __launch_bounds__(TP* TR) k_prolong_pairs(Grid3 g, const float* 
   float h0m = ld(hact, kc0 - 1, rc, ih), g0m = ld(hact, kc0 - 1, rn, ih);
   float h0 = ld(hact, kc0, rc, ih), g0 = ld(hact, kc0, rn, ih);
   float h0p = ld(hact, kc0 + 1, rc, ih), g0p = ld(hact, kc0 + 1, rn, ih);
-  const size_t pl2 = g.plane() >> 1;
-  const size_t q = act ? ((size_t)j * nx + 2 * ip) >> 1 : 0;
+  const int pl2 = (int)(g.plane() >> 1);
+  const int q = act ? (j * nx + 2 * ip) >> 1 : 0;
   float2* X2 = reinterpret_cast<float2*>(x);
   for (int kc = kc0; kc < kc1; ++kc) {
     const float c1 = ld(act, kc + 2, rc, ip), n1 = ld(act, kc + 2, rn, ip);
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(TP* TR) k_prolong_pairs(Grid3 g, const float* 
       if (ip == 0) left = own;             // Neumann ghost = parent
       if (ip == nxc - 1) right = own;
       if (act) {
-        const size_t o = (size_t)k * pl2 + q;
+        const int o = k * pl2 + q;
         const float2 v = mode == 1 ? f2(own, own) : f2(fmaf(0.75f, own, 0.25f * left), fmaf(0.75f, own, 0.25f * right));
         X2[o] = add2(X2[o], v);
       }
@@ -208,6 +210,7 @@ __global__ void __launch_bounds__(TP* TR) k_prolong_pairs(Grid3 g, const float* 
 cudaError_t launch_restrict_pairs(const Grid3& g, const float* a, const float* b, const float* x, float* coarse,
                                   cudaStream_t s) {
   if (!pair_aligned(a) || !pair_aligned(b) || !pair_aligned(x) || g.nx % 2) return cudaErrorMisalignedAddress;
+  if (!cells_fit_int32(g)) return cudaErrorInvalidValue;
   const int gx = (g.nx / 2 + TP - 1) / TP, gy = (g.ny + TR - 1) / TR;
   const int nzc = g.nz / 2;
   const int zc = z_chunks((long long)gx * gy, nzc, 4);
@@ -220,6 +223,7 @@ cudaError_t launch_restrict_pairs(const Grid3& g, const float* a, const float* b
 
 cudaError_t launch_prolong_pairs(const Grid3& g, const float* e, float* x, int mode, cudaStream_t s) {
   if (!pair_aligned(x) || g.nx % 2) return cudaErrorMisalignedAddress;
+  if (!cells_fit_int32(g)) return cudaErrorInvalidValue;
   const int gx = (g.nx / 2 + TP - 1) / TP, gy = (g.ny + TR - 1) / TR;
   const int nzc = g.nz / 2;
   const int zc = z_chunks((long long)gx * gy, nzc, 4);
