@@ -332,12 +332,19 @@ __global__ void __launch_bounds__(RT) k_coef_check(size_t n, const double* __res
                                                    double* __restrict__ partial) {
   __shared__ double sh[RT / 32];
   __shared__ double shm[RT / 32];
-  double mn = 1.0e300, bad = 0.0;
+  // On the integer pipe: a double is positive and finite exactly when its bit
+  // pattern, as a signed 64-bit integer, lies strictly between 0 and that of
+  // +infinity, and such doubles order like their patterns (NaN and negatives fail).
+  long long mnb = __double_as_longlong(1.0e300);
+  int badc = 0;
   for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
-    const double v = a[p];
-    if (!isfinite(v) || !(v > 0.0)) bad += 1.0;
-    else mn = fmin(mn, v);
+    const long long b = __double_as_longlong(a[p]);
+    if (b > 0 && b < 0x7FF0000000000000LL)
+      mnb = b < mnb ? b : mnb;
+    else
+      ++badc;
   }
+  double mn = __longlong_as_double(mnb), bad = (double)badc;
   // block min
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));

@@ -228,8 +228,8 @@ __global__ void __launch_bounds__(256) k_apply_df64_pairs(Grid3 g, DfCoef c, con
 __global__ void k_split(size_t n, const double* __restrict__ a, float2* __restrict__ a2) {
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
     const double v = a[p];
-    const float h = (float)v;
-    a2[p] = make_float2(h, (float)(v - (double)h));
+    const float h = f64_to_f32(v);  // conversions on the integer pipe; only the subtraction is FP64
+    a2[p] = make_float2(h, f64_to_f32(v - f32_to_f64(h)));
   }
 }
 
