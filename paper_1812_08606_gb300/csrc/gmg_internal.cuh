@@ -250,6 +250,10 @@ struct TransportCoef {
   double ih2x, ih2y, ih2z;        // 1/(2h): the central-difference field
   double dih2x, dih2y, dih2z;     // D_alpha / h_alpha^2
 };
+// r = b - A x in FP64 with each face product formed once (32 x 8 column tiles
+// marching in z); the outer solver's true residual.
+cudaError_t launch_residual64_tiled(const Grid3& g, const double* a, const double* b, const double* x, double* r,
+                                   cudaStream_t s);
 // rate_mode 0: the ionization rate computed in place; 1: also stored to rate[];
 // 2: read from rate[] (written by a mode-1 stage with the same phi).
 cudaError_t launch_transport(const Grid3& g, const TransportCoef& tc, const double* base_e, const double* base_p,

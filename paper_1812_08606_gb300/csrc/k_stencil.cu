@@ -256,6 +256,10 @@ template cudaError_t launch_apply<float, float, float>(const Grid3&, const float
 template <typename T>
 cudaError_t launch_residual(const Grid3& g, const T* a, const T* b, const T* x, T* r, T* z, int pc,
                             cudaStream_t s) {
+  if constexpr (std::is_same<T, double>::value) {
+    // the plain FP64 residual (no preconditioner output): every face product once
+    if (x && r && !z && pc == PC_NONE) return launch_residual64_tiled(g, a, b, x, r, s);
+  }
   k_residual<T><<<grid_cells(g), dim3(BX, BY), 0, s>>>(g, a, b, x, r, z, pc);
   return cudaGetLastError();
 }
