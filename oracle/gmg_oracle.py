@@ -209,6 +209,29 @@ def neighbour_sum(grid: Grid, a: np.ndarray, x: np.ndarray) -> np.ndarray:
     return s
 
 
+def apply_operator_at(grid: Grid, a: np.ndarray, x: np.ndarray, cells) -> np.ndarray:
+    """(A x)_p of apply_operator at the listed cells (k, j, i) only, one cell at a
+    time from its 7-point neighbourhood: each interior face adds the face mean
+    (a_p + a_q)/2 times (x_p - x_q) / h^2 (eq. (e18), Sec. 2.2), a plate face adds
+    2 a_p x_p / hz^2 (R1, R2), a side wall adds nothing.  For checks on grids too
+    large for the whole-array form."""
+    nz, ny, nx = x.shape
+    steps = ((0, 0, -1, grid.hx), (0, 0, 1, grid.hx), (0, -1, 0, grid.hy), (0, 1, 0, grid.hy),
+             (-1, 0, 0, grid.hz), (1, 0, 0, grid.hz))
+    out = np.empty(len(cells))
+    for n, (k, j, i) in enumerate(cells):
+        xp, ap = float(x[k, j, i]), float(a[k, j, i])
+        s = 0.0
+        for dk, dj, di, h in steps:
+            kk, jj, ii = k + dk, j + dj, i + di
+            if 0 <= kk < nz and 0 <= jj < ny and 0 <= ii < nx:
+                s += 0.5 * (ap + float(a[kk, jj, ii])) / h**2 * (xp - float(x[kk, jj, ii]))
+            elif dk != 0:
+                s += 2.0 * ap / grid.hz**2 * xp
+        out[n] = s
+    return out
+
+
 def assemble_rhs(grid: Grid, a: np.ndarray, f: np.ndarray, g_bottom: float, g_top: float) -> np.ndarray:
     """b = f + the plate terms 2 a_p g / hz^2 (eq. (e18) with ghosts, R1/R2)."""
     b = np.array(f, dtype=np.float64, copy=True)
@@ -959,6 +982,24 @@ def field_from_potential(grid: Grid, phi: np.ndarray, g_bottom: float, g_top: fl
     ey = central(phi, 1, grid.hy, mirror, mirror)
     ez = central(phi, 0, grid.hz, lambda e: 2.0 * g_bottom - e, lambda e: 2.0 * g_top - e)
     return ex, ey, ez
+
+
+def field_at(grid: Grid, phi: np.ndarray, g_bottom: float, g_top: float, cells) -> np.ndarray:
+    """(Ex, Ey, Ez) of field_from_potential at the listed cells (k, j, i) only,
+    one cell at a time: central differences with a mirror ghost beyond a side
+    wall and 2g - phi beyond a plate (Sec. 2.2, R2).  Returns shape (len, 3)."""
+    nz, ny, nx = phi.shape
+    out = np.empty((len(cells), 3))
+    for n, (k, j, i) in enumerate(cells):
+        c = float(phi[k, j, i])
+        xm = float(phi[k, j, i - 1]) if i > 0 else c
+        xp = float(phi[k, j, i + 1]) if i < nx - 1 else c
+        ym = float(phi[k, j - 1, i]) if j > 0 else c
+        yp = float(phi[k, j + 1, i]) if j < ny - 1 else c
+        zm = float(phi[k - 1, j, i]) if k > 0 else 2.0 * g_bottom - c
+        zp = float(phi[k + 1, j, i]) if k < nz - 1 else 2.0 * g_top - c
+        out[n] = (-(xp - xm) / (2.0 * grid.hx), -(yp - ym) / (2.0 * grid.hy), -(zp - zm) / (2.0 * grid.hz))
+    return out
 
 
 def adjoint_coefficient_grad(grid: Grid, phi: np.ndarray, lam: np.ndarray,
