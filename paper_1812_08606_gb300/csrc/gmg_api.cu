@@ -1674,6 +1674,9 @@ gmg_status transport_coef(const gmg_params* p, const gmg_transport_coef* tc, dou
   t->dih2x = tc->diff_x / (hx * hx);
   t->dih2y = tc->diff_y / (hy * hy);
   t->dih2z = tc->diff_z / (hz * hz);
+  t->dmx = t->mu_e > 0.0 ? tc->diff_x / t->mu_e : 0.0;
+  t->dmy = t->mu_e > 0.0 ? tc->diff_y / t->mu_e : 0.0;
+  t->dmz = t->mu_e > 0.0 ? tc->diff_z / t->mu_e : 0.0;
   return GMG_OK;
 }
 

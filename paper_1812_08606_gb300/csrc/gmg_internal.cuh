@@ -249,6 +249,7 @@ struct TransportCoef {
   double kx, ky, kz;              // 1/h^2: the drift divergence of the scaled face fluxes
   double ih2x, ih2y, ih2z;        // 1/(2h): the central-difference field
   double dih2x, dih2y, dih2z;     // D_alpha / h_alpha^2
+  double dmx, dmy, dmz;           // D_alpha / mu_e (0 when mu_e = 0): diffusion folded into the face values
 };
 // r = b - A x in FP64 with each face product formed once (32 x 8 column tiles
 // marching in z); the outer solver's true residual.

@@ -66,9 +66,10 @@ __device__ __forceinline__ int mirror2(int i, int m) {
 // cell q-1 with the slope of (u2 - u1, u1 - u0); backward flow cell q with that
 // of (u1 - u2, u2 - u3), which is minus the slope of (u2 - u1, u3 - u2) (the
 // limiter is odd under a joint sign change), so both share one evaluation.
-__device__ __forceinline__ double face_value(bool fwd, double u0, double u1, double u2, double u3) {
+// d1 = u2 - u1, the difference across the face.
+__device__ __forceinline__ double face_value(bool fwd, double u0, double u1, double u2, double u3, double d1) {
   const double b = (fwd ? u1 : u3) - (fwd ? u0 : u2);
-  const double k = koren(u2 - u1, b);
+  const double k = koren(d1, b);
   return (fwd ? u1 : u2) + (fwd ? 0.5 : -0.5) * k;
 }
 
@@ -78,13 +79,20 @@ __device__ __forceinline__ double face_value(bool fwd, double u0, double u1, dou
 // mu_p g_p / h (ions along it), the mobility and 1/h being applied once per
 // cell in the divergence.  Ions cross from q-1 to q when dphi > 0, electrons
 // when dphi < 0; at dphi = 0 the flux is zero whichever side is taken.
+// FOLD (mu_e > 0): the electron value also carries the diffusion flux,
+// g_e += (D / mu_e) (n_q - n_{q-1}) with dk = D / mu_e for the face's axis, so
+// that mu_e times its divergence is drift plus diffusion and the cell needs no
+// second differences of n_e.
 struct FaceFlux {
   double e, p;
 };
-__device__ __forceinline__ FaceFlux face_flux(double dphi, double e0, double e1, double e2, double e3, double p0,
-                                              double p1, double p2, double p3) {
+template <bool FOLD>
+__device__ __forceinline__ FaceFlux face_flux(double dphi, double dk, double e0, double e1, double e2, double e3,
+                                              double p0, double p1, double p2, double p3) {
   const bool ion_fwd = dbits(dphi) > 0;
-  return {dphi * face_value(!ion_fwd, e0, e1, e2, e3), dphi * face_value(ion_fwd, p0, p1, p2, p3)};
+  const double d1e = e2 - e1;
+  const double ge = dphi * face_value(!ion_fwd, e0, e1, e2, e3, d1e);
+  return {FOLD ? fma(dk, d1e, ge) : ge, dphi * face_value(ion_fwd, p0, p1, p2, p3, p2 - p1)};
 }
 
 constexpr int TBX = 32, TBY = 8;           // columns per block (one thread each)
@@ -104,7 +112,7 @@ static_assert(DX * DY <= 2 * NT && PX * PY <= 2 * NT, "two staging loads per thr
 // the own cell from the column's register windows, then difference the fluxes.
 // base_e / base_p may be out_e / out_p (each cell reads its own base value before
 // writing).
-template <int RM>
+template <int RM, bool FOLD>
 __global__ void __launch_bounds__(NT, 2) k_transport(Grid3 g, TransportCoef tc, const double* base_e,
                                                     const double* base_p, const double* __restrict__ ev_e,
                                                     const double* __restrict__ ev_p,
@@ -173,7 +181,7 @@ __global__ void __launch_bounds__(NT, 2) k_transport(Grid3 g, TransportCoef tc, 
   double pm = k0 > 0 ? phi[col + (size_t)(k0 - 1) * pl] : 2.0 * tc.g_bottom - pc;
   double pp = k0 < nz - 1 ? phi[col + (size_t)(k0 + 1) * pl] : 2.0 * tc.g_top - pc;
   // z face below plane k0 (cells k0-2 .. k0+1), then the window moves to k0-1 .. k0+2
-  FaceFlux fz_lo = face_flux(pm - pc, ze[0], ze[1], ze[2], ze[3], zp[0], zp[1], zp[2], zp[3]);
+  FaceFlux fz_lo = face_flux<FOLD>(pm - pc, tc.dmz, ze[0], ze[1], ze[2], ze[3], zp[0], zp[1], zp[2], zp[3]);
   {
     const size_t q = col + (size_t)mirror2(k0 + 2, nz) * pl;
 #pragma unroll
@@ -198,33 +206,33 @@ __global__ void __launch_bounds__(NT, 2) k_transport(Grid3 g, TransportCoef tc, 
     const double nu_in = RM == 2 && inside ? rate[p] : 0.0;
 
     {  // x face between i-1 and i; y face between j-1 and j
-      const FaceFlux fx = face_flux(sf[ty + 1][tx] - sf[ty + 1][tx + 1], se[ty + 2][tx],
+      const FaceFlux fx = face_flux<FOLD>(sf[ty + 1][tx] - sf[ty + 1][tx + 1], tc.dmx, se[ty + 2][tx],
                                     se[ty + 2][tx + 1], se[ty + 2][tx + 2], se[ty + 2][tx + 3], sp[ty + 2][tx],
                                     sp[ty + 2][tx + 1], sp[ty + 2][tx + 2], sp[ty + 2][tx + 3]);
       xe[ty][tx] = fx.e;
       xp[ty][tx] = fx.p;
-      const FaceFlux fy = face_flux(sf[ty][tx + 1] - sf[ty + 1][tx + 1], se[ty][tx + 2],
+      const FaceFlux fy = face_flux<FOLD>(sf[ty][tx + 1] - sf[ty + 1][tx + 1], tc.dmy, se[ty][tx + 2],
                                     se[ty + 1][tx + 2], se[ty + 2][tx + 2], se[ty + 3][tx + 2], sp[ty][tx + 2],
                                     sp[ty + 1][tx + 2], sp[ty + 2][tx + 2], sp[ty + 3][tx + 2]);
       ye[ty][tx] = fy.e;
       yp[ty][tx] = fy.p;
     }
     if (ty == 0) {  // the tile's far y faces (between rows j0+TBY-1 and j0+TBY), one per column
-      const FaceFlux f = face_flux(sf[TBY][tx + 1] - sf[TBY + 1][tx + 1], se[TBY][tx + 2],
+      const FaceFlux f = face_flux<FOLD>(sf[TBY][tx + 1] - sf[TBY + 1][tx + 1], tc.dmy, se[TBY][tx + 2],
                                    se[TBY + 1][tx + 2], se[TBY + 2][tx + 2], se[TBY + 3][tx + 2], sp[TBY][tx + 2],
                                    sp[TBY + 1][tx + 2], sp[TBY + 2][tx + 2], sp[TBY + 3][tx + 2]);
       ye[TBY][tx] = f.e;
       yp[TBY][tx] = f.p;
     } else if (ty == 1 && tx < TBY) {  // the far x faces (between i0+TBX-1 and i0+TBX), one per row
       const int r = tx;
-      const FaceFlux f = face_flux(sf[r + 1][TBX] - sf[r + 1][TBX + 1], se[r + 2][TBX],
+      const FaceFlux f = face_flux<FOLD>(sf[r + 1][TBX] - sf[r + 1][TBX + 1], tc.dmx, se[r + 2][TBX],
                                    se[r + 2][TBX + 1], se[r + 2][TBX + 2], se[r + 2][TBX + 3], sp[r + 2][TBX],
                                    sp[r + 2][TBX + 1], sp[r + 2][TBX + 2], sp[r + 2][TBX + 3]);
       xe[r][TBX] = f.e;
       xp[r][TBX] = f.p;
     }
     // z face between k and k+1 (cells k-1 .. k+2)
-    const FaceFlux fz_hi = face_flux(pc - pp, ze[0], ze[1], ze[2], ze[3], zp[0], zp[1], zp[2], zp[3]);
+    const FaceFlux fz_hi = face_flux<FOLD>(pc - pp, tc.dmz, ze[0], ze[1], ze[2], ze[3], zp[0], zp[1], zp[2], zp[3]);
 
     const double ce = ze[1];
     double nu = nu_in;
@@ -241,11 +249,13 @@ __global__ void __launch_bounds__(NT, 2) k_transport(Grid3 g, TransportCoef tc, 
       if (RM == 1 && inside) rate[p] = nu;
     }
     const double src = nu * ce;
-    // electron diffusion with one mirrored layer
+    // electron diffusion with one mirrored layer (folded into the face values when FOLD)
     double diff = 0.0;
-    diff += tc.dih2x * ((se[ty + 2][tx + 3] - 2.0 * ce) + se[ty + 2][tx + 1]);
-    diff += tc.dih2y * ((se[ty + 3][tx + 2] - 2.0 * ce) + se[ty + 1][tx + 2]);
-    diff += tc.dih2z * ((ze[2] - 2.0 * ce) + ze[0]);
+    if (!FOLD) {
+      diff += tc.dih2x * ((se[ty + 2][tx + 3] - 2.0 * ce) + se[ty + 2][tx + 1]);
+      diff += tc.dih2y * ((se[ty + 3][tx + 2] - 2.0 * ce) + se[ty + 1][tx + 2]);
+      diff += tc.dih2z * ((ze[2] - 2.0 * ce) + ze[0]);
+    }
     __syncthreads();  // all faces of plane k written; the tiles of plane k no longer read
 
     if (inside) {  // div of the scaled fluxes: sum over axes of (g_hi - g_lo) / h^2
@@ -255,7 +265,7 @@ __global__ void __launch_bounds__(NT, 2) k_transport(Grid3 g, TransportCoef tc, 
       dp += (yp[ty + 1][tx] - yp[ty][tx]) * tc.ky;
       de += (fz_hi.e - fz_lo.e) * tc.kz;
       dp += (fz_hi.p - fz_lo.p) * tc.kz;
-      out_e[p] = be + c * ((tc.mu_e * de + diff) + src);
+      out_e[p] = FOLD ? be + c * (tc.mu_e * de + src) : be + c * ((tc.mu_e * de + diff) + src);
       out_p[p] = bp + c * (src - tc.mu_p * dp);
     }
     if (more) stage_store();
@@ -287,7 +297,7 @@ cudaError_t transport_slots(int* out) {
   if (g_transport_slots[dev] == 0) {
     int sms = 0, per = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_transport<0>, NT, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_transport<0, true>, NT, 0);
     if (e != cudaSuccess) return e;
     g_transport_slots[dev] = std::max(1, sms * std::max(1, per));
   }
@@ -325,12 +335,18 @@ cudaError_t launch_transport(const Grid3& g, const TransportCoef& tc, const doub
   const int bx = (g.nx + TBX - 1) / TBX, by = (g.ny + TBY - 1) / TBY;
   const int kc = transport_chunk(bx * by, g.nz, slots);
   dim3 grid((unsigned)bx, (unsigned)by, (unsigned)((g.nz + kc - 1) / kc));
-  if (rate_mode == 0)
-    k_transport<0><<<grid, dim3(TBX, TBY), 0, s>>>(g, tc, base_e, base_p, ev_e, ev_p, phi, c, out_e, out_p, rate, kc);
-  else if (rate_mode == 1)
-    k_transport<1><<<grid, dim3(TBX, TBY), 0, s>>>(g, tc, base_e, base_p, ev_e, ev_p, phi, c, out_e, out_p, rate, kc);
-  else
-    k_transport<2><<<grid, dim3(TBX, TBY), 0, s>>>(g, tc, base_e, base_p, ev_e, ev_p, phi, c, out_e, out_p, rate, kc);
+  const dim3 block(TBX, TBY);
+#define GMG_TRANSPORT(RM, FOLD) \
+  k_transport<RM, FOLD><<<grid, block, 0, s>>>(g, tc, base_e, base_p, ev_e, ev_p, phi, c, out_e, out_p, rate, kc)
+  const bool fold = tc.mu_e > 0.0;
+  if (rate_mode == 0) {
+    if (fold) GMG_TRANSPORT(0, true); else GMG_TRANSPORT(0, false);
+  } else if (rate_mode == 1) {
+    if (fold) GMG_TRANSPORT(1, true); else GMG_TRANSPORT(1, false);
+  } else {
+    if (fold) GMG_TRANSPORT(2, true); else GMG_TRANSPORT(2, false);
+  }
+#undef GMG_TRANSPORT
   return cudaGetLastError();
 }
 

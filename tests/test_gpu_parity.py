@@ -945,6 +945,25 @@ def test_transport_stage_matches_oracle(shape, lengths):
     assert torch.equal(be, oe) and torch.equal(bp, op)
 
 
+def test_transport_stage_without_electron_mobility():
+    """mu_e = 0 takes the kernel variant with the electron diffusion as second
+    differences (with mu_e > 0 it rides on the face values); both against the
+    oracle, and both with diffusion."""
+    shape = (12, 20, 40)
+    grid = O.Grid(40, 20, 12, 1.0, 0.8, 0.6)
+    ne, npos = _densities(shape, 360)
+    phi = 2e4 * random_field(361, shape)
+    p = _params(shape, lx=1.0, ly=0.8, lz=0.6, phi_bottom=0.0, phi_top=2e4)
+    for mu_e in (0.0, MU_E):
+        ref_e, ref_p = O.transport_stage(grid, ne, npos, ne, npos, phi, 0.0, 2e4, mu_e, MU_P, DIFFUSION, 3e-12)
+        oe = torch.empty(shape, dtype=torch.float64, device=DEV)
+        op = torch.empty_like(oe)
+        gmg.transport_stage(p, _t(ne), _t(npos), _t(ne), _t(npos), _t(phi), 3e-12, oe, op, mu_e=mu_e, mu_p=MU_P,
+                            diffusion=DIFFUSION)
+        assert np.abs(_np(oe) - ref_e).max() <= 1e-12 * np.abs(ref_e).max()
+        assert np.abs(_np(op) - ref_p).max() <= 1e-12 * np.abs(ref_p).max()
+
+
 def test_transport_stage_rejects_aliasing():
     shape = (8, 8, 8)
     p = _params(shape)
