@@ -39,91 +39,113 @@ int z_chunks(long long xy_blocks, int planes, int min_planes) {
 }
 
 // ---------------------------------------------------------------------------
-// Fused residual + restriction.  Thread (tx, ty): pair ip = bx 32 + tx, fine
-// row j = by 8 + ty; coarse planes [kc0, kc1).  Per fine plane the thread forms
-// r of its pair and adds r.x + r.y to its running sum; after the second plane
-// of a coarse plane the odd row hands its sum to the even row through shared
-// memory (two slots, one barrier per coarse plane), which writes the mean.
+// Fused residual + restriction.  Thread (tx, ty): pair ip = bx 32 + tx and the
+// two fine rows j0 = 2 jc, j0 + 1 of coarse row jc = by 8 + ty; coarse planes
+// [kc0, kc1).  Per fine plane the thread forms r of its four cells (each row
+// is the other's y-neighbour, so only the rows j0 - 1 and j0 + 2 are loaded
+// besides its own) and adds them to a running sum; after the second plane of a
+// coarse plane it writes the mean of the eight children.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(TP* TR, 4) k_restrict_pairs(Grid3 g, const float* __restrict__ a,
+struct RowWin {  // one fine row's x and a at planes k-1, k, k+1
+  float2 xm, xc, xp, am, ac, ap;
+};
+
+__device__ __forceinline__ float2 pair_residual(const Grid3& g, const RowWin& w, float2 bb, float xl, float al,
+                                               float xr, float ar, float mxl, float mxr, float2 as, float2 xs,
+                                               float ms, float2 an, float2 xn, float mn, bool zlo, bool zhi) {
+  const float2 z2 = f2(0.f, 0.f);
+  const float2 fx2 = f2(g.fx, g.fx), fy2 = f2(g.fy, g.fy), fz2 = f2(g.fz, g.fz), fp2 = f2(g.fp, g.fp);
+  const float2 ac = w.ac, xc = w.xc;
+  const float2 fxm = mul2(add2(ac, f2(al, ac.x)), f2(mxl, 1.f));
+  const float2 fxp = mul2(add2(ac, f2(ac.y, ar)), f2(1.f, mxr));
+  float2 sx = mul2(fxm, sub2(xc, f2(xl, xc.x)));
+  sx = fma2(fxp, sub2(xc, f2(xc.y, xr)), sx);
+  float2 sy = mul2(mul2(add2(ac, as), f2(ms, ms)), sub2(xc, xs));
+  sy = fma2(mul2(add2(ac, an), f2(mn, mn)), sub2(xc, xn), sy);
+  const float2 plate = add2(zlo ? z2 : ac, zhi ? z2 : ac);
+  float2 sz = mul2(fp2, mul2(plate, xc));
+  if (zlo) sz = fma2(fz2, mul2(add2(ac, w.am), sub2(xc, w.xm)), sz);
+  if (zhi) sz = fma2(fz2, mul2(add2(ac, w.ap), sub2(xc, w.xp)), sz);
+  return sub2(bb, fma2(fx2, sx, fma2(fy2, sy, sz)));
+}
+
+__global__ void __launch_bounds__(TP* TR, 3) k_restrict_pairs(Grid3 g, const float* __restrict__ a,
                                                            const float* __restrict__ b,
                                                            const float* __restrict__ x, float* __restrict__ coarse,
                                                            int kchunk) {
-  __shared__ float hand[2][TR / 2][TP];
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int nxc = nx / 2, nyc = ny / 2, nzc = nz / 2;
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tx = threadIdx.x;
   const int ip = blockIdx.x * TP + tx;
-  const int j = blockIdx.y * TR + ty;
+  const int jc = blockIdx.y * TR + threadIdx.y;  // coarse row
+  const int j0 = 2 * jc;                          // its first fine row
   const int kc0 = blockIdx.z * kchunk, kc1 = min(nzc, kc0 + kchunk);
-  const bool act = ip < nxc && j < ny;
+  const bool act = ip < nxc && jc < nyc;
   const int i0 = 2 * ip;
   // offsets in 32 bits: the launcher keeps nz + 4 planes of cells below 2^31
   const int pl2 = (int)(g.plane() >> 1);
-  const int q = act ? (j * nx + i0) >> 1 : 0;  // pair offset in a plane
+  const int rs = nx >> 1;                          // pairs per row
+  const int q = act ? (j0 * nx + i0) >> 1 : 0;    // pair offset of row j0 in a plane
   const float2* A2 = reinterpret_cast<const float2*>(a);
   const float2* X2 = reinterpret_cast<const float2*>(x);
   const float2* B2 = reinterpret_cast<const float2*>(b);
   const float mxl = i0 > 0 ? 1.f : 0.f, mxr = i0 + 2 < nx ? 1.f : 0.f;
-  const float my0 = j > 0 ? 1.f : 0.f, my1 = j < ny - 1 ? 1.f : 0.f;
-  const bool ldl = act && tx == 0 && i0 > 0;        // left neighbour outside the warp
+  const float ms = j0 > 0 ? 1.f : 0.f, mn = j0 + 2 < ny ? 1.f : 0.f;  // faces below row j0, above row j0 + 1
+  const bool ldl = act && tx == 0 && i0 > 0;            // left neighbour outside the warp
   const bool ldr = act && tx == TP - 1 && i0 + 2 < nx;  // right neighbour outside the warp
-  const bool lds = act && j > 0, ldn = act && j < ny - 1;
-  const float2 fx2 = f2(g.fx, g.fx), fy2 = f2(g.fy, g.fy), fz2 = f2(g.fz, g.fz), fp2 = f2(g.fp, g.fp);
+  const bool lds = act && j0 > 0, ldn = act && j0 + 2 < ny;
   const float2 z2 = f2(0.f, 0.f);
-  auto load = [&](const float2* P, int k) { return (act && k >= 0 && k < nz) ? __ldg(P + (k * pl2 + q)) : z2; };
+  auto load = [&](const float2* P, int k, int row) {
+    return (act && k >= 0 && k < nz) ? __ldg(P + (k * pl2 + q + row * rs)) : z2;
+  };
 
   const int k0 = 2 * kc0, k1 = 2 * kc1;
-  float2 xm = load(X2, k0 - 1), xc = load(X2, k0), xp = load(X2, k0 + 1);
-  float2 am = load(A2, k0 - 1), ac = load(A2, k0), ap = load(A2, k0 + 1);
+  RowWin w0{load(X2, k0 - 1, 0), load(X2, k0, 0), load(X2, k0 + 1, 0),
+            load(A2, k0 - 1, 0), load(A2, k0, 0), load(A2, k0 + 1, 0)};
+  RowWin w1{load(X2, k0 - 1, 1), load(X2, k0, 1), load(X2, k0 + 1, 1),
+            load(A2, k0 - 1, 1), load(A2, k0, 1), load(A2, k0 + 1, 1)};
   float s = 0.f;
-  int slot = 0;
   for (int k = k0; k < k1; ++k) {
-    const float2 xq = load(X2, k + 2), aq = load(A2, k + 2);
+    const float2 xq0 = load(X2, k + 2, 0), aq0 = load(A2, k + 2, 0);
+    const float2 xq1 = load(X2, k + 2, 1), aq1 = load(A2, k + 2, 1);
     const int o = k * pl2 + q;
-    const float2 bb = act ? __ldg(B2 + o) : z2;
-    const float2 xs = lds ? __ldg(X2 + o - nx / 2) : z2, as = lds ? __ldg(A2 + o - nx / 2) : z2;
-    const float2 xn = ldn ? __ldg(X2 + o + nx / 2) : z2, an = ldn ? __ldg(A2 + o + nx / 2) : z2;
+    const float2 b0 = act ? __ldg(B2 + o) : z2, b1 = act ? __ldg(B2 + o + rs) : z2;
+    const float2 xs = lds ? __ldg(X2 + o - rs) : z2, as = lds ? __ldg(A2 + o - rs) : z2;
+    const float2 xn = ldn ? __ldg(X2 + o + 2 * rs) : z2, an = ldn ? __ldg(A2 + o + 2 * rs) : z2;
     // x-neighbours: lane - 1 holds cell i0 - 1 in .y, lane + 1 holds i0 + 2 in .x
-    float xl = __shfl_up_sync(FULL, xc.y, 1), al = __shfl_up_sync(FULL, ac.y, 1);
-    float xr = __shfl_down_sync(FULL, xc.x, 1), ar = __shfl_down_sync(FULL, ac.x, 1);
-    const float* xs1 = x + 2 * o;  // the pair's first cell
-    const float* as1 = a + 2 * o;
+    float xl0 = __shfl_up_sync(FULL, w0.xc.y, 1), al0 = __shfl_up_sync(FULL, w0.ac.y, 1);
+    float xr0 = __shfl_down_sync(FULL, w0.xc.x, 1), ar0 = __shfl_down_sync(FULL, w0.ac.x, 1);
+    float xl1 = __shfl_up_sync(FULL, w1.xc.y, 1), al1 = __shfl_up_sync(FULL, w1.ac.y, 1);
+    float xr1 = __shfl_down_sync(FULL, w1.xc.x, 1), ar1 = __shfl_down_sync(FULL, w1.ac.x, 1);
     if (tx == 0) {
-      xl = ldl ? __ldg(xs1 - 1) : 0.f;
-      al = ldl ? __ldg(as1 - 1) : 0.f;
+      xl0 = ldl ? __ldg(x + 2 * o - 1) : 0.f;
+      al0 = ldl ? __ldg(a + 2 * o - 1) : 0.f;
+      xl1 = ldl ? __ldg(x + 2 * (o + rs) - 1) : 0.f;
+      al1 = ldl ? __ldg(a + 2 * (o + rs) - 1) : 0.f;
     }
     if (tx == TP - 1) {
-      xr = ldr ? __ldg(xs1 + 2) : 0.f;
-      ar = ldr ? __ldg(as1 + 2) : 0.f;
+      xr0 = ldr ? __ldg(x + 2 * o + 2) : 0.f;
+      ar0 = ldr ? __ldg(a + 2 * o + 2) : 0.f;
+      xr1 = ldr ? __ldg(x + 2 * (o + rs) + 2) : 0.f;
+      ar1 = ldr ? __ldg(a + 2 * (o + rs) + 2) : 0.f;
     }
     if (act) {
       const bool zlo = k > 0, zhi = k < nz - 1;
-      const float2 fxm = mul2(add2(ac, f2(al, ac.x)), f2(mxl, 1.f));
-      const float2 fxp = mul2(add2(ac, f2(ac.y, ar)), f2(1.f, mxr));
-      float2 sx = mul2(fxm, sub2(xc, f2(xl, xc.x)));
-      sx = fma2(fxp, sub2(xc, f2(xc.y, xr)), sx);
-      float2 sy = mul2(mul2(add2(ac, as), f2(my0, my0)), sub2(xc, xs));
-      sy = fma2(mul2(add2(ac, an), f2(my1, my1)), sub2(xc, xn), sy);
-      const float2 plate = add2(zlo ? z2 : ac, zhi ? z2 : ac);
-      float2 sz = mul2(fp2, mul2(plate, xc));
-      if (zlo) sz = fma2(fz2, mul2(add2(ac, am), sub2(xc, xm)), sz);
-      if (zhi) sz = fma2(fz2, mul2(add2(ac, ap), sub2(xc, xp)), sz);
-      const float2 r = sub2(bb, fma2(fx2, sx, fma2(fy2, sy, sz)));
-      s += r.x + r.y;
+      // row j0: below it row j0 - 1, above it row j0 + 1; row j0 + 1: below j0, above j0 + 2
+      const float2 r0 = pair_residual(g, w0, b0, xl0, al0, xr0, ar0, mxl, mxr, as, xs, ms, w1.ac, w1.xc, 1.f, zlo,
+                                      zhi);
+      const float2 r1 = pair_residual(g, w1, b1, xl1, al1, xr1, ar1, mxl, mxr, w0.ac, w0.xc, 1.f, an, xn, mn, zlo,
+                                      zhi);
+      s += (r0.x + r0.y) + (r1.x + r1.y);
     }
     if (k & 1) {
-      if (ty & 1) hand[slot][ty >> 1][tx] = s;
-      __syncthreads();
-      if (!(ty & 1) && act) {
-        const int kc = k >> 1;
-        coarse[(kc * nyc + (j >> 1)) * nxc + ip] = 0.125f * (s + hand[slot][ty >> 1][tx]);
-      }
+      if (act) coarse[((k >> 1) * nyc + jc) * nxc + ip] = 0.125f * s;
       s = 0.f;
-      slot ^= 1;
     }
-    xm = xc; xc = xp; xp = xq;
-    am = ac; ac = ap; ap = aq;
+    w0.xm = w0.xc; w0.xc = w0.xp; w0.xp = xq0;
+    w0.am = w0.ac; w0.ac = w0.ap; w0.ap = aq0;
+    w1.xm = w1.xc; w1.xc = w1.xp; w1.xp = xq1;
+    w1.am = w1.ac; w1.ac = w1.ap; w1.ap = aq1;
   }
 }
 
@@ -209,9 +231,10 @@ __global__ void __launch_bounds__(TP* TR) k_prolong_pairs(Grid3 g, const float* 
 
 cudaError_t launch_restrict_pairs(const Grid3& g, const float* a, const float* b, const float* x, float* coarse,
                                   cudaStream_t s) {
-  if (!pair_aligned(a) || !pair_aligned(b) || !pair_aligned(x) || g.nx % 2) return cudaErrorMisalignedAddress;
+  if (!pair_aligned(a) || !pair_aligned(b) || !pair_aligned(x) || g.nx % 2 || g.ny % 2)
+    return cudaErrorMisalignedAddress;
   if (!cells_fit_int32(g)) return cudaErrorInvalidValue;
-  const int gx = (g.nx / 2 + TP - 1) / TP, gy = (g.ny + TR - 1) / TR;
+  const int gx = (g.nx / 2 + TP - 1) / TP, gy = (g.ny / 2 + TR - 1) / TR;  // one coarse row per thread
   const int nzc = g.nz / 2;
   const int zc = z_chunks((long long)gx * gy, nzc, 4);
   const int kchunk = (nzc + zc - 1) / zc;
