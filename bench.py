@@ -220,6 +220,37 @@ def cpu_baseline(args, steps=1):
                       f"median of {steps} step(s) of {sec:.2f} s, {iters[-1]} FGMRES iterations, numpy single thread"}
 
 
+def _oracle_step_seconds(task):
+    """One oracle step (set-up + solve + E) in a worker process; its seconds."""
+    workload, kappa, n = task
+    from oracle import gmg_oracle as O
+    from streamer_inputs import make_inputs
+    inp = make_inputs(workload, n=n, kappa=kappa)
+    params = O.OracleParams()
+    grid = O.Grid(n, n, n)
+    t0 = time.perf_counter()
+    phi, info, _ = O.solve(params, inp["a"], inp["f"])
+    O.field_from_potential(grid, phi, params.phi_bottom, params.phi_top)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(args):
+    """The same oracle step, as it stands, run as independent copies, one per
+    host core, in spawned worker processes (single-threaded numpy each): the
+    host's aggregate oracle throughput on all its cores."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"   # read by each worker's numpy at import
+    with mp.get_context("spawn").Pool(cores) as pool:
+        secs = pool.map(_oracle_step_seconds, [(args.workload, args.kappa, SAMPLE_N)] * cores)
+    cells = SAMPLE_N**3
+    slowest = max(secs)
+    return {"value": cores * cells / slowest / 1e6, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} independent copies of the {args.workload} step at {SAMPLE_N}^3, one per core "
+                      f"(spawned processes, single-threaded numpy), slowest copy {slowest:.2f} s"}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -385,6 +416,7 @@ def run_ours(args, dist):
 
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(args)
+        out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args)
     ctx.close()
     return out
 
