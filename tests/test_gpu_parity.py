@@ -975,18 +975,20 @@ def test_transport_stage_rejects_aliasing():
         gmg.transport_stage(p, x[0], x[1], x[2], x[3], phi, 1.0, x[0], x[0], mu_e=1.0, mu_p=1.0)   # out_e = out_p
 
 
-@pytest.mark.parametrize("shape,lengths", [(RAGGED, (1.0, 1.0, 1.0)), ((48, 20, 72), (1.0, 0.5, 1.5))])
-def test_transport_step_matches_two_stages_and_oracle(shape, lengths):
+@pytest.mark.parametrize("shape,lengths,mu_e", [(RAGGED, (1.0, 1.0, 1.0), MU_E), ((48, 20, 72), (1.0, 0.5, 1.5), MU_E),
+                                                 ((48, 20, 72), (1.0, 0.5, 1.5), 0.0)])
+def test_transport_step_matches_two_stages_and_oracle(shape, lengths, mu_e):
     """Predictor + corrector with the shared ionization rate: bit-identical to
-    the two transport_stage calls, and to the oracle's stages within 1e-12."""
+    the two transport_stage calls, and to the oracle's stages within 1e-12
+    (mu_e = 0 takes the kernel variant without the diffusion on the faces)."""
     nz, ny, nx = shape
     grid = O.Grid(nx, ny, nz, *lengths)
     ne, npos = _densities(shape, 380)
     phi = 3e4 * random_field(381, shape) + 1e4
     p = _params(shape, lx=lengths[0], ly=lengths[1], lz=lengths[2], phi_bottom=-1e3, phi_top=4e4)
-    kw = dict(mu_e=MU_E, mu_p=MU_P, diffusion=DIFFUSION)
+    kw = dict(mu_e=mu_e, mu_p=MU_P, diffusion=DIFFUSION)
     tau = 2e-12
-    args = (phi, -1e3, 4e4, MU_E, MU_P, DIFFUSION)
+    args = (phi, -1e3, 4e4, mu_e, MU_P, DIFFUSION)
     he_ref, hp_ref = O.transport_stage(grid, ne, npos, ne, npos, *args, 0.5 * tau)
     ref_e, ref_p = O.transport_stage(grid, ne, npos, he_ref, hp_ref, *args, tau)
     z = lambda: torch.empty(shape, dtype=torch.float64, device=DEV)   # noqa: E731
@@ -1003,7 +1005,7 @@ def test_transport_step_matches_two_stages_and_oracle(shape, lengths):
     # the rate is alpha(|E|) mu_e |E| of the central-difference field
     ex, ey, ez = O.field_from_potential(grid, phi, -1e3, 4e4)
     eabs = np.sqrt(ex * ex + ey * ey + ez * ez)
-    np.testing.assert_allclose(_np(rate), O.ionization_coefficient(eabs) * MU_E * eabs, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(_np(rate), O.ionization_coefficient(eabs) * mu_e * eabs, rtol=1e-12, atol=0)
     # in place on n
     be, bp = _t(ne), _t(npos)
     gmg.transport_step(p, be, bp, _t(phi), tau, he, hp, be, bp, rate, **kw)
