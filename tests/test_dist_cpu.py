@@ -60,3 +60,23 @@ def test_two_rank_barrier_max_and_reference_rank_handling():
     out = sorted(q.get(timeout=5) for _ in range(2))
     assert [o[1] for o in out] == [11.0, 11.0]   # both ranks see the max
     assert out[1][2] is None                      # rank 1 does no reference work
+
+
+def test_reference_arm_json_line():
+    """bench.py --impl reference on one rank: the oracle timed on the host,
+    printed as one JSON line with the contract's keys (the ratio's divisor)."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = [ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1]
+    d = json.loads(line)
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 0
+    assert d["unit"] == "Mcells/s" and d["higher_is_better"] is True and d["value"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"] and d["metric"]
