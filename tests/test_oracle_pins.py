@@ -876,18 +876,164 @@ def test_stable_step_keeps_densities_non_negative():
     assert e1.min() >= -1e-6 * ne.max() and p1.min() >= -1e-6 * npos.max()
 
 
-def test_semi_implicit_step_runs_the_solve_and_both_stages():
-    shape = (16, 16, 16)
-    from streamer_inputs import streamer_densities, MU_E, MU_P, DIFFUSION, PHI0
-    ne, npos = streamer_densities(shape, 0)
-    params = O.OracleParams(coarse_min=4, phi_top=PHI0, cycle="auto")
+def _linear_between_plates(shape, g_b, g_t, lz=1.0):
+    """phi_k = g_b + (g_t - g_b) z_k / lz at the cell centres z_k = (k + 1/2) hz:
+    the exact discrete potential for constant a, f = 0 and plate data g_b, g_t."""
+    grid = _grid(shape, (1.0, 1.0, lz))
+    z = (np.arange(shape[0]) + 0.5) * grid.hz
+    phi = np.broadcast_to((g_b + (g_t - g_b) * z / lz)[:, None, None], shape).copy()
+    return grid, phi
+
+
+def test_face_fields_at_the_plates_and_side_walls():
+    """Plate faces use the Dirichlet ghost 2g - phi_p (Sec. 2.2 ghost cells; the
+    potential's plate condition of Sec. 2), side-wall faces the mirror ghost of
+    the homogeneous Neumann condition.  With phi linear between the plates, every
+    z face, both plate faces included, carries -(g_t - g_b)/lz; a ghost g - phi
+    would give -(g_b + s)/hz and (g_t - s)/hz on the plates (s the potential
+    step of one cell), so both plate data are non-zero here.  A side-wall face
+    carries no field whatever phi is."""
+    g_b, g_t, lz = 3.0, -5.0, 2.0
+    shape = (9, 4, 5)
+    grid, phi = _linear_between_plates(shape, g_b, g_t, lz)
+    fx, fy, fz = O.face_fields(grid, phi, g_b, g_t)
+    assert fz.shape == (10, 4, 5)
+    np.testing.assert_allclose(fz, -(g_t - g_b) / lz, rtol=1e-13)
+    np.testing.assert_array_equal(fx, 0.0)
+    np.testing.assert_array_equal(fy, 0.0)
+    # side walls under a potential that varies along every axis
+    rng = np.random.default_rng(11)
+    phi = rng.standard_normal(shape)
+    fx, fy, fz = O.face_fields(grid, phi, g_b, g_t)
+    assert fx.shape == (9, 4, 6) and fy.shape == (9, 5, 5)
+    for wall in (fx[:, :, 0], fx[:, :, -1], fy[:, 0, :], fy[:, -1, :]):
+        np.testing.assert_array_equal(wall, 0.0)
+    # a plate face by hand: bottom ghost 2 g_b - phi_0, top ghost 2 g_t - phi_{m-1}
+    np.testing.assert_allclose(fz[0], -(phi[0] - (2 * g_b - phi[0])) / grid.hz, rtol=1e-14)
+    np.testing.assert_allclose(fz[-1], -((2 * g_t - phi[-1]) - phi[-1]) / grid.hz, rtol=1e-14)
+
+
+def _drift_only(grid, ne, npos, phi, g_b, g_t, mu_e, mu_p):
+    """transport_rhs with the diffusion off, in a field weak enough (|E| <= 2 kV/cm)
+    that the ionization source alpha(|E|) mu_e |E| n_e is below 1e-40 of the
+    density per second (alpha = 5.7 P exp(-260 P/|E|), Sec. 5.2): what is left
+    is the drift -div(v n) alone."""
+    ex, ey, ez = O.field_from_potential(grid, phi, g_b, g_t)
+    eabs = np.sqrt(ex * ex + ey * ey + ez * ez).max()
+    assert eabs <= 2.0e3
+    assert 5.7 * 760.0 * np.exp(-260.0 * 760.0 / eabs) * mu_e * eabs < 1e-40
+    return O.transport_rhs(grid, ne, npos, phi, g_b, g_t, mu_e, mu_p, (0.0, 0.0, 0.0))
+
+
+def test_drift_through_the_plates_with_neumann_density_ghosts():
+    """Drift across the plates.  The densities take homogeneous Neumann ghosts
+    at every boundary (the model's conditions, Sec. 2: all boundaries for n_e,
+    the inflow boundaries for n_p), so a face on a plate carries the upwind
+    ghost's density, and the MUSCL slope of a boundary cell is zero (one of its
+    two differences vanishes).  With phi linear between the plates the field is
+    E_z = -(g_t - g_b)/lz on every z face, plates included.  Electrons drift
+    at v_e = -mu_e E_z (up for g_t > g_b), ions at v_p = mu_p E_z (down).
+
+    For n_k = n0 + c k (k = 0..m-1) the fluxes are worked out by hand:
+    electrons (upwind below): F_0 = F_1 = v n_0, F_k = v (n_{k-1} + c/2) for
+    2 <= k <= m-1, F_m = v n_{m-1}; ions (upwind above): F_0 = v n_0,
+    F_k = v (n_k - c/2) for 1 <= k <= m-2, F_{m-1} = F_m = v n_{m-1}.  So
+    -div(v n) per cell is, bottom to top, electrons: 0, -3vc/2h, -vc/h ...,
+    -vc/2h; ions: -vc/2h, -vc/h ..., -3vc/2h, 0.  A plate that lets no flux
+    through, or a plate ghost g - phi in the field, fails the end cells."""
+    m = 10
+    shape = (m, 3, 4)
+    g_b, g_t = 200.0, 1200.0
+    grid, phi = _linear_between_plates(shape, g_b, g_t)
+    h = grid.hz
+    mu_e, mu_p = 380.0, 3.4
+    ez = -(g_t - g_b)
+    c, n0 = 4.0e10, 1.0e12
+    k = np.arange(m, dtype=np.float64)
+    nk = np.broadcast_to((n0 + c * k)[:, None, None], shape).copy()
+    de, dp = _drift_only(grid, nk, nk, phi, g_b, g_t, mu_e, mu_p)
+    ve, vp = -mu_e * ez, mu_p * ez
+    assert ve > 0 > vp
+    want_e = np.full(m, -ve * c / h)
+    want_e[0], want_e[1], want_e[-1] = 0.0, -1.5 * ve * c / h, -0.5 * ve * c / h
+    want_p = np.full(m, -vp * c / h)
+    want_p[0], want_p[-2], want_p[-1] = -0.5 * vp * c / h, -1.5 * vp * c / h, 0.0
+    scale = abs(ve) * c / h
+    np.testing.assert_allclose(de, np.broadcast_to(want_e[:, None, None], shape), rtol=0,
+                               atol=1e-12 * scale)
+    np.testing.assert_allclose(dp, np.broadcast_to(want_p[:, None, None], shape), rtol=0,
+                               atol=1e-12 * abs(vp) * c / h)
+    # a uniform density: the plate inflow carries the ghost's density, so no cell changes
+    flat = np.full(shape, n0)
+    de, dp = _drift_only(grid, flat, flat, phi, g_b, g_t, mu_e, mu_p)
+    np.testing.assert_allclose(de, 0.0, atol=1e-13 * ve * n0 / h)
+    np.testing.assert_allclose(dp, 0.0, atol=1e-13 * abs(vp) * n0 / h)
+
+
+def test_drift_against_the_side_walls():
+    """Drift towards a side wall.  phi = -e0 x gives E_x = e0 on the interior
+    x faces and none on the walls (mirror ghost of the Neumann condition), so
+    nothing crosses a wall.  Electrons move at v = -mu_e e0 (towards x = 0),
+    ions at mu_p e0 (away from it).  For n_i = n0 + c i and electrons (upwind
+    on the right): F_i = v (n_i - c/2) for 1 <= i <= m-2, F_{m-1} = v n_{m-1},
+    walls 0; so -div(v n) is -v (n_0 + c/2)/h in the first cell (inflow piles
+    up at the wall), -v c/h inside, -3vc/2h in cell m-2 and v n_{m-1}/h in the
+    last cell (outflow, no inflow).  Ions (upwind on the left): F_1 = v n_0,
+    F_i = v (n_{i-1} + c/2) for 2 <= i <= m-1; -div: -v n_0/h, -3vc/2h, -vc/h
+    ..., and v (n_{m-2} + c/2)/h in the last cell.  The plates (phi = 0 there,
+    so their faces carry a field) are kept out: layers 1..m-2 only."""
+    m = 11
+    grid, phi, e0 = _uniform_field_case(m=m, e0=50.0)
+    h = grid.hx
+    mu_e, mu_p = 380.0, 3.4
+    c, n0 = 3.0e10, 1.0e12
+    n = n0 + c * np.arange(m, dtype=np.float64)
+    dens = np.broadcast_to(n, grid.shape).copy()
+    de, dp = _drift_only(grid, dens, dens, phi, 0.0, 0.0, mu_e, mu_p)
+    de, dp = de[1:-1], dp[1:-1]
+    v = -mu_e * e0
+    want_e = np.full(m, -v * c / h)
+    want_e[0] = -v * (n[0] + 0.5 * c) / h
+    want_e[-2] = -1.5 * v * c / h
+    want_e[-1] = v * n[-1] / h
+    u = mu_p * e0
+    want_p = np.full(m, -u * c / h)
+    want_p[0] = -u * n[0] / h
+    want_p[1] = -1.5 * u * c / h
+    want_p[-1] = u * (n[-2] + 0.5 * c) / h
+    np.testing.assert_allclose(de, np.broadcast_to(want_e, de.shape), rtol=1e-12, atol=1e-12 * abs(v) * c / h)
+    np.testing.assert_allclose(dp, np.broadcast_to(want_p, dp.shape), rtol=1e-12, atol=1e-12 * u * c / h)
+
+
+def test_semi_implicit_step_on_a_neutral_uniform_plasma():
+    """The whole step of eqs. (e1)-(e2) in closed form.  Uniform n_e = n_p = n0:
+    eq. (semi2) gives f = 0 and a constant coefficient, so the discrete
+    potential is linear between the plates (exact for e18 with the 2g - phi
+    ghost); E_z = -phi_0 on every face and cell; the drift of a uniform
+    density cancels in every cell (Neumann ghosts at the plates), diffusion
+    vanishes, and only the ionization source lam n_e = alpha(|E|) mu_e |E| n_e
+    acts, so the predictor-corrector gives n_e (1 + tau lam + (tau lam)^2/2) and
+    n_p + tau lam n_e (1 + tau lam/2) in every cell, boundary cells included."""
+    from streamer_inputs import MU_E, MU_P, DIFFUSION, PHI0
+    shape = (16, 8, 8)
+    n0 = 5.0e13
+    ne = np.full(shape, n0)
+    npos = np.full(shape, n0)
+    tau = 2e-12
+    params = O.OracleParams(coarse_min=4, phi_top=PHI0, rtol=1e-13)
     e_over = O.ELEMENTARY_CHARGE / O.VACUUM_PERMITTIVITY_CM
-    ne1, np1, phi, info = O.semi_implicit_step(params, ne, npos, 2e-12, MU_E, MU_P, DIFFUSION, e_over)
-    assert info.converged and info.true_rel_residual < 1e-8
-    grid = _grid(shape)
-    args = (phi, 0.0, PHI0, MU_E, MU_P, DIFFUSION)
-    he, hp = O.transport_stage(grid, ne, npos, ne, npos, *args, 1e-12)
-    e_ref, p_ref = O.transport_stage(grid, ne, npos, he, hp, *args, 2e-12)
-    np.testing.assert_array_equal(ne1, e_ref)
-    np.testing.assert_array_equal(np1, p_ref)
-    assert np.all(np.isfinite(ne1)) and not np.array_equal(ne1, ne)
+    ne1, np1, phi, info = O.semi_implicit_step(params, ne, npos, tau, MU_E, MU_P, DIFFUSION, e_over)
+    assert info.converged
+    _, lin = _linear_between_plates(shape, 0.0, PHI0)
+    np.testing.assert_allclose(phi, lin, rtol=0, atol=1e-10 * PHI0)
+    lam = IONIZATION_RATE(PHI0, abs(MU_E))
+    tl = tau * lam
+    assert 1e-4 < tl < 1e-1
+    np.testing.assert_allclose(ne1, n0 * (1 + tl + 0.5 * tl * tl), rtol=1e-12)
+    np.testing.assert_allclose(np1, n0 + tl * n0 * (1 + 0.5 * tl), rtol=1e-12)
+
+
+def IONIZATION_RATE(e_abs, mu_e):
+    """alpha(|E|) mu_e |E| with alpha = 5.7 P exp(-260 P/|E|) cm^-1, P = 760 Torr
+    (Sec. 5.2), written out for the closed-form step."""
+    return 5.7 * 760.0 * np.exp(-260.0 * 760.0 / e_abs) * mu_e * e_abs
