@@ -427,11 +427,12 @@ gmg_status gmg_profile_get(gmg_ctx* ctx, int k, const char** name, long long* la
  * Scratch: one file-scope __device__ array sized for
  * GMG_NOALLOC_MAX_UNKNOWNS unknowns (about 6 MB), held by every GPU that
  * loads the library until the process exits; the call makes no device or
- * pinned-host allocation.  The array's address is looked up on the first call
- * made on each device (with that device current).  Every call overwrites the
- * whole array; calls that overlap on the GPU race on it.
+ * pinned-host allocation.  Each call looks up the array's address on the
+ * current device (cudaGetSymbolAddress), so it is valid on any device and
+ * after a device reset.  Every call overwrites the whole array; calls that
+ * overlap on the GPU race on it.
  * Errors: GMG_ERR_ARG if nx*ny*nz > GMG_NOALLOC_MAX_UNKNOWNS or an argument is
- * invalid, GMG_ERR_BREAKDOWN if the operator is not positive definite,
+ * invalid (a side below 1, a length not positive or not finite), GMG_ERR_BREAKDOWN if the operator is not positive definite,
  * GMG_ERR_CUDA.  Synchronises the stream once (to read the factorisation
  * status). */
 #define GMG_NOALLOC_MAX_UNKNOWNS 512

@@ -13,7 +13,7 @@
 // The array is shared by every call: a call overwrites all of it before
 // reading it, and calls that overlap on the GPU (two streams, two host
 // threads) race on it.
-#include <mutex>
+#include <cmath>
 
 #include "../../include/gmg.h"
 #include "gmg_internal.cuh"
@@ -29,25 +29,15 @@ constexpr size_t SCRATCH_DOUBLES = 3 * MAT + 32;
 
 static __device__ __align__(256) double g_noalloc_scratch[SCRATCH_DOUBLES];
 
-constexpr int MAX_DEVICES = 64;
-double* g_scratch_ptr[MAX_DEVICES] = {};
-std::mutex g_scratch_mutex;
-
-// Device address of the scratch array on the current device (looked up once
-// per device with that device current).
+// Device address of the scratch array on the current device.  Looked up on
+// every call, with the calling device current: the lookup is cheap, and a
+// cached address would go stale if the module were loaded again (for
+// instance after cudaDeviceReset).
 cudaError_t scratch_address(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -64,6 +54,7 @@ extern "C" gmg_status gmg_coarse_solve_noalloc(const gmg_params* p, const double
   if (!p || !a_dev || !b_dev || !x_dev) return GMG_ERR_ARG;
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return GMG_ERR_ARG;
   if (!(p->lx > 0) || !(p->ly > 0) || !(p->lz > 0)) return GMG_ERR_ARG;
+  if (!std::isfinite(p->lx) || !std::isfinite(p->ly) || !std::isfinite(p->lz)) return GMG_ERR_ARG;
   const long long n = (long long)p->nx * p->ny * p->nz;
   if (n > NMAX) return GMG_ERR_ARG;  // beyond the fixed scratch: nx*ny*nz <= GMG_NOALLOC_MAX_UNKNOWNS
   double* scratch = nullptr;

@@ -644,16 +644,19 @@ def test_adjoint_grad_kernel_matches_oracle():
 
 
 def test_autograd_finite_differences_and_cpu_adjoint():
-    """Central differences on 64 seeded entries of a 32^3 instance.
+    """Central differences on 64 seeded entries of a 32^3 instance, at the
+    configured step of 1e-6 relative for the coefficient a.
 
     L is linear in f, so a large step (1 or |f_q|) is exact up to the solve
-    error.  For a, the step is 1e-3 relative: the truncation error is ~1e-6
-    relative, while a 1e-6 step would sit below the noise floor left by the
-    solve tolerance (|dL| ~ |lambda . r| with ||r|| ~ rtol ||b||)."""
+    error.  For a, the 1e-6 step leaves a truncation error near 1e-12; what
+    limits the check is the solve error of L (|dL| ~ |lambda . r| with
+    ||r|| ~ rtol ||b||), divided by the step, so the forward solves run to
+    rtol = 1e-13 (the flexible FP64 outer loop reaches it around the FP32
+    V-cycle)."""
     from paper_1812_08606_gb300 import PoissonSolver
     inp = make_inputs("adjoint", n=32)
     shape = inp["a"].shape
-    solver = PoissonSolver(shape, rtol=1e-12, precision=gmg.GMG_PREC_MIXED)
+    solver = PoissonSolver(shape, rtol=1e-13, precision=gmg.GMG_PREC_MIXED, max_iters=60)
     a = _t(inp["a"]).requires_grad_(True)
     f = _t(inp["f"]).requires_grad_(True)
     w = _t(inp["w"])
@@ -672,7 +675,7 @@ def test_autograd_finite_differences_and_cpu_adjoint():
     for q in idx:
         for grad, base, which in ((ga, base_a, "a"), (gf, base_f, "f")):
             v = abs(float(base.view(-1)[q]))
-            h = 1e-3 * v if which == "a" else max(v, 1.0)
+            h = 1e-6 * v if which == "a" else max(v, 1.0)
             plus, minus = base.clone(), base.clone()
             plus.view(-1)[q] += h
             minus.view(-1)[q] -= h
@@ -693,6 +696,53 @@ def test_autograd_finite_differences_and_cpu_adjoint():
     gmg.fgmres_solve(ctx, base_f, x1, homogeneous_bc=True)
     gmg.fgmres_solve(ctx, w, x2, homogeneous_bc=True)
     assert float((w * x1).sum()) == pytest.approx(float((base_f * x2).sum()), rel=1e-10)
+
+
+def test_autograd_raises_when_a_solve_does_not_converge():
+    """A forward or adjoint solve stopped by max_iters must not hand back phi
+    or a gradient as if it were converged."""
+    from paper_1812_08606_gb300 import PoissonSolver
+    inp = make_inputs("adjoint", n=16)
+    shape = inp["a"].shape
+    solver = PoissonSolver(shape, rtol=1e-12, max_iters=1, coarse_min=2)
+    a = _t(inp["a"]).requires_grad_(True)
+    f = _t(inp["f"]).requires_grad_(True)
+    with pytest.raises(gmg.GMGError) as e:
+        solver.solve(a, f)
+    assert e.value.status == gmg.GMG_ERR_NOT_CONVERGED
+    # the adjoint solve alone: a forward solve that converges, an adjoint capped at one step
+    solver2 = PoissonSolver(shape, rtol=1e-12, max_iters=40, coarse_min=2)
+    phi = solver2.solve(a, f)
+    assert solver2.last_info.converged
+    solver2.params.max_iters = 1
+    solver2.close()
+    solver2.ctx = None
+    solver2.set_coefficient(a)   # a new context with the one-step cap
+    with pytest.raises(gmg.GMGError):
+        torch.autograd.grad((_t(inp["w"]) * phi).sum(), (a, f))
+    # non-strict: the unconverged result comes back with its info
+    loose = PoissonSolver(shape, rtol=1e-12, max_iters=1, coarse_min=2, strict=False)
+    loose.solve(a.detach(), f.detach())
+    assert not loose.last_info.converged
+
+
+def test_autograd_follows_the_current_torch_stream():
+    """With stream=None the library runs on whatever stream is current at the
+    call, so the solve sees f written on a side stream just before it."""
+    from paper_1812_08606_gb300 import PoissonSolver
+    inp = make_inputs("adjoint", n=16)
+    shape = inp["a"].shape
+    solver = PoissonSolver(shape, rtol=1e-10, coarse_min=2)
+    a = _t(inp["a"])
+    ref = solver.solve(a, _t(inp["f"])).clone()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        f = torch.empty(shape, dtype=torch.float64, device=DEV)
+        torch.cuda._sleep(2_000_000)    # keep the side stream busy before f is written
+        f.copy_(_t(inp["f"]))
+        phi = solver.solve(a, f)
+    side.synchronize()
+    assert _rel(_np(phi), _np(ref)) < 1e-12
 
 
 def test_autograd_matches_cpu_adjoint_64():

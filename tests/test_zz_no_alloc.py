@@ -71,3 +71,15 @@ def test_noalloc_rejects_sizes_beyond_the_scratch():
     buf = torch.zeros(p.nx * p.ny * p.nz, dtype=torch.float64, device=DEV)
     st = lib.gmg_coarse_solve_noalloc(ctypes.byref(p), buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), None)
     assert st == gmg.GMG_ERR_ARG
+
+
+@pytest.mark.parametrize("field,value", [("lx", float("inf")), ("lz", float("nan")), ("ly", 0.0)])
+def test_noalloc_rejects_lengths_that_are_not_positive_and_finite(field, value):
+    """An infinite length would make the face coefficients vanish silently;
+    the call refuses it, as gmg_setup does."""
+    lib = gmg.load()
+    p = gmg.gmg_default_params(4, 4, 4)
+    setattr(p, field, value)
+    buf = torch.ones(64, dtype=torch.float64, device=DEV)
+    st = lib.gmg_coarse_solve_noalloc(ctypes.byref(p), buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), None)
+    assert st == gmg.GMG_ERR_ARG
