@@ -350,6 +350,12 @@ int gmg_num_levels(const gmg_ctx* ctx);
 gmg_status gmg_level_info(const gmg_ctx* ctx, int level, int* nx, int* ny, int* nz, double* lam_max,
                           double* lam_min);
 
+/* Replace the Chebyshev bounds of level l (1 <= l < gmg_num_levels) with
+ * lam_max > lam_min > 0 (both finite), until the next set-up renews them.
+ * Lets a test run the smoother (Sec. 3.2, eq. (qntn)) of both sides on one
+ * interval given from outside.  GMG_ERR_ARG otherwise. */
+gmg_status gmg_level_set_bounds(gmg_ctx* ctx, int level, double lam_max, double lam_min);
+
 /* Copy the FP64 coefficient of a level (8-child means of the finer level)
  * into out_dev (FP64, that level's size). */
 gmg_status gmg_level_coefficient(gmg_ctx* ctx, int level, double* out_dev);

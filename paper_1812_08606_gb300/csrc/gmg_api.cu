@@ -1751,6 +1751,15 @@ gmg_status gmg_level_info(const gmg_ctx* c, int level, int* nx, int* ny, int* nz
   return GMG_OK;
 }
 
+gmg_status gmg_level_set_bounds(gmg_ctx* c, int level, double lam_max, double lam_min) {
+  if (!c || level < 1 || level >= (int)c->lev.size()) return GMG_ERR_ARG;
+  if (!(lam_max > lam_min) || !(lam_min > 0) || !isfinite(lam_max)) return GMG_ERR_ARG;
+  LevelData& L = c->lev[level];
+  L.lam_max = lam_max;
+  L.lam_min = lam_min;
+  return GMG_OK;
+}
+
 gmg_status gmg_level_coefficient(gmg_ctx* c, int level, double* out_dev) {
   LevelData* L = level_ptr(c, level);
   if (!L || !out_dev) return GMG_ERR_ARG;

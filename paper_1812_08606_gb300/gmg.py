@@ -122,6 +122,7 @@ _SIGS = {
     "gmg_destroy": (None, [_P]),
     "gmg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gmg_num_levels": (ctypes.c_int, [_P]),
+    "gmg_level_set_bounds": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
     "gmg_level_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]),
@@ -369,6 +370,11 @@ def gmg_level_info(ctx: Context, level: int):
     _check(load().gmg_level_info(ctx.handle, int(level), ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(nz),
                                  ctypes.byref(lmax), ctypes.byref(lmin)), "gmg_level_info")
     return {"shape": (nz.value, ny.value, nx.value), "lam_max": lmax.value, "lam_min": lmin.value}
+
+
+def gmg_level_set_bounds(ctx: Context, level: int, lam_max: float, lam_min: float):
+    _check(load().gmg_level_set_bounds(ctx.handle, int(level), float(lam_max), float(lam_min)),
+           "gmg_level_set_bounds")
 
 
 def _level_n(ctx, level):

@@ -63,6 +63,25 @@ def _rel(x, ref):
     return np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300)
 
 
+def _maxrel(x, ref):
+    """Largest element-wise difference, relative to the largest |ref|."""
+    return float(np.abs(np.asarray(x) - np.asarray(ref)).max() / max(np.abs(ref).max(), 1e-300))
+
+
+# An element-wise bound beside every relative-norm bound: a norm can hide a few
+# wrong cells (a plate row, a tile seam) in a large grid, a maximum cannot.
+ELEMENT_FACTOR = 10.0
+
+
+def _close(x, ref, tol, what=""):
+    """Relative L2 error below tol and every element within ELEMENT_FACTOR * tol
+    of the largest |ref|; returns (l2, max) for printing."""
+    l2, mx = _rel(x, ref), _maxrel(x, ref)
+    assert l2 < tol, (what, "l2", l2, tol)
+    assert mx < ELEMENT_FACTOR * tol, (what, "max", mx, ELEMENT_FACTOR * tol)
+    return l2, mx
+
+
 def _oracle_hierarchy(a, p):
     op = O.OracleParams(lx=p.lx, ly=p.ly, lz=p.lz, phi_bottom=p.phi_bottom, phi_top=p.phi_top,
                         coarse_min=p.coarse_min, cheb_steps=p.cheb_steps, restart=p.restart,
@@ -91,7 +110,7 @@ def test_apply_operator_and_rhs_fp64(shape, lengths):
     gmg.apply_operator(ctx, _t(x), y)
     grid = _ogrid(shape, p)
     ref = O.apply_operator(grid, a, x)
-    assert _rel(_np(y), ref) < 1e-14
+    _close(_np(y), ref, 1e-14)
     b = torch.empty_like(y)
     gmg.assemble_rhs(ctx, _t(f), b)
     np.testing.assert_allclose(_np(b), O.assemble_rhs(grid, a, f, 0.3, -2.0), rtol=1e-14, atol=1e-12)
@@ -171,7 +190,7 @@ def test_level_coefficients_and_operators(prec):
         gmg.gmg_level_apply(ctx, lev, _t(xin, dt), y)
         ref = O.apply_operator(_ogrid(s), ain, xin)
         tol = 1e-14 if dt == torch.float64 else 5e-6
-        assert _rel(_np(y), ref) < tol, lev
+        _close(_np(y), ref, tol, lev)
         if lev > 0:
             ref_a = O.coarsen_coefficient(ref_a)
 
@@ -193,8 +212,11 @@ def test_smoother_preconditioner_and_chebyshev(prec, pc):
     fp32 = dt == torch.float32
     q = (lambda v: v.astype(np.float32).astype(np.float64)) if fp32 else (lambda v: v)
     tol = 2e-5 if fp32 else 1e-13
+    # the oracle's own bounds drive both sides' Chebyshev steps
+    hier = O.build_hierarchy(_ogrid(shape), a, op)
     oa = a
     for lev in range(gmg.gmg_num_levels(ctx) - 1, 0, -1):
+        gmg.gmg_level_set_bounds(ctx, lev, hier.levels[lev].lam_max, hier.levels[lev].lam_min)
         info = gmg.gmg_level_info(ctx, lev)
         s = info["shape"]
         g = _ogrid(s)
@@ -202,17 +224,24 @@ def test_smoother_preconditioner_and_chebyshev(prec, pc):
         z = torch.empty(s, dtype=dt, device=DEV)
         gmg.gmg_level_smoother_pc(ctx, lev, _t(r, dt), z)
         ref = O.smoother_preconditioner(g, q(oa), r, op.smoother_pc)
-        assert _rel(_np(z), ref) < tol, ("pc", lev)
-        # Chebyshev from zero and from a given x, with the GPU's bounds
+        _close(_np(z), ref, tol, ("pc", lev))
+        # Chebyshev from zero and from a given x, with the oracle's bounds
         b = q(random_field(121 + lev, s))
         x0 = q(random_field(131 + lev, s))
         for x_is_zero in (True, False):
             x = _t(x0, dt)
             gmg.gmg_level_smooth(ctx, lev, _t(b, dt), x, x_is_zero)
-            ref = O.chebyshev_smooth(g, q(oa), b, None if x_is_zero else x0, info["lam_max"], info["lam_min"],
+            lv = hier.levels[lev]
+            ref = O.chebyshev_smooth(g, q(oa), b, None if x_is_zero else x0, lv.lam_max, lv.lam_min,
                                      p.cheb_steps, op.smoother_pc)
-            assert _rel(_np(x), ref) < 5 * tol, ("cheb", lev, x_is_zero)
+            _close(_np(x), ref, 5 * tol, ("cheb", lev, x_is_zero))
         oa = O.coarsen_coefficient(oa)
+
+
+# A Chebyshev interval for smoother-only checks: the SSOR-preconditioned
+# spectrum lies in (0, 1], and 1.1 x / 0.1 x of a Ritz value near 1 is what
+# the set-up finds (Sec. 3.2).
+FIXED_LAM_MAX, FIXED_LAM_MIN = 1.0989, 0.0999
 
 
 @pytest.mark.parametrize("shape,cm", [((48, 40, 72), 5), ((64, 64, 64), 4), (RAGGED, 2)])
@@ -224,6 +253,8 @@ def test_fused_smoother_matches_separate_kernels_and_oracle(shape, cm):
     ctxs = [gmg.gmg_setup(_params(shape, coarse_min=cm, smoother_kernel=k), _t(a)) for k in (0, 1)]
     oa = a
     for lev in range(gmg.gmg_num_levels(ctxs[0]) - 1, 0, -1):
+        for ctx in ctxs:   # one interval, given from outside, for every side
+            gmg.gmg_level_set_bounds(ctx, lev, FIXED_LAM_MAX, FIXED_LAM_MIN)
         info = gmg.gmg_level_info(ctxs[0], lev)
         s = info["shape"]
         b = random_field(300 + lev, s).astype(np.float32)
@@ -235,10 +266,10 @@ def test_fused_smoother_matches_separate_kernels_and_oracle(shape, cm):
                 gmg.gmg_level_smooth(ctx, lev, _t(b, torch.float32), x, x_is_zero)
                 outs.append(_np(x))
             ref = O.chebyshev_smooth(_ogrid(s), oa.astype(np.float32).astype(np.float64), b.astype(np.float64),
-                                     None if x_is_zero else x0.astype(np.float64), info["lam_max"],
-                                     info["lam_min"], 3, "sgs")
-            assert _rel(outs[0], outs[1]) < 1e-5, (lev, x_is_zero)
-            assert _rel(outs[0], ref) < 1e-4, (lev, x_is_zero)
+                                     None if x_is_zero else x0.astype(np.float64), FIXED_LAM_MAX,
+                                     FIXED_LAM_MIN, 3, "sgs")
+            _close(outs[0], outs[1], 1e-5, (lev, x_is_zero))
+            _close(outs[0], ref, 1e-4, (lev, x_is_zero))
         oa = O.coarsen_coefficient(oa)
     v = random_field(320, shape)
     zs = []
@@ -246,7 +277,7 @@ def test_fused_smoother_matches_separate_kernels_and_oracle(shape, cm):
         z = torch.empty(shape, dtype=torch.float64, device=DEV)
         gmg.gmg_apply_preconditioner(ctx, _t(v), z)
         zs.append(_np(z))
-    assert _rel(zs[0], zs[1]) < 1e-5
+    _close(zs[0], zs[1], 1e-5)
     f = make_inputs("twochannel512", shape=shape)["f"]
     its = []
     for ctx in ctxs:
@@ -291,12 +322,12 @@ def test_transfers_and_coarse_solve(prec, mode, shape):
         coarse = torch.empty(sc, dtype=dt, device=DEV)
         gmg.gmg_level_residual_restrict(ctx, lev, _t(b, dt), _t(x, dt), coarse)
         ref = O.restrict(b - O.apply_operator(_ogrid(s), q(oa), x))
-        assert _rel(_np(coarse), ref) < (5e-5 if fp32 else 1e-13), ("restrict", lev)
+        _close(_np(coarse), ref, (5e-5 if fp32 else 1e-13), ("restrict", lev))
         e = q(random_field(171 + lev, sc))
         xt = _t(x, dt)
         gmg.gmg_level_prolong_add(ctx, lev, _t(e, dt), xt)
         ref = x + O.prolong(e, ["trilinear", "constant"][mode])
-        assert _rel(_np(xt), ref) < tol, ("prolong", lev)
+        _close(_np(xt), ref, tol, ("prolong", lev))
         oa = O.coarsen_coefficient(oa)
     # coarsest direct solve
     sc = gmg.gmg_level_info(ctx, 0)["shape"]
@@ -305,7 +336,7 @@ def test_transfers_and_coarse_solve(prec, mode, shape):
     gmg.gmg_coarse_solve(ctx, _t(b, dt), x)
     A = O.dense_operator(_ogrid(sc), oa)
     ref = np.linalg.solve(A, b.ravel()).reshape(sc)
-    assert _rel(_np(x), ref) < (1e-5 if fp32 else 1e-12)
+    _close(_np(x), ref, (1e-5 if fp32 else 1e-12))
 
 
 def _offset_view(arr, dtype):
@@ -336,11 +367,11 @@ def test_solve_with_unaligned_right_hand_side():
     b1, b2 = torch.empty_like(f_al), torch.empty_like(f_al)
     gmg.assemble_rhs(ctx, f_al, b1)
     gmg.assemble_rhs(ctx, f_off, b2)
-    assert _rel(_np(b2), _np(b1)) < 1e-15
+    _close(_np(b2), _np(b1), 1e-15)
     x1, x2 = torch.zeros_like(f_al), torch.zeros_like(f_al)
     i1, i2 = gmg.fgmres_solve(ctx, f_al, x1), gmg.fgmres_solve(ctx, f_off, x2)
     assert i1.converged and i2.converged and i1.iterations == i2.iterations
-    assert _rel(_np(x2), _np(x1)) < 1e-12
+    _close(_np(x2), _np(x1), 1e-12)
 
 
 def test_level_ops_accept_arrays_off_the_pair_alignment():
@@ -361,20 +392,20 @@ def test_level_ops_accept_arrays_off_the_pair_alignment():
     c2 = torch.empty(sc, dtype=torch.float32, device=DEV)
     gmg.gmg_level_residual_restrict(ctx, lev, _t(b, torch.float32), _t(x0, torch.float32), c1)
     gmg.gmg_level_residual_restrict(ctx, lev, _offset_view(b, torch.float32), _offset_view(x0, torch.float32), c2)
-    assert _rel(_np(c2), _np(c1)) < 1e-5
+    _close(_np(c2), _np(c1), 1e-5)
     # prolongation
     x1 = _t(x0, torch.float32)
     x2 = _offset_view(x0, torch.float32)
     gmg.gmg_level_prolong_add(ctx, lev, _t(e, torch.float32), x1)
     gmg.gmg_level_prolong_add(ctx, lev, _t(e, torch.float32), x2)
-    assert _rel(_np(x2), _np(x1)) < 1e-6
+    _close(_np(x2), _np(x1), 1e-6)
     # smoothing (fused kernel for aligned arrays, separate kernels otherwise)
     for x_is_zero in (True, False):
         x1 = _t(x0, torch.float32)
         x2 = _offset_view(x0, torch.float32)
         gmg.gmg_level_smooth(ctx, lev, _t(b, torch.float32), x1, x_is_zero)
         gmg.gmg_level_smooth(ctx, lev, _offset_view(b, torch.float32), x2, x_is_zero)
-        assert _rel(_np(x2), _np(x1)) < 1e-5, x_is_zero
+        _close(_np(x2), _np(x1), 1e-5, x_is_zero)
 
 
 @pytest.mark.parametrize("shape,cm", [(RAGGED, 2), ((32, 32, 32), 4), ((20, 16, 16), 4)])
@@ -386,7 +417,7 @@ def test_vcycle_fp64_matches_oracle(shape, cm):
     v = random_field(190, shape)
     z = torch.empty(shape, dtype=torch.float64, device=DEV)
     gmg.gmg_apply_preconditioner(ctx, _t(v), z)
-    assert _rel(_np(z), O.vcycle(hier, v)) < 1e-12
+    _close(_np(z), O.vcycle(hier, v), 1e-12)
 
 
 def test_vcycle_mixed_close_to_oracle():
@@ -398,7 +429,7 @@ def test_vcycle_mixed_close_to_oracle():
     v = random_field(191, shape)
     z = torch.empty(shape, dtype=torch.float64, device=DEV)
     gmg.gmg_apply_preconditioner(ctx, _t(v), z)
-    assert _rel(_np(z), O.vcycle(hier, v)) < 1e-4
+    _close(_np(z), O.vcycle(hier, v), 1e-4)
 
 
 # ---------------------------------------------------------------------------
@@ -428,7 +459,7 @@ def test_fp64_solve_matches_oracle(workload, n, orth):
     assert _true_residual(shape, p, inp["a"], inp["f"], out) < 1e-8
     assert info.true_rel_residual == pytest.approx(rinfo.true_rel_residual, rel=1e-4)
     np.testing.assert_allclose(info.history, rinfo.history, rtol=1e-5)
-    assert _rel(out, ref) < 1e-10
+    _close(out, ref, 1e-10)
 
 
 @pytest.mark.parametrize("workload,n,kappa,arith", [("const32", 32, None, 1), ("channel128", 64, None, 1),
@@ -449,7 +480,7 @@ def test_mixed_solve_residual_and_error(workload, n, kappa, arith):
           f"phi rel err {_rel(out, ref):.2e}")
     assert info.converged and tr < 1e-8
     assert abs(info.iterations - rinfo.iterations) <= 2
-    assert _rel(out, ref) < 1e-6
+    _close(out, ref, 1e-6)
 
 
 def test_warm_start_and_restart():
@@ -535,7 +566,7 @@ def test_host_buffer_solve_matches_device_solve():
     np.testing.assert_array_equal(phi_h.numpy(), _np(phi_d))
     ex, ey, ez = O.field_from_potential(_ogrid(shape), phi_h.numpy(), 0.0, 1.0)
     for got, ref in zip(e, (ex, ey, ez)):
-        assert _rel(got.numpy().astype(np.float64), ref) < 1e-6
+        _close(got.numpy().astype(np.float64), ref, 1e-6)
 
 
 def test_pipelined_host_solves_match_synchronous_ones():
@@ -640,19 +671,20 @@ def test_adjoint_grad_kernel_matches_oracle():
     out = torch.empty(shape, dtype=torch.float64, device=DEV)
     gmg.adjoint_coefficient_grad(ctx, _t(phi), _t(lam), out)
     ref = O.adjoint_coefficient_grad(_ogrid(shape, p), phi, lam, 0.4, 1.3)
-    assert _rel(_np(out), ref) < 1e-14
+    _close(_np(out), ref, 1e-14)
 
 
 def test_autograd_finite_differences_and_cpu_adjoint():
-    """Central differences on 64 seeded entries of a 32^3 instance, at the
-    configured step of 1e-6 relative for the coefficient a.
+    """Central differences on 64 seeded entries of a 32^3 instance.
 
     L is linear in f, so a large step (1 or |f_q|) is exact up to the solve
-    error.  For a, the 1e-6 step leaves a truncation error near 1e-12; what
-    limits the check is the solve error of L (|dL| ~ |lambda . r| with
-    ||r|| ~ rtol ||b||), divided by the step, so the forward solves run to
-    rtol = 1e-13 (the flexible FP64 outer loop reaches it around the FP32
-    V-cycle)."""
+    error.  For a, two steps: the configured 1e-6 relative step and a 1e-3
+    step.  At 1e-6 the truncation error is near 1e-12 and what limits the
+    check is the solve error of L (|dL| ~ |lambda . r| with ||r|| ~ rtol ||b||)
+    divided by the step: with the forward solves at rtol = 1e-13 the worst of
+    the 64 entries was measured 3.4e-4 off (the rest closer), so the check at
+    that step is 1e-3.  The 1e-3 step, whose truncation error is ~1e-6 and
+    whose noise is 1000 times smaller, is held to 1e-4."""
     from paper_1812_08606_gb300 import PoissonSolver
     inp = make_inputs("adjoint", n=32)
     shape = inp["a"].shape
@@ -671,11 +703,13 @@ def test_autograd_finite_differences_and_cpu_adjoint():
             return float((w * solver.solve(av, fv)).sum())
 
     base_a, base_f = a.detach().clone(), f.detach().clone()
-    worst = 0.0
+    errs = {("a", 1e-6): [], ("a", 1e-3): [], ("f", None): []}
+    tols = {("a", 1e-6): 1e-3, ("a", 1e-3): 1e-4, ("f", None): 1e-4}
     for q in idx:
-        for grad, base, which in ((ga, base_a, "a"), (gf, base_f, "f")):
+        for (which, step), bucket in errs.items():
+            grad, base = (ga, base_a) if which == "a" else (gf, base_f)
             v = abs(float(base.view(-1)[q]))
-            h = 1e-6 * v if which == "a" else max(v, 1.0)
+            h = step * v if which == "a" else max(v, 1.0)
             plus, minus = base.clone(), base.clone()
             plus.view(-1)[q] += h
             minus.view(-1)[q] -= h
@@ -685,9 +719,10 @@ def test_autograd_finite_differences_and_cpu_adjoint():
                 fd = (L(base_a, plus) - L(base_a, minus)) / (2 * h)
             g = grad.ravel()[q]
             err = abs(g - fd) / max(abs(fd), 1e-4 * np.abs(grad).max())
-            worst = max(worst, err)
-            assert err < 1e-4, (which, q, g, fd)
-    print(f"worst FD relative mismatch {worst:.2e}")
+            bucket.append(err)
+            assert err < tols[(which, step)], (which, step, q, g, fd)
+    for key, e in errs.items():
+        print(f"FD {key}: median {np.median(e):.2e}, max {np.max(e):.2e}")
     # dot test: w . A^{-1} f = f . A^{-1} w on the homogeneous problem
     ctx = solver.ctx
     solver.set_coefficient(base_a)
@@ -742,7 +777,7 @@ def test_autograd_follows_the_current_torch_stream():
         f.copy_(_t(inp["f"]))
         phi = solver.solve(a, f)
     side.synchronize()
-    assert _rel(_np(phi), _np(ref)) < 1e-12
+    _close(_np(phi), _np(ref), 1e-12)
 
 
 def test_autograd_matches_cpu_adjoint_64():
@@ -757,9 +792,9 @@ def test_autograd_matches_cpu_adjoint_64():
     phi, _, hier = O.solve(op, inp["a"], inp["f"])
     lam, _, _ = O.solve(op, inp["a"], inp["w"], homogeneous=True, hierarchy=hier)
     ga = O.adjoint_coefficient_grad(_ogrid(shape), phi, lam, 0.0, 1.0)
-    ef, ea = _rel(_np(f.grad), lam), _rel(_np(a.grad), ga)
-    print(f"adjoint vs CPU at 64^3: dL/df {ef:.2e}, dL/da {ea:.2e}")
-    assert ef < 1e-7 and ea < 1e-6
+    ef = _close(_np(f.grad), lam, 1e-7, "dL/df")
+    ea = _close(_np(a.grad), ga, 1e-6, "dL/da")
+    print(f"adjoint vs CPU at 64^3 (l2, max): dL/df {ef}, dL/da {ea}")
 
 
 # ---------------------------------------------------------------------------
@@ -776,7 +811,7 @@ def test_fmg_preconditioner_fp64_matches_oracle(shape, cm):
     v = random_field(331, shape)
     z = torch.empty(shape, dtype=torch.float64, device=DEV)
     gmg.gmg_apply_preconditioner(ctx, _t(v), z)
-    assert _rel(_np(z), O.fmg(hier, v)) < 1e-12
+    _close(_np(z), O.fmg(hier, v), 1e-12)
 
 
 def test_fmg_preconditioner_mixed_close_to_oracle():
@@ -788,7 +823,7 @@ def test_fmg_preconditioner_mixed_close_to_oracle():
     v = random_field(332, shape)
     z = torch.empty(shape, dtype=torch.float64, device=DEV)
     gmg.gmg_apply_preconditioner(ctx, _t(v), z)
-    assert _rel(_np(z), O.fmg(hier, v)) < 1e-4
+    _close(_np(z), O.fmg(hier, v), 1e-4)
 
 
 @pytest.mark.parametrize("workload,n", [("channel128", 32), ("twochannel512", 32)])
@@ -802,7 +837,7 @@ def test_fmg_solve_fp64_matches_oracle(workload, n):
     info = gmg.fgmres_solve(ctx, _t(inp["f"]), phi)
     assert info.fmg == 1
     assert info.iterations == rinfo.iterations
-    assert _rel(_np(phi), ref) < 1e-10
+    _close(_np(phi), ref, 1e-10)
     assert info.true_rel_residual < 1e-8
 
 
@@ -924,7 +959,7 @@ def test_anisotropic_fp64_solve_matches_oracle(cycle):
     phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
     info = gmg.fgmres_solve(ctx, _t(f), phi)
     assert info.iterations == rinfo.iterations
-    assert _rel(_np(phi), ref) < 1e-10
+    _close(_np(phi), ref, 1e-10)
 
 
 @pytest.mark.parametrize("shape", [(40, 32, 32), (80, 64, 64)])
@@ -937,7 +972,7 @@ def test_anisotropic_mixed_solve_meets_tolerance(shape):
     assert info.fmg == 1 and info.true_rel_residual < 1e-8
     assert _true_residual(shape, _oracle_hierarchy(a, p), a, f, _np(phi)) < 1e-8
     ref, _, _ = O.solve(O.OracleParams(coarse_min=4, phi_top=PHI0, rtol=1e-11), a, f)
-    assert _rel(_np(phi), ref) < 1e-6
+    _close(_np(phi), ref, 1e-6)
 
 
 # ---------------------------------------------------------------------------
@@ -958,7 +993,7 @@ def test_krylov_fp64_matches_oracle(method):
     info = gmg.gmg_krylov_solve(ctx, method, _t(inp["f"]), phi)
     assert info.converged and info.true_rel_residual < 1e-8
     assert info.iterations == rinfo.iterations, (info.iterations, rinfo.iterations)
-    assert _rel(_np(phi), ref) < 1e-9
+    _close(_np(phi), ref, 1e-9)
 
 
 @pytest.mark.parametrize("method", KRYLOV)
@@ -1148,7 +1183,7 @@ def test_semi_implicit_step_fp64_matches_oracle():
     op = torch.empty_like(oe)
     info = st.step(_t(ne), _t(npos), oe, op)
     assert info.iterations == rinfo.iterations and info.fmg == 1
-    assert _rel(_np(st.phi), ref_phi) < 1e-10
+    _close(_np(st.phi), ref_phi, 1e-10)
     assert np.abs(_np(oe) - ref_e).max() <= 1e-9 * np.abs(ref_e).max()
     assert np.abs(_np(op) - ref_p).max() <= 1e-9 * np.abs(ref_p).max()
     st.close()
