@@ -35,9 +35,17 @@ the design notes of the repository):
 
 R1 boundary-face coefficient on the plates equals the cell's own coefficient;
 R2 Dirichlet ghost phi_g = 2 g - phi_p (linear extrapolation to the plate);
-R3 coarse operators are re-discretised from the 8-child mean of ``a``;
-R4 restriction = mean of 8 children, prolongation = cell-centred trilinear
-   (piecewise constant available as an option);
+R3 coarse operators (default, "series") carry one coefficient per face,
+   homogenised from the finer level's faces: along the face normal the three
+   fine links between the two coarse cell centres act in series, across it
+   the four fine columns act in parallel; the plates' faces likewise.  The
+   alternative "mean" re-discretises eq. (e18) from the 8-child mean of a;
+R4 restriction = mean of 8 children; prolongation (default "opdep") =
+   per axis a 1-D interpolation between the parent and the neighbour on the
+   child's side weighted by the series conductances of the fine links in
+   between (harmonic), combined as a tensor product over x, y, z; with a
+   constant coefficient it is the cell-centred trilinear one, which stays an
+   option, as does piecewise constant;
 R5 "one-step local SSOR" = one symmetric Gauss-Seidel sweep (omega = 1) in
    red-black order (red = (i+j+k) even): red, black, red half-sweeps;
 R6 "quadratic-polynomial" Chebyshev: the smoother is defined by p_n in
@@ -89,7 +97,8 @@ class OracleParams:
     eig_steps: int = 10          # Sec. 3.2
     eig_hi: float = 1.1          # Sec. 3.2
     eig_lo: float = 0.1          # Sec. 3.2
-    prolongation: str = "trilinear"   # R4; or "constant"
+    prolongation: str = "opdep"       # R4; or "trilinear", "constant"
+    coarsening: str = "series"        # R3; or "mean"
     smoother_pc: str = "sgs"          # R5; or "jacobi", "identity"
     cycle: str = "v"             # preconditioner: "v", "fmg", or "auto" (FMG for a zero guess, Sec. 3.2)
 
@@ -134,13 +143,44 @@ class Grid:
 # ---------------------------------------------------------------------------
 
 
-def face_coefficients(grid: Grid, a: np.ndarray):
+@dataclass
+class FaceCoefficients:
+    """A 7-point operator of the form of eq. (e18) given by one coefficient per
+    face instead of the face means of a cell coefficient (the coarse levels of
+    reading R3).  a-values, before the division by h^2:
+      ax (nz, ny, nx-1): face between cells i and i+1 along x; ay, az likewise;
+      bottom, top (ny, nx): the plate faces (a coefficient over the half cell
+      between the cell centre and the plate, as a_p is in R1).
+    The side walls carry no flux."""
+
+    ax: np.ndarray
+    ay: np.ndarray
+    az: np.ndarray
+    bottom: np.ndarray
+    top: np.ndarray
+
+    @property
+    def shape(self):
+        return (self.az.shape[0] + 1,) + self.bottom.shape
+
+
+def faces_of_cells(a: np.ndarray) -> FaceCoefficients:
+    """The face form of eq. (e18): interior faces the mean of the two cells
+    (Sec. 2.2), plate faces the cell's own coefficient (R1)."""
+    return FaceCoefficients(0.5 * (a[:, :, 1:] + a[:, :, :-1]), 0.5 * (a[:, 1:, :] + a[:, :-1, :]),
+                            0.5 * (a[1:] + a[:-1]), np.array(a[0], copy=True), np.array(a[-1], copy=True))
+
+
+def face_coefficients(grid: Grid, a):
     """Interior face coefficients divided by h^2 (eq. (e18) and the face means
-    P_{i+1/2,j,k} = (P_{i+1,j,k} + P_{i,j,k}) / 2 of Sec. 2.2).
+    P_{i+1/2,j,k} = (P_{i+1,j,k} + P_{i,j,k}) / 2 of Sec. 2.2), or the stored
+    face values of a FaceCoefficients operator.
 
     Returns (cx, cy, cz) with cx[k,j,i] the coefficient of the face between
     cells i and i+1 (shape (nz,ny,nx-1)), and likewise for y and z.
     """
+    if isinstance(a, FaceCoefficients):
+        return a.ax / grid.hx**2, a.ay / grid.hy**2, a.az / grid.hz**2
     cx = 0.5 * (a[:, :, 1:] + a[:, :, :-1]) / grid.hx**2
     cy = 0.5 * (a[:, 1:, :] + a[:, :-1, :]) / grid.hy**2
     cz = 0.5 * (a[1:, :, :] + a[:-1, :, :]) / grid.hz**2
@@ -152,7 +192,10 @@ def plate_coefficients(grid: Grid, a: np.ndarray):
 
     A plate face carries a_f = a_p (R1) and the ghost value 2g - phi_p (R2), so
     its flux a_p (phi_p - phi_g) / hz^2 = 2 a_p (phi_p - g) / hz^2.
+    A FaceCoefficients operator gives its plate a-values the same way.
     """
+    if isinstance(a, FaceCoefficients):
+        return 2.0 * a.bottom / grid.hz**2, 2.0 * a.top / grid.hz**2
     return 2.0 * a[0] / grid.hz**2, 2.0 * a[-1] / grid.hz**2
 
 
@@ -402,8 +445,58 @@ def restrict(fine: np.ndarray) -> np.ndarray:
 
 
 def coarsen_coefficient(a: np.ndarray) -> np.ndarray:
-    """Coarse coefficient = mean of the 8 children (R3)."""
+    """Coarse coefficient = mean of the 8 children (R3, "mean")."""
     return restrict(a)
+
+
+def _pair_mean(u: np.ndarray, axis: int) -> np.ndarray:
+    """Mean of neighbouring pairs (2m, 2m+1) along axis."""
+    u = np.moveaxis(u, axis, 0)
+    return np.moveaxis(0.5 * (u[0::2] + u[1::2]), 0, axis)
+
+
+def coarsen_faces(a) -> FaceCoefficients:
+    """The coarse operator of R3 ("series") from the finer level's operator
+    (a cell coefficient of eq. (e18) or a FaceCoefficients).
+
+    Take the coarse face between coarse cells I-1 and I along an axis.  Along
+    the path between their centres lie, in series, half of the inner fine link
+    of cell I-1 (between its two children), the whole fine link shared by the
+    two coarse cells, and half of the inner fine link of cell I.  With fine
+    link a-values A1, A2, A3 over the fine spacing h, the path of length 2h has
+    the a-value 2 / (1/(2 A1) + 1/A2 + 1/(2 A3)).  The four fine columns that
+    cross the coarse face act in parallel: the coarse face takes their mean.
+    A coarse plate face: half the inner link of the boundary coarse cell in
+    series with the fine plate face (a-value over h/2), 2 / (1/A + 1/P), and
+    the mean over the four fine columns.  With a constant coefficient every
+    coarse face gets that constant, which is eq. (e18) re-discretised."""
+    f = a if isinstance(a, FaceCoefficients) else faces_of_cells(a)
+
+    def along(links, axis):
+        # links: interior fine faces along axis (n-1 of them); coarse interior faces m = 0..n/2-2
+        u = np.moveaxis(links, axis, 0)
+        s = 2.0 / (0.5 / u[0:-2:2] + 1.0 / u[1:-1:2] + 0.5 / u[2::2])
+        return np.moveaxis(s, 0, axis)
+
+    ax = along(f.ax, 2)
+    ax = _pair_mean(_pair_mean(ax, 1), 0)
+    ay = along(f.ay, 1)
+    ay = _pair_mean(_pair_mean(ay, 2), 0)
+    az = along(f.az, 0)
+    az = _pair_mean(_pair_mean(az, 2), 1)
+    bottom = _pair_mean(_pair_mean(2.0 / (1.0 / f.az[0] + 1.0 / f.bottom), 1), 0)
+    top = _pair_mean(_pair_mean(2.0 / (1.0 / f.az[-1] + 1.0 / f.top), 1), 0)
+    return FaceCoefficients(ax, ay, az, bottom, top)
+
+
+def coarsen_level(a, params) -> object:
+    """The next coarser level's operator (R3): FaceCoefficients ("series") or
+    the 8-child mean of the cell coefficient ("mean")."""
+    if params.coarsening == "series":
+        return coarsen_faces(a)
+    if params.coarsening == "mean":
+        return coarsen_coefficient(a)
+    raise ValueError(params.coarsening)
 
 
 def _prolong_axis(e: np.ndarray, axis: int, dirichlet: bool) -> np.ndarray:
@@ -424,10 +517,87 @@ def _prolong_axis(e: np.ndarray, axis: int, dirichlet: bool) -> np.ndarray:
     return np.moveaxis(out, 0, axis)
 
 
-def prolong(coarse: np.ndarray, kind: str = "trilinear") -> np.ndarray:
-    """Coarse-to-fine interpolation P_{l-1,l} (R4)."""
+def _opdep_parent_weight(links: np.ndarray, n: int, plate_lo, plate_hi) -> np.ndarray:
+    """Weight of the parent for each fine cell along one axis (axis 0 of the
+    arrays), from the series resistances of the fine links (R4, "opdep").
+
+    links[m] (m = 0..n-2): a-value of the fine link between cells m and m+1.
+    A child sits half a fine cell from its parent's centre (which lies on the
+    parent's inner link); towards the neighbour on its side lie the fine link
+    it shares with that coarse cell and half of the neighbour's inner link.  In
+    units of h: R_parent = 1/(2 A_inner), R_neighbour = 1/A_shared +
+    1/(2 A_neighbour_inner); the child takes the conductance-weighted mean
+    (1/R_p e_p + 1/R_n e_n) / (1/R_p + 1/R_n).  At a side wall there is no
+    neighbour (weight 1 on the parent, the Neumann mirror); at a plate the
+    neighbour is the plate itself, value 0, over the half cell with the plate
+    face's a-value P: R_n = 1/(2 P) (plate_lo / plate_hi; None for a wall)."""
+    m = n // 2
+    w = np.ones((n,) + links.shape[1:])
+    for I in range(m):
+        c = 2 * I                      # child nearer the lower neighbour I-1
+        rp = 0.5 / links[c]
+        if I > 0:
+            rn = 1.0 / links[c - 1] + 0.5 / links[c - 2]
+            w[c] = (1.0 / rp) / (1.0 / rp + 1.0 / rn)
+        elif plate_lo is not None:
+            rn = 0.5 / plate_lo
+            w[c] = (1.0 / rp) / (1.0 / rp + 1.0 / rn)
+        c = 2 * I + 1                  # child nearer the upper neighbour I+1
+        rp = 0.5 / links[c - 1]
+        if I < m - 1:
+            rn = 1.0 / links[c] + 0.5 / links[c + 1]
+            w[c] = (1.0 / rp) / (1.0 / rp + 1.0 / rn)
+        elif plate_hi is not None:
+            rn = 0.5 / plate_hi
+            w[c] = (1.0 / rp) / (1.0 / rp + 1.0 / rn)
+    return w
+
+
+def prolong_weights(fine_coef):
+    """Per fine cell, the parent weights (wx, wy, wz) of the operator-dependent
+    prolongation into the level whose operator is fine_coef (R4, "opdep")."""
+    f = fine_coef if isinstance(fine_coef, FaceCoefficients) else faces_of_cells(fine_coef)
+    nz, ny, nx = f.az.shape[0] + 1, f.ay.shape[1] + 1, f.ax.shape[2] + 1
+    wx = np.moveaxis(_opdep_parent_weight(np.moveaxis(f.ax, 2, 0), nx, None, None), 0, 2)
+    wy = np.moveaxis(_opdep_parent_weight(np.moveaxis(f.ay, 1, 0), ny, None, None), 0, 1)
+    wz = _opdep_parent_weight(f.az, nz, f.bottom, f.top)
+    return wx, wy, wz
+
+
+def _prolong_opdep(coarse: np.ndarray, fine_coef) -> np.ndarray:
+    """e_child = sum over the 8 combinations of (parent or neighbour) per axis
+    of the product of the per-axis weights times that coarse value; the
+    neighbour beyond a plate is 0, beyond a side wall it has weight 0."""
+    wx, wy, wz = prolong_weights(fine_coef)
+    nzc, nyc, nxc = coarse.shape
+    nz, ny, nx = 2 * nzc, 2 * nyc, 2 * nxc
+    k, j, i = np.arange(nz), np.arange(ny), np.arange(nx)
+    own = (k // 2, j // 2, i // 2)
+    nbr = (np.where(k % 2 == 0, k // 2 - 1, k // 2 + 1), np.where(j % 2 == 0, j // 2 - 1, j // 2 + 1),
+           np.where(i % 2 == 0, i // 2 - 1, i // 2 + 1))
+    inside = [(nbr[0] >= 0) & (nbr[0] < nzc), (nbr[1] >= 0) & (nbr[1] < nyc), (nbr[2] >= 0) & (nbr[2] < nxc)]
+    out = np.zeros((nz, ny, nx))
+    for sz in (0, 1):
+        for sy in (0, 1):
+            for sx in (0, 1):
+                kk = np.clip(nbr[0], 0, nzc - 1) if sz else own[0]
+                jj = np.clip(nbr[1], 0, nyc - 1) if sy else own[1]
+                ii = np.clip(nbr[2], 0, nxc - 1) if sx else own[2]
+                val = coarse[kk[:, None, None], jj[None, :, None], ii[None, None, :]]
+                if sz:   # beyond a plate the neighbour value is the homogeneous Dirichlet 0
+                    val = val * inside[0][:, None, None]
+                w = (1.0 - wz if sz else wz) * (1.0 - wy if sy else wy) * (1.0 - wx if sx else wx)
+                out += w * val
+    return out
+
+
+def prolong(coarse: np.ndarray, kind: str = "trilinear", fine_coef=None) -> np.ndarray:
+    """Coarse-to-fine interpolation P_{l-1,l} (R4); "opdep" needs the fine
+    level's operator (cell coefficient or FaceCoefficients)."""
     if kind == "constant":
         return coarse.repeat(2, axis=0).repeat(2, axis=1).repeat(2, axis=2)
+    if kind == "opdep":
+        return _prolong_opdep(coarse, fine_coef)
     if kind != "trilinear":
         raise ValueError(kind)
     e = _prolong_axis(coarse, 2, dirichlet=False)   # x: Neumann walls
@@ -439,7 +609,7 @@ def prolong(coarse: np.ndarray, kind: str = "trilinear") -> np.ndarray:
 @dataclass
 class Level:
     grid: Grid
-    a: np.ndarray
+    a: object          # cell coefficient (finest level, or R3 "mean") or FaceCoefficients
     lam_max: float = 0.0
     lam_min: float = 0.0
     lam_hat: float = 0.0
@@ -472,7 +642,7 @@ def build_hierarchy(grid: Grid, a: np.ndarray, params: OracleParams) -> Hierarch
     fine_to_coarse = [Level(grid, np.asarray(a, dtype=np.float64))]
     for _ in range(nlev - 1):
         prev = fine_to_coarse[-1]
-        fine_to_coarse.append(Level(prev.grid.coarser(), coarsen_coefficient(prev.a)))
+        fine_to_coarse.append(Level(prev.grid.coarser(), coarsen_level(prev.a, params)))
     hier = Hierarchy(params, list(reversed(fine_to_coarse)))
     for lev in hier.levels[1:]:
         lev.lam_max, lev.lam_min, lev.lam_hat = estimate_eig_bounds(lev.grid, lev.a, params)
@@ -506,7 +676,7 @@ def vcycle(hier: Hierarchy, b: np.ndarray, level: int | None = None) -> np.ndarr
     x = chebyshev_smooth(lev.grid, lev.a, b, None, lev.lam_max, lev.lam_min, p.cheb_steps, p.smoother_pc)
     r = b - apply_operator(lev.grid, lev.a, x)
     e = vcycle(hier, restrict(r), level - 1)
-    x = x + prolong(e, p.prolongation)
+    x = x + prolong(e, p.prolongation, lev.a)
     x = chebyshev_smooth(lev.grid, lev.a, b, x, lev.lam_max, lev.lam_min, p.cheb_steps, p.smoother_pc)
     return x
 
@@ -524,7 +694,7 @@ def vcycle_from(hier: Hierarchy, b: np.ndarray, x: np.ndarray, level: int | None
     x = chebyshev_smooth(lev.grid, lev.a, b, x, lev.lam_max, lev.lam_min, p.cheb_steps, p.smoother_pc)
     r = b - apply_operator(lev.grid, lev.a, x)
     e = vcycle(hier, restrict(r), level - 1)
-    x = x + prolong(e, p.prolongation)
+    x = x + prolong(e, p.prolongation, lev.a)
     x = chebyshev_smooth(lev.grid, lev.a, b, x, lev.lam_max, lev.lam_min, p.cheb_steps, p.smoother_pc)
     return x
 
@@ -543,7 +713,7 @@ def fmg(hier: Hierarchy, b: np.ndarray) -> np.ndarray:
         rhs[level - 1] = restrict(rhs[level])
     x = coarse_solve(hier, rhs[0])
     for level in range(1, top + 1):
-        x = vcycle_from(hier, rhs[level], prolong(x, p.prolongation), level)
+        x = vcycle_from(hier, rhs[level], prolong(x, p.prolongation, hier.levels[level].a), level)
     return x
 
 

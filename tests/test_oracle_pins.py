@@ -395,6 +395,168 @@ def test_transfers_reproduce_constants_and_linears():
     np.testing.assert_allclose(pc[0], 0.5, atol=1e-15)
 
 
+def test_series_coarsening_of_a_constant_is_rediscretisation():
+    """With a constant coefficient every coarse face, plates included, carries
+    that constant (R3 reduces to eq. (e18) on the coarse grid): the coarse
+    operator equals the re-discretised one on every level."""
+    shape = (16, 8, 12)
+    grid = _grid(shape, (1.2, 0.7, 2.0))
+    a = np.full(shape, 3.25)
+    f = O.faces_of_cells(a)
+    g = grid
+    for _ in range(2):
+        f = O.coarsen_faces(f)
+        g = g.coarser()
+        x = random_field(90, g.shape)
+        np.testing.assert_allclose(O.apply_operator(g, f, x), O.apply_operator(g, np.full(g.shape, 3.25), x),
+                                   rtol=1e-13, atol=1e-12)
+
+
+def _layered(n, seed, contrast=1e4):
+    return random_coefficient(seed, (n,), contrast=contrast)
+
+
+def test_series_coarsening_keeps_the_plate_to_plate_resistance():
+    """A medium layered in z (a = a(z)) is a chain of resistors between the
+    plates.  On the fine grid of eq. (e18) its resistance per unit area is
+    sum_links hz / a_link + (hz/2)/a_0 + (hz/2)/a_{n-1} (the face means of
+    Sec. 2.2, the plate faces of R1 over half a cell).  Series coarsening must
+    keep that total on every level, H/A per coarse link and (H/2)/P per plate;
+    a wrong half factor, a swapped link or an arithmetic mean along the
+    normal changes it."""
+    nz = 32
+    az = _layered(nz, 91)
+    shape = (nz, 8, 8)
+    a = np.broadcast_to(az[:, None, None], shape).copy()
+    h = 1.0 / nz
+    fine = np.sum(h / (0.5 * (az[1:] + az[:-1]))) + 0.5 * h / az[0] + 0.5 * h / az[-1]
+    f = O.faces_of_cells(a)
+    H = h
+    for _ in range(3):
+        f = O.coarsen_faces(f)
+        H *= 2
+        col = f.az[:, 0, 0]
+        total = np.sum(H / col) + 0.5 * H / f.bottom[0, 0] + 0.5 * H / f.top[0, 0]
+        assert total == pytest.approx(fine, rel=1e-13)
+        for v in (f.az, f.bottom, f.top):        # no variation across the layers' planes
+            assert np.ptp(v, axis=(-2, -1)).max() <= 1e-12 * v.max()
+
+
+def test_series_coarsening_keeps_the_parallel_conductance():
+    """A medium layered in x, a = a(x), conducts in z through parallel columns:
+    the total conductance of a z-face, sum over its columns of a / h^2 times
+    the column's area, is kept on every level (the arithmetic mean across)."""
+    nx = 16
+    ax_ = _layered(nx, 92, contrast=1e3)
+    shape = (8, 4, nx)
+    a = np.broadcast_to(ax_[None, None, :], shape).copy()
+    f = O.faces_of_cells(a)
+    total = ax_.sum()           # per unit height: sum of the columns' a times width h = 1/nx, times nx
+    for lev in range(2):
+        f = O.coarsen_faces(f)
+        m = f.az.shape[2]
+        assert f.az[0, 0].sum() * (nx / m) == pytest.approx(total, rel=1e-13)
+        assert f.bottom[0].sum() * (nx / m) == pytest.approx(total, rel=1e-13)
+
+
+@pytest.mark.parametrize("axis", [2, 1])
+def test_series_coarsening_along_x_and_y_matches_the_fine_chain(axis):
+    """The same series rule along x and y: for a medium layered along that
+    axis, the first coarse level's links from the first coarse cell's centre to
+    the last one's (the midpoints of their inner fine links) add up to the fine
+    chain in between: half of each end's inner link and every link between."""
+    n = 32
+    av = _layered(n, 93 + axis)
+    shape = [8, 8, 8]
+    shape[axis] = n
+    idx = [None, None, None]
+    idx[axis] = slice(None)
+    a = np.broadcast_to(av[tuple(idx)], shape).copy()
+    h = 1.0 / n
+    links = 0.5 * (av[1:] + av[:-1])
+    f = O.coarsen_faces(a)
+    coarse = f.ax[0, 0] if axis == 2 else f.ay[0, :, 0]
+    fine = np.sum(h / links[1:n - 2]) + 0.5 * h / links[0] + 0.5 * h / links[n - 2]
+    assert np.sum(2 * h / coarse) == pytest.approx(fine, rel=1e-13)
+    other = f.ax if axis == 2 else f.ay
+    assert np.ptp(np.moveaxis(other, axis, -1), axis=(0, 1)).max() <= 1e-12 * other.max()
+
+
+def _constant_flux_profile(links, h, start=0.0):
+    """Potential at the cell centres of a 1-D chain with unit flux through every
+    link: phi_{m+1} = phi_m - h / A_m."""
+    phi = np.empty(links.size + 1)
+    phi[0] = start
+    for m in range(links.size):
+        phi[m + 1] = phi[m] - h / links[m]
+    return phi
+
+
+def test_opdep_prolongation_is_exact_for_a_constant_flux_in_z():
+    """In a medium layered in z, a potential that carries one flux through every
+    fine link (and through the bottom plate, where it is 0) is linear in the
+    resistance along the path.  Its values at the coarse centres (the
+    midpoints of the inner fine links) interpolated by the operator-dependent
+    prolongation give the fine values back, the boundary child at the bottom
+    plate included (R4, "opdep").  Trilinear weights do not."""
+    nz = 16
+    az = _layered(nz, 94)
+    shape = (nz, 2, 4)
+    a = np.broadcast_to(az[:, None, None], shape).copy()
+    h = 1.0 / nz
+    links = 0.5 * (az[1:] + az[:-1])
+    # unit flux downwards into the bottom plate (value 0 there): phi_0 = (h/2)/a_0
+    phi = _constant_flux_profile(-links, h, start=0.5 * h / az[0])
+    coarse = 0.5 * (phi[0::2] + phi[1::2])      # midpoint of each coarse cell's inner link
+    c3 = np.broadcast_to(coarse[:, None, None], (nz // 2, 1, 2)).copy()
+    got = O.prolong(c3, "opdep", a)
+    want = np.broadcast_to(phi[:, None, None], shape)
+    np.testing.assert_allclose(got[:-1], want[:-1], rtol=1e-12)   # the top child meets the top plate's 0
+    tri = O.prolong(c3, "trilinear")
+    assert np.abs(tri[:-1] - want[:-1]).max() > 1e-3 * np.abs(want).max()
+
+
+def test_opdep_prolongation_is_exact_for_a_constant_flux_in_x():
+    """The same along x, away from the two wall children (which copy their
+    parent, the Neumann mirror)."""
+    nx = 16
+    axv = _layered(nx, 95)
+    shape = (2, 2, nx)
+    a = np.broadcast_to(axv[None, None, :], shape).copy()
+    h = 1.0 / nx
+    links = 0.5 * (axv[1:] + axv[:-1])
+    phi = _constant_flux_profile(links, h, start=1.0)
+    coarse = 0.5 * (phi[0::2] + phi[1::2])
+    c3 = np.broadcast_to(coarse[None, None, :], (1, 1, nx // 2)).copy()
+    # z: one coarse plane between the plates; its z weights multiply every x value alike
+    got = O.prolong(c3, "opdep", a)
+    wz = O.prolong_weights(a)[2]
+    np.testing.assert_allclose(got[:, :, 1:-1] / wz[:, :, 1:-1], np.broadcast_to(phi[1:-1], (2, 2, nx - 2)),
+                               rtol=1e-12)
+    np.testing.assert_allclose(got[:, :, 0] / wz[:, :, 0], coarse[0], rtol=1e-14)
+    np.testing.assert_allclose(got[:, :, -1] / wz[:, :, -1], coarse[-1], rtol=1e-14)
+
+
+def test_opdep_prolongation_of_a_constant_coefficient_is_trilinear():
+    rng = np.random.default_rng(96)
+    for shape in ((8, 6, 10), (4, 4, 4), (16, 8, 12)):
+        a = np.full(shape, 7.0)
+        e = rng.standard_normal(tuple(s // 2 for s in shape))
+        np.testing.assert_allclose(O.prolong(e, "opdep", a), O.prolong(e, "trilinear"), rtol=0, atol=1e-14)
+        np.testing.assert_allclose(O.prolong(e, "opdep", O.faces_of_cells(a)), O.prolong(e, "trilinear"),
+                                   rtol=0, atol=1e-14)
+
+
+def test_series_coarse_operators_are_symmetric_positive_definite():
+    shape = (8, 8, 8)
+    a = random_coefficient(97, shape, contrast=1e4)
+    f = O.coarsen_faces(a)
+    g = _grid(shape).coarser()
+    A = O.dense_operator(g, f)
+    np.testing.assert_allclose(A, A.T, rtol=0, atol=1e-12 * np.abs(A).max())
+    assert np.linalg.eigvalsh(A).min() > 0
+
+
 def _dense_from_map(fn, n, shape):
     m = np.zeros((n, n))
     for i in range(n):
@@ -404,15 +566,19 @@ def _dense_from_map(fn, n, shape):
     return m
 
 
-@pytest.mark.parametrize("coarse_min,prolongation", [(4, "trilinear"), (2, "trilinear"), (2, "constant")])
-def test_vcycle_equals_appendix_a_recursion(coarse_min, prolongation):
+TRANSFER_CASES = [(4, "opdep", "series"), (2, "opdep", "series"), (2, "trilinear", "series"),
+                  (4, "trilinear", "mean"), (2, "trilinear", "mean"), (2, "constant", "mean")]
+
+
+@pytest.mark.parametrize("coarse_min,prolongation,coarsening", TRANSFER_CASES)
+def test_vcycle_equals_appendix_a_recursion(coarse_min, prolongation, coarsening):
     """vcycle(v) = M_L v with M_1 = A_1^{-1}, M_l = Q_l P_l + P_l +
     Q_l P_{l-1,l} M_{l-1} R_{l,l-1} (I - A_l P_l) (Appendix A), where the
     smoother x -> Q_l x + P_l b (eq. (e19)) is read off as dense matrices."""
     shape = (8, 8, 8)
     grid = _grid(shape)
     a = random_coefficient(11, shape, contrast=50.0)
-    params = O.OracleParams(coarse_min=coarse_min, prolongation=prolongation, cheb_steps=3)
+    params = O.OracleParams(coarse_min=coarse_min, prolongation=prolongation, cheb_steps=3, coarsening=coarsening)
     hier = O.build_hierarchy(grid, a, params)
     M = None
     for li, lev in enumerate(hier.levels):
@@ -430,7 +596,7 @@ def test_vcycle_equals_appendix_a_recursion(coarse_min, prolongation):
         cshape = hier.levels[li - 1].grid.shape
         nc = hier.levels[li - 1].grid.size
         R = np.array([O.restrict(e.reshape(lev.grid.shape)).ravel() for e in np.eye(n)]).T
-        Pr = np.array([O.prolong(e.reshape(cshape), prolongation).ravel() for e in np.eye(nc)]).T
+        Pr = np.array([O.prolong(e.reshape(cshape), prolongation, lev.a).ravel() for e in np.eye(nc)]).T
         M = Q @ P + P + Q @ Pr @ M @ R @ (np.eye(n) - A @ P)
     v = random_field(12, shape)
     np.testing.assert_allclose(O.vcycle(hier, v).ravel(), M @ v.ravel(), rtol=1e-10, atol=1e-12)
@@ -589,15 +755,15 @@ def test_adjoint_dot_product_identity():
 # ---------------------------------------------------------------------------
 
 
-@pytest.mark.parametrize("coarse_min,prolongation", [(4, "trilinear"), (2, "trilinear"), (2, "constant")])
-def test_fmg_equals_dense_recursion(coarse_min, prolongation):
+@pytest.mark.parametrize("coarse_min,prolongation,coarsening", TRANSFER_CASES)
+def test_fmg_equals_dense_recursion(coarse_min, prolongation, coarsening):
     """A V-cycle from a guess x0 is the consistent iteration x0 + M_l (b - A_l x0),
     so full multigrid is the matrix F_l = P F_{l-1} R + M_l (I - A_l P F_{l-1} R)
     with F_1 = A_1^{-1}; M_l is read off the zero-guess V-cycle as a dense matrix."""
     shape = (8, 8, 8)
     grid = _grid(shape)
     a = random_coefficient(41, shape, contrast=30.0)
-    params = O.OracleParams(coarse_min=coarse_min, prolongation=prolongation)
+    params = O.OracleParams(coarse_min=coarse_min, prolongation=prolongation, coarsening=coarsening)
     hier = O.build_hierarchy(grid, a, params)
     F = None
     for li, lev in enumerate(hier.levels):
@@ -610,7 +776,7 @@ def test_fmg_equals_dense_recursion(coarse_min, prolongation):
         cshape = hier.levels[li - 1].grid.shape
         nc = hier.levels[li - 1].grid.size
         R = np.array([O.restrict(e.reshape(lev.grid.shape)).ravel() for e in np.eye(n)]).T
-        Pr = np.array([O.prolong(e.reshape(cshape), prolongation).ravel() for e in np.eye(nc)]).T
+        Pr = np.array([O.prolong(e.reshape(cshape), prolongation, lev.a).ravel() for e in np.eye(nc)]).T
         X0 = Pr @ F @ R
         F = X0 + M @ (np.eye(n) - A @ X0)
     v = random_field(42, shape)
