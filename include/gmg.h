@@ -65,10 +65,35 @@ typedef enum gmg_status {
  * residual are FP64 in both modes. */
 typedef enum gmg_precision { GMG_PREC_FP64 = 0, GMG_PREC_MIXED = 1 } gmg_precision;
 
+/* Coarse-to-fine interpolation of the V-cycle (the paper's transfer figure is
+ * lost).  GMG_PROLONG_OPDEP: per axis the fine child takes the parent and the
+ * coarse neighbour on its side, weighted by the series conductances of the
+ * fine links in between (the child sits half a fine cell from its parent's
+ * centre; towards the neighbour lie the link the two coarse cells share and
+ * half of the neighbour's inner link); a neighbour beyond a plate is the
+ * homogeneous Dirichlet value 0, beyond a side wall it has weight 0; the
+ * three axes combine as a tensor product.  With a constant coefficient it is
+ * the trilinear interpolation. */
 typedef enum gmg_prolongation {
   GMG_PROLONG_TRILINEAR = 0, /* cell-centred trilinear (3/4, 1/4 per axis) */
-  GMG_PROLONG_CONSTANT = 1   /* piecewise constant injection               */
+  GMG_PROLONG_CONSTANT = 1,  /* piecewise constant injection               */
+  GMG_PROLONG_OPDEP = 2      /* operator-dependent weights (default)       */
 } gmg_prolongation;
+
+/* Coarse-grid operators (Sec. 3.2 is silent on them).  Both keep a 7-point
+ * operator on every level.  GMG_COARSEN_SERIES gives each coarse face its own
+ * coefficient: along the face normal the three fine links between the two
+ * coarse cell centres (half of each coarse cell's inner link and the link
+ * they share) add in series, across it the four fine columns that cross the
+ * face add in parallel (their mean); a plate face takes half the inner link
+ * of its coarse cell in series with the fine plate face.  A constant
+ * coefficient gives the re-discretised operator.  GMG_COARSEN_MEAN
+ * re-discretises eq. (e18) with the 8-child mean of the cell coefficient. */
+typedef enum gmg_coarsening {
+  GMG_COARSEN_MEAN = 0,      /* cell coefficient = 8-child mean             */
+  GMG_COARSEN_SERIES = 1     /* per-face series-parallel coefficients
+                                (default)                                   */
+} gmg_coarsening;
 
 typedef enum gmg_smoother_pc {
   GMG_PC_SGS = 0,      /* one symmetric Gauss-Seidel sweep, red-black order */
@@ -148,6 +173,7 @@ typedef struct gmg_params {
                                   ny >= 16, nz >= 8); 1: separate residual
                                   and half-sweep kernels everywhere          */
   int cycle;                   /* gmg_cycle                                  */
+  int coarsening;              /* gmg_coarsening                             */
 } gmg_params;
 
 typedef struct gmg_solve_info {
@@ -168,12 +194,14 @@ typedef struct gmg_solve_info {
  * plate data 0 / 1, coarse_min 4, 3 Chebyshev steps (a quadratic p_n, Sec.
  * 3.2), restart 20 (the paper uses 30, Sec. 3.1), rtol 1e-8 (Sec. 5.2),
  * 10 Arnoldi steps with factors 1.1 / 0.1 (Sec. 3.2), mixed precision,
- * trilinear prolongation, SGS smoother preconditioner, MGS, double-float
- * Arnoldi product in mixed precision. */
+ * operator-dependent prolongation, series-parallel coarse operators, SGS
+ * smoother preconditioner, MGS, double-float Arnoldi product in mixed
+ * precision. */
 void gmg_default_params(gmg_params* p, int nx, int ny, int nz);
 
 /* Build a context: copy the cell coefficient a (a_dev, FP64, > 0 and finite),
- * form the coarse coefficients (8-child means), estimate the Chebyshev
+ * form the coarse operators (params.coarsening), the prolongation weights of
+ * every level (GMG_PROLONG_OPDEP), estimate the Chebyshev
  * bounds of every smoothed level by Arnoldi on B^{-1} A_l (Sec. 3.2) and
  * factor the coarsest operator (Sec. 3.2, "sequential direct solver").
  * stream: a cudaStream_t or NULL.  On success *out owns all workspace.
@@ -356,9 +384,20 @@ gmg_status gmg_level_info(const gmg_ctx* ctx, int level, int* nx, int* ny, int* 
  * interval given from outside.  GMG_ERR_ARG otherwise. */
 gmg_status gmg_level_set_bounds(gmg_ctx* ctx, int level, double lam_max, double lam_min);
 
-/* Copy the FP64 coefficient of a level (8-child means of the finer level)
- * into out_dev (FP64, that level's size). */
+/* Copy the FP64 cell coefficient of a level (the finest level's a, or the
+ * 8-child means with GMG_COARSEN_MEAN) into out_dev (FP64, that level's
+ * size).  GMG_ERR_ARG on a level that carries face coefficients. */
 gmg_status gmg_level_coefficient(gmg_ctx* ctx, int level, double* out_dev);
+
+/* The face coefficients of a level's operator, divided by h^2 (the matrix
+ * entries), widened to FP64: kx_dev[k][j][i] couples cells i-1 and i (0 at
+ * i = 0), ky_dev likewise along y (0 at j = 0), kz_dev[k][j][i] couples
+ * k-1 and k, and at k = 0 holds the bottom plate's 2 a / hz^2-type entry;
+ * ktop_dev[j][i] (ny*nx) the top plate's.  Each of kx, ky, kz has the
+ * level's size.  Works on every level (cell-form levels give the face means
+ * of eq. (e18)). */
+gmg_status gmg_level_faces(gmg_ctx* ctx, int level, double* kx_dev, double* ky_dev, double* kz_dev,
+                           double* ktop_dev);
 
 /* One V-cycle from a zero guess, z = M v (Appendix A), or full multigrid if
  * the context's cycle is GMG_CYCLE_FMG: v_dev, z_dev FP64 of the finest size.

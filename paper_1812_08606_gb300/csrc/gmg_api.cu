@@ -183,7 +183,7 @@ enum KernelClass : int {
   K_COARSE_F32, K_DOT, K_FINALIZE, K_AXPY, K_SCALE, K_UPDATE_X, K_CAST, K_COPY, K_RHS, K_FIELD, K_ADJOINT,
   K_COARSEN, K_COEF_CHECK, K_HASH, K_COARSE_ASSEMBLE, K_COARSE_FACTOR, K_DOT_F32, K_AXPY_F32, K_APPLY_DF64,
   K_SPLIT, K_CHEB_FUSED, K_CGS_DOTS, K_CGS_DOTS_F32, K_CGS_UPDATE, K_CGS_UPDATE_F32, K_LIN3, K_MGS, K_MGS_F32,
-  K_SCALE_ROUND, NK
+  K_SCALE_ROUND, K_COARSEN_FACES, K_PROLONG_WEIGHTS, NK
 };
 static const char* const kKernelNames[NK] = {
     "apply_f64", "apply_outer_f64a_f32x", "apply_f32", "residual_f64", "residual_f32", "sgs_half_f64",
@@ -192,7 +192,8 @@ static const char* const kKernelNames[NK] = {
     "multi_axpy", "scale", "update_solution", "cast", "copy", "rhs", "field", "adjoint_grad", "coarsen_coef",
     "coef_check", "hash_vector", "coarse_assemble", "coarse_factor", "multi_dot_f32", "multi_axpy_f32",
     "apply_outer_df64", "split_coef", "cheb_sgs_fused_f32", "cgs_dots", "cgs_dots_f32", "cgs_update",
-    "cgs_update_f32", "vector_lin3", "mgs_pass", "mgs_pass_f32", "scale_round"};
+    "cgs_update_f32", "vector_lin3", "mgs_pass", "mgs_pass_f32", "scale_round", "coarsen_faces",
+    "prolong_weights"};
 
 struct ProfPending {
   int cls;
@@ -211,6 +212,13 @@ struct LevelData {
   void *x = nullptr, *b = nullptr, *r = nullptr, *z = nullptr, *d = nullptr;  // level precision
   float* x2 = nullptr;  // second x buffer of the fused smoother (ping-pong), when fused
   bool fused = false;
+  // face form (coarse levels of GMG_COARSEN_SERIES): kx | ky | kz (n each) |
+  // ktop (nx * ny), level precision; no cell coefficient then
+  bool faces = false;
+  void* kf = nullptr;
+  // parent weights wx | wy | wz (3 n, level precision) of the prolongation into
+  // this level (GMG_PROLONG_OPDEP, levels >= 1)
+  void* wp = nullptr;
   double lam_max = 0, lam_min = 0, lam_hat = 0;
 };
 
@@ -510,7 +518,8 @@ gmg_status validate(const gmg_params* p, int* nlevels) {
   if (p->eig_steps < 1 || p->eig_steps > EIG_MAX_STEPS) return GMG_ERR_ARG;
   if (!(p->eig_hi > p->eig_lo) || !(p->eig_lo > 0) || !isfinite(p->eig_hi)) return GMG_ERR_ARG;
   if (p->precision != GMG_PREC_FP64 && p->precision != GMG_PREC_MIXED) return GMG_ERR_ARG;
-  if (p->prolongation != 0 && p->prolongation != 1) return GMG_ERR_ARG;
+  if (p->prolongation < GMG_PROLONG_TRILINEAR || p->prolongation > GMG_PROLONG_OPDEP) return GMG_ERR_ARG;
+  if (p->coarsening != GMG_COARSEN_MEAN && p->coarsening != GMG_COARSEN_SERIES) return GMG_ERR_ARG;
   if (p->smoother_pc < 0 || p->smoother_pc > 2) return GMG_ERR_ARG;
   if (p->orthogonalization != 0 && p->orthogonalization != 1) return GMG_ERR_ARG;
   if (p->outer_arith != GMG_OUTER_FP64 && p->outer_arith != GMG_OUTER_DOUBLE_FLOAT) return GMG_ERR_ARG;
@@ -618,16 +627,69 @@ const float* level_a<float>(const LevelData& L) { return L.a32; }
 template <>
 const double* level_a<double>(const LevelData& L) { return L.a64; }
 
+template <typename T>
+Faces<T> level_faces(const LevelData& L) {
+  const T* k = (const T*)L.kf;
+  Faces<T> F;
+  F.kx = k;
+  F.ky = k + L.n;
+  F.kz = k + 2 * L.n;
+  F.ktop = k + 3 * L.n;
+  return F;
+}
+
+// Level kernels in level precision T, on the level's cell coefficient or faces.
+template <typename T>
+gmg_status lv_apply(gmg_ctx* c, const LevelData& L, const T* x, T* y) {
+  if (!L.faces) return prof_apply<T, T, T>(c, L.g, level_a<T>(L), x, y, c->s);
+  const double bytes = ((double)L.n * 5.0 + (double)L.g.plane()) * sizeof(T);
+  return run_kernel(c, is_f32<T>() ? K_APPLY_F32 : K_APPLY_F64, bytes,
+                    [&]() { return launch_apply_faces<T, T, T>(L.g, level_faces<T>(L), x, y, c->s); });
+}
+template <typename T>
+gmg_status lv_residual(gmg_ctx* c, const LevelData& L, const T* b, const T* x, T* r, T* z, int pc) {
+  if (!L.faces) return prof_residual<T>(c, L.g, level_a<T>(L), b, x, r, z, pc, c->s);
+  const double n = (double)L.n, e = sizeof(T);
+  const double zw = pc == PC_SGS ? 0.5 * n : (pc == PC_NONE ? 0.0 : n);
+  const double bytes = n * e * (4 + (x ? 1 : 0) + (r ? 1 : 0)) + zw * e;
+  return run_kernel(c, is_f32<T>() ? K_RESIDUAL_F32 : K_RESIDUAL_F64, bytes,
+                    [&]() { return launch_residual_faces<T>(L.g, level_faces<T>(L), b, x, r, z, pc, c->s); });
+}
+template <typename T>
+gmg_status lv_sgs_half(gmg_ctx* c, const LevelData& L, const T* r, T* z, int color, T* d, T* x, double c1, double c2,
+                       int flags) {
+  if (!L.faces) return prof_sgs_half<T>(c, L.g, level_a<T>(L), r, z, color, d, x, c1, c2, flags, c->s);
+  const double n = (double)L.n, e = sizeof(T), h = 0.5 * n;
+  double bytes = 3.0 * n * e + h * e * 3;
+  if (flags & CHEB_UPDATE) bytes += h * e * (((flags & CHEB_FIRST) ? 1 : 2) + ((flags & CHEB_XZERO) ? 1 : 2));
+  return run_kernel(c, is_f32<T>() ? K_SGS_F32 : K_SGS_F64, bytes, [&]() {
+    return launch_sgs_half_faces<T>(L.g, level_faces<T>(L), r, z, color, d, x, c1, c2, flags, c->s);
+  });
+}
+template <typename T>
+gmg_status lv_residual_restrict(gmg_ctx* c, const LevelData& L, const T* b, const T* x, T* coarse) {
+  if (!L.faces || !x) return prof_residual_restrict<T>(c, L.g, level_a<T>(L), b, x, coarse, c->s);
+  return run_kernel(c, is_f32<T>() ? K_RESTRICT_F32 : K_RESTRICT_F64, (double)L.n * sizeof(T) * (5.0 + 0.125), [&]() {
+    return launch_residual_restrict_faces<T>(L.g, level_faces<T>(L), b, x, coarse, c->s);
+  });
+}
+// x += P e into level L (e on the level below).
+template <typename T>
+gmg_status lv_prolong(gmg_ctx* c, const LevelData& L, const T* e, T* x) {
+  if (c->p.prolongation != GMG_PROLONG_OPDEP) return prof_prolong_add<T>(c, L.g, e, x, c->p.prolongation, c->s);
+  return run_kernel(c, is_f32<T>() ? K_PROLONG_F32 : K_PROLONG_F64, (double)L.n * sizeof(T) * (5.0 + 0.125),
+                    [&]() { return launch_prolong_opdep<T>(L.g, e, x, (const T*)L.wp, c->s); });
+}
+
 // z = B^{-1} r on a level in precision T (the smoother's preconditioner).
 template <typename T>
 gmg_status smoother_pc(gmg_ctx* c, const LevelData& L, const T* r, T* z) {
   const int pc = c->p.smoother_pc;
-  const T* a = level_a<T>(L);
   if (pc == GMG_PC_IDENTITY) return map_err(cudaMemcpyAsync(z, r, L.n * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
-  CKS(prof_residual<T>(c, L.g, a, r, nullptr, nullptr, z, pc == GMG_PC_SGS ? PC_SGS : PC_JACOBI, c->s));
+  CKS(lv_residual<T>(c, L, r, (const T*)nullptr, (T*)nullptr, z, pc == GMG_PC_SGS ? PC_SGS : PC_JACOBI));
   if (pc == GMG_PC_SGS) {
-    CKS(prof_sgs_half<T>(c, L.g, a, r, z, 1, nullptr, nullptr, 0, 0, 0, c->s));
-    CKS(prof_sgs_half<T>(c, L.g, a, r, z, 0, nullptr, nullptr, 0, 0, 0, c->s));
+    CKS(lv_sgs_half<T>(c, L, r, z, 1, (T*)nullptr, (T*)nullptr, 0, 0, 0));
+    CKS(lv_sgs_half<T>(c, L, r, z, 0, (T*)nullptr, (T*)nullptr, 0, 0, 0));
   }
   return GMG_OK;
 }
@@ -645,7 +707,6 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
   T* V = f32 ? (T*)c->Z : (T*)(void*)c->V;  // (steps+1) vectors of n, stride n
   T* t1 = f32 ? (T*)L.r : (T*)(void*)c->bvec;
   T* t2 = f32 ? (T*)L.z : (T*)(void*)c->w;
-  const T* a = level_a<T>(L);
   CKS(prof_hash_vector<T>(c, n, V, c->s));
   CKS(norm_dev<T>(c, n, V, SL_NORM));
   CKS(prof_scale<T>(c, n, V, V, c->dscal + SL_NORM + 1, c->s));
@@ -662,7 +723,7 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
       CKS(prof_cheb_sgs_fused(c, L.g, L.a32, (const float*)L.b, (const float*)(V + (size_t)j * n), L.x2,
                               (float*)t2, 0.0, -1.0, CHEB_UPDATE | CHEB_FIRST, c->s));
     } else {
-      CKS(prof_apply<T, T, T>(c, L.g, a, V + (size_t)j * n, t1, c->s));
+      CKS(lv_apply<T>(c, L, V + (size_t)j * n, t1));
       CKS(smoother_pc<T>(c, L, t1, t2));
     }
     // One classical Gram-Schmidt pass in FP32: the bounds only steer the FP32
@@ -708,6 +769,49 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
   return GMG_OK;
 }
 
+// Coarse operators (8-child means or series-parallel faces) and the
+// prolongation weights, in level precision T from the finest level's
+// coefficient (FP32 copy in mixed precision).
+template <typename T>
+gmg_status build_operators(gmg_ctx* c) {
+  const int top = (int)c->lev.size() - 1;
+  if (c->p.coarsening == GMG_COARSEN_SERIES) {
+    for (int l = top; l >= 1; --l) {
+      const LevelData& Fi = c->lev[l];
+      LevelData& Co = c->lev[l - 1];
+      T* k = (T*)Co.kf;
+      const T* a = Fi.faces ? nullptr : level_a<T>(Fi);
+      const Faces<T> FF = Fi.faces ? level_faces<T>(Fi) : Faces<T>{};
+      const double bytes = (a ? 1.0 : 3.0) * Fi.n * sizeof(T) + (3.0 * Co.n + Co.g.plane()) * sizeof(T);
+      CKS(run_kernel(c, K_COARSEN_FACES, bytes, [&]() {
+        return launch_coarsen_faces<T>(Fi.g, a, FF, k, k + Co.n, k + 2 * Co.n, k + 3 * Co.n, c->s);
+      }));
+    }
+  } else {
+    for (int l = top; l >= 1; --l)
+      CKS(prof_coarsen_coef(c, c->lev[l].g, c->lev[l].a64, c->lev[l - 1].a64,
+                            c->mixed ? c->lev[l - 1].a32 : nullptr, c->s));
+  }
+  if (c->p.prolongation == GMG_PROLONG_OPDEP) {
+    for (int l = 1; l <= top; ++l) {
+      const LevelData& L = c->lev[l];
+      const T* a = L.faces ? nullptr : level_a<T>(L);
+      const Faces<T> FF = L.faces ? level_faces<T>(L) : Faces<T>{};
+      const double bytes = ((a ? 1.0 : 3.0) + 3.0) * L.n * sizeof(T);
+      CKS(run_kernel(c, K_PROLONG_WEIGHTS, bytes,
+                     [&]() { return launch_prolong_weights<T>(L.g, a, FF, (T*)L.wp, c->s); }));
+    }
+  }
+  return GMG_OK;
+}
+
+template <typename T>
+gmg_status assemble_coarse_faces(gmg_ctx* c, const LevelData& C0) {
+  return run_kernel(c, K_COARSE_ASSEMBLE, 8.0 * C0.n * C0.n, [&]() {
+    return launch_coarse_assemble_faces<T>(C0.g, level_faces<T>(C0), c->cA, c->s);
+  });
+}
+
 gmg_status build(gmg_ctx* c, const double* a_dev) {
   const double t0 = now_ms();
   LevelData& F = c->lev.back();
@@ -719,13 +823,14 @@ gmg_status build(gmg_ctx* c, const double* a_dev) {
   CKS(prof_copy_d(c, F.n, a_dev, F.a64, c->s));
   if (c->mixed) CKS(prof_cast_d2f(c, F.n, F.a64, F.a32, c->s));
   if (F.a2) CKS(prof_split(c, F.n, F.a64, F.a2, c->s));
-  for (int l = (int)c->lev.size() - 1; l >= 1; --l)
-    CKS(prof_coarsen_coef(c, c->lev[l].g, c->lev[l].a64, c->lev[l - 1].a64, c->mixed ? c->lev[l - 1].a32 : nullptr,
-                           c->s));
+  CKS(c->mixed ? build_operators<float>(c) : build_operators<double>(c));
   for (int l = 1; l < (int)c->lev.size(); ++l) CKS(c->mixed ? eig_bounds<float>(c, l) : eig_bounds<double>(c, l));
   // coarsest: dense Cholesky and explicit inverse
   const LevelData& C0 = c->lev[0];
-  CKS(prof_coarse_assemble(c, C0.g, C0.a64, c->cA, c->s));
+  if (C0.faces)
+    CKS(c->mixed ? assemble_coarse_faces<float>(c, C0) : assemble_coarse_faces<double>(c, C0));
+  else
+    CKS(prof_coarse_assemble(c, C0.g, C0.a64, c->cA, c->s));
   CKS(prof_coarse_factor(c, c->nc, c->cA, c->cW, c->cinv64, c->cinv32, c->cstatus, c->s));
   CK(launch_words_to_host(c->cstatus, c->hstat_dev, sizeof(int), c->s));
   CK(cudaStreamSynchronize(c->s));
@@ -750,7 +855,6 @@ const double* coarse_inv<double>(const gmg_ctx* c) { return c->cinv64; }
 template <typename T>
 gmg_status smooth(gmg_ctx* c, int l, const T* b, T* x, bool x_is_zero) {
   const LevelData& L = c->lev[l];
-  const T* a = level_a<T>(L);
   T* r = (T*)L.r;
   T* z = (T*)L.z;
   T* d = (T*)L.d;
@@ -772,15 +876,15 @@ gmg_status smooth(gmg_ctx* c, int l, const T* b, T* x, bool x_is_zero) {
     }
     const T* rr;
     if (st == 0 && x_is_zero) {
-      CKS(prof_residual<T>(c, L.g, a, b, nullptr, nullptr, z, pc, c->s));
+      CKS(lv_residual<T>(c, L, b, (const T*)nullptr, (T*)nullptr, z, pc));
       rr = b;
     } else {
-      CKS(prof_residual<T>(c, L.g, a, b, x, r, z, pc, c->s));
+      CKS(lv_residual<T>(c, L, b, x, r, z, pc));
       rr = r;
     }
     if (pc == GMG_PC_SGS) {
-      CKS(prof_sgs_half<T>(c, L.g, a, rr, z, 1, d, x, c1, c2, flags, c->s));
-      CKS(prof_sgs_half<T>(c, L.g, a, rr, z, 0, d, x, c1, c2, flags, c->s));
+      CKS(lv_sgs_half<T>(c, L, rr, z, 1, d, x, c1, c2, flags));
+      CKS(lv_sgs_half<T>(c, L, rr, z, 0, d, x, c1, c2, flags));
     } else {
       CKS(prof_cheb_update<T>(c, L.n, z, d, x, c1, c2, flags, c->s));
     }
@@ -822,7 +926,6 @@ gmg_status vcycle(gmg_ctx* c, int l, const T* b, T* x, bool from_guess = false) 
   if (l == 0) return (prof_coarse_apply<T>(c, c->nc, coarse_inv<T>(c), b, x, c->s));
   const LevelData& L = c->lev[l];
   const LevelData& Lc = c->lev[l - 1];
-  const T* a = level_a<T>(L);
   if constexpr (sizeof(T) == 4) {
     if (L.fused) {
       // pre-smoothing ends in the buffer that post-smoothing does not write first
@@ -830,16 +933,16 @@ gmg_status vcycle(gmg_ctx* c, int l, const T* b, T* x, bool from_guess = false) 
       float* pre = (c->p.cheb_steps % 2) ? U : x;
       float* pre_alt = (pre == U) ? x : U;
       CKS(smooth_fused(c, l, b, from_guess ? x : nullptr, pre, pre_alt));
-      CKS(prof_residual_restrict<float>(c, L.g, a, b, pre, (float*)Lc.b, c->s));
+      CKS(lv_residual_restrict<float>(c, L, b, pre, (float*)Lc.b));
       CKS(vcycle<float>(c, l - 1, (const float*)Lc.b, (float*)Lc.x));
-      CKS(prof_prolong_add<float>(c, L.g, (const float*)Lc.x, pre, c->p.prolongation, c->s));
+      CKS(lv_prolong<float>(c, L, (const float*)Lc.x, pre));
       return smooth_fused(c, l, b, pre, x, U);
     }
   }
   CKS(smooth<T>(c, l, b, x, !from_guess));
-  CKS(prof_residual_restrict<T>(c, L.g, a, b, x, (T*)Lc.b, c->s));
+  CKS(lv_residual_restrict<T>(c, L, b, x, (T*)Lc.b));
   CKS(vcycle<T>(c, l - 1, (const T*)Lc.b, (T*)Lc.x));
-  CKS(prof_prolong_add<T>(c, L.g, (const T*)Lc.x, x, c->p.prolongation, c->s));
+  CKS(lv_prolong<T>(c, L, (const T*)Lc.x, x));
   CKS(smooth<T>(c, l, b, x, false));
   return GMG_OK;
 }
@@ -854,8 +957,7 @@ template <typename T>
 gmg_status fmg(gmg_ctx* c, int top, const T* b, T* z) {
   const T* bl = b;
   for (int l = top; l >= 1; --l) {
-    CKS(prof_residual_restrict<T>(c, c->lev[l].g, level_a<T>(c->lev[l]), bl, (const T*)nullptr,
-                                  (T*)c->lev[l - 1].b, c->s));
+    CKS(lv_residual_restrict<T>(c, c->lev[l], bl, (const T*)nullptr, (T*)c->lev[l - 1].b));
     bl = (const T*)c->lev[l - 1].b;
   }
   CKS(prof_coarse_apply<T>(c, c->nc, coarse_inv<T>(c), (const T*)c->lev[0].b, (T*)c->lev[0].x, c->s));
@@ -864,7 +966,7 @@ gmg_status fmg(gmg_ctx* c, int top, const T* b, T* z) {
     T* xl = l == top ? z : (T*)L.x;
     const T* blv = l == top ? b : (const T*)L.b;
     CK(cudaMemsetAsync(xl, 0, L.n * sizeof(T), c->s));
-    CKS(prof_prolong_add<T>(c, L.g, (const T*)c->lev[l - 1].x, xl, c->p.prolongation, c->s));
+    CKS(lv_prolong<T>(c, L, (const T*)c->lev[l - 1].x, xl));
     CKS(vcycle<T>(c, l, blv, xl, true));
   }
   return GMG_OK;
@@ -1326,12 +1428,13 @@ void gmg_default_params(gmg_params* p, int nx, int ny, int nz) {
   p->eig_hi = 1.1;
   p->eig_lo = 0.1;
   p->precision = GMG_PREC_MIXED;
-  p->prolongation = GMG_PROLONG_TRILINEAR;
+  p->prolongation = GMG_PROLONG_OPDEP;
   p->smoother_pc = GMG_PC_SGS;
   p->orthogonalization = GMG_ORTH_MGS;
   p->outer_arith = GMG_OUTER_DOUBLE_FLOAT;
   p->smoother_kernel = 0;
   p->cycle = GMG_CYCLE_V;
+  p->coarsening = GMG_COARSEN_SERIES;
 }
 
 const char* gmg_status_string(gmg_status s) {
@@ -1399,15 +1502,23 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
   for (int l = 0; l < L; ++l) {
     LevelData& D = c->lev[l];
     const bool top = l == L - 1;
-    if ((st = dalloc(c, &D.a64, D.n)) != GMG_OK) return fail(st);
-    if (c->mixed && (st = dalloc(c, &D.a32, D.n)) != GMG_OK) return fail(st);
+    D.faces = p->coarsening == GMG_COARSEN_SERIES && !top;
+    if (D.faces) {
+      if ((st = dev_alloc(c, &D.kf, (3 * D.n + D.g.plane()) * c->esz)) != GMG_OK) return fail(st);
+    } else {
+      if ((st = dalloc(c, &D.a64, D.n)) != GMG_OK) return fail(st);
+      if (c->mixed && (st = dalloc(c, &D.a32, D.n)) != GMG_OK) return fail(st);
+    }
+    if (l > 0 && p->prolongation == GMG_PROLONG_OPDEP &&
+        (st = dev_alloc(c, &D.wp, 3 * D.n * c->esz)) != GMG_OK)
+      return fail(st);
     if (top && c->mixed && p->outer_arith == GMG_OUTER_DOUBLE_FLOAT) {
       if ((st = dalloc(c, &D.a2, D.n)) != GMG_OK) return fail(st);
       D.dc = make_df_coef(D.g);
     }
     if (!top && (st = dev_alloc(c, &D.x, D.n * c->esz)) != GMG_OK) return fail(st);
     if ((!top || c->mixed) && (st = dev_alloc(c, &D.b, D.n * c->esz)) != GMG_OK) return fail(st);
-    D.fused = c->mixed && l > 0 && p->smoother_pc == GMG_PC_SGS && p->smoother_kernel == 0 &&
+    D.fused = c->mixed && l > 0 && !D.faces && p->smoother_pc == GMG_PC_SGS && p->smoother_kernel == 0 &&
               fused_smoother_eligible(D.g);
     if (D.fused && (st = dalloc(c, &D.x2, D.n)) != GMG_OK) return fail(st);
     if (l > 0 || L == 1) {
@@ -1762,8 +1873,21 @@ gmg_status gmg_level_set_bounds(gmg_ctx* c, int level, double lam_max, double la
 
 gmg_status gmg_level_coefficient(gmg_ctx* c, int level, double* out_dev) {
   LevelData* L = level_ptr(c, level);
-  if (!L || !out_dev) return GMG_ERR_ARG;
+  if (!L || !out_dev || L->faces) return GMG_ERR_ARG;
   return (prof_copy_d(c, L->n, L->a64, out_dev, c->s));
+}
+
+gmg_status gmg_level_faces(gmg_ctx* c, int level, double* kx, double* ky, double* kz, double* ktop) {
+  LevelData* L = level_ptr(c, level);
+  if (!L || !kx || !ky || !kz || !ktop) return GMG_ERR_ARG;
+  if (!L->faces) return map_err(launch_faces_of_cells<double>(L->g, L->a64, kx, ky, kz, ktop, c->s));
+  double* outs[4] = {kx, ky, kz, ktop};
+  const size_t cnt[4] = {L->n, L->n, L->n, L->g.plane()};
+  for (int q = 0; q < 4; ++q) {
+    if (c->mixed) CKS(prof_cast_f2d(c, cnt[q], (const float*)L->kf + q * L->n, outs[q], c->s));
+    else CKS(prof_copy_d(c, cnt[q], (const double*)L->kf + q * L->n, outs[q], c->s));
+  }
+  return GMG_OK;
 }
 
 gmg_status gmg_apply_preconditioner(gmg_ctx* c, const double* v_dev, double* z_dev) {
@@ -1796,8 +1920,8 @@ gmg_status gmg_apply_outer(gmg_ctx* c, const float* z, double* w) {
 gmg_status gmg_level_apply(gmg_ctx* c, int level, const void* x, void* y) {
   LevelData* L = level_ptr(c, level);
   if (!L || !x || !y) return GMG_ERR_ARG;
-  if (c->mixed) return (prof_apply<float, float, float>(c, L->g, L->a32, (const float*)x, (float*)y, c->s));
-  return (prof_apply<double, double, double>(c, L->g, L->a64, (const double*)x, (double*)y, c->s));
+  if (c->mixed) return lv_apply<float>(c, *L, (const float*)x, (float*)y);
+  return lv_apply<double>(c, *L, (const double*)x, (double*)y);
 }
 
 gmg_status gmg_level_smooth(gmg_ctx* c, int level, const void* b, void* x, int x_is_zero) {
@@ -1825,18 +1949,15 @@ gmg_status gmg_level_smoother_pc(gmg_ctx* c, int level, const void* r, void* z) 
 gmg_status gmg_level_residual_restrict(gmg_ctx* c, int level, const void* b, const void* x, void* coarse) {
   LevelData* L = level_ptr(c, level);
   if (!L || level == 0 || !b || !x || !coarse) return GMG_ERR_ARG;
-  if (c->mixed)
-    return (prof_residual_restrict<float>(c, L->g, L->a32, (const float*)b, (const float*)x, (float*)coarse,
-                                                   c->s));
-  return (prof_residual_restrict<double>(c, L->g, L->a64, (const double*)b, (const double*)x,
-                                                  (double*)coarse, c->s));
+  if (c->mixed) return lv_residual_restrict<float>(c, *L, (const float*)b, (const float*)x, (float*)coarse);
+  return lv_residual_restrict<double>(c, *L, (const double*)b, (const double*)x, (double*)coarse);
 }
 
 gmg_status gmg_level_prolong_add(gmg_ctx* c, int level, const void* e, void* x) {
   LevelData* L = level_ptr(c, level);
   if (!L || level == 0 || !e || !x) return GMG_ERR_ARG;
-  if (c->mixed) return (prof_prolong_add<float>(c, L->g, (const float*)e, (float*)x, c->p.prolongation, c->s));
-  return (prof_prolong_add<double>(c, L->g, (const double*)e, (double*)x, c->p.prolongation, c->s));
+  if (c->mixed) return lv_prolong<float>(c, *L, (const float*)e, (float*)x);
+  return lv_prolong<double>(c, *L, (const double*)e, (double*)x);
 }
 
 gmg_status gmg_coarse_solve(gmg_ctx* c, const void* b, void* x) {

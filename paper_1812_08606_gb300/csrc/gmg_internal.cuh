@@ -46,6 +46,18 @@ struct GridCoef<double> {
 
 Grid3 make_grid(int nx, int ny, int nz, double lx, double ly, double lz);
 
+// Face form of a level's operator (the coarse levels of the series-parallel
+// coarsening, k_faces.cu): matrix entries (coefficient / h^2) of the low faces
+// of every cell, kx (0 at i = 0), ky (0 at j = 0), kz (the bottom plate's
+// entry at k = 0), and the top plate's entries ktop (nx * ny).
+template <typename T>
+struct Faces {
+  const T* kx = nullptr;
+  const T* ky = nullptr;
+  const T* kz = nullptr;
+  const T* ktop = nullptr;
+};
+
 // Smoother-preconditioner choice, matching gmg_smoother_pc.
 enum PcKind : int { PC_SGS = 0, PC_JACOBI = 1, PC_IDENTITY = 2, PC_NONE = 3 };
 
@@ -214,6 +226,40 @@ inline bool pair_aligned(const void* p) { return ((uintptr_t)p & 7) == 0; }
 cudaError_t launch_restrict_pairs(const Grid3& g, const float* a, const float* b, const float* x, float* coarse,
                                   cudaStream_t s);
 cudaError_t launch_prolong_pairs(const Grid3& g, const float* e, float* x, int mode, cudaStream_t s);
+
+// ---- Face-form levels and the operator-dependent prolongation (k_faces.cu) ----
+// y = A x, r/z of the smoother residual, a red-black half-sweep and the fused
+// residual + restriction, as the cell-form launchers above but on faces.
+template <typename T, typename TX, typename TY>
+cudaError_t launch_apply_faces(const Grid3& g, const Faces<T>& F, const TX* x, TY* y, cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual_faces(const Grid3& g, const Faces<T>& F, const T* b, const T* x, T* r, T* z, int pc,
+                                  cudaStream_t s);
+template <typename T>
+cudaError_t launch_sgs_half_faces(const Grid3& g, const Faces<T>& F, const T* r, T* z, int color, T* d, T* x,
+                                  double c1, double c2, int flags, cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual_restrict_faces(const Grid3& g, const Faces<T>& F, const T* b, const T* x, T* coarse,
+                                           cudaStream_t s);
+// The coarse level's faces (kx, ky, kz, ktop, coarse size) from fine grid g
+// whose operator is the cell coefficient a (non-null) or the faces F.
+template <typename T>
+cudaError_t launch_coarsen_faces(const Grid3& g, const T* a, const Faces<T>& F, T* kx, T* ky, T* kz, T* ktop,
+                                 cudaStream_t s);
+// Parent weights (wx | wy | wz, 3 n) of the prolongation into grid g, from its
+// operator (cell coefficient a or faces F).
+template <typename T>
+cudaError_t launch_prolong_weights(const Grid3& g, const T* a, const Faces<T>& F, T* w, cudaStream_t s);
+// x_fine += P e with those weights; g is the fine grid.
+template <typename T>
+cudaError_t launch_prolong_opdep(const Grid3& g, const T* e, T* x, const T* w, cudaStream_t s);
+// FP64 face entries of a cell-form level (eq. (e18)).
+template <typename T>
+cudaError_t launch_faces_of_cells(const Grid3& g, const T* a, double* kx, double* ky, double* kz, double* ktop,
+                                  cudaStream_t s);
+// Dense coarsest operator (n x n, FP64) from faces.
+template <typename T>
+cudaError_t launch_coarse_assemble_faces(const Grid3& g, const Faces<T>& F, double* A, cudaStream_t s);
 
 // coarse coefficient = mean of the 8 children (FP64), plus an FP32 copy if c32.
 cudaError_t launch_coarsen_coef(const Grid3& g_fine, const double* a, double* ac, float* ac32,

@@ -29,6 +29,9 @@ GMG_PREC_FP64 = 0
 GMG_PREC_MIXED = 1
 GMG_PROLONG_TRILINEAR = 0
 GMG_PROLONG_CONSTANT = 1
+GMG_PROLONG_OPDEP = 2
+GMG_COARSEN_MEAN = 0
+GMG_COARSEN_SERIES = 1
 GMG_PC_SGS = 0
 GMG_PC_JACOBI = 1
 GMG_PC_IDENTITY = 2
@@ -61,6 +64,7 @@ class gmg_params(ctypes.Structure):
         ("eig_hi", ctypes.c_double), ("eig_lo", ctypes.c_double), ("precision", ctypes.c_int),
         ("prolongation", ctypes.c_int), ("smoother_pc", ctypes.c_int), ("orthogonalization", ctypes.c_int),
         ("outer_arith", ctypes.c_int), ("smoother_kernel", ctypes.c_int), ("cycle", ctypes.c_int),
+        ("coarsening", ctypes.c_int),
     ]
 
 
@@ -122,6 +126,7 @@ _SIGS = {
     "gmg_destroy": (None, [_P]),
     "gmg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gmg_num_levels": (ctypes.c_int, [_P]),
+    "gmg_level_faces": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P]),
     "gmg_level_set_bounds": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
     "gmg_level_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
@@ -370,6 +375,17 @@ def gmg_level_info(ctx: Context, level: int):
     _check(load().gmg_level_info(ctx.handle, int(level), ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(nz),
                                  ctypes.byref(lmax), ctypes.byref(lmin)), "gmg_level_info")
     return {"shape": (nz.value, ny.value, nx.value), "lam_max": lmax.value, "lam_min": lmin.value}
+
+
+def gmg_level_faces(ctx: Context, level: int):
+    """(kx, ky, kz, ktop) FP64 device tensors: the level's face matrix entries."""
+    shape = gmg_level_info(ctx, level)["shape"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    kx, ky, kz = (torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(3))
+    ktop = torch.empty(shape[1:], dtype=torch.float64, device=dev)
+    _check(load().gmg_level_faces(ctx.handle, int(level), kx.data_ptr(), ky.data_ptr(), kz.data_ptr(),
+                                  ktop.data_ptr()), "gmg_level_faces")
+    return kx, ky, kz, ktop
 
 
 def gmg_level_set_bounds(ctx: Context, level: int, lam_max: float, lam_min: float):

@@ -123,7 +123,7 @@ def test_vcycle_whole_column_split_elementwise(split_case):
     levels = [O.Level(O.Grid(nx, ny, nz), a)]
     for _ in range(L - 1):
         prev = levels[-1]
-        levels.append(O.Level(prev.grid.coarser(), O.coarsen_coefficient(prev.a)))
+        levels.append(O.Level(prev.grid.coarser(), O.coarsen_level(prev.a, params)))
     hier = O.Hierarchy(params, list(reversed(levels)))
     for lev in hier.levels[1:]:
         lev.lam_max, lev.lam_min = LAM_MAX, LAM_MIN

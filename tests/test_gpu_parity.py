@@ -86,10 +86,45 @@ def _oracle_hierarchy(a, p):
     op = O.OracleParams(lx=p.lx, ly=p.ly, lz=p.lz, phi_bottom=p.phi_bottom, phi_top=p.phi_top,
                         coarse_min=p.coarse_min, cheb_steps=p.cheb_steps, restart=p.restart,
                         max_iters=p.max_iters, rtol=p.rtol, eig_steps=p.eig_steps, eig_hi=p.eig_hi,
-                        eig_lo=p.eig_lo, prolongation=["trilinear", "constant"][p.prolongation],
+                        eig_lo=p.eig_lo, prolongation=["trilinear", "constant", "opdep"][p.prolongation],
                         smoother_pc=["sgs", "jacobi", "identity"][p.smoother_pc],
-                        cycle=["v", "fmg", "auto"][p.cycle])
+                        cycle=["v", "fmg", "auto"][p.cycle], coarsening=["mean", "series"][p.coarsening])
     return op
+
+
+def _olevels(a, p):
+    """The oracle's operator of every level (index 0 = coarsest, as the
+    library numbers them): the cell coefficient on the finest level and, below,
+    what the context's coarsening makes of it (FaceCoefficients or 8-child
+    means)."""
+    op = _oracle_hierarchy(a, p)
+    ops = [a]
+    for _ in range(O.level_count(p.nx, p.ny, p.nz, p.coarse_min) - 1):
+        ops.append(O.coarsen_level(ops[-1], op))
+    return ops[::-1]
+
+
+def _q32(op):
+    """The FP32 rounding of an operator (cell coefficient or faces), in FP64."""
+    r = lambda v: v.astype(np.float32).astype(np.float64)   # noqa: E731
+    if isinstance(op, O.FaceCoefficients):
+        return O.FaceCoefficients(r(op.ax), r(op.ay), r(op.az), r(op.bottom), r(op.top))
+    return r(op)
+
+
+def _face_entries(grid, op):
+    """(kx, ky, kz, ktop) of an oracle operator in the library's face layout:
+    matrix entries of each cell's low faces, the bottom plate at k = 0."""
+    cx, cy, cz = O.face_coefficients(grid, op)
+    pb, pt = O.plate_coefficients(grid, op)
+    kx = np.zeros(grid.shape)
+    kx[:, :, 1:] = cx
+    ky = np.zeros(grid.shape)
+    ky[:, 1:, :] = cy
+    kz = np.empty(grid.shape)
+    kz[1:] = cz
+    kz[0] = pb
+    return kx, ky, kz, pt
 
 
 # ---------------------------------------------------------------------------
@@ -166,33 +201,45 @@ def test_mixed_eigen_bounds_close_to_fp64():
         assert info["lam_max"] == pytest.approx(hier.levels[lev].lam_max, rel=1e-4)
 
 
+@pytest.mark.parametrize("coarsening", [gmg.GMG_COARSEN_SERIES, gmg.GMG_COARSEN_MEAN])
 @pytest.mark.parametrize("prec", [gmg.GMG_PREC_FP64, gmg.GMG_PREC_MIXED])
-def test_level_coefficients_and_operators(prec):
+def test_level_coefficients_and_operators(prec, coarsening):
+    """Every level's operator against the oracle's: the 8-child means or the
+    series-parallel faces element by element (the face entries of the
+    finest, cell-coefficient level too), and y = A_l x."""
     shape = RAGGED
     a = random_coefficient(104, shape, contrast=1e3)
-    p = _params(shape, coarse_min=2, precision=prec)
+    p = _params(shape, coarse_min=2, precision=prec, coarsening=coarsening)
     ctx = gmg.gmg_setup(p, _t(a))
     L = gmg.gmg_num_levels(ctx)
     assert L == 4
-    ref_a = a
+    ops = _olevels(a, p)
     dt = ctx.level_dtype
+    fp32 = dt == torch.float32
     for lev in range(L - 1, -1, -1):
         info = gmg.gmg_level_info(ctx, lev)
         s = info["shape"]
-        assert s == ref_a.shape
-        ac = torch.empty(s, dtype=torch.float64, device=DEV)
-        gmg.gmg_level_coefficient(ctx, lev, ac)
-        np.testing.assert_allclose(_np(ac), ref_a, rtol=1e-15)
+        g = _ogrid(s)
+        op = ops[lev]
+        if not isinstance(op, O.FaceCoefficients):
+            assert s == op.shape
+            ac = torch.empty(s, dtype=torch.float64, device=DEV)
+            gmg.gmg_level_coefficient(ctx, lev, ac)
+            np.testing.assert_allclose(_np(ac), op, rtol=1e-15)
+        else:
+            with pytest.raises(gmg.GMGError):
+                gmg.gmg_level_coefficient(ctx, lev, torch.empty(s, dtype=torch.float64, device=DEV))
+        ftol = 5e-6 if (fp32 and isinstance(op, O.FaceCoefficients)) else 1e-14
+        for got, want, name in zip(gmg.gmg_level_faces(ctx, lev), _face_entries(g, op), "xyzt"):
+            got = _np(got)
+            assert np.all(np.abs(got - want) <= ftol * np.abs(want) + 1e-300), (lev, name)
         x = random_field(105 + lev, s)
-        xin = x.astype(np.float32).astype(np.float64) if dt == torch.float32 else x
-        ain = ref_a.astype(np.float32).astype(np.float64) if dt == torch.float32 else ref_a
+        xin = x.astype(np.float32).astype(np.float64) if fp32 else x
         y = torch.empty(s, dtype=dt, device=DEV)
         gmg.gmg_level_apply(ctx, lev, _t(xin, dt), y)
-        ref = O.apply_operator(_ogrid(s), ain, xin)
+        ref = O.apply_operator(g, _q32(op) if fp32 else op, xin)
         tol = 1e-14 if dt == torch.float64 else 5e-6
         _close(_np(y), ref, tol, lev)
-        if lev > 0:
-            ref_a = O.coarsen_coefficient(ref_a)
 
 
 # ---------------------------------------------------------------------------
@@ -210,12 +257,12 @@ def test_smoother_preconditioner_and_chebyshev(prec, pc):
     ctx = gmg.gmg_setup(p, _t(a))
     dt = ctx.level_dtype
     fp32 = dt == torch.float32
-    q = (lambda v: v.astype(np.float32).astype(np.float64)) if fp32 else (lambda v: v)
+    q = _q32 if fp32 else (lambda v: v)
     tol = 2e-5 if fp32 else 1e-13
     # the oracle's own bounds drive both sides' Chebyshev steps
     hier = O.build_hierarchy(_ogrid(shape), a, op)
-    oa = a
     for lev in range(gmg.gmg_num_levels(ctx) - 1, 0, -1):
+        oa = hier.levels[lev].a
         gmg.gmg_level_set_bounds(ctx, lev, hier.levels[lev].lam_max, hier.levels[lev].lam_min)
         info = gmg.gmg_level_info(ctx, lev)
         s = info["shape"]
@@ -235,7 +282,6 @@ def test_smoother_preconditioner_and_chebyshev(prec, pc):
             ref = O.chebyshev_smooth(g, q(oa), b, None if x_is_zero else x0, lv.lam_max, lv.lam_min,
                                      p.cheb_steps, op.smoother_pc)
             _close(_np(x), ref, 5 * tol, ("cheb", lev, x_is_zero))
-        oa = O.coarsen_coefficient(oa)
 
 
 # A Chebyshev interval for smoother-only checks: the SSOR-preconditioned
@@ -251,8 +297,9 @@ def test_fused_smoother_matches_separate_kernels_and_oracle(shape, cm):
     partial 64 x 16 tiles and several z-chunks."""
     a = make_inputs("twochannel512", shape=shape)["a"]
     ctxs = [gmg.gmg_setup(_params(shape, coarse_min=cm, smoother_kernel=k), _t(a)) for k in (0, 1)]
-    oa = a
+    ops = _olevels(a, ctxs[0].params)
     for lev in range(gmg.gmg_num_levels(ctxs[0]) - 1, 0, -1):
+        oa = _q32(ops[lev])
         for ctx in ctxs:   # one interval, given from outside, for every side
             gmg.gmg_level_set_bounds(ctx, lev, FIXED_LAM_MAX, FIXED_LAM_MIN)
         info = gmg.gmg_level_info(ctxs[0], lev)
@@ -265,12 +312,11 @@ def test_fused_smoother_matches_separate_kernels_and_oracle(shape, cm):
                 x = _t(x0, torch.float32)
                 gmg.gmg_level_smooth(ctx, lev, _t(b, torch.float32), x, x_is_zero)
                 outs.append(_np(x))
-            ref = O.chebyshev_smooth(_ogrid(s), oa.astype(np.float32).astype(np.float64), b.astype(np.float64),
+            ref = O.chebyshev_smooth(_ogrid(s), oa, b.astype(np.float64),
                                      None if x_is_zero else x0.astype(np.float64), FIXED_LAM_MAX,
                                      FIXED_LAM_MIN, 3, "sgs")
             _close(outs[0], outs[1], 1e-5, (lev, x_is_zero))
             _close(outs[0], ref, 1e-4, (lev, x_is_zero))
-        oa = O.coarsen_coefficient(oa)
     v = random_field(320, shape)
     zs = []
     for ctx in ctxs:
@@ -304,16 +350,21 @@ def test_eigen_bounds_match_oracle():
 # spans 3 and 2 warps and the x-neighbours cross warp and block boundaries.
 @pytest.mark.parametrize("shape", [RAGGED, (8, 24, 144)])
 @pytest.mark.parametrize("prec", [gmg.GMG_PREC_FP64, gmg.GMG_PREC_MIXED])
-@pytest.mark.parametrize("mode", [gmg.GMG_PROLONG_TRILINEAR, gmg.GMG_PROLONG_CONSTANT])
-def test_transfers_and_coarse_solve(prec, mode, shape):
+@pytest.mark.parametrize("mode,coarsening", [(gmg.GMG_PROLONG_OPDEP, gmg.GMG_COARSEN_SERIES),
+                                             (gmg.GMG_PROLONG_OPDEP, gmg.GMG_COARSEN_MEAN),
+                                             (gmg.GMG_PROLONG_TRILINEAR, gmg.GMG_COARSEN_SERIES),
+                                             (gmg.GMG_PROLONG_TRILINEAR, gmg.GMG_COARSEN_MEAN),
+                                             (gmg.GMG_PROLONG_CONSTANT, gmg.GMG_COARSEN_MEAN)])
+def test_transfers_and_coarse_solve(prec, mode, coarsening, shape):
     a = random_coefficient(150, shape, contrast=1e2)
-    p = _params(shape, coarse_min=2, precision=prec, prolongation=mode)
+    p = _params(shape, coarse_min=2, precision=prec, prolongation=mode, coarsening=coarsening)
     ctx = gmg.gmg_setup(p, _t(a))
     dt = ctx.level_dtype
     fp32 = dt == torch.float32
-    q = (lambda v: v.astype(np.float32).astype(np.float64)) if fp32 else (lambda v: v)
+    q = _q32 if fp32 else (lambda v: v)
     tol = 2e-6 if fp32 else 1e-14
-    oa = a
+    ops = _olevels(a, p)
+    kind = ["trilinear", "constant", "opdep"][mode]
     L = gmg.gmg_num_levels(ctx)
     for lev in range(L - 1, 0, -1):
         s = gmg.gmg_level_info(ctx, lev)["shape"]
@@ -321,20 +372,19 @@ def test_transfers_and_coarse_solve(prec, mode, shape):
         b, x = q(random_field(151 + lev, s)), q(random_field(161 + lev, s))
         coarse = torch.empty(sc, dtype=dt, device=DEV)
         gmg.gmg_level_residual_restrict(ctx, lev, _t(b, dt), _t(x, dt), coarse)
-        ref = O.restrict(b - O.apply_operator(_ogrid(s), q(oa), x))
+        ref = O.restrict(b - O.apply_operator(_ogrid(s), q(ops[lev]), x))
         _close(_np(coarse), ref, (5e-5 if fp32 else 1e-13), ("restrict", lev))
         e = q(random_field(171 + lev, sc))
         xt = _t(x, dt)
         gmg.gmg_level_prolong_add(ctx, lev, _t(e, dt), xt)
-        ref = x + O.prolong(e, ["trilinear", "constant"][mode])
+        ref = x + O.prolong(e, kind, q(ops[lev]))
         _close(_np(xt), ref, tol, ("prolong", lev))
-        oa = O.coarsen_coefficient(oa)
     # coarsest direct solve
     sc = gmg.gmg_level_info(ctx, 0)["shape"]
     b = q(random_field(180, sc))
     x = torch.empty(sc, dtype=dt, device=DEV)
     gmg.gmg_coarse_solve(ctx, _t(b, dt), x)
-    A = O.dense_operator(_ogrid(sc), oa)
+    A = O.dense_operator(_ogrid(sc), ops[0])
     ref = np.linalg.solve(A, b.ravel()).reshape(sc)
     _close(_np(x), ref, (1e-5 if fp32 else 1e-12))
 

@@ -37,8 +37,10 @@ def _t(x):
 
 def _coarse_case(shape, coarse_min, seed, lengths=(1.0, 1.0, 1.0)):
     nz, ny, nx = shape
+    # the allocation-free solve takes a cell coefficient (eq. (e18)), so the
+    # context keeps cell coefficients on its coarse levels (8-child means)
     p = gmg.gmg_default_params(nx, ny, nz, coarse_min=coarse_min, precision=gmg.GMG_PREC_FP64,
-                               lx=lengths[0], ly=lengths[1], lz=lengths[2])
+                               lx=lengths[0], ly=lengths[1], lz=lengths[2], coarsening=gmg.GMG_COARSEN_MEAN)
     ctx = gmg.gmg_setup(p, _t(random_coefficient(seed, shape, contrast=1e3)))
     info = gmg.gmg_level_info(ctx, 0)
     cshape = info["shape"]
