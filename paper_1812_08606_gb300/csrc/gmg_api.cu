@@ -673,6 +673,16 @@ gmg_status lv_residual_restrict(gmg_ctx* c, const LevelData& L, const T* b, cons
     return launch_residual_restrict_faces<T>(L.g, level_faces<T>(L), b, x, coarse, c->s);
   });
 }
+// One fused Chebyshev + SSOR step on an FP32 level (cell or face form).
+gmg_status lv_cheb_fused(gmg_ctx* c, const LevelData& L, const float* b, const float* xin, float* xout,
+                         double c1, double c2, int flags) {
+  if (!L.faces) return prof_cheb_sgs_fused(c, L.g, L.a32, b, xin, xout, (float*)L.d, c1, c2, flags, c->s);
+  const double words = 2.0 + (xin ? 1.0 : 0.0) + ((flags & CHEB_FIRST) ? 0.0 : 1.0) + 2.0 + 2.0;
+  return run_kernel(c, K_CHEB_FUSED, 4.0 * words * L.n, [&]() {
+    return launch_cheb_sgs_fused_faces(L.g, level_faces<float>(L), b, xin, xout, (float*)L.d, c1, c2, flags, c->s);
+  });
+}
+
 // x += P e into level L (e on the level below).
 template <typename T>
 gmg_status lv_prolong(gmg_ctx* c, const LevelData& L, const T* e, T* x) {
@@ -720,8 +730,13 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
   if (fused_mv) CK(cudaMemsetAsync(L.b, 0, n * sizeof(float), c->s));
   for (int j = 0; j < steps; ++j) {
     if (fused_mv) {
-      CKS(prof_cheb_sgs_fused(c, L.g, L.a32, (const float*)L.b, (const float*)(V + (size_t)j * n), L.x2,
-                              (float*)t2, 0.0, -1.0, CHEB_UPDATE | CHEB_FIRST, c->s));
+      {
+        // the product writes d = B^{-1} A v into t2: the level's own d stays untouched
+        LevelData Lt = L;
+        Lt.d = t2;
+        CKS(lv_cheb_fused(c, Lt, (const float*)L.b, (const float*)(V + (size_t)j * n), L.x2, 0.0, -1.0,
+                          CHEB_UPDATE | CHEB_FIRST));
+      }
     } else {
       CKS(lv_apply<T>(c, L, V + (size_t)j * n, t1));
       CKS(smoother_pc<T>(c, L, t1, t2));
@@ -915,7 +930,7 @@ gmg_status smooth_fused(gmg_ctx* c, int l, const float* b, const float* xin, flo
     }
     float* dst = ((s - 1 - st) % 2 == 0) ? target : alt;
     if (dst == cur) return GMG_ERR_ARG;
-    CKS(prof_cheb_sgs_fused(c, L.g, L.a32, b, cur, dst, (float*)L.d, c1, c2, flags, c->s));
+    CKS(lv_cheb_fused(c, L, b, cur, dst, c1, c2, flags));
     cur = dst;
   }
   return GMG_OK;
@@ -1518,7 +1533,7 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
     }
     if (!top && (st = dev_alloc(c, &D.x, D.n * c->esz)) != GMG_OK) return fail(st);
     if ((!top || c->mixed) && (st = dev_alloc(c, &D.b, D.n * c->esz)) != GMG_OK) return fail(st);
-    D.fused = c->mixed && l > 0 && !D.faces && p->smoother_pc == GMG_PC_SGS && p->smoother_kernel == 0 &&
+    D.fused = c->mixed && l > 0 && p->smoother_pc == GMG_PC_SGS && p->smoother_kernel == 0 &&
               fused_smoother_eligible(D.g);
     if (D.fused && (st = dalloc(c, &D.x2, D.n)) != GMG_OK) return fail(st);
     if (l > 0 || L == 1) {

@@ -198,6 +198,9 @@ cudaError_t launch_sgs_half(const Grid3& g, const T* a, const T* r, T* z, int co
 bool fused_smoother_eligible(const Grid3& g);
 cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b, const float* xin, float* xout,
                                   float* d, double c1, double c2, int flags, cudaStream_t s);
+// The same step on a face-form level (all face arrays 8-byte aligned).
+cudaError_t launch_cheb_sgs_fused_faces(const Grid3& g, const Faces<float>& F, const float* b, const float* xin,
+                                        float* xout, float* d, double c1, double c2, int flags, cudaStream_t s);
 
 // Pointwise Chebyshev update on all cells: d = c1 d + c2 z; x += d.
 template <typename T>

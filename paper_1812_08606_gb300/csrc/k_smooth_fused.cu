@@ -53,10 +53,14 @@ constexpr int RP = 32, RW = 2 * RP, HX = 4, HY = 3, FTX = RW - 2 * HX, FTY = 18,
 constexpr int PPL = RP * RH;  // pairs per region plane = threads per block
 constexpr int NAS = 4, NXS = 2, NZS = 2;
 constexpr size_t FUSED_SMEM = (size_t)(NAS + NXS) * PPL * sizeof(float2) + (size_t)(2 * NZS) * PPL * sizeof(float);
+// The face-form variant also keeps NAS planes of the y-face entries (the cell
+// form's a planes hold the x-face entries there).
+constexpr size_t FUSED_SMEM_FACE = FUSED_SMEM + (size_t)NAS * PPL * sizeof(float2);
 
 struct FusedArgs {
   Grid3 g;
-  const float* a;
+  const float* a;   // cell form (FACE = false)
+  Faces<float> f;   // face form (FACE = true)
   const float* b;
   const float* xin;  // null: x_in = 0
   float* xout;
@@ -76,10 +80,20 @@ __device__ __forceinline__ float lane(float2 v, int i) { return i ? v.y : v.x; }
 
 // Planes [k0, k1) of tile (bx, by).  Leaves shared memory in use: the caller
 // synchronises before the next segment.
+//
+// FACE: the level's operator is given by face entries (the coarse levels of
+// the series-parallel coarsening).  The shared planes of a then hold the
+// pairs' x-face entries (left face of each cell), a second set of planes the
+// y-face entries (face below each cell), and the register window of a holds
+// the z-face entries (face below each cell; the plane above the top one is the
+// top plate's entries).  Entries beyond the domain load as zero and a plate's
+// neighbour value is zero, so the plate and wall cases need no branches.
+template <bool FACE>
 __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, const int bx, const int by,
                                               const int k0, const int k1) {
-  float2* const As = smf2;               // NAS planes of a
-  float2* const Xs = As + NAS * PPL;     // NXS planes of x_in
+  float2* const As = smf2;               // NAS planes of a (FACE: x-face entries)
+  float2* const Ys = As + NAS * PPL;     // FACE: NAS planes of y-face entries
+  float2* const Xs = FACE ? Ys + NAS * PPL : As + NAS * PPL;  // NXS planes of x_in
   float* const Z1s = reinterpret_cast<float*>(Xs + NXS * PPL);  // red z of the residual stage
   float* const ZBs = Z1s + NZS * PPL;                              // black z
   const Grid3& g = P.g;
@@ -106,7 +120,10 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
   const int blo = max(0, k0 - 1), bhi = min(nz, k1 + 1);
   // pair offsets in 32 bits (fused_smoother_eligible keeps (nz + 4) planes of pairs below 2^31)
   const int qo = in ? (gy * nx + gx0) >> 1 : 0;  // pair offset in a plane
-  const float2* A2 = reinterpret_cast<const float2*>(P.a);
+  const float2* A2 = reinterpret_cast<const float2*>(FACE ? P.f.kz : P.a);  // FACE: z-face entries
+  const float2* KX2 = reinterpret_cast<const float2*>(P.f.kx);
+  const float2* KY2 = reinterpret_cast<const float2*>(P.f.ky);
+  const float2* KT2 = reinterpret_cast<const float2*>(P.f.ktop);
   const float2* X2 = reinterpret_cast<const float2*>(P.xin);
   const float2* B2 = reinterpret_cast<const float2*>(P.b);
   const float2* D2 = reinterpret_cast<const float2*>(P.d);
@@ -122,11 +139,18 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
   float z1w0 = 0.f, z1w1 = 0.f, z1w2 = 0.f;                               // red z: t-3 .. t-1
   float zbw0 = 0.f, zbw1 = 0.f, zbw2 = 0.f;                               // black z: t-4 .. t-2
   float2 pa = zero2, px = zero2, pb = zero2, pbn = zero2, pd = zero2, pdn = zero2;
+  float2 pkx = zero2, pky = zero2;  // FACE: x- and y-face entries of the next plane
   {
     const int k = k0 - 3;
     if (in && k >= 0 && k < nz) {
       pa = __ldg(A2 + (k * pl2 + qo));
       if (!xzero) px = __ldg(X2 + (k * pl2 + qo));
+      if constexpr (FACE) {
+        pkx = __ldg(KX2 + (k * pl2 + qo));
+        pky = __ldg(KY2 + (k * pl2 + qo));
+      }
+    } else if (FACE && in && k == nz) {
+      pa = __ldg(KT2 + qo);
     }
   }
 
@@ -141,14 +165,26 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
     // ---- commit plane t (prefetched during the previous step) ----
     aw0 = aw1; aw1 = aw2; aw2 = aw3; aw3 = aw4; aw4 = pa;
     xw0 = xw1; xw1 = xw2; xw2 = xw3; xw3 = px;
-    As[(t & 3) * PPL + me] = pa;
+    if constexpr (FACE) {
+      As[(t & 3) * PPL + me] = pkx;
+      Ys[(t & 3) * PPL + me] = pky;
+    } else {
+      As[(t & 3) * PPL + me] = pa;
+    }
     Xs[(t & 1) * PPL + me] = px;
     // ---- prefetch for the next step ----
     pa = px = zero2;
+    if constexpr (FACE) pkx = pky = zero2;
     const int ot = t * pl2 + qo;  // pair offset of plane t
     if (in && (ST || (t + 1 >= 0 && t + 1 < nz && t + 1 <= k1 + 2))) {
       pa = __ldg(A2 + (ot + pl2));
       if (!xzero) px = __ldg(X2 + (ot + pl2));
+      if constexpr (FACE) {
+        pkx = __ldg(KX2 + (ot + pl2));
+        pky = __ldg(KY2 + (ot + pl2));
+      }
+    } else if (FACE && !ST && in && t + 1 == nz && t + 1 <= k1 + 2) {
+      pa = __ldg(KT2 + qo);  // the top plate's entries, as the z face above plane nz - 1
     }
     if (rst && (ST || (t >= rlo && t < rhi))) pbn = __ldg(B2 + ot);
     if (fst && !first && (ST || (t - 2 >= k0 && t - 2 < k1))) pdn = __ldg(D2 + (ot - 2 * pl2));
@@ -158,7 +194,30 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
     {
       float2 r = zero2, di = zero2;
       float z1 = 0.f;
-      if (rst && (ST || (kr >= rlo && kr < rhi))) {
+      if (FACE && rst && (ST || (kr >= rlo && kr < rhi))) {
+        // face form: D = sum of the six entries; A x with zero beyond the plates
+        const float2* xc = Xs + (kr & 1) * PPL;
+        const float2 kxo = As[(kr & 3) * PPL + me], kxn = As[(kr & 3) * PPL + me + 1];
+        const float2 fxm = kxo, fxp = make_float2(kxo.y, kxn.x);
+        const float2 fym = Ys[(kr & 3) * PPL + me], fyp = Ys[(kr & 3) * PPL + me + RP];
+        const float2 fzm = aw3, fzp = aw4;  // planes kr and kr + 1
+        const float2 D = add2(add2(add2(fxm, fxp), add2(fym, fyp)), add2(fzm, fzp));
+        r = pb;
+        if (!xzero) {
+          const float2 x2 = xw2;  // plane kr
+          const float2 xl = xc[me - 1], xr = xc[me + 1];
+          const float2 xL = make_float2(xl.y, x2.x), xR = make_float2(x2.y, xr.x);
+          float2 ax = mul2(fxm, sub2(x2, xL));
+          ax = fma2(fxp, sub2(x2, xR), ax);
+          ax = fma2(fym, sub2(x2, xc[me - RP]), ax);
+          ax = fma2(fyp, sub2(x2, xc[me + RP]), ax);
+          ax = fma2(fzm, sub2(x2, xw1), ax);
+          ax = fma2(fzp, sub2(x2, xw3), ax);
+          r = sub2(r, ax);
+        }
+        di = make_float2(__fdividef(1.f, D.x), __fdividef(1.f, D.y));
+        z1 = lane(r, L) * lane(di, L);
+      } else if (!FACE && rst && (ST || (kr >= rlo && kr < rhi))) {
         const bool zlo = ST || kr > 0, zhi = ST || kr < nz - 1;
         const float2* ac = As + (kr & 3) * PPL;
         const float2* xc = Xs + (kr & 1) * PPL;
@@ -210,7 +269,18 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
     {
       float zb = 0.f;
       const bool colok = L ? bcol1 : bcol0;
-      if (bst && colok && (ST || (kb >= blo && kb < bhi))) {
+      if (FACE && bst && colok && (ST || (kb >= blo && kb < bhi))) {
+        const float* zc = Z1s + (kb & 1) * PPL;
+        const float2 kxo = As[(kb & 3) * PPL + me];
+        const float fout = L ? As[(kb & 3) * PPL + me + 1].x : kxo.x;
+        float N = kxo.y * z1w1;                          // the face between the pair's cells
+        N = fmaf(fout, L ? zc[me + 1] : zc[me - 1], N);
+        N = fmaf(lane(Ys[(kb & 3) * PPL + me], L), zc[me - RP], N);
+        N = fmaf(lane(Ys[(kb & 3) * PPL + me + RP], L), zc[me + RP], N);
+        N = fmaf(lane(aw2, L), z1w0, N);                 // z faces of plane kb (below) and kb + 1 (above)
+        N = fmaf(lane(aw3, L), z1w2, N);
+        zb = (lane(rw1, L) + N) * lane(dw1, L);
+      } else if (!FACE && bst && colok && (ST || (kb >= blo && kb < bhi))) {
         const bool zlo = ST || kb > 0, zhi = ST || kb < nz - 1;
         const float2* ac = As + (kb & 3) * PPL;
         const float* zc = Z1s + (kb & 1) * PPL;
@@ -234,21 +304,34 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
     // ---- final stage, plane kf = t - 3: red z and the Chebyshev update ----
     const int kf = t - 3;
     if (fst && (ST || (kf >= k0 && kf < k1))) {
-      const bool zlo = ST || kf > 0, zhi = ST || kf < nz - 1;
-      const float2* ac = As + (kf & 3) * PPL;
-      const float* zc = ZBs + (kf & 1) * PPL;
-      const float a0 = lane(aw1, L);      // plane kf
-      const float ain = lane(aw1, L ^ 1);
-      const float aout = L ? ac[me + 1].x : ac[me - 1].y;
-      const float mout = L ? mxr : mxl;
-      float sx = (a0 + ain) * zbw1;  // zbw1: black z of this pair, plane kf
-      sx = fmaf((a0 + aout) * mout, L ? zc[me + 1] : zc[me - 1], sx);
-      float sy = (a0 + lane(ac[me - RP], L)) * my0 * zc[me - RP];
-      sy = fmaf((a0 + lane(ac[me + RP], L)) * my1, zc[me + RP], sy);
-      float sz = 0.f;
-      if (zlo) sz = (a0 + lane(aw0, L)) * zbw0;
-      if (zhi) sz = fmaf(a0 + lane(aw2, L), zbw2, sz);
-      const float N = fmaf(g.fx, sx, fmaf(g.fy, sy, g.fz * sz));
+      float N;
+      if constexpr (FACE) {
+        const float* zc = ZBs + (kf & 1) * PPL;
+        const float2 kxo = As[(kf & 3) * PPL + me];
+        const float fout = L ? As[(kf & 3) * PPL + me + 1].x : kxo.x;
+        N = kxo.y * zbw1;
+        N = fmaf(fout, L ? zc[me + 1] : zc[me - 1], N);
+        N = fmaf(lane(Ys[(kf & 3) * PPL + me], L), zc[me - RP], N);
+        N = fmaf(lane(Ys[(kf & 3) * PPL + me + RP], L), zc[me + RP], N);
+        N = fmaf(lane(aw1, L), zbw0, N);               // z faces of plane kf (below) and kf + 1 (above)
+        N = fmaf(lane(aw2, L), zbw2, N);
+      } else {
+        const bool zlo = ST || kf > 0, zhi = ST || kf < nz - 1;
+        const float2* ac = As + (kf & 3) * PPL;
+        const float* zc = ZBs + (kf & 1) * PPL;
+        const float a0 = lane(aw1, L);      // plane kf
+        const float ain = lane(aw1, L ^ 1);
+        const float aout = L ? ac[me + 1].x : ac[me - 1].y;
+        const float mout = L ? mxr : mxl;
+        float sx = (a0 + ain) * zbw1;  // zbw1: black z of this pair, plane kf
+        sx = fmaf((a0 + aout) * mout, L ? zc[me + 1] : zc[me - 1], sx);
+        float sy = (a0 + lane(ac[me - RP], L)) * my0 * zc[me - RP];
+        sy = fmaf((a0 + lane(ac[me + RP], L)) * my1, zc[me + RP], sy);
+        float sz = 0.f;
+        if (zlo) sz = (a0 + lane(aw0, L)) * zbw0;
+        if (zhi) sz = fmaf(a0 + lane(aw2, L), zbw2, sz);
+        N = fmaf(g.fx, sx, fmaf(g.fy, sy, g.fz * sz));
+      }
       const float zr = (lane(rw0, L) + N) * lane(dw0, L);
       const float2 z = L ? make_float2(zbw1, zr) : make_float2(zr, zbw1);
       const float2 c2 = sc2(P.c2);
@@ -291,6 +374,7 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
   }
 }
 
+template <bool FACE>
 __global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
   extern __shared__ float2 smf2[];
   const int nz = P.g.nz;
@@ -299,7 +383,7 @@ __global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
   const long long full = P.units / nz / G;
   for (long long r = 0; r < full; ++r) {
     const int tile = (int)(r * G + b);
-    fused_segment(P, smf2, tile % P.tiles_x, tile / P.tiles_x, 0, nz);
+    fused_segment<FACE>(P, smf2, tile % P.tiles_x, tile / P.tiles_x, 0, nz);
     __syncthreads();
   }
   // leftover columns: an equal contiguous share of their (tile, plane) units
@@ -310,7 +394,7 @@ __global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
     const int tile = (int)(u / nz);
     const int k0 = (int)(u - (long long)tile * nz);
     const int k1 = (int)min((long long)nz, k0 + (end - u));
-    fused_segment(P, smf2, tile % P.tiles_x, tile / P.tiles_x, k0, k1);
+    fused_segment<FACE>(P, smf2, tile % P.tiles_x, tile / P.tiles_x, k0, k1);
     u += k1 - k0;
     __syncthreads();
   }
@@ -319,25 +403,39 @@ __global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
 // Per device: the kernel's shared-memory attribute is set and its resident
 // block count known (0 = not yet).  Guarded by a mutex for host threads.
 constexpr int kMaxDevices = 64;
-int g_fused_slots[kMaxDevices] = {};
+int g_fused_slots[2][kMaxDevices] = {};
 std::mutex g_fused_mutex;
 
+template <bool FACE>
 cudaError_t fused_slots(int* out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  const size_t smem = FACE ? FUSED_SMEM_FACE : FUSED_SMEM;
   std::lock_guard<std::mutex> lock(g_fused_mutex);
-  if (g_fused_slots[dev] == 0) {
-    e = cudaFuncSetAttribute(k_cheb_sgs_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM);
+  int& slots = g_fused_slots[FACE ? 1 : 0][dev];
+  if (slots == 0) {
+    e = cudaFuncSetAttribute(k_cheb_sgs_fused<FACE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int sms = 0, per = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cheb_sgs_fused, PPL, FUSED_SMEM);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cheb_sgs_fused<FACE>, PPL, smem);
     if (e != cudaSuccess) return e;
-    g_fused_slots[dev] = std::max(1, sms * std::max(1, per));
+    slots = std::max(1, sms * std::max(1, per));
   }
-  *out = g_fused_slots[dev];
+  *out = slots;
   return cudaSuccess;
+}
+
+template <bool FACE>
+cudaError_t launch_fused(const FusedArgs& P, long long units, cudaStream_t s) {
+  int slots = 0;
+  const cudaError_t e = fused_slots<FACE>(&slots);
+  if (e != cudaSuccess) return e;
+  // one block per resident slot, but at least 4 planes per block on small grids
+  const long long blocks = std::max(1LL, std::min((long long)slots, units / 4));
+  k_cheb_sgs_fused<FACE><<<(unsigned)blocks, dim3(RP, RH), FACE ? FUSED_SMEM_FACE : FUSED_SMEM, s>>>(P);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -351,16 +449,21 @@ cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b
                                     float* d, double c1, double c2, int flags, cudaStream_t s) {
   if (!pair_aligned(a) || !pair_aligned(b) || (xin && !pair_aligned(xin)) || !pair_aligned(xout) || !pair_aligned(d))
     return cudaErrorMisalignedAddress;
-  int slots = 0;
-  const cudaError_t e = fused_slots(&slots);
-  if (e != cudaSuccess) return e;
   const int tx = (g.nx + FTX - 1) / FTX, ty = (g.ny + FTY - 1) / FTY;
   const long long units = (long long)tx * ty * g.nz;
-  // one block per resident slot, but at least 4 planes per block on small grids
-  const long long blocks = std::max(1LL, std::min((long long)slots, units / 4));
-  FusedArgs P{g, a, b, xin, xout, d, (float)c1, (float)c2, flags, tx, units};
-  k_cheb_sgs_fused<<<(unsigned)blocks, dim3(RP, RH), FUSED_SMEM, s>>>(P);
-  return cudaGetLastError();
+  FusedArgs P{g, a, Faces<float>{}, b, xin, xout, d, (float)c1, (float)c2, flags, tx, units};
+  return launch_fused<false>(P, units, s);
+}
+
+cudaError_t launch_cheb_sgs_fused_faces(const Grid3& g, const Faces<float>& F, const float* b, const float* xin,
+                                        float* xout, float* d, double c1, double c2, int flags, cudaStream_t s) {
+  if (!pair_aligned(F.kx) || !pair_aligned(F.ky) || !pair_aligned(F.kz) || !pair_aligned(F.ktop) ||
+      !pair_aligned(b) || (xin && !pair_aligned(xin)) || !pair_aligned(xout) || !pair_aligned(d))
+    return cudaErrorMisalignedAddress;
+  const int tx = (g.nx + FTX - 1) / FTX, ty = (g.ny + FTY - 1) / FTY;
+  const long long units = (long long)tx * ty * g.nz;
+  FusedArgs P{g, nullptr, F, b, xin, xout, d, (float)c1, (float)c2, flags, tx, units};
+  return launch_fused<true>(P, units, s);
 }
 
 }  // namespace gmg
