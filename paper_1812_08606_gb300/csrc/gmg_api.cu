@@ -496,9 +496,17 @@ gmg_status prof_apply_df64(gmg_ctx* c, const Grid3& g, const DfCoef& dc, const f
                            cudaStream_t s) {
   GMG_RUN(K_APPLY_DF64, 20.0 * g.n(), launch_apply_df64(g, dc, a2, z, w, s));
 }
+// Words per cell a fused step moves: a, b (not for the eigen product), x_in (if
+// any), d (unless the first step), x_out (not for the eigen product), d
+// (unless the last step).
+double fused_words(bool xin, int flags) {
+  const bool eig = (flags & CHEB_EIG) != 0;
+  return 1.0 + (eig ? 0.0 : 1.0) + (xin ? 1.0 : 0.0) + ((flags & CHEB_FIRST) ? 0.0 : 1.0) + (eig ? 0.0 : 1.0) +
+         ((flags & CHEB_LAST) ? 0.0 : 1.0);
+}
 gmg_status prof_cheb_sgs_fused(gmg_ctx* c, const Grid3& g, const float* a, const float* b, const float* xin,
                                float* xout, float* d, double c1, double c2, int flags, cudaStream_t s) {
-  const double words = 2.0 + (xin ? 1.0 : 0.0) + ((flags & CHEB_FIRST) ? 0.0 : 1.0) + 2.0;
+  const double words = fused_words(xin != nullptr, flags);
   GMG_RUN(K_CHEB_FUSED, 4.0 * words * g.n(), launch_cheb_sgs_fused(g, a, b, xin, xout, d, c1, c2, flags, s));
 }
 gmg_status prof_split(gmg_ctx* c, size_t n, const double* a, float2* a2, cudaStream_t s) {
@@ -677,7 +685,7 @@ gmg_status lv_residual_restrict(gmg_ctx* c, const LevelData& L, const T* b, cons
 gmg_status lv_cheb_fused(gmg_ctx* c, const LevelData& L, const float* b, const float* xin, float* xout,
                          double c1, double c2, int flags) {
   if (!L.faces) return prof_cheb_sgs_fused(c, L.g, L.a32, b, xin, xout, (float*)L.d, c1, c2, flags, c->s);
-  const double words = 2.0 + (xin ? 1.0 : 0.0) + ((flags & CHEB_FIRST) ? 0.0 : 1.0) + 2.0 + 2.0;
+  const double words = fused_words(xin != nullptr, flags) + 2.0;  // three face arrays instead of a
   return run_kernel(c, K_CHEB_FUSED, 4.0 * words * L.n, [&]() {
     return launch_cheb_sgs_fused_faces(L.g, level_faces<float>(L), b, xin, xout, (float*)L.d, c1, c2, flags, c->s);
   });
@@ -725,9 +733,9 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
   // After a breakdown (||w|| = 0) the later vectors are zero and their columns
   // are dropped on the host.
   const bool fused_mv = sizeof(T) == 4 && L.fused;
-  // On levels with the fused smoother, one fused step forms the product:
-  // with b = 0, x_in = v and c2 = -1 its direction d equals B^{-1}(A v).
-  if (fused_mv) CK(cudaMemsetAsync(L.b, 0, n * sizeof(float), c->s));
+  // On levels with the fused smoother, one fused step forms the product: with
+  // b = 0 (not read), x_in = v and c2 = -1 its direction d equals B^{-1}(A v);
+  // x_out is not written.
   for (int j = 0; j < steps; ++j) {
     if (fused_mv) {
       {
@@ -735,7 +743,7 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
         LevelData Lt = L;
         Lt.d = t2;
         CKS(lv_cheb_fused(c, Lt, (const float*)L.b, (const float*)(V + (size_t)j * n), L.x2, 0.0, -1.0,
-                          CHEB_UPDATE | CHEB_FIRST));
+                          CHEB_UPDATE | CHEB_FIRST | CHEB_EIG));
       }
     } else {
       CKS(lv_apply<T>(c, L, V + (size_t)j * n, t1));
@@ -928,6 +936,7 @@ gmg_status smooth_fused(gmg_ctx* c, int l, const float* b, const float* xin, flo
       c2 = 2.0 * rho_new / delta;
       rho = rho_new;
     }
+    if (st == s - 1) flags |= CHEB_LAST;
     float* dst = ((s - 1 - st) % 2 == 0) ? target : alt;
     if (dst == cur) return GMG_ERR_ARG;
     CKS(lv_cheb_fused(c, L, b, cur, dst, c1, c2, flags));

@@ -61,8 +61,11 @@ struct Faces {
 // Smoother-preconditioner choice, matching gmg_smoother_pc.
 enum PcKind : int { PC_SGS = 0, PC_JACOBI = 1, PC_IDENTITY = 2, PC_NONE = 3 };
 
-// Flags of the Chebyshev update fused into the smoother kernels.
-enum ChebFlags : int { CHEB_UPDATE = 1, CHEB_FIRST = 2, CHEB_XZERO = 4 };
+// Flags of the Chebyshev update fused into the smoother kernels.  The fused
+// kernel also takes CHEB_LAST (the last step of a smoothing: d is dead after
+// it and not written) and CHEB_EIG (the eigen-estimate product B^{-1} A x_in:
+// b is taken as zero and not read, only d is written).
+enum ChebFlags : int { CHEB_UPDATE = 1, CHEB_FIRST = 2, CHEB_XZERO = 4, CHEB_LAST = 8, CHEB_EIG = 16 };
 
 // ----------------------------------------------------------------------------
 // Device helpers

@@ -78,6 +78,13 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 sc2(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float lane(float2 v, int i) { return i ? v.y : v.x; }
 
+// Kind of step, fixed at compile time (each kind is its own kernel, so the
+// step carries no runtime tests for it): the first step of a smoothing (d =
+// c2 z, d not read), with x_in = 0 (pre-smoothing from zero: x_in not read),
+// the last step (d is dead afterwards: not written), and the eigen-estimate
+// product (b = 0 is not read and x_out not written: only d = B^{-1} A x_in).
+enum StepMode : int { M_FIRST = 1, M_XZERO = 2, M_LAST = 4, M_EIG = 8 };
+
 // Planes [k0, k1) of tile (bx, by).  Leaves shared memory in use: the caller
 // synchronises before the next segment.
 //
@@ -88,7 +95,7 @@ __device__ __forceinline__ float lane(float2 v, int i) { return i ? v.y : v.x; }
 // the z-face entries (face below each cell; the plane above the top one is the
 // top plate's entries).  Entries beyond the domain load as zero and a plate's
 // neighbour value is zero, so the plate and wall cases need no branches.
-template <bool FACE>
+template <bool FACE, int MODE>
 __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, const int bx, const int by,
                                               const int k0, const int k1) {
   float2* const As = smf2;               // NAS planes of a (FACE: x-face entries)
@@ -103,8 +110,10 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
   const int me = ty * RP + tx;
   const int gx0 = bx * FTX - HX + 2 * tx;
   const int gy = by * FTY - HY + ty;
-  const bool xzero = P.xin == nullptr;
-  const bool first = (P.flags & CHEB_FIRST) != 0;
+  constexpr bool xzero = (MODE & M_XZERO) != 0;
+  constexpr bool first = (MODE & M_FIRST) != 0;
+  constexpr bool keep_d = (MODE & M_LAST) == 0;
+  constexpr bool eig = (MODE & M_EIG) != 0;
   const bool in = gx0 >= 0 && gx0 < nx && gy >= 0 && gy < ny;  // nx even: both cells or neither
   const bool rst = in && tx >= 1 && tx <= RP - 2 && ty >= 1 && ty <= RH - 2;            // residual: tile + 2
   const bool bst = in && ty >= 2 && ty <= RH - 3;                                        // black: tile + 1
@@ -186,7 +195,7 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
     } else if (FACE && !ST && in && t + 1 == nz && t + 1 <= k1 + 2) {
       pa = __ldg(KT2 + qo);  // the top plate's entries, as the z face above plane nz - 1
     }
-    if (rst && (ST || (t >= rlo && t < rhi))) pbn = __ldg(B2 + ot);
+    if (!eig && rst && (ST || (t >= rlo && t < rhi))) pbn = __ldg(B2 + ot);
     if (fst && !first && (ST || (t - 2 >= k0 && t - 2 < k1))) pdn = __ldg(D2 + (ot - 2 * pl2));
 
     // ---- residual stage, plane kr = t - 1: r, 1/D (both cells), red z ----
@@ -337,8 +346,8 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
       const float2 c2 = sc2(P.c2);
       const float2 dv = first ? mul2(c2, z) : fma2(sc2(P.c1), pd, mul2(c2, z));
       const int q = kf * pl2 + qo;
-      reinterpret_cast<float2*>(P.d)[q] = dv;
-      reinterpret_cast<float2*>(P.xout)[q] = xzero ? dv : add2(xw0, dv);
+      if constexpr (keep_d) reinterpret_cast<float2*>(P.d)[q] = dv;
+      if constexpr (!eig) reinterpret_cast<float2*>(P.xout)[q] = xzero ? dv : add2(xw0, dv);
     }
     pb = pbn;
     pd = pdn;
@@ -374,7 +383,7 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
   }
 }
 
-template <bool FACE>
+template <bool FACE, int MODE>
 __global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
   extern __shared__ float2 smf2[];
   const int nz = P.g.nz;
@@ -383,7 +392,7 @@ __global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
   const long long full = P.units / nz / G;
   for (long long r = 0; r < full; ++r) {
     const int tile = (int)(r * G + b);
-    fused_segment<FACE>(P, smf2, tile % P.tiles_x, tile / P.tiles_x, 0, nz);
+    fused_segment<FACE, MODE>(P, smf2, tile % P.tiles_x, tile / P.tiles_x, 0, nz);
     __syncthreads();
   }
   // leftover columns: an equal contiguous share of their (tile, plane) units
@@ -394,7 +403,7 @@ __global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
     const int tile = (int)(u / nz);
     const int k0 = (int)(u - (long long)tile * nz);
     const int k1 = (int)min((long long)nz, k0 + (end - u));
-    fused_segment<FACE>(P, smf2, tile % P.tiles_x, tile / P.tiles_x, k0, k1);
+    fused_segment<FACE, MODE>(P, smf2, tile % P.tiles_x, tile / P.tiles_x, k0, k1);
     u += k1 - k0;
     __syncthreads();
   }
@@ -406,6 +415,20 @@ constexpr int kMaxDevices = 64;
 int g_fused_slots[2][kMaxDevices] = {};
 std::mutex g_fused_mutex;
 
+// The step kinds the library launches: pre-smoothing from zero (first, x_in =
+// 0), first with x_in, middle, last (each with or without x_in = 0 for a
+// one-step smoothing), and the eigen-estimate product.
+constexpr int kModes[] = {M_FIRST | M_XZERO, M_FIRST | M_XZERO | M_LAST, M_FIRST, M_FIRST | M_LAST, 0, M_LAST,
+                          M_FIRST | M_EIG};
+
+template <bool FACE, int MODE>
+cudaError_t set_smem() {
+  return cudaFuncSetAttribute(k_cheb_sgs_fused<FACE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(FACE ? FUSED_SMEM_FACE : FUSED_SMEM));
+}
+
+// Per device and form: the shared-memory attribute of every step kind is set
+// and the resident block count known (0 = not yet).
 template <bool FACE>
 cudaError_t fused_slots(int* out) {
   int dev = 0;
@@ -416,10 +439,14 @@ cudaError_t fused_slots(int* out) {
   std::lock_guard<std::mutex> lock(g_fused_mutex);
   int& slots = g_fused_slots[FACE ? 1 : 0][dev];
   if (slots == 0) {
-    e = cudaFuncSetAttribute(k_cheb_sgs_fused<FACE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t es[] = {set_smem<FACE, kModes[0]>(), set_smem<FACE, kModes[1]>(), set_smem<FACE, kModes[2]>(),
+                              set_smem<FACE, kModes[3]>(), set_smem<FACE, kModes[4]>(), set_smem<FACE, kModes[5]>(),
+                              set_smem<FACE, kModes[6]>()};
+    for (cudaError_t q : es)
+      if (q != cudaSuccess) return q;
     int sms = 0, per = 0;
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cheb_sgs_fused<FACE>, PPL, smem);
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cheb_sgs_fused<FACE, 0>, PPL, smem);
     if (e != cudaSuccess) return e;
     slots = std::max(1, sms * std::max(1, per));
   }
@@ -434,7 +461,20 @@ cudaError_t launch_fused(const FusedArgs& P, long long units, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   // one block per resident slot, but at least 4 planes per block on small grids
   const long long blocks = std::max(1LL, std::min((long long)slots, units / 4));
-  k_cheb_sgs_fused<FACE><<<(unsigned)blocks, dim3(RP, RH), FACE ? FUSED_SMEM_FACE : FUSED_SMEM, s>>>(P);
+  const dim3 grid((unsigned)blocks), block(RP, RH);
+  const size_t smem = FACE ? FUSED_SMEM_FACE : FUSED_SMEM;
+  const int mode = ((P.flags & CHEB_FIRST) ? M_FIRST : 0) | (P.xin ? 0 : M_XZERO) | ((P.flags & CHEB_LAST) ? M_LAST : 0) |
+                   ((P.flags & CHEB_EIG) ? M_EIG : 0);
+  switch (mode) {
+    case M_FIRST | M_XZERO: k_cheb_sgs_fused<FACE, M_FIRST | M_XZERO><<<grid, block, smem, s>>>(P); break;
+    case M_FIRST | M_XZERO | M_LAST: k_cheb_sgs_fused<FACE, M_FIRST | M_XZERO | M_LAST><<<grid, block, smem, s>>>(P); break;
+    case M_FIRST: k_cheb_sgs_fused<FACE, M_FIRST><<<grid, block, smem, s>>>(P); break;
+    case M_FIRST | M_LAST: k_cheb_sgs_fused<FACE, M_FIRST | M_LAST><<<grid, block, smem, s>>>(P); break;
+    case 0: k_cheb_sgs_fused<FACE, 0><<<grid, block, smem, s>>>(P); break;
+    case M_LAST: k_cheb_sgs_fused<FACE, M_LAST><<<grid, block, smem, s>>>(P); break;
+    case M_FIRST | M_EIG: k_cheb_sgs_fused<FACE, M_FIRST | M_EIG><<<grid, block, smem, s>>>(P); break;
+    default: return cudaErrorInvalidValue;  // x_in = 0 needs the first step; the product is a first step with x_in
+  }
   return cudaGetLastError();
 }
 
