@@ -183,7 +183,7 @@ enum KernelClass : int {
   K_COARSE_F32, K_DOT, K_FINALIZE, K_AXPY, K_SCALE, K_UPDATE_X, K_CAST, K_COPY, K_RHS, K_FIELD, K_ADJOINT,
   K_COARSEN, K_COEF_CHECK, K_HASH, K_COARSE_ASSEMBLE, K_COARSE_FACTOR, K_DOT_F32, K_AXPY_F32, K_APPLY_DF64,
   K_SPLIT, K_CHEB_FUSED, K_CGS_DOTS, K_CGS_DOTS_F32, K_CGS_UPDATE, K_CGS_UPDATE_F32, K_LIN3, K_MGS, K_MGS_F32,
-  K_SCALE_ROUND, K_COARSEN_FACES, K_PROLONG_WEIGHTS, NK
+  K_SCALE_ROUND, K_COARSEN_FACES, K_PROLONG_WEIGHTS, K_HOST_GAP, NK
 };
 static const char* const kKernelNames[NK] = {
     "apply_f64", "apply_outer_f64a_f32x", "apply_f32", "residual_f64", "residual_f32", "sgs_half_f64",
@@ -193,7 +193,7 @@ static const char* const kKernelNames[NK] = {
     "coef_check", "hash_vector", "coarse_assemble", "coarse_factor", "multi_dot_f32", "multi_axpy_f32",
     "apply_outer_df64", "split_coef", "cheb_sgs_fused_f32", "cgs_dots", "cgs_dots_f32", "cgs_update",
     "cgs_update_f32", "vector_lin3", "mgs_pass", "mgs_pass_f32", "scale_round", "coarsen_faces",
-    "prolong_weights"};
+    "prolong_weights", "host_round_trip"};
 
 struct ProfPending {
   int cls;
@@ -549,11 +549,30 @@ gmg_status validate(const gmg_params* p, int* nlevels) {
 }
 
 // Read `count` device scalars from slot `slot` into ctx->hpin[slot...]; synchronises.
-gmg_status read_scalars(gmg_ctx* c, int slot, int count) {
+// With gap_start non-null (profiling on), an event is recorded on the stream
+// just before the synchronisation: it completes when the GPU has finished the
+// work the host waits for, and the interval from it to the next event the
+// host records (host_gap_end) is the time the GPU waits for the host.
+gmg_status read_scalars(gmg_ctx* c, int slot, int count, cudaEvent_t* gap_start = nullptr) {
   CK(launch_words_to_host(c->dscal + slot, c->hpin_dev + slot, sizeof(double) * count, c->s));
+  if (gap_start && c->prof_on && (*gap_start = prof_event(c)) != nullptr) cudaEventRecord(*gap_start, c->s);
   CK(cudaStreamSynchronize(c->s));
   prof_collect(c);
   return GMG_OK;
+}
+
+// Close a host round trip opened by read_scalars: the GPU sat idle from
+// gap_start until this event, enqueued once the host has done its part.
+void host_gap_end(gmg_ctx* c, cudaEvent_t gap_start) {
+  if (!gap_start) return;
+  cudaEvent_t e1 = prof_event(c);
+  if (e1 && cudaEventRecord(e1, c->s) == cudaSuccess) {
+    c->pend.push_back({K_HOST_GAP, gap_start, e1, 0.0});
+    c->k_launch[K_HOST_GAP] += 1;
+  } else {
+    c->ev_pool.push_back(gap_start);
+    if (e1) c->ev_pool.push_back(e1);
+  }
 }
 
 // Device: out slots [slot, slot+2) = (||w||, 1/||w||).
@@ -622,8 +641,8 @@ void gather_column(gmg_ctx* c, int k, double* h) {
   h[k] = c->hpin[SL_NORM];
 }
 
-gmg_status read_column(gmg_ctx* c, int k, double* h) {
-  CKS(read_scalars(c, 0, SL_NORM + 2));
+gmg_status read_column(gmg_ctx* c, int k, double* h, cudaEvent_t* gap_start = nullptr) {
+  CKS(read_scalars(c, 0, SL_NORM + 2, gap_start));
   gather_column(c, k, h);
   return GMG_OK;
 }
@@ -1100,7 +1119,9 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
         CKS(precondition(c, vj, zj));                    // z_j = M v_j (one V-cycle)
         CKS(apply_outer(c, zj, c->w));                   // w = A z_j
         CKS(orthogonalize(c, n, c->V, n, j + 1, c->w));   // Gram-Schmidt: h_{i,j}
-        CKS(read_column(c, j + 1, col.data()));          // h_{j+1,j} = ||w||
+        cudaEvent_t gap = nullptr;                       // the GPU's wait for the host's Givens step
+        CKS(read_column(c, j + 1, col.data(), &gap));    // h_{j+1,j} = ||w||
+        host_gap_end(c, gap);  // the Givens update below takes about a microsecond more
         for (int i = 0; i <= j + 1; ++i)
           if (!isfinite(col[i])) fail = true;
         if (fail) {
