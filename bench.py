@@ -367,6 +367,7 @@ def run_ours(args, dist):
         "iterations": last.iterations,
         "true_rel_residual": last.true_rel_residual,
         "setup_ms": round(statistics.mean(i.setup_ms for i in infos), 3),
+        "setup_share": round(statistics.mean(i.setup_ms for i in infos) / ms_step, 3),
         "solve_ms": round(statistics.mean(i.solve_ms for i in infos), 3),
         "res_history": [float("%.3e" % h) for h in last.history],
         "roofline": {"bound": "hbm", "kernel": top["name"], "achieved": round(achieved, 1), "peak": peak,

@@ -27,6 +27,7 @@
 // is R_n / (R_n + R_p).  At a side wall the parent's weight is 1; at a plate
 // the neighbour is the plate (value 0) with R_n = 1/k_plate.  The three axes
 // combine as a tensor product.
+#include <algorithm>
 #include <type_traits>
 
 #include "gmg_internal.cuh"
@@ -317,6 +318,94 @@ __global__ void __launch_bounds__(BX* BY) k_prolong_opdep(Grid3 g, const T* __re
   x[p] += v;
 }
 
+// The same prolongation in FP32 with one thread per fine cell pair (2 ic,
+// 2 ic + 1) of one fine row j, marching through coarse planes [kc0, kc1)
+// (fine planes 2 kc, 2 kc + 1).  The thread keeps its coarse column ic (rows jc
+// and the y-neighbour row jn, planes kc - 1 .. kc + 1) in registers; the
+// columns ic - 1 and ic + 1 come from the neighbouring lanes by shuffle (the
+// first and last lane of a warp load theirs).  Each fine cell interpolates the
+// two columns it needs in y and z with its own weights, then combines them in
+// x.  Weights, x and e are read as float2 pairs: 8-byte aligned arrays, nx even.
+constexpr int PTP = 32;  // pairs per row = lanes
+constexpr int PTR = 8;   // fine rows per block
+constexpr unsigned FULLMASK = 0xffffffffu;
+
+__global__ void __launch_bounds__(PTP* PTR) k_prolong_opdep_pairs(Grid3 g, const float* __restrict__ e,
+                                                                float* __restrict__ x, const float* __restrict__ w,
+                                                                int kchunk) {
+  const int nx = g.nx, ny = g.ny;
+  const int nxc = nx / 2, nyc = ny / 2, nzc = g.nz / 2;
+  const int tx = threadIdx.x;
+  const int ip = blockIdx.x * PTP + tx;
+  const int j = blockIdx.y * PTR + threadIdx.y;
+  const int kc0 = blockIdx.z * kchunk, kc1 = min(nzc, kc0 + kchunk);
+  const bool act = ip < nxc && j < ny;
+  const int jc = j >> 1;
+  int jn = (j & 1) ? jc + 1 : jc - 1;
+  if (jn < 0 || jn >= nyc) jn = jc;  // side wall: the weight array gives this neighbour weight 0
+  const int ih = tx == 0 ? ip - 1 : (tx == PTP - 1 ? ip + 1 : -1);  // the edge lanes' extra column
+  const bool hact = act && ih >= 0 && ih < nxc;
+  // 32-bit offsets: the launcher keeps nz + 4 planes of fine cells below 2^31
+  const int pc = nyc * nxc;
+  const int rc = act ? jc * nxc : 0, rn = act ? jn * nxc : 0;
+  auto ld = [&](bool on, int kc, int row, int col) {
+    return (on && kc >= 0 && kc < nzc) ? __ldg(e + (kc * pc + row + col)) : 0.f;
+  };
+  // coarse planes kc - 1, kc, kc + 1 of rows (jc, jn): own column (c*, n*) and extra column (h*, q*)
+  float cm = ld(act, kc0 - 1, rc, ip), nm = ld(act, kc0 - 1, rn, ip);
+  float c0 = ld(act, kc0, rc, ip), n0 = ld(act, kc0, rn, ip);
+  float cp = ld(act, kc0 + 1, rc, ip), np = ld(act, kc0 + 1, rn, ip);
+  float hm = ld(hact, kc0 - 1, rc, ih), qm = ld(hact, kc0 - 1, rn, ih);
+  float h0 = ld(hact, kc0, rc, ih), q0 = ld(hact, kc0, rn, ih);
+  float hp = ld(hact, kc0 + 1, rc, ih), qp = ld(hact, kc0 + 1, rn, ih);
+  const int n = (int)g.n();
+  const int pl2 = (int)(g.plane() >> 1);
+  const int q = act ? (j * nx + 2 * ip) >> 1 : 0;
+  float2* X2 = reinterpret_cast<float2*>(x);
+  const float2* WX = reinterpret_cast<const float2*>(w);
+  const float2* WY = reinterpret_cast<const float2*>(w + n);
+  const float2* WZ = reinterpret_cast<const float2*>(w + 2 * n);
+  for (int kc = kc0; kc < kc1; ++kc) {
+    const float c1 = ld(act, kc + 2, rc, ip), n1 = ld(act, kc + 2, rn, ip);
+    const float h1 = ld(hact, kc + 2, rc, ih), q1 = ld(hact, kc + 2, rn, ih);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int k = 2 * kc + half;
+      // the plane beyond the parent's on this child's side; zero beyond a plate
+      const bool kin = half ? kc + 1 < nzc : kc > 0;
+      const float oc = half ? cp : cm, on = half ? np : nm;   // own column, neighbour plane
+      const float ho = half ? hp : hm, qo = half ? qp : qm;   // extra column, neighbour plane
+      const float oz = kin ? oc : 0.f, ozn = kin ? on : 0.f, hz = kin ? ho : 0.f, qz = kin ? qo : 0.f;
+      // columns ic - 1 (from the lane on the left) and ic + 1 (on the right): rows jc, jn at kc and beyond
+      float lc = __shfl_up_sync(FULLMASK, c0, 1), ln = __shfl_up_sync(FULLMASK, n0, 1);
+      float lz = __shfl_up_sync(FULLMASK, oz, 1), lzn = __shfl_up_sync(FULLMASK, ozn, 1);
+      float uc = __shfl_down_sync(FULLMASK, c0, 1), un = __shfl_down_sync(FULLMASK, n0, 1);
+      float uz = __shfl_down_sync(FULLMASK, oz, 1), uzn = __shfl_down_sync(FULLMASK, ozn, 1);
+      if (tx == 0) { lc = h0; ln = q0; lz = hz; lzn = qz; }
+      if (tx == PTP - 1) { uc = h0; un = q0; uz = hz; uzn = qz; }
+      if (act) {
+        const int o = k * pl2 + q;
+        const float2 wx = __ldg(WX + o), wy = __ldg(WY + o), wz = __ldg(WZ + o);
+        // y then z for one column with a cell's weights
+        auto yz = [](float wyv, float wzv, float e00, float e01, float e10, float e11) {
+          const float a0 = fmaf(wyv, e00 - e01, e01);  // wy e(jc) + (1 - wy) e(jn), plane kc
+          const float a1 = fmaf(wyv, e10 - e11, e11);  // the same on the neighbour plane
+          return fmaf(wzv, a0 - a1, a1);
+        };
+        const float own0 = yz(wy.x, wz.x, c0, n0, oz, ozn), left = yz(wy.x, wz.x, lc, ln, lz, lzn);
+        const float own1 = yz(wy.y, wz.y, c0, n0, oz, ozn), right = yz(wy.y, wz.y, uc, un, uz, uzn);
+        const float v0 = fmaf(wx.x, own0 - left, left), v1 = fmaf(wx.y, own1 - right, right);
+        float2 xv = X2[o];
+        xv.x += v0;
+        xv.y += v1;
+        X2[o] = xv;
+      }
+    }
+    cm = c0; nm = n0; c0 = cp; n0 = np; cp = c1; np = n1;
+    hm = h0; qm = q0; h0 = hp; q0 = qp; hp = h1; qp = q1;
+  }
+}
+
 // Dense coarsest operator from faces, one thread per row.
 template <typename T>
 __global__ void k_coarse_assemble_faces(Grid3 g, Faces<T> F, double* __restrict__ A) {
@@ -399,6 +488,20 @@ cudaError_t launch_prolong_weights(const Grid3& g, const T* a, const Faces<T>& F
 
 template <typename T>
 cudaError_t launch_prolong_opdep(const Grid3& g, const T* e, T* x, const T* w, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (pair_aligned(x) && pair_aligned(w) && g.nx % 2 == 0 && cells_fit_int32(g) && g.n() % 2 == 0) {
+      const int gx = (g.nx / 2 + PTP - 1) / PTP, gy = (g.ny + PTR - 1) / PTR;
+      const int nzc = g.nz / 2;
+      // about two waves of 8 blocks per SM, at least 4 coarse planes per block
+      const long long target = 152LL * 8 * 2, xy = (long long)gx * gy;
+      const int zc = (int)std::max(1LL, std::min((target + xy - 1) / xy, (long long)std::max(1, nzc / 4)));
+      const int kchunk = (nzc + zc - 1) / zc;
+      const int gz = (nzc + kchunk - 1) / kchunk;
+      k_prolong_opdep_pairs<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)gz), dim3(PTP, PTR), 0, s>>>(g, e, x, w,
+                                                                                                kchunk);
+      return cudaGetLastError();
+    }
+  }
   k_prolong_opdep<T><<<grid_cells(g), dim3(BX, BY), 0, s>>>(g, e, x, w);
   return cudaGetLastError();
 }
