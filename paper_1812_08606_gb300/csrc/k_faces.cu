@@ -199,13 +199,19 @@ struct Links {
   }
 };
 
+// Quotients of the set-up: in FP32 the fast hardware reciprocal (about 2 ulp;
+// the coarse operators and the weights only shape the FP32 preconditioner),
+// in FP64 the correctly rounded division.
+__device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double quot(double a, double b) { return a / b; }
+
 template <typename T>
 __device__ __forceinline__ T series3(T k1, T k2, T k3) {
-  return (T)1 / ((T)1 / k1 + (T)2 / k2 + (T)1 / k3);
+  return quot((T)1, quot((T)1, k1) + quot((T)2, k2) + quot((T)1, k3));
 }
 template <typename T>
 __device__ __forceinline__ T series_plate(T kin, T kplate) {
-  return (T)1 / ((T)1 / kin + (T)2 / kplate);
+  return quot((T)1, quot((T)1, kin) + quot((T)2, kplate));
 }
 
 // One thread per coarse cell (I, J, K): its low faces and, on the last coarse
@@ -262,17 +268,17 @@ __device__ __forceinline__ T parent_weight(int c, int n, bool plates, F lk) {
   const int m = n / 2, I = c >> 1;
   T rp, rn;
   if ((c & 1) == 0) {
-    rp = (T)0.5 / lk(c + 1);
-    if (I > 0) rn = (T)1 / lk(c) + (T)0.5 / lk(c - 1);
-    else if (plates) rn = (T)1 / lk(0);
+    rp = quot((T)0.5, lk(c + 1));
+    if (I > 0) rn = quot((T)1, lk(c)) + quot((T)0.5, lk(c - 1));
+    else if (plates) rn = quot((T)1, lk(0));
     else return (T)1;
   } else {
-    rp = (T)0.5 / lk(c);
-    if (I < m - 1) rn = (T)1 / lk(c + 1) + (T)0.5 / lk(c + 2);
-    else if (plates) rn = (T)1 / lk(n);
+    rp = quot((T)0.5, lk(c));
+    if (I < m - 1) rn = quot((T)1, lk(c + 1)) + quot((T)0.5, lk(c + 2));
+    else if (plates) rn = quot((T)1, lk(n));
     else return (T)1;
   }
-  return rn / (rn + rp);
+  return quot(rn, rn + rp);
 }
 
 template <typename T, bool CELL>
