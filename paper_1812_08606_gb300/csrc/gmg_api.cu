@@ -183,7 +183,7 @@ enum KernelClass : int {
   K_COARSE_F32, K_DOT, K_FINALIZE, K_AXPY, K_SCALE, K_UPDATE_X, K_CAST, K_COPY, K_RHS, K_FIELD, K_ADJOINT,
   K_COARSEN, K_COEF_CHECK, K_HASH, K_COARSE_ASSEMBLE, K_COARSE_FACTOR, K_DOT_F32, K_AXPY_F32, K_APPLY_DF64,
   K_SPLIT, K_CHEB_FUSED, K_CGS_DOTS, K_CGS_DOTS_F32, K_CGS_UPDATE, K_CGS_UPDATE_F32, K_LIN3, K_MGS, K_MGS_F32,
-  K_SCALE_ROUND, K_COARSEN_FACES, K_PROLONG_WEIGHTS, K_HOST_GAP, NK
+  K_SCALE_ROUND, K_COARSEN_FACES, K_PROLONG_WEIGHTS, K_GRAM, K_HOST_GAP, NK
 };
 static const char* const kKernelNames[NK] = {
     "apply_f64", "apply_outer_f64a_f32x", "apply_f32", "residual_f64", "residual_f32", "sgs_half_f64",
@@ -193,7 +193,7 @@ static const char* const kKernelNames[NK] = {
     "coef_check", "hash_vector", "coarse_assemble", "coarse_factor", "multi_dot_f32", "multi_axpy_f32",
     "apply_outer_df64", "split_coef", "cheb_sgs_fused_f32", "cgs_dots", "cgs_dots_f32", "cgs_update",
     "cgs_update_f32", "vector_lin3", "mgs_pass", "mgs_pass_f32", "scale_round", "coarsen_faces",
-    "prolong_weights", "host_round_trip"};
+    "prolong_weights", "gram_f32", "host_round_trip"};
 
 struct ProfPending {
   int cls;
@@ -496,18 +496,26 @@ gmg_status prof_apply_df64(gmg_ctx* c, const Grid3& g, const DfCoef& dc, const f
                            cudaStream_t s) {
   GMG_RUN(K_APPLY_DF64, 20.0 * g.n(), launch_apply_df64(g, dc, a2, z, w, s));
 }
-// Words per cell a fused step moves: a, b (not for the eigen product), x_in (if
-// any), d (unless the first step), x_out (not for the eigen product), d
-// (unless the last step).
+// Words per cell a fused step moves: a, b (not for the eigen-estimate basis
+// step), x_in (if any), d (unless the first step), x_out, d (unless the last
+// step or the basis step).
 double fused_words(bool xin, int flags) {
   const bool eig = (flags & CHEB_EIG) != 0;
-  return 1.0 + (eig ? 0.0 : 1.0) + (xin ? 1.0 : 0.0) + ((flags & CHEB_FIRST) ? 0.0 : 1.0) + (eig ? 0.0 : 1.0) +
-         ((flags & CHEB_LAST) ? 0.0 : 1.0);
+  return 1.0 + (eig ? 0.0 : 1.0) + (xin ? 1.0 : 0.0) + ((flags & CHEB_FIRST) ? 0.0 : 1.0) + 1.0 +
+         ((flags & CHEB_LAST) || eig ? 0.0 : 1.0);
 }
 gmg_status prof_cheb_sgs_fused(gmg_ctx* c, const Grid3& g, const float* a, const float* b, const float* xin,
-                               float* xout, float* d, double c1, double c2, int flags, cudaStream_t s) {
+                               float* xout, float* d, double c1, double c2, double ce, int flags, cudaStream_t s) {
   const double words = fused_words(xin != nullptr, flags);
-  GMG_RUN(K_CHEB_FUSED, 4.0 * words * g.n(), launch_cheb_sgs_fused(g, a, b, xin, xout, d, c1, c2, flags, s));
+  GMG_RUN(K_CHEB_FUSED, 4.0 * words * g.n(), launch_cheb_sgs_fused(g, a, b, xin, xout, d, c1, c2, ce, flags, s));
+}
+gmg_status prof_gram(gmg_ctx* c, size_t n, const float* V, size_t ldv, int nv, double* partial, cudaStream_t s) {
+  GMG_RUN(K_GRAM, 4.0 * n * nv, launch_gram(n, V, ldv, nv, partial, s));
+}
+template <typename T>
+gmg_status prof_three_term(gmg_ctx* c, size_t n, const T* t, const T* v, const T* u, T* out, double alpha,
+                           double beta, double gamma, cudaStream_t s) {
+  GMG_RUN(K_LIN3, (double)sizeof(T) * n * (u ? 4 : 3), launch_three_term<T>(n, t, v, u, out, alpha, beta, gamma, s));
 }
 gmg_status prof_split(gmg_ctx* c, size_t n, const double* a, float2* a2, cudaStream_t s) {
   GMG_RUN(K_SPLIT, 16.0 * n, launch_split(n, a, a2, s));
@@ -702,11 +710,12 @@ gmg_status lv_residual_restrict(gmg_ctx* c, const LevelData& L, const T* b, cons
 }
 // One fused Chebyshev + SSOR step on an FP32 level (cell or face form).
 gmg_status lv_cheb_fused(gmg_ctx* c, const LevelData& L, const float* b, const float* xin, float* xout,
-                         double c1, double c2, int flags) {
-  if (!L.faces) return prof_cheb_sgs_fused(c, L.g, L.a32, b, xin, xout, (float*)L.d, c1, c2, flags, c->s);
+                         double c1, double c2, int flags, double ce = 0.0) {
+  if (!L.faces) return prof_cheb_sgs_fused(c, L.g, L.a32, b, xin, xout, (float*)L.d, c1, c2, ce, flags, c->s);
   const double words = fused_words(xin != nullptr, flags) + 2.0;  // three face arrays instead of a
   return run_kernel(c, K_CHEB_FUSED, 4.0 * words * L.n, [&]() {
-    return launch_cheb_sgs_fused_faces(L.g, level_faces<float>(L), b, xin, xout, (float*)L.d, c1, c2, flags, c->s);
+    return launch_cheb_sgs_fused_faces(L.g, level_faces<float>(L), b, xin, xout, (float*)L.d, c1, c2, ce, flags,
+                                       c->s);
   });
 }
 
@@ -731,6 +740,110 @@ gmg_status smoother_pc(gmg_ctx* c, const LevelData& L, const T* r, T* z) {
   return GMG_OK;
 }
 
+// Largest real Ritz value of the Krylov space of the eigen estimate, FP32
+// levels with the SSOR preconditioner.  Arnoldi (Sec. 3.2) projects
+// M = B^{-1} A_l on K_m(M, v_0) with an orthonormal basis; any basis of the
+// same nested spaces gives the same projection up to a similarity, so the
+// same Ritz values.  For symmetric Gauss-Seidel B - A_l = L D^{-1} L^T is
+// positive semi-definite, so M has its spectrum in (0, 1], and the Chebyshev
+// basis of 2M - I on it,
+//   v_1 = (2M - I) v_0,  v_{j+1} = 2 (2M - I) v_j - v_{j-1},
+// stays well conditioned.  Each basis vector is one fused smoother pass; one
+// pass over v_0 .. v_m then forms the Gram matrix G = K^T K.  With G_m = R^T R
+// (Cholesky), K_m R^{-1} is Arnoldi's orthonormal basis, and
+// H_m = R^{-T} (K_m^T M K_m) R^{-1} its Hessenberg matrix, where
+// M v_0 = (v_1 + v_0)/2 and M v_j = (v_{j+1} + 2 v_j + v_{j-1})/4 make
+// K_m^T M K_m a combination of columns of G.  This replaces Gram-Schmidt's
+// passes over all previous vectors at every step (about m^2 vector passes)
+// by m + 1.  A Cholesky pivot below kGramPivotTol of its diagonal entry is
+// what FP32 vectors cannot resolve: the space ends there (Arnoldi's
+// breakdown) and the projection keeps the vectors before it.
+constexpr double kGramPivotTol = 1e-6;
+
+gmg_status ritz_chebyshev_basis(gmg_ctx* c, int l, double* lam_out) {
+  LevelData& L = c->lev[l];
+  const size_t n = L.n;
+  const int m = c->p.eig_steps;
+  float* V = (float*)c->Z;  // (m + 1) vectors of n, stride n
+  CKS(prof_hash_vector<float>(c, n, V, c->s));
+  CKS(norm_dev<float>(c, n, V, SL_NORM));
+  CKS(prof_scale<float>(c, n, V, V, c->dscal + SL_NORM + 1, c->s));
+  for (int j = 0; j < m; ++j) {
+    // v_{j+1} = alpha M v_j + beta v_j + gamma v_{j-1}
+    const double alpha = j == 0 ? 2.0 : 4.0, beta = j == 0 ? -1.0 : -2.0, gamma = j == 0 ? 0.0 : -1.0;
+    const float* vj = V + (size_t)j * n;
+    float* vprev = j == 0 ? nullptr : V + (size_t)(j - 1) * n;
+    float* vnext = V + (size_t)(j + 1) * n;
+    if (L.fused) {
+      // the basis step reads v_{j-1} through d (never written) and forms
+      // x_out = beta x_in + gamma d - (-alpha) B^{-1} A x_in with b = 0
+      LevelData Lt = L;
+      Lt.d = vprev;
+      CKS(lv_cheb_fused(c, Lt, (const float*)L.b, vj, vnext, gamma, -alpha,
+                        CHEB_UPDATE | CHEB_EIG | (j == 0 ? CHEB_FIRST : 0), beta));
+    } else {
+      CKS(lv_apply<float>(c, L, vj, (float*)L.r));
+      CKS(smoother_pc<float>(c, L, (const float*)L.r, (float*)L.z));
+      CKS(prof_three_term<float>(c, n, (const float*)L.z, vj, vprev, vnext, alpha, beta, gamma, c->s));
+    }
+  }
+  const int nv = m + 1, np = nv * (nv + 1) / 2;
+  CKS(prof_gram(c, n, V, n, nv, c->partial, c->s));
+  CKS(prof_finalize(c, c->partial, reduce_blocks(n), np, c->eigH, 0, c->s));
+  CK(launch_words_to_host(c->eigH, c->heig_dev, sizeof(double) * (size_t)np, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  prof_collect(c);
+  std::vector<double> G((size_t)nv * nv);
+  for (int i = 0, q = 0; i < nv; ++i)
+    for (int j = i; j < nv; ++j, ++q) {
+      const double gij = c->heig[q];
+      if (!isfinite(gij)) return GMG_ERR_NONFINITE;
+      G[(size_t)i * nv + j] = G[(size_t)j * nv + i] = gij;
+    }
+  // G_k = R^T R, R upper triangular (stride m)
+  std::vector<double> R((size_t)m * m, 0.0);
+  int k = m;
+  for (int j = 0; j < m; ++j) {
+    for (int i = 0; i < j; ++i) {
+      double t = G[(size_t)i * nv + j];
+      for (int p = 0; p < i; ++p) t -= R[(size_t)p * m + i] * R[(size_t)p * m + j];
+      R[(size_t)i * m + j] = t / R[(size_t)i * m + i];
+    }
+    double dd = G[(size_t)j * nv + j];
+    for (int p = 0; p < j; ++p) dd -= R[(size_t)p * m + j] * R[(size_t)p * m + j];
+    if (!(dd > kGramPivotTol * G[(size_t)j * nv + j])) {
+      k = j;
+      break;
+    }
+    R[(size_t)j * m + j] = sqrt(dd);
+  }
+  if (k == 0) return GMG_ERR_BREAKDOWN;
+  // Y = R^{-T} C with C = K_k^T M K_k (forward substitution by columns), then H = Y R^{-1}
+  std::vector<double> Y((size_t)k * k), H((size_t)k * k);
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i < k; ++i) {
+      const double* g = &G[(size_t)i * nv];
+      double t = j == 0 ? 0.5 * (g[1] + g[0]) : 0.25 * (g[j + 1] + 2.0 * g[j] + g[j - 1]);
+      for (int p = 0; p < i; ++p) t -= R[(size_t)p * m + i] * Y[(size_t)p * k + j];
+      Y[(size_t)i * k + j] = t / R[(size_t)i * m + i];
+    }
+  for (int r = 0; r < k; ++r)
+    for (int j = 0; j < k; ++j) {
+      double t = Y[(size_t)r * k + j];
+      for (int p = 0; p < j; ++p) t -= H[(size_t)r * k + p] * R[(size_t)p * m + j];
+      H[(size_t)r * k + j] = t / R[(size_t)j * m + j];
+    }
+  // H is upper Hessenberg in exact arithmetic; below the subdiagonal there is only rounding
+  for (int r = 2; r < k; ++r)
+    for (int j = 0; j < r - 1; ++j) H[(size_t)r * k + j] = 0.0;
+  std::vector<double> wr, wi;
+  if (hessenberg_eigs(H, k, wr, wi) != 0) return GMG_ERR_BREAKDOWN;
+  double lam = -1e300;
+  for (int i = 0; i < k; ++i) lam = std::max(lam, wr[i]);
+  *lam_out = lam;
+  return GMG_OK;
+}
+
 // lambda_max, lambda* of level l: Arnoldi on B^{-1} A_l (Sec. 3.2) in the
 // level precision T.  FP64: basis in V, temporaries bvec / w.  FP32 (the
 // mixed-precision set-up; the bounds only steer the FP32 smoother): basis in
@@ -744,6 +857,15 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
   T* V = f32 ? (T*)c->Z : (T*)(void*)c->V;  // (steps+1) vectors of n, stride n
   T* t1 = f32 ? (T*)L.r : (T*)(void*)c->bvec;
   T* t2 = f32 ? (T*)L.z : (T*)(void*)c->w;
+  if (f32 && c->p.smoother_pc == GMG_PC_SGS && steps + 1 <= kGramMaxVectors) {
+    double lam = 0.0;
+    CKS(ritz_chebyshev_basis(c, l, &lam));
+    if (!(lam > 0) || !isfinite(lam)) return GMG_ERR_BREAKDOWN;
+    L.lam_hat = lam;
+    L.lam_max = c->p.eig_hi * lam;
+    L.lam_min = c->p.eig_lo * lam;
+    return GMG_OK;
+  }
   CKS(prof_hash_vector<T>(c, n, V, c->s));
   CKS(norm_dev<T>(c, n, V, SL_NORM));
   CKS(prof_scale<T>(c, n, V, V, c->dscal + SL_NORM + 1, c->s));
@@ -752,18 +874,13 @@ gmg_status eig_bounds(gmg_ctx* c, int l) {
   // After a breakdown (||w|| = 0) the later vectors are zero and their columns
   // are dropped on the host.
   const bool fused_mv = sizeof(T) == 4 && L.fused;
-  // On levels with the fused smoother, one fused step forms the product: with
-  // b = 0 (not read), x_in = v and c2 = -1 its direction d equals B^{-1}(A v);
-  // x_out is not written.
+  // On levels with the fused smoother, one fused basis step forms the product:
+  // with b = 0 (not read), x_in = v, c2 = -1 and ce = 0 its x_out is B^{-1}(A v).
   for (int j = 0; j < steps; ++j) {
     if (fused_mv) {
-      {
-        // the product writes d = B^{-1} A v into t2: the level's own d stays untouched
-        LevelData Lt = L;
-        Lt.d = t2;
-        CKS(lv_cheb_fused(c, Lt, (const float*)L.b, (const float*)(V + (size_t)j * n), L.x2, 0.0, -1.0,
-                          CHEB_UPDATE | CHEB_FIRST | CHEB_EIG));
-      }
+      // the basis step with ce = 0 and no d: t2 = B^{-1} A v; the level's d stays untouched
+      CKS(lv_cheb_fused(c, L, (const float*)L.b, (const float*)(V + (size_t)j * n), (float*)t2, 0.0, -1.0,
+                        CHEB_UPDATE | CHEB_FIRST | CHEB_EIG, 0.0));
     } else {
       CKS(lv_apply<T>(c, L, V + (size_t)j * n, t1));
       CKS(smoother_pc<T>(c, L, t1, t2));
@@ -1580,7 +1697,8 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
   if ((st = dev_alloc(c, &c->Z, nz_vec * N * c->esz)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->w, N)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->bvec, N)) != GMG_OK) return fail(st);
-  if ((st = dalloc(c, &c->partial, (size_t)1024 * 64)) != GMG_OK) return fail(st);
+  // 1024 blocks x up to 78 sums (the Gram matrix of 12 vectors)
+  if ((st = dalloc(c, &c->partial, (size_t)1024 * 80)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->dscal, N_SCAL)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->cA, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->cW, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);

@@ -63,8 +63,9 @@ enum PcKind : int { PC_SGS = 0, PC_JACOBI = 1, PC_IDENTITY = 2, PC_NONE = 3 };
 
 // Flags of the Chebyshev update fused into the smoother kernels.  The fused
 // kernel also takes CHEB_LAST (the last step of a smoothing: d is dead after
-// it and not written) and CHEB_EIG (the eigen-estimate product B^{-1} A x_in:
-// b is taken as zero and not read, only d is written).
+// it and not written) and CHEB_EIG (a step of the eigen estimate's Krylov
+// basis: b is taken as zero and not read, d is read unless CHEB_FIRST and
+// never written, x_out = ce x_in + c1 d - c2 B^{-1} A x_in).
 enum ChebFlags : int { CHEB_UPDATE = 1, CHEB_FIRST = 2, CHEB_XZERO = 4, CHEB_LAST = 8, CHEB_EIG = 16 };
 
 // ----------------------------------------------------------------------------
@@ -197,13 +198,15 @@ cudaError_t launch_sgs_half(const Grid3& g, const T* a, const T* r, T* z, int co
 
 // One Chebyshev step with the red-black SSOR preconditioner in one pass
 // (FP32): x_out = x_in + d, d = c1 d + c2 B^{-1}(b - A x_in); xin null means
-// x_in = 0.  x_out must not alias x_in; d is updated in place.
+// x_in = 0.  x_out must not alias x_in; d is updated in place.  ce is read
+// only with CHEB_EIG.
 bool fused_smoother_eligible(const Grid3& g);
 cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b, const float* xin, float* xout,
-                                  float* d, double c1, double c2, int flags, cudaStream_t s);
+                                  float* d, double c1, double c2, double ce, int flags, cudaStream_t s);
 // The same step on a face-form level (all face arrays 8-byte aligned).
 cudaError_t launch_cheb_sgs_fused_faces(const Grid3& g, const Faces<float>& F, const float* b, const float* xin,
-                                        float* xout, float* d, double c1, double c2, int flags, cudaStream_t s);
+                                        float* xout, float* d, double c1, double c2, double ce, int flags,
+                                        cudaStream_t s);
 
 // Pointwise Chebyshev update on all cells: d = c1 d + c2 z; x += d.
 template <typename T>
@@ -336,6 +339,15 @@ cudaError_t launch_cgs_dots(size_t n, const T* w, const T* V, size_t ldv, int k,
 template <typename T>
 cudaError_t launch_cgs_update(size_t n, T* w, const T* V, size_t ldv, int k, const double* h1, const double* h2,
                               double* partial, cudaStream_t s);
+// Gram matrix of nv (2..kGramMaxVectors) FP32 vectors of length n, row stride
+// ldv: partial[b * nv(nv+1)/2 + q] = block b's part of (v_i, v_j), q over the
+// upper triangle i <= j row by row.
+constexpr int kGramMaxVectors = 12;
+cudaError_t launch_gram(size_t n, const float* V, size_t ldv, int nv, double* partial, cudaStream_t s);
+// out = alpha t + beta v + gamma u (u null: the last term is left out).
+template <typename T>
+cudaError_t launch_three_term(size_t n, const T* t, const T* v, const T* u, T* out, double alpha, double beta,
+                              double gamma, cudaStream_t s);
 // out[i] = sum_b partial[b*k + i] (+ out[i] if accumulate) for i < k; one block per output.
 cudaError_t launch_finalize(const double* partial, int nblocks, int k, double* out, int accumulate,
                             cudaStream_t s);

@@ -204,6 +204,74 @@ __global__ void __launch_bounds__(RT) k_cgs_update_f4(size_t n4, float4* __restr
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
+// ---- Gram matrix of a few FP32 vectors (the eigen estimate's Krylov basis) ----
+// partial[b * NP + q], q running over the upper triangle i <= j row by row:
+// block b's part of (v_i, v_j).  One pass reads each vector once.  Per-thread
+// FP32 sums (reduce_blocks gives each thread at most a few hundred pieces at
+// the sizes of a level), FP64 across threads and blocks.
+template <int NV>
+__global__ void __launch_bounds__(RT) k_gram_f4(size_t n4, const float4* __restrict__ V, size_t ldv4,
+                                                double* __restrict__ partial) {
+  constexpr int NP = NV * (NV + 1) / 2;
+  __shared__ double sh[RT / 32];
+  float acc[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) acc[q] = 0.f;
+  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n4; p += (size_t)gridDim.x * RT) {
+    float4 v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = V[i * ldv4 + p];
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+      for (int j = i; j < NV; ++j, ++q)
+        acc[q] = fmaf(v[i].w, v[j].w, fmaf(v[i].z, v[j].z, fmaf(v[i].y, v[j].y, fmaf(v[i].x, v[j].x, acc[q]))));
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const double t = block_sum<RT>((double)acc[q], sh);
+    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * NP + q] = t;
+  }
+}
+
+// The same on single elements (n or the row stride not a multiple of 4).
+template <int NV>
+__global__ void __launch_bounds__(RT) k_gram(size_t n, const float* __restrict__ V, size_t ldv,
+                                             double* __restrict__ partial) {
+  constexpr int NP = NV * (NV + 1) / 2;
+  __shared__ double sh[RT / 32];
+  float acc[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) acc[q] = 0.f;
+  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
+    float v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = V[i * ldv + p];
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+      for (int j = i; j < NV; ++j, ++q) acc[q] = fmaf(v[i], v[j], acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const double t = block_sum<RT>((double)acc[q], sh);
+    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * NP + q] = t;
+  }
+}
+
+// out = alpha t + beta v + gamma u (u null: gamma = 0), FP32 arithmetic.
+template <typename T>
+__global__ void k_three_term(size_t n, const T* __restrict__ t, const T* __restrict__ v, const T* __restrict__ u,
+                             T* __restrict__ out, T alpha, T beta, T gamma) {
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+    T r = fma(alpha, t[p], beta * v[p]);
+    if (u) r = fma(gamma, u[p], r);
+    out[p] = r;
+  }
+}
+
 __global__ void __launch_bounds__(RT) k_finalize(const double* __restrict__ partial, int nblocks, int k,
                                                  double* __restrict__ out, int accumulate) {
   __shared__ double sh[RT / 32];
@@ -540,6 +608,42 @@ cudaError_t launch_cgs_update(size_t n, T* w, const T* V, size_t ldv, int k, con
 GMG_INST(float)
 GMG_INST(double)
 #undef GMG_INST
+
+cudaError_t launch_gram(size_t n, const float* V, size_t ldv, int nv, double* partial, cudaStream_t s) {
+  const int nb = reduce_blocks(n);
+  if (n % 4 == 0 && ldv % 4 == 0 && ((uintptr_t)V & 15) == 0) {
+    const float4* V4 = reinterpret_cast<const float4*>(V);
+    switch (nv) {
+#define GMG_CASE(K) \
+  case K: k_gram_f4<K><<<nb, RT, 0, s>>>(n / 4, V4, ldv / 4, partial); break;
+      GMG_CASE(2) GMG_CASE(3) GMG_CASE(4) GMG_CASE(5) GMG_CASE(6) GMG_CASE(7) GMG_CASE(8) GMG_CASE(9)
+      GMG_CASE(10) GMG_CASE(11) GMG_CASE(12)
+#undef GMG_CASE
+      default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+  switch (nv) {
+#define GMG_CASE(K) \
+  case K: k_gram<K><<<nb, RT, 0, s>>>(n, V, ldv, partial); break;
+    GMG_CASE(2) GMG_CASE(3) GMG_CASE(4) GMG_CASE(5) GMG_CASE(6) GMG_CASE(7) GMG_CASE(8) GMG_CASE(9)
+    GMG_CASE(10) GMG_CASE(11) GMG_CASE(12)
+#undef GMG_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_three_term(size_t n, const T* t, const T* v, const T* u, T* out, double alpha, double beta,
+                              double gamma, cudaStream_t s) {
+  k_three_term<T><<<flat_blocks(n), 256, 0, s>>>(n, t, v, u, out, (T)alpha, (T)beta, (T)gamma);
+  return cudaGetLastError();
+}
+template cudaError_t launch_three_term<float>(size_t, const float*, const float*, const float*, float*, double,
+                                              double, double, cudaStream_t);
 
 cudaError_t launch_scale_value(size_t n, const double* src, double* dst, double alpha, cudaStream_t s) {
   k_scale_value<<<flat_blocks(n), 256, 0, s>>>(n, src, dst, alpha);

@@ -66,6 +66,7 @@ struct FusedArgs {
   float* xout;
   float* d;
   float c1, c2;
+  float ce;         // the eigen-estimate basis step: coefficient of x_in in x_out
   int flags;
   int tiles_x;      // tiles along x
   long long units;  // tiles x nz (one unit = one z-plane of one tile)
@@ -82,7 +83,8 @@ __device__ __forceinline__ float lane(float2 v, int i) { return i ? v.y : v.x; }
 // step carries no runtime tests for it): the first step of a smoothing (d =
 // c2 z, d not read), with x_in = 0 (pre-smoothing from zero: x_in not read),
 // the last step (d is dead afterwards: not written), and the eigen-estimate
-// product (b = 0 is not read and x_out not written: only d = B^{-1} A x_in).
+// basis step (b = 0 is not read, d is read unless M_FIRST but never written,
+// and x_out = ce x_in + c1 d + c2 z with z = -B^{-1} A x_in).
 enum StepMode : int { M_FIRST = 1, M_XZERO = 2, M_LAST = 4, M_EIG = 8 };
 
 // Planes [k0, k1) of tile (bx, by).  Leaves shared memory in use: the caller
@@ -112,8 +114,8 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
   const int gy = by * FTY - HY + ty;
   constexpr bool xzero = (MODE & M_XZERO) != 0;
   constexpr bool first = (MODE & M_FIRST) != 0;
-  constexpr bool keep_d = (MODE & M_LAST) == 0;
   constexpr bool eig = (MODE & M_EIG) != 0;
+  constexpr bool keep_d = (MODE & M_LAST) == 0 && !eig;
   const bool in = gx0 >= 0 && gx0 < nx && gy >= 0 && gy < ny;  // nx even: both cells or neither
   const bool rst = in && tx >= 1 && tx <= RP - 2 && ty >= 1 && ty <= RH - 2;            // residual: tile + 2
   const bool bst = in && ty >= 2 && ty <= RH - 3;                                        // black: tile + 1
@@ -347,7 +349,10 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
       const float2 dv = first ? mul2(c2, z) : fma2(sc2(P.c1), pd, mul2(c2, z));
       const int q = kf * pl2 + qo;
       if constexpr (keep_d) reinterpret_cast<float2*>(P.d)[q] = dv;
-      if constexpr (!eig) reinterpret_cast<float2*>(P.xout)[q] = xzero ? dv : add2(xw0, dv);
+      if constexpr (eig)
+        reinterpret_cast<float2*>(P.xout)[q] = fma2(sc2(P.ce), xw0, dv);
+      else
+        reinterpret_cast<float2*>(P.xout)[q] = xzero ? dv : add2(xw0, dv);
     }
     pb = pbn;
     pd = pdn;
@@ -417,9 +422,9 @@ std::mutex g_fused_mutex;
 
 // The step kinds the library launches: pre-smoothing from zero (first, x_in =
 // 0), first with x_in, middle, last (each with or without x_in = 0 for a
-// one-step smoothing), and the eigen-estimate product.
+// one-step smoothing), and the eigen-estimate basis step without and with d.
 constexpr int kModes[] = {M_FIRST | M_XZERO, M_FIRST | M_XZERO | M_LAST, M_FIRST, M_FIRST | M_LAST, 0, M_LAST,
-                          M_FIRST | M_EIG};
+                          M_FIRST | M_EIG, M_EIG};
 
 template <bool FACE, int MODE>
 cudaError_t set_smem() {
@@ -441,7 +446,7 @@ cudaError_t fused_slots(int* out) {
   if (slots == 0) {
     const cudaError_t es[] = {set_smem<FACE, kModes[0]>(), set_smem<FACE, kModes[1]>(), set_smem<FACE, kModes[2]>(),
                               set_smem<FACE, kModes[3]>(), set_smem<FACE, kModes[4]>(), set_smem<FACE, kModes[5]>(),
-                              set_smem<FACE, kModes[6]>()};
+                              set_smem<FACE, kModes[6]>(), set_smem<FACE, kModes[7]>()};
     for (cudaError_t q : es)
       if (q != cudaSuccess) return q;
     int sms = 0, per = 0;
@@ -463,8 +468,9 @@ cudaError_t launch_fused(const FusedArgs& P, long long units, cudaStream_t s) {
   const long long blocks = std::max(1LL, std::min((long long)slots, units / 4));
   const dim3 grid((unsigned)blocks), block(RP, RH);
   const size_t smem = FACE ? FUSED_SMEM_FACE : FUSED_SMEM;
-  const int mode = ((P.flags & CHEB_FIRST) ? M_FIRST : 0) | (P.xin ? 0 : M_XZERO) | ((P.flags & CHEB_LAST) ? M_LAST : 0) |
-                   ((P.flags & CHEB_EIG) ? M_EIG : 0);
+  const bool eig = (P.flags & CHEB_EIG) != 0;
+  const int mode = ((P.flags & CHEB_FIRST) ? M_FIRST : 0) | (P.xin ? 0 : M_XZERO) |
+                   ((P.flags & CHEB_LAST) && !eig ? M_LAST : 0) | (eig ? M_EIG : 0);
   switch (mode) {
     case M_FIRST | M_XZERO: k_cheb_sgs_fused<FACE, M_FIRST | M_XZERO><<<grid, block, smem, s>>>(P); break;
     case M_FIRST | M_XZERO | M_LAST: k_cheb_sgs_fused<FACE, M_FIRST | M_XZERO | M_LAST><<<grid, block, smem, s>>>(P); break;
@@ -473,7 +479,8 @@ cudaError_t launch_fused(const FusedArgs& P, long long units, cudaStream_t s) {
     case 0: k_cheb_sgs_fused<FACE, 0><<<grid, block, smem, s>>>(P); break;
     case M_LAST: k_cheb_sgs_fused<FACE, M_LAST><<<grid, block, smem, s>>>(P); break;
     case M_FIRST | M_EIG: k_cheb_sgs_fused<FACE, M_FIRST | M_EIG><<<grid, block, smem, s>>>(P); break;
-    default: return cudaErrorInvalidValue;  // x_in = 0 needs the first step; the product is a first step with x_in
+    case M_EIG: k_cheb_sgs_fused<FACE, M_EIG><<<grid, block, smem, s>>>(P); break;
+    default: return cudaErrorInvalidValue;  // x_in = 0 needs the first step; the basis step needs x_in
   }
   return cudaGetLastError();
 }
@@ -486,23 +493,24 @@ bool fused_smoother_eligible(const Grid3& g) {
 }
 
 cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b, const float* xin, float* xout,
-                                    float* d, double c1, double c2, int flags, cudaStream_t s) {
+                                    float* d, double c1, double c2, double ce, int flags, cudaStream_t s) {
   if (!pair_aligned(a) || !pair_aligned(b) || (xin && !pair_aligned(xin)) || !pair_aligned(xout) || !pair_aligned(d))
     return cudaErrorMisalignedAddress;
   const int tx = (g.nx + FTX - 1) / FTX, ty = (g.ny + FTY - 1) / FTY;
   const long long units = (long long)tx * ty * g.nz;
-  FusedArgs P{g, a, Faces<float>{}, b, xin, xout, d, (float)c1, (float)c2, flags, tx, units};
+  FusedArgs P{g, a, Faces<float>{}, b, xin, xout, d, (float)c1, (float)c2, (float)ce, flags, tx, units};
   return launch_fused<false>(P, units, s);
 }
 
 cudaError_t launch_cheb_sgs_fused_faces(const Grid3& g, const Faces<float>& F, const float* b, const float* xin,
-                                        float* xout, float* d, double c1, double c2, int flags, cudaStream_t s) {
+                                        float* xout, float* d, double c1, double c2, double ce, int flags,
+                                        cudaStream_t s) {
   if (!pair_aligned(F.kx) || !pair_aligned(F.ky) || !pair_aligned(F.kz) || !pair_aligned(F.ktop) ||
       !pair_aligned(b) || (xin && !pair_aligned(xin)) || !pair_aligned(xout) || !pair_aligned(d))
     return cudaErrorMisalignedAddress;
   const int tx = (g.nx + FTX - 1) / FTX, ty = (g.ny + FTY - 1) / FTY;
   const long long units = (long long)tx * ty * g.nz;
-  FusedArgs P{g, nullptr, F, b, xin, xout, d, (float)c1, (float)c2, flags, tx, units};
+  FusedArgs P{g, nullptr, F, b, xin, xout, d, (float)c1, (float)c2, (float)ce, flags, tx, units};
   return launch_fused<true>(P, units, s);
 }
 

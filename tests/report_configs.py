@@ -166,7 +166,9 @@ def cmd_gpu(json_out: str | None) -> None:
 
 def adjoint_rows(torch, gmg, O, dev):
     """Config 5: central differences at 32^3 (64 seeded entries of a and f,
-    steps 1e-6 and 1e-3 relative for a) and the CPU adjoint at 64^3."""
+    steps 1e-6 and 1e-3 relative for a; at 1e-6 also with each solve's
+    first-order error lambda . r~ added, r~ = b - A x~ from the oracle's
+    operator, lambda from its adjoint solve) and the CPU adjoint at 64^3."""
     from paper_1812_08606_gb300 import PoissonSolver
     from streamer_inputs import make_inputs
     out = {"case": "config 5: adjoint"}
@@ -180,12 +182,21 @@ def adjoint_rows(torch, gmg, O, dev):
     ga, gf = a.grad.cpu().numpy(), f.grad.cpu().numpy()
     idx = np.random.default_rng(20181225).choice(a.numel(), size=64, replace=False)
     base_a, base_f = a.detach().clone(), f.detach().clone()
+    prm = solver.params
+    grid = O.Grid(shape[2], shape[1], shape[0], prm.lx, prm.ly, prm.lz)
+    op = O.OracleParams(lx=prm.lx, ly=prm.ly, lz=prm.lz, phi_bottom=prm.phi_bottom, phi_top=prm.phi_top,
+                        rtol=1e-13, max_iters=60)
+    lam_o, _, _ = O.solve(op, inp["a"], inp["w"], homogeneous=True)
 
     def L(av, fv):
         with torch.no_grad():
-            return float((w * solver.solve(av, fv)).sum())
+            phi = solver.solve(av, fv)
+            val = float((w * phi).sum())
+        an, fn, ph = (t.cpu().numpy() for t in (av, fv, phi))
+        r = O.assemble_rhs(grid, an, fn, prm.phi_bottom, prm.phi_top) - O.apply_operator(grid, an, ph)
+        return val, float(np.sum(lam_o * r))
     for which, step in (("a", 1e-6), ("a", 1e-3), ("f", None)):
-        errs = []
+        errs, errs_c = [], []
         for q in idx:
             grad, base = (ga, base_a) if which == "a" else (gf, base_f)
             v = abs(float(base.view(-1)[q]))
@@ -193,9 +204,14 @@ def adjoint_rows(torch, gmg, O, dev):
             plus, minus = base.clone(), base.clone()
             plus.view(-1)[q] += h
             minus.view(-1)[q] -= h
-            fd = ((L(plus, base_f) - L(minus, base_f)) if which == "a" else (L(base_a, plus) - L(base_a, minus))) / (2 * h)
-            errs.append(abs(grad.ravel()[q] - fd) / max(abs(fd), 1e-4 * np.abs(grad).max()))
+            (lp, ep), (lm, em) = (L(plus, base_f), L(minus, base_f)) if which == "a" else (L(base_a, plus), L(base_a, minus))
+            sc = lambda x: max(abs(x), 1e-4 * np.abs(grad).max())
+            fd, fdc = (lp - lm) / (2 * h), ((lp + ep) - (lm + em)) / (2 * h)
+            errs.append(abs(grad.ravel()[q] - fd) / sc(fd))
+            errs_c.append(abs(grad.ravel()[q] - fdc) / sc(fdc))
         out[f"fd_{which}_{step}"] = {"median": float(np.median(errs)), "max": float(np.max(errs))}
+        if which == "a" and step == 1e-6:
+            out[f"fd_{which}_{step}_corrected"] = {"median": float(np.median(errs_c)), "max": float(np.max(errs_c))}
     inp = make_inputs("adjoint", n=64)
     shape = inp["a"].shape
     solver = PoissonSolver(shape, rtol=1e-12)
