@@ -765,9 +765,9 @@ gmg_status ritz_chebyshev_basis(gmg_ctx* c, int l, double* lam_out) {
   const size_t n = L.n;
   const int m = c->p.eig_steps;
   float* V = (float*)c->Z;  // (m + 1) vectors of n, stride n
+  // v_0: the hash start vector as it is (entries in [-1, 1)); the projection
+  // does not depend on the basis' scale, so it is not normalised
   CKS(prof_hash_vector<float>(c, n, V, c->s));
-  CKS(norm_dev<float>(c, n, V, SL_NORM));
-  CKS(prof_scale<float>(c, n, V, V, c->dscal + SL_NORM + 1, c->s));
   for (int j = 0; j < m; ++j) {
     // v_{j+1} = alpha M v_j + beta v_j + gamma v_{j-1}
     const double alpha = j == 0 ? 2.0 : 4.0, beta = j == 0 ? -1.0 : -2.0, gamma = j == 0 ? 0.0 : -1.0;

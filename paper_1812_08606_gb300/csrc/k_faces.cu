@@ -214,16 +214,20 @@ __device__ __forceinline__ T series_plate(T kin, T kplate) {
   return quot((T)1, quot((T)1, kin) + quot((T)2, kplate));
 }
 
-// One thread per coarse cell (I, J, K): its low faces and, on the last coarse
+// One thread per coarse column (I, J) of a 32 x 8 block, marching through
+// kchunk coarse planes: per coarse cell its low faces and, on the last coarse
 // plane, its top plate face.  g is the fine grid.
 template <typename T, bool CELL>
-__global__ void k_coarsen_faces(Links<T, CELL> L, T* __restrict__ kx, T* __restrict__ ky, T* __restrict__ kz,
-                                T* __restrict__ ktop) {
+__global__ void __launch_bounds__(256) k_coarsen_faces(Links<T, CELL> L, T* __restrict__ kx, T* __restrict__ ky,
+                                                       T* __restrict__ kz, T* __restrict__ ktop, int kchunk) {
   const Grid3& g = L.g;
   const int nxc = g.nx / 2, nyc = g.ny / 2, nzc = g.nz / 2;
-  const size_t nc = (size_t)nxc * nyc * nzc;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nc; q += (size_t)gridDim.x * blockDim.x) {
-    const int I = (int)(q % nxc), J = (int)((q / nxc) % nyc), K = (int)(q / ((size_t)nxc * nyc));
+  const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 8 + threadIdx.y;
+  if (I >= nxc || J >= nyc) return;
+  const int K0 = blockIdx.z * kchunk, K1 = min(nzc, K0 + kchunk);
+  const size_t plc = (size_t)nxc * nyc;
+  size_t q = (size_t)K0 * plc + (size_t)J * nxc + I;
+  for (int K = K0; K < K1; ++K, q += plc) {
     T sx = (T)0, sy = (T)0, sz = (T)0, st = (T)0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -281,12 +285,17 @@ __device__ __forceinline__ T parent_weight(int c, int n, bool plates, F lk) {
   return quot(rn, rn + rp);
 }
 
+// One thread per (i, j) column of a 32 x 8 block, marching through kchunk
+// planes: cell indices come from the grid, with no division per cell.
 template <typename T, bool CELL>
-__global__ void k_prolong_weights(Links<T, CELL> L, T* __restrict__ w) {
+__global__ void __launch_bounds__(256) k_prolong_weights(Links<T, CELL> L, T* __restrict__ w, int kchunk) {
   const Grid3& g = L.g;
-  const size_t n = g.n();
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(p % g.nx), j = (int)((p / g.nx) % g.ny), k = (int)(p / g.plane());
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  const int k0 = blockIdx.z * kchunk, k1 = min(g.nz, k0 + kchunk);
+  const size_t n = g.n(), pl = g.plane();
+  size_t p = (size_t)k0 * pl + (size_t)j * g.nx + i;
+  for (int k = k0; k < k1; ++k, p += pl) {
     w[p] = parent_weight<T>(i, g.nx, false, [&](int m) { return L.x(m, j, k); });
     w[n + p] = parent_weight<T>(j, g.ny, false, [&](int m) { return L.y(i, m, k); });
     w[2 * n + p] = parent_weight<T>(k, g.nz, true, [&](int m) { return L.z(i, j, m); });
@@ -475,20 +484,38 @@ cudaError_t launch_residual_restrict_faces(const Grid3& g, const Faces<T>& F, co
   return cudaGetLastError();
 }
 
+namespace {
+// Grid of 32 x 8 column blocks over an nx x ny x nz box, with z cut into chunks
+// for about two waves of 8 blocks per SM (at least 4 planes per chunk).
+struct ColumnLaunch {
+  dim3 grid;
+  int kchunk;
+};
+ColumnLaunch column_launch(int nx, int ny, int nz) {
+  const int gx = (nx + 31) / 32, gy = (ny + 7) / 8;
+  const long long target = 152LL * 8 * 2, xy = (long long)gx * gy;
+  const int zc = (int)std::max(1LL, std::min((target + xy - 1) / xy, (long long)std::max(1, nz / 4)));
+  const int kchunk = (nz + zc - 1) / zc;
+  return {dim3((unsigned)gx, (unsigned)gy, (unsigned)((nz + kchunk - 1) / kchunk)), kchunk};
+}
+}  // namespace
+
 template <typename T>
 cudaError_t launch_coarsen_faces(const Grid3& g, const T* a, const Faces<T>& F, T* kx, T* ky, T* kz, T* ktop,
                                  cudaStream_t s) {
-  const unsigned blocks = flat_blocks(g.n() / 8, 256);
-  if (a) k_coarsen_faces<T, true><<<blocks, 256, 0, s>>>(Links<T, true>{g, a, F}, kx, ky, kz, ktop);
-  else k_coarsen_faces<T, false><<<blocks, 256, 0, s>>>(Links<T, false>{g, a, F}, kx, ky, kz, ktop);
+  const ColumnLaunch cl = column_launch(g.nx / 2, g.ny / 2, g.nz / 2);
+  const dim3 block(32, 8);
+  if (a) k_coarsen_faces<T, true><<<cl.grid, block, 0, s>>>(Links<T, true>{g, a, F}, kx, ky, kz, ktop, cl.kchunk);
+  else k_coarsen_faces<T, false><<<cl.grid, block, 0, s>>>(Links<T, false>{g, a, F}, kx, ky, kz, ktop, cl.kchunk);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_prolong_weights(const Grid3& g, const T* a, const Faces<T>& F, T* w, cudaStream_t s) {
-  const unsigned blocks = flat_blocks(g.n(), 256);
-  if (a) k_prolong_weights<T, true><<<blocks, 256, 0, s>>>(Links<T, true>{g, a, F}, w);
-  else k_prolong_weights<T, false><<<blocks, 256, 0, s>>>(Links<T, false>{g, a, F}, w);
+  const ColumnLaunch cl = column_launch(g.nx, g.ny, g.nz);
+  const dim3 block(32, 8);
+  if (a) k_prolong_weights<T, true><<<cl.grid, block, 0, s>>>(Links<T, true>{g, a, F}, w, cl.kchunk);
+  else k_prolong_weights<T, false><<<cl.grid, block, 0, s>>>(Links<T, false>{g, a, F}, w, cl.kchunk);
   return cudaGetLastError();
 }
 

@@ -206,27 +206,27 @@ __global__ void __launch_bounds__(RT) k_cgs_update_f4(size_t n4, float4* __restr
 
 // ---- Gram matrix of a few FP32 vectors (the eigen estimate's Krylov basis) ----
 // partial[b * NP + q], q running over the upper triangle i <= j row by row:
-// block b's part of (v_i, v_j).  One pass reads each vector once.  Per-thread
-// FP32 sums (reduce_blocks gives each thread at most a few hundred pieces at
-// the sizes of a level), FP64 across threads and blocks.
+// block b's part of (v_i, v_j).  One pass reads each vector once, in float2
+// pieces: the NP accumulators and two values per vector fit two blocks per
+// SM.  Per-thread FP32 sums (reduce_blocks gives each thread at most about a
+// thousand elements at the sizes of a level), FP64 across threads and blocks.
 template <int NV>
-__global__ void __launch_bounds__(RT) k_gram_f4(size_t n4, const float4* __restrict__ V, size_t ldv4,
-                                                double* __restrict__ partial) {
+__global__ void __launch_bounds__(RT, 2) k_gram_f2(size_t n2, const float2* __restrict__ V, size_t ldv2,
+                                                   double* __restrict__ partial) {
   constexpr int NP = NV * (NV + 1) / 2;
   __shared__ double sh[RT / 32];
   float acc[NP];
 #pragma unroll
   for (int q = 0; q < NP; ++q) acc[q] = 0.f;
-  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n4; p += (size_t)gridDim.x * RT) {
-    float4 v[NV];
+  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n2; p += (size_t)gridDim.x * RT) {
+    float2 v[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] = V[i * ldv4 + p];
+    for (int i = 0; i < NV; ++i) v[i] = V[i * ldv2 + p];
     int q = 0;
 #pragma unroll
     for (int i = 0; i < NV; ++i)
 #pragma unroll
-      for (int j = i; j < NV; ++j, ++q)
-        acc[q] = fmaf(v[i].w, v[j].w, fmaf(v[i].z, v[j].z, fmaf(v[i].y, v[j].y, fmaf(v[i].x, v[j].x, acc[q]))));
+      for (int j = i; j < NV; ++j, ++q) acc[q] = fmaf(v[i].y, v[j].y, fmaf(v[i].x, v[j].x, acc[q]));
   }
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(RT) k_gram_f4(size_t n4, const float4* __restr
   }
 }
 
-// The same on single elements (n or the row stride not a multiple of 4).
+// The same on single elements (n or the row stride odd).
 template <int NV>
 __global__ void __launch_bounds__(RT) k_gram(size_t n, const float* __restrict__ V, size_t ldv,
                                              double* __restrict__ partial) {
@@ -611,11 +611,11 @@ GMG_INST(double)
 
 cudaError_t launch_gram(size_t n, const float* V, size_t ldv, int nv, double* partial, cudaStream_t s) {
   const int nb = reduce_blocks(n);
-  if (n % 4 == 0 && ldv % 4 == 0 && ((uintptr_t)V & 15) == 0) {
-    const float4* V4 = reinterpret_cast<const float4*>(V);
+  if (n % 2 == 0 && ldv % 2 == 0 && ((uintptr_t)V & 7) == 0) {
+    const float2* V2 = reinterpret_cast<const float2*>(V);
     switch (nv) {
 #define GMG_CASE(K) \
-  case K: k_gram_f4<K><<<nb, RT, 0, s>>>(n / 4, V4, ldv / 4, partial); break;
+  case K: k_gram_f2<K><<<nb, RT, 0, s>>>(n / 2, V2, ldv / 2, partial); break;
       GMG_CASE(2) GMG_CASE(3) GMG_CASE(4) GMG_CASE(5) GMG_CASE(6) GMG_CASE(7) GMG_CASE(8) GMG_CASE(9)
       GMG_CASE(10) GMG_CASE(11) GMG_CASE(12)
 #undef GMG_CASE
