@@ -97,7 +97,11 @@ enum StepMode : int { M_FIRST = 1, M_XZERO = 2, M_LAST = 4, M_EIG = 8 };
 // the z-face entries (face below each cell; the plane above the top one is the
 // top plate's entries).  Entries beyond the domain load as zero and a plate's
 // neighbour value is zero, so the plate and wall cases need no branches.
-template <bool FACE, int MODE>
+//
+// INNER: the tile's region (tile + halo) lies inside the domain in x and y
+// (inner_tile), so every cell of the region exists and no x or y face of it
+// is a wall: the range tests and the wall masks are left out.
+template <bool FACE, int MODE, bool INNER>
 __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, const int bx, const int by,
                                               const int k0, const int k1) {
   float2* const As = smf2;               // NAS planes of a (FACE: x-face entries)
@@ -116,7 +120,7 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
   constexpr bool first = (MODE & M_FIRST) != 0;
   constexpr bool eig = (MODE & M_EIG) != 0;
   constexpr bool keep_d = (MODE & M_LAST) == 0 && !eig;
-  const bool in = gx0 >= 0 && gx0 < nx && gy >= 0 && gy < ny;  // nx even: both cells or neither
+  const bool in = INNER || (gx0 >= 0 && gx0 < nx && gy >= 0 && gy < ny);  // nx even: both cells or neither
   const bool rst = in && tx >= 1 && tx <= RP - 2 && ty >= 1 && ty <= RH - 2;            // residual: tile + 2
   const bool bst = in && ty >= 2 && ty <= RH - 3;                                        // black: tile + 1
   const bool fst = in && tx >= HX / 2 && tx < RP - HX / 2 && ty >= HY && ty < RH - HY;  // final: tile
@@ -125,6 +129,9 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
   const float mxl = gx0 > 0 ? 1.f : 0.f;       // face left of the first cell
   const float mxr = gx0 + 2 < nx ? 1.f : 0.f;  // face right of the second cell
   const float my0 = gy > 0 ? 1.f : 0.f, my1 = gy < ny - 1 ? 1.f : 0.f;
+  // a face value times its wall mask (1 on every face of an inner tile)
+  auto wall = [](float v, float m) { return INNER ? v : v * m; };
+  auto wall2 = [](float2 v, float2 m) { return INNER ? v : mul2(v, m); };
   const float2 fx2 = sc2(g.fx), fy2 = sc2(g.fy), fz2 = sc2(g.fz), fp2 = sc2(g.fp);
   const float2 zero2 = make_float2(0.f, 0.f);
   const int rlo = max(0, k0 - 2), rhi = min(nz, k1 + 2);
@@ -235,9 +242,9 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
         const float2 a2 = aw3;  // plane kr
         const float2 al = ac[me - 1], ar = ac[me + 1];
         const float2 aL = make_float2(al.y, a2.x), aR = make_float2(a2.y, ar.x);
-        const float2 fxm = mul2(add2(a2, aL), make_float2(mxl, 1.f));
-        const float2 fxp = mul2(add2(a2, aR), make_float2(1.f, mxr));
-        const float2 fym = mul2(add2(a2, ac[me - RP]), sc2(my0)), fyp = mul2(add2(a2, ac[me + RP]), sc2(my1));
+        const float2 fxm = wall2(add2(a2, aL), make_float2(mxl, 1.f));
+        const float2 fxp = wall2(add2(a2, aR), make_float2(1.f, mxr));
+        const float2 fym = wall2(add2(a2, ac[me - RP]), sc2(my0)), fyp = wall2(add2(a2, ac[me + RP]), sc2(my1));
         const float2 fzm = zlo ? add2(a2, aw2) : zero2, fzp = zhi ? add2(a2, aw4) : zero2;
         float2 D;
         if constexpr (ST) {
@@ -300,9 +307,9 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
         const float aout = L ? ac[me + 1].x : ac[me - 1].y;
         const float mout = L ? mxr : mxl;
         float sx = (a0 + ain) * z1w1;                   // z1w1: red z of this pair, plane kb
-        sx = fmaf((a0 + aout) * mout, L ? zc[me + 1] : zc[me - 1], sx);
-        float sy = (a0 + lane(ac[me - RP], L)) * my0 * zc[me - RP];
-        sy = fmaf((a0 + lane(ac[me + RP], L)) * my1, zc[me + RP], sy);
+        sx = fmaf(wall(a0 + aout, mout), L ? zc[me + 1] : zc[me - 1], sx);
+        float sy = wall(a0 + lane(ac[me - RP], L), my0) * zc[me - RP];
+        sy = fmaf(wall(a0 + lane(ac[me + RP], L), my1), zc[me + RP], sy);
         float sz = 0.f;
         if (zlo) sz = (a0 + lane(aw1, L)) * z1w0;
         if (zhi) sz = fmaf(a0 + lane(aw3, L), z1w2, sz);
@@ -335,9 +342,9 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
         const float aout = L ? ac[me + 1].x : ac[me - 1].y;
         const float mout = L ? mxr : mxl;
         float sx = (a0 + ain) * zbw1;  // zbw1: black z of this pair, plane kf
-        sx = fmaf((a0 + aout) * mout, L ? zc[me + 1] : zc[me - 1], sx);
-        float sy = (a0 + lane(ac[me - RP], L)) * my0 * zc[me - RP];
-        sy = fmaf((a0 + lane(ac[me + RP], L)) * my1, zc[me + RP], sy);
+        sx = fmaf(wall(a0 + aout, mout), L ? zc[me + 1] : zc[me - 1], sx);
+        float sy = wall(a0 + lane(ac[me - RP], L), my0) * zc[me - RP];
+        sy = fmaf(wall(a0 + lane(ac[me + RP], L), my1), zc[me + RP], sy);
         float sz = 0.f;
         if (zlo) sz = (a0 + lane(aw0, L)) * zbw0;
         if (zhi) sz = fmaf(a0 + lane(aw2, L), zbw2, sz);
@@ -388,28 +395,47 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
   }
 }
 
+// Tile (bx, by)'s region, x from bx FTX - HX to bx FTX - HX + RW - 1 and y
+// from by FTY - HY to by FTY - HY + RH - 1, lies inside the domain with no
+// cell of it on a wall: the first cell is past x = 0 and y = 0 and one cell
+// beyond the last is still inside.
+__device__ __forceinline__ bool inner_tile(const Grid3& g, int bx, int by) {
+  return bx >= 1 && by >= 1 && bx * FTX - HX + RW < g.nx && by * FTY - HY + RH < g.ny;
+}
+
 template <bool FACE, int MODE>
 __global__ void __launch_bounds__(PPL, 1) k_cheb_sgs_fused(const FusedArgs P) {
   extern __shared__ float2 smf2[];
   const int nz = P.g.nz;
   const long long G = gridDim.x, b = blockIdx.x;
-  // whole columns: tile r G + b in round r
+  // whole columns first: tile r G + b in round r < full; then the leftover
+  // columns: an equal contiguous share of their (tile, plane) units
   const long long full = P.units / nz / G;
-  for (long long r = 0; r < full; ++r) {
-    const int tile = (int)(r * G + b);
-    fused_segment<FACE, MODE>(P, smf2, tile % P.tiles_x, tile / P.tiles_x, 0, nz);
-    __syncthreads();
-  }
-  // leftover columns: an equal contiguous share of their (tile, plane) units
   const long long base = full * G * nz, rest = P.units - base;
   long long u = base + rest * b / G;
   const long long end = base + rest * (b + 1) / G;
-  while (u < end) {
-    const int tile = (int)(u / nz);
-    const int k0 = (int)(u - (long long)tile * nz);
-    const int k1 = (int)min((long long)nz, k0 + (end - u));
-    fused_segment<FACE, MODE>(P, smf2, tile % P.tiles_x, tile / P.tiles_x, k0, k1);
-    u += k1 - k0;
+  long long r = 0;
+  for (;;) {
+    int tile, k0, k1;
+    if (r < full) {
+      tile = (int)(r * G + b);
+      k0 = 0;
+      k1 = nz;
+      ++r;
+    } else if (u < end) {
+      tile = (int)(u / nz);
+      k0 = (int)(u - (long long)tile * nz);
+      k1 = (int)min((long long)nz, k0 + (end - u));
+      u += k1 - k0;
+    } else {
+      break;
+    }
+    const int bx = tile % P.tiles_x, by = tile / P.tiles_x;
+    // (the face form has no wall masks: it keeps one form of the segment)
+    if (!FACE && inner_tile(P.g, bx, by))
+      fused_segment<FACE, MODE, !FACE>(P, smf2, bx, by, k0, k1);
+    else
+      fused_segment<FACE, MODE, false>(P, smf2, bx, by, k0, k1);
     __syncthreads();
   }
 }
