@@ -230,7 +230,6 @@ struct gmg_ctx {
   std::vector<LevelData> lev;  // 0 = coarsest
   int nc = 0;
   double *cA = nullptr, *cW = nullptr, *cinv64 = nullptr;
-  float* cinv32 = nullptr;
   int* cstatus = nullptr;
   int nv = 0;
   double* V = nullptr;
@@ -387,8 +386,8 @@ gmg_status prof_prolong_add(gmg_ctx* c, const Grid3& g, const T* e, T* x, int mo
           launch_prolong_add<T>(g, e, x, mode, s));
 }
 template <typename T>
-gmg_status prof_coarse_apply(gmg_ctx* c, int n, const T* Ainv, const T* b, T* x, cudaStream_t s) {
-  GMG_RUN(is_f32<T>() ? K_COARSE_F32 : K_COARSE_F64, ((double)n * n + 2.0 * n) * sizeof(T),
+gmg_status prof_coarse_apply(gmg_ctx* c, int n, const double* Ainv, const T* b, T* x, cudaStream_t s) {
+  GMG_RUN(is_f32<T>() ? K_COARSE_F32 : K_COARSE_F64, (double)n * n * 8.0 + 2.0 * n * sizeof(T),
           launch_coarse_apply<T>(n, Ainv, b, x, s));
 }
 template <typename T>
@@ -990,7 +989,7 @@ gmg_status build(gmg_ctx* c, const double* a_dev) {
     CKS(c->mixed ? assemble_coarse_faces<float>(c, C0) : assemble_coarse_faces<double>(c, C0));
   else
     CKS(prof_coarse_assemble(c, C0.g, C0.a64, c->cA, c->s));
-  CKS(prof_coarse_factor(c, c->nc, c->cA, c->cW, c->cinv64, c->cinv32, c->cstatus, c->s));
+  CKS(prof_coarse_factor(c, c->nc, c->cA, c->cW, c->cinv64, nullptr, c->cstatus, c->s));
   CK(launch_words_to_host(c->cstatus, c->hstat_dev, sizeof(int), c->s));
   CK(cudaStreamSynchronize(c->s));
   if (c->hstat[0] != 0) return GMG_ERR_BREAKDOWN;
@@ -1001,13 +1000,6 @@ gmg_status build(gmg_ctx* c, const double* a_dev) {
 // ---------------------------------------------------------------------------
 // V-cycle (Sec. 3.2, Appendix A)
 // ---------------------------------------------------------------------------
-
-template <typename T>
-const T* coarse_inv(const gmg_ctx* c);
-template <>
-const float* coarse_inv<float>(const gmg_ctx* c) { return c->cinv32; }
-template <>
-const double* coarse_inv<double>(const gmg_ctx* c) { return c->cinv64; }
 
 // cheb_steps Chebyshev steps with the smoother preconditioner; x_is_zero
 // starts from x = 0 (then r = b and x's contents are ignored).
@@ -1083,7 +1075,7 @@ gmg_status smooth_fused(gmg_ctx* c, int l, const float* b, const float* xin, flo
 
 template <typename T>
 gmg_status vcycle(gmg_ctx* c, int l, const T* b, T* x, bool from_guess = false) {
-  if (l == 0) return (prof_coarse_apply<T>(c, c->nc, coarse_inv<T>(c), b, x, c->s));
+  if (l == 0) return (prof_coarse_apply<T>(c, c->nc, c->cinv64, b, x, c->s));
   const LevelData& L = c->lev[l];
   const LevelData& Lc = c->lev[l - 1];
   if constexpr (sizeof(T) == 4) {
@@ -1120,7 +1112,7 @@ gmg_status fmg(gmg_ctx* c, int top, const T* b, T* z) {
     CKS(lv_residual_restrict<T>(c, c->lev[l], bl, (const T*)nullptr, (T*)c->lev[l - 1].b));
     bl = (const T*)c->lev[l - 1].b;
   }
-  CKS(prof_coarse_apply<T>(c, c->nc, coarse_inv<T>(c), (const T*)c->lev[0].b, (T*)c->lev[0].x, c->s));
+  CKS(prof_coarse_apply<T>(c, c->nc, c->cinv64, (const T*)c->lev[0].b, (T*)c->lev[0].x, c->s));
   for (int l = 1; l <= top; ++l) {
     const LevelData& L = c->lev[l];
     T* xl = l == top ? z : (T*)L.x;
@@ -1703,7 +1695,6 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
   if ((st = dalloc(c, &c->cA, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->cW, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->cinv64, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
-  if ((st = dalloc(c, &c->cinv32, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->cstatus, 4)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->eigH, (size_t)EIG_STRIDE * EIG_MAX_STEPS)) != GMG_OK) return fail(st);
   {
@@ -2125,7 +2116,7 @@ gmg_status gmg_level_prolong_add(gmg_ctx* c, int level, const void* e, void* x) 
 
 gmg_status gmg_coarse_solve(gmg_ctx* c, const void* b, void* x) {
   if (!c || !b || !x) return GMG_ERR_ARG;
-  if (c->mixed) return (prof_coarse_apply<float>(c, c->nc, c->cinv32, (const float*)b, (float*)x, c->s));
+  if (c->mixed) return (prof_coarse_apply<float>(c, c->nc, c->cinv64, (const float*)b, (float*)x, c->s));
   return (prof_coarse_apply<double>(c, c->nc, c->cinv64, (const double*)b, (double*)x, c->s));
 }
 

@@ -407,8 +407,10 @@ cudaError_t launch_coarse_assemble(const Grid3& g, const double* a, double* A, c
 // status[0] = 0 on success, 1 + column if a pivot was not positive.
 cudaError_t launch_coarse_factor(int n, double* A, double* work, double* Ainv, float* Ainv32,
                                  int* status, cudaStream_t s);
-// x = Ainv b (dense matvec), level precision.
+// x = Ainv b (dense matvec): b and x in level precision, the FP64 inverse and
+// FP64 sums (an FP32 inverse of the ill-conditioned coarsest operator would
+// lose up to cond(A) x 2^-24 of the coarse correction).
 template <typename T>
-cudaError_t launch_coarse_apply(int n, const T* Ainv, const T* b, T* x, cudaStream_t s);
+cudaError_t launch_coarse_apply(int n, const double* Ainv, const T* b, T* x, cudaStream_t s);
 
 }  // namespace gmg

@@ -221,15 +221,15 @@ __global__ void __launch_bounds__(1024) k_coarse_factor(int n, double* __restric
 
 // x = Ainv b, one warp per row.
 template <typename T>
-__global__ void k_coarse_apply(int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x) {
+__global__ void k_coarse_apply(int n, const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
-  T s = (T)0;
-  for (int c = lane; c < n; c += 32) s += Ainv[(size_t)warp * n + c] * b[c];
+  double s = 0.0;
+  for (int c = lane; c < n; c += 32) s += Ainv[(size_t)warp * n + c] * (double)b[c];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) x[warp] = s;
+  if (lane == 0) x[warp] = (T)s;
 }
 
 }  // namespace
@@ -286,12 +286,12 @@ cudaError_t launch_coarse_factor(int n, double* A, double* work, double* Ainv, f
 }
 
 template <typename T>
-cudaError_t launch_coarse_apply(int n, const T* Ainv, const T* b, T* x, cudaStream_t s) {
+cudaError_t launch_coarse_apply(int n, const double* Ainv, const T* b, T* x, cudaStream_t s) {
   const int warps_per_block = 8;
   k_coarse_apply<T><<<(n + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(n, Ainv, b, x);
   return cudaGetLastError();
 }
-template cudaError_t launch_coarse_apply<float>(int, const float*, const float*, float*, cudaStream_t);
+template cudaError_t launch_coarse_apply<float>(int, const double*, const float*, float*, cudaStream_t);
 template cudaError_t launch_coarse_apply<double>(int, const double*, const double*, double*, cudaStream_t);
 
 }  // namespace gmg
