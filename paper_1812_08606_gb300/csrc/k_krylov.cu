@@ -209,12 +209,32 @@ __global__ void __launch_bounds__(RT) k_cgs_update_f4(size_t n4, float4* __restr
 // block b's part of (v_i, v_j).  One pass reads each vector once, in float2
 // pieces: the NP accumulators and two values per vector fit two blocks per
 // SM.  Per-thread FP32 sums (reduce_blocks gives each thread at most about a
-// thousand elements at the sizes of a level), FP64 across threads and blocks.
+// thousand elements at the sizes of a level) and FP32 sums over a warp, then
+// FP64 over the block's warps and over blocks: the NP block sums cost one
+// barrier, not 2 NP, and no FP64 shuffle chains on the 1/64-rate FP64 pipe.
+template <int NP>
+__device__ __forceinline__ void gram_block_sums(const float (&acc)[NP], double* __restrict__ out) {
+  __shared__ float red[RT / 32][NP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    float t = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) red[warp][q] = t;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < NP; q += RT) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < RT / 32; ++w) t += (double)red[w][q];
+    out[q] = t;
+  }
+}
 template <int NV>
 __global__ void __launch_bounds__(RT, 2) k_gram_f2(size_t n2, const float2* __restrict__ V, size_t ldv2,
                                                    double* __restrict__ partial) {
   constexpr int NP = NV * (NV + 1) / 2;
-  __shared__ double sh[RT / 32];
   float acc[NP];
 #pragma unroll
   for (int q = 0; q < NP; ++q) acc[q] = 0.f;
@@ -228,11 +248,7 @@ __global__ void __launch_bounds__(RT, 2) k_gram_f2(size_t n2, const float2* __re
 #pragma unroll
       for (int j = i; j < NV; ++j, ++q) acc[q] = fmaf(v[i].y, v[j].y, fmaf(v[i].x, v[j].x, acc[q]));
   }
-#pragma unroll
-  for (int q = 0; q < NP; ++q) {
-    const double t = block_sum<RT>((double)acc[q], sh);
-    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * NP + q] = t;
-  }
+  gram_block_sums<NP>(acc, partial + (size_t)blockIdx.x * NP);
 }
 
 // The same on single elements (n or the row stride odd).
@@ -240,7 +256,6 @@ template <int NV>
 __global__ void __launch_bounds__(RT) k_gram(size_t n, const float* __restrict__ V, size_t ldv,
                                              double* __restrict__ partial) {
   constexpr int NP = NV * (NV + 1) / 2;
-  __shared__ double sh[RT / 32];
   float acc[NP];
 #pragma unroll
   for (int q = 0; q < NP; ++q) acc[q] = 0.f;
@@ -254,11 +269,7 @@ __global__ void __launch_bounds__(RT) k_gram(size_t n, const float* __restrict__
 #pragma unroll
       for (int j = i; j < NV; ++j, ++q) acc[q] = fmaf(v[i], v[j], acc[q]);
   }
-#pragma unroll
-  for (int q = 0; q < NP; ++q) {
-    const double t = block_sum<RT>((double)acc[q], sh);
-    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * NP + q] = t;
-  }
+  gram_block_sums<NP>(acc, partial + (size_t)blockIdx.x * NP);
 }
 
 // out = alpha t + beta v + gamma u (u null: gamma = 0), FP32 arithmetic.
