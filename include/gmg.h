@@ -348,12 +348,14 @@ gmg_status gmg_solve_host(gmg_ctx* ctx, const double* a_host, const double* f_ho
                           gmg_solve_info* info);
 
 /* gmg_solve_host, pipelined: returns once the solve has finished (info filled)
- * with the copy-out of phi (and E) still in flight on the context's copy-out
- * stream.  phi_host and ex/ey/ez_host must stay valid and unread until
- * gmg_host_wait(ctx) returns; a_host, f_host and phi0_host have been consumed
- * only when the next call, or gmg_host_wait, returns.  A following call may be
- * made at once: its uploads and set-up overlap this copy-out (the link carries
- * both directions at once), and its own staging writes wait for it.  Errors
+ * and the field kernel is enqueued; the copy-out of phi (and E) is held back.
+ * The next host-array call enqueues it on the context's copy-out stream once
+ * its own upload of a is done (the set-up waits for that upload, which so has
+ * the link to itself), and it then overlaps that call's set-up and solve;
+ * gmg_host_wait enqueues it if no call comes first.  phi_host and ex/ey/ez_host
+ * must stay valid and unread until gmg_host_wait(ctx) returns; a_host, f_host
+ * and phi0_host have been consumed only when the next call, or gmg_host_wait,
+ * returns.  The next call's staging writes wait for the copy-out.  Errors
  * return like gmg_solve_host, with every copy completed. */
 gmg_status gmg_solve_host_async(gmg_ctx* ctx, const double* a_host, const double* f_host, const double* phi0_host,
                                 double* phi_host, void* ex_host, void* ey_host, void* ez_host, int field_fp32,

@@ -257,6 +257,14 @@ struct gmg_ctx {
   // potential's copy-out overlaps the field kernel
   cudaStream_t cs = nullptr, cso = nullptr;  // input and copy-out streams
   cudaEvent_t ev_in = nullptr, ev_a = nullptr, ev_out = nullptr, ev_done = nullptr;
+  // gmg_solve_host_async's copy-out of phi (and E), left for the next call to
+  // enqueue once its upload of a is done, or for gmg_host_wait
+  struct PendingOut {
+    bool on = false;
+    double* phi = nullptr;
+    void *ex = nullptr, *ey = nullptr, *ez = nullptr;
+    size_t bytes = 0, ebytes = 0;
+  } pend_out;
   float setup_ms = 0.f;
   // per-kernel profile
   bool prof_on = false;
@@ -1763,10 +1771,32 @@ gmg_status adjoint_coefficient_grad(gmg_ctx* c, const double* phi_dev, const dou
 namespace {
 
 // The host-array solve.  wait = true: returns with every copy done.  wait =
-// false (pipelined): returns once the solve has finished and the copy-out of
-// phi and E is enqueued on the copy-out stream; gmg_host_wait completes it, and
-// the next call's uploads and set-up overlap it (the staging arrays of phi and E
-// are rewritten only after it, through the event ev_done).
+// false (pipelined): returns once the solve has finished and the field kernel
+// is enqueued.  The copy-out of phi and E is held back: the next call enqueues
+// it once its upload of a is done, so that the upload the set-up waits for does
+// not share the link with the copy-out (both directions at once run at about
+// 146 GB/s each instead of 210 and 193), and the copy-out then overlaps the
+// set-up; gmg_host_wait enqueues it if no call came.  The staging arrays of phi
+// and E are rewritten only after it, through the event ev_done.
+
+// Enqueue the held-back copy-out on the copy-out stream, after the compute
+// stream's work (ev_out) and, if given, after the event `after`.
+gmg_status flush_pending_out(gmg_ctx* c, cudaEvent_t after) {
+  auto& po = c->pend_out;
+  if (!po.on) return GMG_OK;
+  po.on = false;
+  if (after) CK(cudaStreamWaitEvent(c->cso, after, 0));
+  CK(cudaStreamWaitEvent(c->cso, c->ev_out, 0));
+  CK(cudaMemcpyAsync(po.phi, c->st_phi, po.bytes, cudaMemcpyDeviceToHost, c->cso));
+  if (po.ex) {
+    CK(cudaMemcpyAsync(po.ex, c->st_ex, po.ebytes, cudaMemcpyDeviceToHost, c->cso));
+    CK(cudaMemcpyAsync(po.ey, c->st_ey, po.ebytes, cudaMemcpyDeviceToHost, c->cso));
+    CK(cudaMemcpyAsync(po.ez, c->st_ez, po.ebytes, cudaMemcpyDeviceToHost, c->cso));
+  }
+  CK(cudaEventRecord(c->ev_done, c->cso));
+  return GMG_OK;
+}
+
 gmg_status solve_host_impl(gmg_ctx* c, const double* a_host, const double* f_host, const double* phi0_host,
                            double* phi_host, void* ex_host, void* ey_host, void* ez_host, int field_fp32,
                            gmg_solve_info* info, bool wait) {
@@ -1800,6 +1830,8 @@ gmg_status solve_host_impl(gmg_ctx* c, const double* a_host, const double* f_hos
   // touches the host arrays after the call.
   auto finish = [&](gmg_status st) {
     if (!wait && (st == GMG_OK || st == GMG_ERR_NOT_CONVERGED)) return st;
+    const gmg_status ps = flush_pending_out(c, nullptr);  // an earlier call's copy-out, after an error
+    if (st == GMG_OK) st = ps;
     const cudaError_t e1 = cudaStreamSynchronize(c->cs);
     const cudaError_t e2 = cudaStreamSynchronize(c->cso);
     const cudaError_t e3 = cudaStreamSynchronize(c->s);
@@ -1822,6 +1854,11 @@ gmg_status solve_host_impl(gmg_ctx* c, const double* a_host, const double* f_hos
     CKF(cudaEventRecord(c->ev_a, c->cs));
     CKF(cudaStreamWaitEvent(c->s, c->ev_a, 0));
   }
+  // the previous pipelined call's copy-out, after this call's upload of a
+  {
+    const gmg_status ps = flush_pending_out(c, a_host ? c->ev_a : nullptr);
+    if (ps != GMG_OK) return finish(ps);
+  }
   CKF(cudaMemcpyAsync(c->st_f, f_host, bytes, cudaMemcpyHostToDevice, c->cs));
   CKF(cudaStreamWaitEvent(c->cs, c->ev_done, 0));
   if (phi0_host)
@@ -1836,22 +1873,37 @@ gmg_status solve_host_impl(gmg_ctx* c, const double* a_host, const double* f_hos
   CKF(cudaStreamWaitEvent(c->s, c->ev_in, 0));
   gmg_status st = solve_impl(c, c->st_f, c->st_phi, 0, info);
   if (st != GMG_OK && st != GMG_ERR_NOT_CONVERGED) return finish(st);
-  // phi leaves on the copy-out stream while the field kernel runs
-  CKF(cudaEventRecord(c->ev_out, c->s));
-  CKF(cudaStreamWaitEvent(c->cso, c->ev_out, 0));
-  CKF(cudaMemcpyAsync(phi_host, c->st_phi, bytes, cudaMemcpyDeviceToHost, c->cso));
+  if (wait) {
+    // phi leaves on the copy-out stream while the field kernel runs
+    CKF(cudaEventRecord(c->ev_out, c->s));
+    CKF(cudaStreamWaitEvent(c->cso, c->ev_out, 0));
+    CKF(cudaMemcpyAsync(phi_host, c->st_phi, bytes, cudaMemcpyDeviceToHost, c->cso));
+  }
   if (want_e) {
     const gmg_status fs = field_from_potential(c, c->st_phi, c->st_ex, c->st_ey, c->st_ez, field_fp32);
     if (fs != GMG_OK) return finish(fs);
-    CKF(cudaEventRecord(c->ev_out, c->s));
-    CKF(cudaStreamWaitEvent(c->cso, c->ev_out, 0));
-    CKF(cudaMemcpyAsync(ex_host, c->st_ex, n * esz, cudaMemcpyDeviceToHost, c->cso));
-    CKF(cudaMemcpyAsync(ey_host, c->st_ey, n * esz, cudaMemcpyDeviceToHost, c->cso));
-    CKF(cudaMemcpyAsync(ez_host, c->st_ez, n * esz, cudaMemcpyDeviceToHost, c->cso));
+    if (wait) {
+      CKF(cudaEventRecord(c->ev_out, c->s));
+      CKF(cudaStreamWaitEvent(c->cso, c->ev_out, 0));
+      CKF(cudaMemcpyAsync(ex_host, c->st_ex, n * esz, cudaMemcpyDeviceToHost, c->cso));
+      CKF(cudaMemcpyAsync(ey_host, c->st_ey, n * esz, cudaMemcpyDeviceToHost, c->cso));
+      CKF(cudaMemcpyAsync(ez_host, c->st_ez, n * esz, cudaMemcpyDeviceToHost, c->cso));
+    }
   }
-  // the next call rewrites phi's staging array (and, after its solve, E's) only
-  // once this copy-out is done: its input stream waits on ev_done
-  CKF(cudaEventRecord(c->ev_done, c->cso));
+  if (wait) {
+    // the next call rewrites phi's staging array (and, after its solve, E's) only
+    // once this copy-out is done: its input stream waits on ev_done
+    CKF(cudaEventRecord(c->ev_done, c->cso));
+  } else {
+    CKF(cudaEventRecord(c->ev_out, c->s));
+    c->pend_out.on = true;
+    c->pend_out.phi = phi_host;
+    c->pend_out.ex = want_e ? ex_host : nullptr;
+    c->pend_out.ey = want_e ? ey_host : nullptr;
+    c->pend_out.ez = want_e ? ez_host : nullptr;
+    c->pend_out.bytes = bytes;
+    c->pend_out.ebytes = n * esz;
+  }
 #undef CKF
   return finish(st);
 }
@@ -1874,9 +1926,11 @@ gmg_status gmg_solve_host_async(gmg_ctx* c, const double* a_host, const double* 
 gmg_status gmg_host_wait(gmg_ctx* c) {
   if (!c) return GMG_ERR_ARG;
   if (!c->cs) return GMG_OK;  // no host-array solve yet
+  const gmg_status ps = flush_pending_out(c, nullptr);
   const cudaError_t e1 = cudaStreamSynchronize(c->cs);
   const cudaError_t e2 = cudaStreamSynchronize(c->cso);
   const cudaError_t e3 = cudaStreamSynchronize(c->s);
+  if (ps != GMG_OK) return ps;
   if (e1 != cudaSuccess) return map_err(e1);
   if (e2 != cudaSuccess) return map_err(e2);
   return e3 == cudaSuccess ? GMG_OK : map_err(e3);

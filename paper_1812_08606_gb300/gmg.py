@@ -346,8 +346,10 @@ def gmg_solve_host(ctx: Context, a_host, f_host, phi_host, phi0_host=None, ex_ho
 
 def gmg_solve_host_async(ctx: Context, a_host, f_host, phi_host, phi0_host=None, ex_host=None, ey_host=None,
                          ez_host=None):
-    """gmg_solve_host, pipelined: returns with the copy-out of phi (and E) in
-    flight; gmg_host_wait(ctx) completes it before the host arrays are read."""
+    """gmg_solve_host, pipelined: returns once the solve is done, with the
+    copy-out of phi (and E) held back for the next host-array call (after its
+    upload of a) or for gmg_host_wait(ctx), which completes it before the host
+    arrays are read."""
     return _solve_host("gmg_solve_host_async", ctx, a_host, f_host, phi_host, phi0_host, ex_host, ey_host, ez_host)
 
 

@@ -662,6 +662,51 @@ def test_pipelined_host_solves_match_synchronous_ones():
     ctx_s.close()
 
 
+def test_pipelined_host_copy_out_completes_on_the_next_call_or_the_wait():
+    """The pipelined call holds its copy-out back for the next call (after that
+    call's upload of a) or for gmg_host_wait.  An async call followed by a
+    synchronous one: both results are complete when the synchronous call
+    returns.  An async call that reuses the coefficient (a_host NULL), then
+    gmg_host_wait: complete too.  All equal the synchronous results bit for bit."""
+    shape = (16, 24, 32)
+    p = _params(shape)
+    cases = []
+    for seed in (530, 531):
+        a = 1.0 + 0.5 * (random_field(seed, shape) + 1.0)
+        f = random_field(seed + 10, shape)
+        cases.append((torch.from_numpy(a).pin_memory(), torch.from_numpy(f).pin_memory()))
+
+    def bufs(fill):
+        phi = torch.full(shape, fill, dtype=torch.float64).pin_memory()
+        return phi, [torch.full(shape, fill, dtype=torch.float32).pin_memory() for _ in range(3)]
+
+    ctx_s = gmg.gmg_setup(p, _t(np.ones(shape)))
+    want = []
+    for a_h, f_h in cases:
+        phi, e = bufs(0.0)
+        gmg.gmg_solve_host(ctx_s, a_h, f_h, phi, None, *e)
+        want.append((phi, e))
+    f_only = torch.from_numpy(random_field(545, shape)).pin_memory()
+    phi3, e3 = bufs(0.0)
+    gmg.gmg_solve_host(ctx_s, None, f_only, phi3, None, *e3)
+
+    ctx_a = gmg.gmg_setup(p, _t(np.ones(shape)))
+    got0, got1, got3 = bufs(np.nan), bufs(np.nan), bufs(np.nan)
+    assert gmg.gmg_solve_host_async(ctx_a, cases[0][0], cases[0][1], got0[0], None, *got0[1]).converged
+    assert gmg.gmg_solve_host(ctx_a, cases[1][0], cases[1][1], got1[0], None, *got1[1]).converged
+    for (pw, ew), (pg, eg) in zip(want, (got0, got1)):
+        assert torch.equal(pw, pg)
+        for a_, b_ in zip(ew, eg):
+            assert torch.equal(a_, b_)
+    assert gmg.gmg_solve_host_async(ctx_a, None, f_only, got3[0], None, *got3[1]).converged
+    gmg.gmg_host_wait(ctx_a)
+    assert torch.equal(phi3, got3[0])
+    for a_, b_ in zip(e3, got3[1]):
+        assert torch.equal(a_, b_)
+    ctx_a.close()
+    ctx_s.close()
+
+
 def test_full_size_solve_step_sampled_parity():
     """The benchmarked solve step at full size (512^3 two-channel workload, mixed
     precision, the bench's parameters): converged, with the true FP64 residual
