@@ -4,6 +4,8 @@
 // scaling for v_{j+1} = w / h_{j+1,j}, and the solution update x = x0 + Z_k y_k.
 // Reductions use a fixed number of blocks and a fixed summation order, so a
 // result does not depend on scheduling.
+#include <type_traits>
+
 #include "gmg_internal.cuh"
 
 namespace gmg {
@@ -392,6 +394,45 @@ __global__ void __launch_bounds__(RT) k_update_solution_k(size_t n, double* __re
   }
 }
 
+// The same update for FP32 Z (the mixed FGMRES): the sum s = Z y is formed in
+// double-float arithmetic on the FP32 pipe and added to x with one FP64 add.
+// Each y_i is split once per block into y_hi + y_lo (FP32, 48 bits together);
+// y_hi z is exact as ph + pe (pe by FMA), y_lo z is rounded, and the terms are
+// added with the two-sum of Knuth, so s carries about 2^-47 of the largest term
+// (FP64 FMAs: about 2^-52).  The correction is added to an FP64 x, which keeps
+// its own 53 bits; with GB300's FP64 rate at 1/64 of FP32, the K FP64 FMAs per
+// element of the FP64 form bind it to the FP64 pipe.
+template <int K>
+__global__ void __launch_bounds__(RT) k_update_solution_df(size_t n, double* __restrict__ x,
+                                                           const float* __restrict__ Z, size_t ldz,
+                                                           const double* __restrict__ y) {
+  __shared__ float yh[K], yl[K];
+  if (threadIdx.x < K) {
+    const double v = y[threadIdx.x];
+    const float h = (float)v;
+    yh[threadIdx.x] = h;
+    yl[threadIdx.x] = (float)(v - (double)h);
+  }
+  __syncthreads();
+  for (size_t p = blockIdx.x * (size_t)RT + threadIdx.x; p < n; p += (size_t)gridDim.x * RT) {
+    float zv[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) zv[i] = Z[i * ldz + p];
+    float sh = 0.f, sl = 0.f;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      // rounded-operation intrinsics: no contraction into FMAs may change ph or the two-sum
+      const float ph = __fmul_rn(yh[i], zv[i]);
+      const float pl = fmaf(yl[i], zv[i], fmaf(yh[i], zv[i], -ph));
+      const float t = __fadd_rn(sh, ph), bb = __fsub_rn(t, sh);
+      const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(ph, bb));
+      sl = __fadd_rn(sl, __fadd_rn(err, pl));
+      sh = t;
+    }
+    x[p] += f32_to_f64(sh) + f32_to_f64(sl);
+  }
+}
+
 // out = a1 v1 + a2 v2 + a3 v3 in FP64 (the vector updates of CG, FCG, CGS and
 // BiCGSTAB); FP32 terms are widened exactly, a null vector drops its term, and
 // out may be v3 or a double v1 / v2 (each element is read before it is written).
@@ -718,6 +759,15 @@ cudaError_t launch_update_solution(size_t n, double* x, const TZ* Z, size_t ldz,
                                    cudaStream_t s) {
   if (k < 1 || k > 64) return cudaErrorInvalidValue;
   const int nb = reduce_blocks(n);
+  if constexpr (std::is_same<TZ, float>::value) {
+    switch (k) {
+#define GMG_CASE(K) \
+  case K: k_update_solution_df<K><<<nb, RT, 0, s>>>(n, x, Z, ldz, y); return cudaGetLastError();
+      GMG_CASES32(GMG_CASE)
+#undef GMG_CASE
+      default: break;  // past 32 vectors: the FP64 form below
+    }
+  }
   switch (k) {
 #define GMG_CASE(K) \
   case K: k_update_solution_k<K, TZ><<<nb, RT, 0, s>>>(n, x, Z, ldz, y); break;
