@@ -265,24 +265,36 @@ __global__ void k_faces_of_cells(Links<T, true> L, double* __restrict__ kx, doub
   }
 }
 
-// Parent weight along one axis for fine index c of n (n even) with link
-// entries lk(m) (m = 1..n-1 interior; lk(0), lk(n) the plates when `plates`).
+// Parent weight R_n / (R_n + R_p) along one axis for fine index c of n (n
+// even) with link entries lk(m) (m = 1..n-1 interior; lk(0), lk(n) the plates
+// when `plates`), with the denominators cleared: one quotient instead of four,
+// the same value up to rounding.  Low child (c even), links k0 = lk(c-1),
+// k1 = lk(c), k2 = lk(c+1) (to its sibling):
+//   R_n = 1/k1 + 1/(2 k0), R_p = 1/(2 k2)  =>  w = (2 k0 + k1) k2 / ((2 k0 + k1) k2 + k0 k1);
+// the high child mirrors it (k0 = lk(c) to its sibling, k1 = lk(c+1), k2 = lk(c+2));
+// next to a plate (R_n = 1/k_plate, R_p = 1/(2 k_in)): w = 2 k_in / (2 k_in + k_plate).
+// Products of two entries stay far inside the FP32 range.
 template <typename T, typename F>
 __device__ __forceinline__ T parent_weight(int c, int n, bool plates, F lk) {
   const int m = n / 2, I = c >> 1;
-  T rp, rn;
   if ((c & 1) == 0) {
-    rp = quot((T)0.5, lk(c + 1));
-    if (I > 0) rn = quot((T)1, lk(c)) + quot((T)0.5, lk(c - 1));
-    else if (plates) rn = quot((T)1, lk(0));
-    else return (T)1;
-  } else {
-    rp = quot((T)0.5, lk(c));
-    if (I < m - 1) rn = quot((T)1, lk(c + 1)) + quot((T)0.5, lk(c + 2));
-    else if (plates) rn = quot((T)1, lk(n));
-    else return (T)1;
+    const T k2 = lk(c + 1);
+    if (I > 0) {
+      const T k0 = lk(c - 1), k1 = lk(c);
+      const T s = ((T)2 * k0 + k1) * k2;
+      return quot(s, s + k0 * k1);
+    }
+    if (plates) return quot((T)2 * k2, (T)2 * k2 + lk(0));
+    return (T)1;
   }
-  return quot(rn, rn + rp);
+  const T k0 = lk(c);
+  if (I < m - 1) {
+    const T k1 = lk(c + 1), k2 = lk(c + 2);
+    const T s = ((T)2 * k2 + k1) * k0;
+    return quot(s, s + k1 * k2);
+  }
+  if (plates) return quot((T)2 * k0, (T)2 * k0 + lk(n));
+  return (T)1;
 }
 
 // One thread per (i, j) column of a 32 x 8 block, marching through kchunk
