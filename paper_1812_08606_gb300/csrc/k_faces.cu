@@ -205,13 +205,16 @@ struct Links {
 __device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double quot(double a, double b) { return a / b; }
 
+// 1 / (1/k1 + 2/k2 + 1/k3) as k1 k3 / (k1 + k3 + 2 k1 k3 / k2): two quotients
+// instead of four, and no product of more than two entries (no overflow).
 template <typename T>
 __device__ __forceinline__ T series3(T k1, T k2, T k3) {
-  return quot((T)1, quot((T)1, k1) + quot((T)2, k2) + quot((T)1, k3));
+  const T p = k1 * k3;
+  return quot(p, k1 + k3 + (T)2 * quot(p, k2));
 }
 template <typename T>
 __device__ __forceinline__ T series_plate(T kin, T kplate) {
-  return quot((T)1, quot((T)1, kin) + quot((T)2, kplate));
+  return quot(kin * kplate, kplate + (T)2 * kin);  // 1 / (1/kin + 2/kplate)
 }
 
 // One thread per coarse column (I, J) of a 32 x 8 block, marching through
