@@ -1687,6 +1687,8 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
       if ((st = dev_alloc(c, &D.r, D.n * c->esz)) != GMG_OK) return fail(st);
       if ((st = dev_alloc(c, &D.z, D.n * c->esz)) != GMG_OK) return fail(st);
       if ((st = dev_alloc(c, &D.d, D.n * c->esz)) != GMG_OK) return fail(st);
+      // the fused smoother's first step with x_in reads d with weight 0: d must hold finite values
+      if (D.fused && cudaMemset(D.d, 0, D.n * c->esz) != cudaSuccess) return fail(GMG_ERR_CUDA);
     }
   }
   const size_t N = c->lev.back().n;

@@ -79,6 +79,18 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 sc2(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float lane(float2 v, int i) { return i ? v.y : v.x; }
 
+// A prefetch load issued where it stands: a volatile read-only load with a
+// memory clobber is not moved past the shared-memory work that follows it, so
+// its latency stays hidden behind the step's three stages.  (Without it the
+// compiler placed the next plane's loads late in some step kinds: the first
+// post-smoothing step waited 4.1 cycles per instruction on them and ran 38%
+// slower than a middle step, which moves more bytes.)
+__device__ __forceinline__ float2 ldg_early(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p) : "memory");
+  return v;
+}
+
 // Kind of step, fixed at compile time (each kind is its own kernel, so the
 // step carries no runtime tests for it): the first step of a smoothing (d =
 // c2 z, d not read), with x_in = 0 (pre-smoothing from zero: x_in not read),
@@ -195,17 +207,17 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
     if constexpr (FACE) pkx = pky = zero2;
     const int ot = t * pl2 + qo;  // pair offset of plane t
     if (in && (ST || (t + 1 >= 0 && t + 1 < nz && t + 1 <= k1 + 2))) {
-      pa = __ldg(A2 + (ot + pl2));
-      if (!xzero) px = __ldg(X2 + (ot + pl2));
+      pa = ldg_early(A2 + (ot + pl2));
+      if (!xzero) px = ldg_early(X2 + (ot + pl2));
       if constexpr (FACE) {
-        pkx = __ldg(KX2 + (ot + pl2));
-        pky = __ldg(KY2 + (ot + pl2));
+        pkx = ldg_early(KX2 + (ot + pl2));
+        pky = ldg_early(KY2 + (ot + pl2));
       }
     } else if (FACE && !ST && in && t + 1 == nz && t + 1 <= k1 + 2) {
-      pa = __ldg(KT2 + qo);  // the top plate's entries, as the z face above plane nz - 1
+      pa = ldg_early(KT2 + qo);  // the top plate's entries, as the z face above plane nz - 1
     }
-    if (!eig && rst && (ST || (t >= rlo && t < rhi))) pbn = __ldg(B2 + ot);
-    if (fst && !first && (ST || (t - 2 >= k0 && t - 2 < k1))) pdn = __ldg(D2 + (ot - 2 * pl2));
+    if (!eig && rst && (ST || (t >= rlo && t < rhi))) pbn = ldg_early(B2 + ot);
+    if (fst && !first && (ST || (t - 2 >= k0 && t - 2 < k1))) pdn = ldg_early(D2 + (ot - 2 * pl2));
 
     // ---- residual stage, plane kr = t - 1: r, 1/D (both cells), red z ----
     const int kr = t - 1;
@@ -447,10 +459,14 @@ int g_fused_slots[2][kMaxDevices] = {};
 std::mutex g_fused_mutex;
 
 // The step kinds the library launches: pre-smoothing from zero (first, x_in =
-// 0), first with x_in, middle, last (each with or without x_in = 0 for a
-// one-step smoothing), and the eigen-estimate basis step without and with d.
-constexpr int kModes[] = {M_FIRST | M_XZERO, M_FIRST | M_XZERO | M_LAST, M_FIRST, M_FIRST | M_LAST, 0, M_LAST,
-                          M_FIRST | M_EIG, M_EIG};
+// 0; also as a one-step smoothing), middle, last, and the eigen-estimate basis
+// step without and with d.  The first step with x_in runs as a middle step (or
+// a last one) with c1 = 0: fma(0, d, c2 z) = c2 z exactly for finite d, and the
+// library keeps d finite (zeroed when allocated, written only by smoothing
+// steps).  Compiled as its own kind it ran 38% slower than a middle step that
+// moves more bytes (1.42 against 1.04 ms at 512^3, on any data), stalled on
+// global loads (4.1 cycles per instruction against 0.5).
+constexpr int kModes[] = {M_FIRST | M_XZERO, M_FIRST | M_XZERO | M_LAST, 0, M_LAST, M_FIRST | M_EIG, M_EIG};
 
 template <bool FACE, int MODE>
 cudaError_t set_smem() {
@@ -471,8 +487,7 @@ cudaError_t fused_slots(int* out) {
   int& slots = g_fused_slots[FACE ? 1 : 0][dev];
   if (slots == 0) {
     const cudaError_t es[] = {set_smem<FACE, kModes[0]>(), set_smem<FACE, kModes[1]>(), set_smem<FACE, kModes[2]>(),
-                              set_smem<FACE, kModes[3]>(), set_smem<FACE, kModes[4]>(), set_smem<FACE, kModes[5]>(),
-                              set_smem<FACE, kModes[6]>(), set_smem<FACE, kModes[7]>()};
+                              set_smem<FACE, kModes[3]>(), set_smem<FACE, kModes[4]>(), set_smem<FACE, kModes[5]>()};
     for (cudaError_t q : es)
       if (q != cudaSuccess) return q;
     int sms = 0, per = 0;
@@ -486,7 +501,7 @@ cudaError_t fused_slots(int* out) {
 }
 
 template <bool FACE>
-cudaError_t launch_fused(const FusedArgs& P, long long units, cudaStream_t s) {
+cudaError_t launch_fused(const FusedArgs& P0, long long units, cudaStream_t s) {
   int slots = 0;
   const cudaError_t e = fused_slots<FACE>(&slots);
   if (e != cudaSuccess) return e;
@@ -494,14 +509,17 @@ cudaError_t launch_fused(const FusedArgs& P, long long units, cudaStream_t s) {
   const long long blocks = std::max(1LL, std::min((long long)slots, units / 4));
   const dim3 grid((unsigned)blocks), block(RP, RH);
   const size_t smem = FACE ? FUSED_SMEM_FACE : FUSED_SMEM;
+  FusedArgs P = P0;
   const bool eig = (P.flags & CHEB_EIG) != 0;
-  const int mode = ((P.flags & CHEB_FIRST) ? M_FIRST : 0) | (P.xin ? 0 : M_XZERO) |
-                   ((P.flags & CHEB_LAST) && !eig ? M_LAST : 0) | (eig ? M_EIG : 0);
+  int mode = ((P.flags & CHEB_FIRST) ? M_FIRST : 0) | (P.xin ? 0 : M_XZERO) |
+             ((P.flags & CHEB_LAST) && !eig ? M_LAST : 0) | (eig ? M_EIG : 0);
+  if ((mode & (M_FIRST | M_XZERO | M_EIG)) == M_FIRST) {  // the first step with x_in: see kModes
+    mode &= ~M_FIRST;
+    P.c1 = 0.f;
+  }
   switch (mode) {
     case M_FIRST | M_XZERO: k_cheb_sgs_fused<FACE, M_FIRST | M_XZERO><<<grid, block, smem, s>>>(P); break;
     case M_FIRST | M_XZERO | M_LAST: k_cheb_sgs_fused<FACE, M_FIRST | M_XZERO | M_LAST><<<grid, block, smem, s>>>(P); break;
-    case M_FIRST: k_cheb_sgs_fused<FACE, M_FIRST><<<grid, block, smem, s>>>(P); break;
-    case M_FIRST | M_LAST: k_cheb_sgs_fused<FACE, M_FIRST | M_LAST><<<grid, block, smem, s>>>(P); break;
     case 0: k_cheb_sgs_fused<FACE, 0><<<grid, block, smem, s>>>(P); break;
     case M_LAST: k_cheb_sgs_fused<FACE, M_LAST><<<grid, block, smem, s>>>(P); break;
     case M_FIRST | M_EIG: k_cheb_sgs_fused<FACE, M_FIRST | M_EIG><<<grid, block, smem, s>>>(P); break;
