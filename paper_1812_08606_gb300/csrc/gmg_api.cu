@@ -783,11 +783,12 @@ gmg_status ritz_chebyshev_basis(gmg_ctx* c, int l, double* lam_out) {
     float* vnext = V + (size_t)(j + 1) * n;
     if (L.fused) {
       // the basis step reads v_{j-1} through d (never written) and forms
-      // x_out = beta x_in + gamma d - (-alpha) B^{-1} A x_in with b = 0
+      // x_out = beta x_in + gamma d - (-alpha) B^{-1} A x_in with b = 0; for
+      // j = 0, d = v_0 with gamma = 0 (the kind that reads d runs faster than
+      // the one that does not: 0.88 against 0.99 ms at 512^3)
       LevelData Lt = L;
-      Lt.d = vprev;
-      CKS(lv_cheb_fused(c, Lt, (const float*)L.b, vj, vnext, gamma, -alpha,
-                        CHEB_UPDATE | CHEB_EIG | (j == 0 ? CHEB_FIRST : 0), beta));
+      Lt.d = j == 0 ? (float*)vj : vprev;
+      CKS(lv_cheb_fused(c, Lt, (const float*)L.b, vj, vnext, gamma, -alpha, CHEB_UPDATE | CHEB_EIG, beta));
     } else {
       CKS(lv_apply<float>(c, L, vj, (float*)L.r));
       CKS(smoother_pc<float>(c, L, (const float*)L.r, (float*)L.z));

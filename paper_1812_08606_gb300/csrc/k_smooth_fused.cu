@@ -79,18 +79,6 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 sc2(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float lane(float2 v, int i) { return i ? v.y : v.x; }
 
-// A prefetch load issued where it stands: a volatile read-only load with a
-// memory clobber is not moved past the shared-memory work that follows it, so
-// its latency stays hidden behind the step's three stages.  (Without it the
-// compiler placed the next plane's loads late in some step kinds: the first
-// post-smoothing step waited 4.1 cycles per instruction on them and ran 38%
-// slower than a middle step, which moves more bytes.)
-__device__ __forceinline__ float2 ldg_early(const float2* p) {
-  float2 v;
-  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p) : "memory");
-  return v;
-}
-
 // Kind of step, fixed at compile time (each kind is its own kernel, so the
 // step carries no runtime tests for it): the first step of a smoothing (d =
 // c2 z, d not read), with x_in = 0 (pre-smoothing from zero: x_in not read),
@@ -207,17 +195,17 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
     if constexpr (FACE) pkx = pky = zero2;
     const int ot = t * pl2 + qo;  // pair offset of plane t
     if (in && (ST || (t + 1 >= 0 && t + 1 < nz && t + 1 <= k1 + 2))) {
-      pa = ldg_early(A2 + (ot + pl2));
-      if (!xzero) px = ldg_early(X2 + (ot + pl2));
+      pa = __ldg(A2 + (ot + pl2));
+      if (!xzero) px = __ldg(X2 + (ot + pl2));
       if constexpr (FACE) {
-        pkx = ldg_early(KX2 + (ot + pl2));
-        pky = ldg_early(KY2 + (ot + pl2));
+        pkx = __ldg(KX2 + (ot + pl2));
+        pky = __ldg(KY2 + (ot + pl2));
       }
     } else if (FACE && !ST && in && t + 1 == nz && t + 1 <= k1 + 2) {
-      pa = ldg_early(KT2 + qo);  // the top plate's entries, as the z face above plane nz - 1
+      pa = __ldg(KT2 + qo);  // the top plate's entries, as the z face above plane nz - 1
     }
-    if (!eig && rst && (ST || (t >= rlo && t < rhi))) pbn = ldg_early(B2 + ot);
-    if (fst && !first && (ST || (t - 2 >= k0 && t - 2 < k1))) pdn = ldg_early(D2 + (ot - 2 * pl2));
+    if (!eig && rst && (ST || (t >= rlo && t < rhi))) pbn = __ldg(B2 + ot);
+    if (fst && !first && (ST || (t - 2 >= k0 && t - 2 < k1))) pdn = __ldg(D2 + (ot - 2 * pl2));
 
     // ---- residual stage, plane kr = t - 1: r, 1/D (both cells), red z ----
     const int kr = t - 1;
