@@ -852,10 +852,12 @@ gmg_status ritz_chebyshev_basis(gmg_ctx* c, int l, double* lam_out) {
   return GMG_OK;
 }
 
-// lambda_max, lambda* of level l: Arnoldi on B^{-1} A_l (Sec. 3.2) in the
-// level precision T.  FP64: basis in V, temporaries bvec / w.  FP32 (the
-// mixed-precision set-up; the bounds only steer the FP32 smoother): basis in
-// Z, temporaries the level's r / z.
+// lambda_max, lambda* of level l: the largest Ritz value of B^{-1} A_l
+// (Sec. 3.2) in the level precision T.  FP32 with the SSOR preconditioner and
+// at most 11 steps (the mixed-precision set-up; the bounds only steer the FP32
+// smoother): the Chebyshev basis and its Gram matrix (ritz_chebyshev_basis).
+// Otherwise Arnoldi with Gram-Schmidt: FP64 basis in V, temporaries bvec / w;
+// FP32 basis in Z, temporaries the level's r / z.
 template <typename T>
 gmg_status eig_bounds(gmg_ctx* c, int l) {
   LevelData& L = c->lev[l];

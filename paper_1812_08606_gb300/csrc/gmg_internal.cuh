@@ -403,7 +403,7 @@ cudaError_t launch_split(size_t n, const double* a, float2* a2, cudaStream_t s);
 // ---- Coarsest level: dense SPD operator, Cholesky, explicit inverse ----
 // A (n x n, row-major, n = g.n()) from the coarse coefficient.
 cudaError_t launch_coarse_assemble(const Grid3& g, const double* a, double* A, cudaStream_t s);
-// In place: A -> L (lower Cholesky factor), then Ainv = A^{-1} (FP64) and an FP32 copy.
+// In place: A -> L (lower Cholesky factor), then Ainv = A^{-1} (FP64) and, if Ainv32 is not null, an FP32 copy.
 // status[0] = 0 on success, 1 + column if a pivot was not positive.
 cudaError_t launch_coarse_factor(int n, double* A, double* work, double* Ainv, float* Ainv32,
                                  int* status, cudaStream_t s);
