@@ -79,6 +79,11 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 sc2(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float lane(float2 v, int i) { return i ? v.y : v.x; }
 
+// Bring a line into L2 ahead of its load (no register, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Kind of step, fixed at compile time (each kind is its own kernel, so the
 // step carries no runtime tests for it): the first step of a smoothing (d =
 // c2 z, d not read), with x_in = 0 (pre-smoothing from zero: x_in not read),
@@ -206,6 +211,23 @@ __device__ __forceinline__ void fused_segment(const FusedArgs& P, float2* smf2, 
     }
     if (!eig && rst && (ST || (t >= rlo && t < rhi))) pbn = __ldg(B2 + ot);
     if (fst && !first && (ST || (t - 2 >= k0 && t - 2 < k1))) pdn = __ldg(D2 + (ot - 2 * pl2));
+    // From zero (no x_in, r = b) a step has the least work, shorter than the
+    // loaded memory latency: bring the plane after next into L2 so that the
+    // loads above find their lines there (1.03 -> 0.75 ms at 512^3).  The
+    // other kinds hide the latency with their work, and the extra instructions
+    // made them 9-13% slower.
+    if (xzero && in) {
+      if (t + 2 >= 0 && t + 2 < nz) {
+        prefetch_l2(A2 + (ot + 2 * pl2));
+        if (!xzero) prefetch_l2(X2 + (ot + 2 * pl2));
+        if constexpr (FACE) {
+          prefetch_l2(KX2 + (ot + 2 * pl2));
+          prefetch_l2(KY2 + (ot + 2 * pl2));
+        }
+      }
+      if (!eig && t + 1 >= 0 && t + 1 < nz) prefetch_l2(B2 + (ot + pl2));
+      if (!first && t - 1 >= 0 && t - 1 < nz) prefetch_l2(D2 + (ot - pl2));
+    }
 
     // ---- residual stage, plane kr = t - 1: r, 1/D (both cells), red z ----
     const int kr = t - 1;
