@@ -415,6 +415,14 @@ __global__ void __launch_bounds__(PTP* PTR) k_prolong_opdep_pairs(Grid3 g, const
       if (tx == PTP - 1) { uc = h0; un = q0; uz = hz; uzn = qz; }
       if (act) {
         const int o = k * pl2 + q;
+        // this cell's weights and x two planes ahead into L2: the loads below have
+        // no lead, and with them the kernel ran at 5.0 TB/s instead of 6.8
+        if (k + 2 < g.nz) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(WX + o + 2 * pl2));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(WY + o + 2 * pl2));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(WZ + o + 2 * pl2));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(X2 + o + 2 * pl2));
+        }
         const float2 wx = __ldg(WX + o), wy = __ldg(WY + o), wz = __ldg(WZ + o);
         // y then z for one column with a cell's weights
         auto yz = [](float wyv, float wzv, float e00, float e01, float e10, float e11) {
