@@ -68,6 +68,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--smoother-kernel", type=int, default=0, choices=[0, 2],
+                    help="0: the finest level's fused smoother fed by bulk-tensor copies; 2: without them")
     ap.add_argument("--no-regimes", action="store_true",
                     help="skip the first-step (FMG) and warm-started time-step measurements")
     ap.add_argument("--regime-steps", type=int, default=3)
@@ -284,7 +286,7 @@ def run_ours(args, dist):
     phi = torch.zeros_like(f)
     ex, ey, ez = (torch.empty((n, n, n), dtype=torch.float32, device=dev) for _ in range(3))
     stream = torch.cuda.current_stream()
-    params = gmg.gmg_default_params(n, n, n, precision=gmg.GMG_PREC_MIXED)
+    params = gmg.gmg_default_params(n, n, n, precision=gmg.GMG_PREC_MIXED, smoother_kernel=args.smoother_kernel)
     ctx = gmg.gmg_setup(params, a, stream)
 
     infos = []

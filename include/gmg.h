@@ -170,8 +170,12 @@ typedef struct gmg_params {
                                   product w = A z_j in GMG_PREC_MIXED        */
   int smoother_kernel;         /* 0: one fused pass per Chebyshev step where
                                   the level allows it (FP32, SGS, nx >= 32,
-                                  ny >= 16, nz >= 8); 1: separate residual
-                                  and half-sweep kernels everywhere          */
+                                  ny >= 16, nz >= 8), on the finest level fed
+                                  by bulk-tensor copies where nx % 4 == 0,
+                                  nx >= 64, ny >= 26 and the arrays are
+                                  16-byte aligned; 1: separate residual and
+                                  half-sweep kernels everywhere; 2: the fused
+                                  pass without the bulk-tensor copies        */
   int cycle;                   /* gmg_cycle                                  */
   int coarsening;              /* gmg_coarsening                             */
 } gmg_params;

@@ -514,7 +514,9 @@ double fused_words(bool xin, int flags) {
 gmg_status prof_cheb_sgs_fused(gmg_ctx* c, const Grid3& g, const float* a, const float* b, const float* xin,
                                float* xout, float* d, double c1, double c2, double ce, int flags, cudaStream_t s) {
   const double words = fused_words(xin != nullptr, flags);
-  GMG_RUN(K_CHEB_FUSED, 4.0 * words * g.n(), launch_cheb_sgs_fused(g, a, b, xin, xout, d, c1, c2, ce, flags, s));
+  int* tma_status = c->p.smoother_kernel == 0 ? c->cstatus + 1 : nullptr;
+  GMG_RUN(K_CHEB_FUSED, 4.0 * words * g.n(),
+          launch_cheb_sgs_fused(g, a, b, xin, xout, d, c1, c2, ce, flags, tma_status, s));
 }
 gmg_status prof_gram(gmg_ctx* c, size_t n, const float* V, size_t ldv, int nv, double* partial, cudaStream_t s) {
   GMG_RUN(K_GRAM, 4.0 * n * nv, launch_gram(n, V, ldv, nv, partial, s));
@@ -546,7 +548,7 @@ gmg_status validate(const gmg_params* p, int* nlevels) {
   if (p->smoother_pc < 0 || p->smoother_pc > 2) return GMG_ERR_ARG;
   if (p->orthogonalization != 0 && p->orthogonalization != 1) return GMG_ERR_ARG;
   if (p->outer_arith != GMG_OUTER_FP64 && p->outer_arith != GMG_OUTER_DOUBLE_FLOAT) return GMG_ERR_ARG;
-  if (p->smoother_kernel != 0 && p->smoother_kernel != 1) return GMG_ERR_ARG;
+  if (p->smoother_kernel < 0 || p->smoother_kernel > 2) return GMG_ERR_ARG;
   if (p->cycle < GMG_CYCLE_V || p->cycle > GMG_CYCLE_AUTO) return GMG_ERR_ARG;
   if ((double)p->nx * p->ny * p->nz > 4.0e9) return GMG_ERR_ARG;
   int nx = p->nx, ny = p->ny, nz = p->nz, L = 1;
@@ -1001,8 +1003,9 @@ gmg_status build(gmg_ctx* c, const double* a_dev) {
   else
     CKS(prof_coarse_assemble(c, C0.g, C0.a64, c->cA, c->s));
   CKS(prof_coarse_factor(c, c->nc, c->cA, c->cW, c->cinv64, nullptr, c->cstatus, c->s));
-  CK(launch_words_to_host(c->cstatus, c->hstat_dev, sizeof(int), c->s));
+  CK(launch_words_to_host(c->cstatus, c->hstat_dev, 2 * sizeof(int), c->s));
   CK(cudaStreamSynchronize(c->s));
+  if (c->hstat[1] != 0) return GMG_ERR_CUDA;  // a smoother step's copies did not arrive
   if (c->hstat[0] != 0) return GMG_ERR_BREAKDOWN;
   c->setup_ms = (float)(now_ms() - t0);
   return GMG_OK;
@@ -1308,8 +1311,10 @@ gmg_status solve_impl(gmg_ctx* c, const double* f, double* x, int homogeneous, g
     }
   }
 done:
+  CK(launch_words_to_host(c->cstatus + 1, c->hstat_dev + 1, sizeof(int), c->s));
   CK(cudaStreamSynchronize(c->s));
   prof_collect(c);
+  if (c->hstat[1] != 0) result = GMG_ERR_CUDA;  // a smoother step's copies did not arrive
   loc.solve_ms = (float)(now_ms() - t0);
   loc.precond_calls = (int)c->precond_calls;
   if (info) *info = loc;
@@ -1554,8 +1559,10 @@ gmg_status solve_short(gmg_ctx* c, int method, const double* f, double* x, int h
       loc.restarts++;
     }
   }
+  CK(launch_words_to_host(c->cstatus + 1, c->hstat_dev + 1, sizeof(int), c->s));
   CK(cudaStreamSynchronize(c->s));
   prof_collect(c);
+  if (c->hstat[1] != 0) result = GMG_ERR_CUDA;  // a smoother step's copies did not arrive
   loc.solve_ms = (float)(now_ms() - t0);
   loc.precond_calls = (int)c->precond_calls;
   if (info) *info = loc;
@@ -1683,7 +1690,7 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
     }
     if (!top && (st = dev_alloc(c, &D.x, D.n * c->esz)) != GMG_OK) return fail(st);
     if ((!top || c->mixed) && (st = dev_alloc(c, &D.b, D.n * c->esz)) != GMG_OK) return fail(st);
-    D.fused = c->mixed && l > 0 && p->smoother_pc == GMG_PC_SGS && p->smoother_kernel == 0 &&
+    D.fused = c->mixed && l > 0 && p->smoother_pc == GMG_PC_SGS && p->smoother_kernel != 1 &&
               fused_smoother_eligible(D.g);
     if (D.fused && (st = dalloc(c, &D.x2, D.n)) != GMG_OK) return fail(st);
     if (l > 0 || L == 1) {
@@ -1708,7 +1715,10 @@ gmg_status gmg_setup(const gmg_params* p, const double* a_dev, void* stream, gmg
   if ((st = dalloc(c, &c->cA, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->cW, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
   if ((st = dalloc(c, &c->cinv64, (size_t)c->nc * c->nc)) != GMG_OK) return fail(st);
+  // cstatus[0]: the coarse factorisation's status; cstatus[1]: waits of the
+  // copy-fed smoother that ran out (sticky)
   if ((st = dalloc(c, &c->cstatus, 4)) != GMG_OK) return fail(st);
+  if (cudaMemset(c->cstatus, 0, 4 * sizeof(int)) != cudaSuccess) return fail(GMG_ERR_CUDA);
   if ((st = dalloc(c, &c->eigH, (size_t)EIG_STRIDE * EIG_MAX_STEPS)) != GMG_OK) return fail(st);
   {
     // mapped, so that kernels write the scalars the host reads (read_scalars)

@@ -200,9 +200,20 @@ cudaError_t launch_sgs_half(const Grid3& g, const T* a, const T* r, T* z, int co
 // (FP32): x_out = x_in + d, d = c1 d + c2 B^{-1}(b - A x_in); xin null means
 // x_in = 0.  x_out must not alias x_in; d is updated in place.  ce is read
 // only with CHEB_EIG.
+// With tma_status non-null the step runs, where tma_smoother_eligible allows
+// it, on the kernel fed by bulk-tensor copies (k_smooth_tma.cu), which counts
+// in *tma_status the waits for its copies that ran out (none when correct).
 bool fused_smoother_eligible(const Grid3& g);
 cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b, const float* xin, float* xout,
-                                  float* d, double c1, double c2, double ce, int flags, cudaStream_t s);
+                                  float* d, double c1, double c2, double ce, int flags, int* tma_status,
+                                  cudaStream_t s);
+// The copy-fed kernel's conditions: a smoothing step (not CHEB_EIG), nx a
+// multiple of 4 (16-byte rows) and at least 64, ny at least 26, a, b, x_in
+// and d 16-byte aligned, x_out 8-byte aligned.
+bool tma_smoother_eligible(const Grid3& g, const float* a, const float* b, const float* xin, const float* xout,
+                           const float* d, int flags);
+cudaError_t launch_cheb_sgs_tma(const Grid3& g, const float* a, const float* b, const float* xin, float* xout,
+                                float* d, double c1, double c2, int flags, int* status, cudaStream_t s);
 // The same step on a face-form level (all face arrays 8-byte aligned).
 cudaError_t launch_cheb_sgs_fused_faces(const Grid3& g, const Faces<float>& F, const float* b, const float* xin,
                                         float* xout, float* d, double c1, double c2, double ce, int flags,

@@ -59,18 +59,19 @@ def test_twochannel512_solve_and_field_properties():
         assert np.abs(g - r).max() < 1e-5 * np.abs(r).max()
 
 
-# The fused smoother hands out whole tile columns (56 x 18 tiles, one resident
-# block per SM) before it splits the leftover columns into z-segments.  The
-# grids of the kernel-level parity tests have fewer tiles than blocks, so only
-# the split runs there; this grid has 19 x 29 = 551 tiles, so on 152 SMs every
-# block takes 3 whole columns first and the 95 left over are split.
+# The fused smoother hands out whole tile columns (one resident block per SM)
+# before it splits the leftover columns into z-segments.  The grids of the
+# kernel-level parity tests have fewer tiles than blocks, so only the split
+# runs there.  On this grid the finest level runs on the copy-fed kernel (56 x
+# 20 tiles): 19 x 26 = 494 tiles, so on 152 SMs every block takes 3 whole
+# columns first and the 38 left over are split.
 SPLIT_SHAPE = (64, 512, 1024)          # (nz, ny, nx); coarsest 2 x 16 x 32 with coarse_min 2
 LAM_MAX, LAM_MIN = 1.0989, 0.0999       # one interval, given to both sides
 
 
 def _tiles(shape):
     nz, ny, nx = shape
-    return -(-nx // 56) * -(-ny // 18)
+    return -(-nx // 56) * -(-ny // 20)
 
 
 def _maxrel(x, ref):
