@@ -36,21 +36,22 @@ DEFAULT_WORKLOAD = "twochannel512"
 SAMPLE_N = 64          # CPU-oracle sample grid (same workload shape, 262,144 cells)
 L2_BYTES = 129 * 2**20
 
-# From one ncu capture of the dominant kernel on a smaller grid (the full-size
-# workload is too large to capture under the profiling size rule): DRAM bytes
-# (read + write) divided by the launch's algorithmic bytes.  Traffic grows with
-# the cells processed, so traffic per average full-size launch = ratio x its
-# algorithmic bytes.  Keyed by kernel class, with the sha1 of the kernel's
-# source at capture time; if the source changed since, traffic is null.
+# From one ncu capture of the dominant kernel class's main launch at full size
+# (DRAM byte counters only, one pass): DRAM bytes (read + write) divided by the
+# launch's algorithmic bytes, so traffic per average launch of the class =
+# ratio x its algorithmic bytes.  Keyed by kernel class, with the sha1 of the
+# kernels' sources at capture time; if a source changed since, traffic is null.
 PROFILE_MIN_BYTES = 64e6
 
 NCU_TRAFFIC = {
     "cheb_sgs_fused_f32": {
-        "source": "paper_1812_08606_gb300/csrc/k_smooth_fused.cu",
-        "sha": "ab6ab2c373b81759d9abd054c4f1dd17f54b9570",
-        # twochannel 256^3, finest-level middle step (x_in and d present): 398,684,160 DRAM bytes (291,295,232
-        # read + 107,388,928 written) / 402,653,184 algorithmic
-        "dram_over_algorithmic": 398684160 / 402653184,
+        # the class of fused-smoother launches: the finest level's smoothing steps on the copy-fed kernel and the
+        # plain kernel's eigen basis steps and face-form levels
+        "sources": ["paper_1812_08606_gb300/csrc/k_smooth_tma.cu", "paper_1812_08606_gb300/csrc/k_smooth_fused.cu"],
+        "sha": "136246fc9fcdfca79f6d256621ad408d8a547502",
+        # twochannel 512^3, a copy-fed middle step (x_in and d present), one-pass ncu metrics: 4.02e9 DRAM bytes
+        # (2.96e9 read + 1.06e9 written) / 3,221,225,472 algorithmic
+        "dram_over_algorithmic": 4.02e9 / 3221225472,
     },
 }
 
@@ -188,10 +189,14 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def source_sha(path):
+def source_sha(paths):
+    """SHA-1 over the named source files, in order."""
     import hashlib
-    with open(os.path.join(ROOT, path), "rb") as fh:
-        return hashlib.sha1(fh.read()).hexdigest()
+    h = hashlib.sha1()
+    for path in paths:
+        with open(os.path.join(ROOT, path), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def make_workload(args):
@@ -339,7 +344,7 @@ def run_ours(args, dist):
     achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
     tr = NCU_TRAFFIC.get(top["name"])
     traffic = None
-    if tr and tr.get("sha") == source_sha(tr["source"]):
+    if tr and tr.get("sha") == source_sha(tr["sources"]):
         traffic = round(tr["dram_over_algorithmic"] * per_launch_bytes)
     total_prof_ms = sum(r["ms"] for r in prof)
     kernels = [{"name": r["name"], "launches": r["launches"], "ms": round(r["ms"], 3),
