@@ -296,14 +296,16 @@ def test_smoother_preconditioner_and_chebyshev(prec, pc):
 FIXED_LAM_MAX, FIXED_LAM_MIN = 1.0989, 0.0999
 
 
-@pytest.mark.parametrize("shape,cm", [((48, 40, 72), 5), ((64, 64, 64), 4), (RAGGED, 2)])
+@pytest.mark.parametrize("shape,cm", [((48, 40, 72), 5), ((64, 64, 64), 4), (RAGGED, 2), ((8, 28, 64), 2)])
 def test_fused_smoother_matches_separate_kernels_and_oracle(shape, cm):
     """The fused one-pass Chebyshev + red-black SSOR step against the
     separate residual / half-sweep kernels and the oracle, on grids with
     partial tiles and several z-chunks.  smoother_kernel 0 runs the finest
-    level of the 48 x 40 x 72 and 64^3 grids on the kernel fed by bulk-tensor
-    copies (56 x 20 tiles) and 2 the same step without them (56 x 18 tiles):
-    the same arithmetic in the same order, so the two agree bit for bit."""
+    level of the 48 x 40 x 72, 64^3 and 8 x 28 x 64 grids on the kernel fed by
+    bulk-tensor copies (56 x 20 tiles; 8 x 28 x 64 is near the smallest grid it
+    takes: 4 tiles, 8 blocks with 4 planes each) and 2 the same step without
+    them (56 x 18 tiles): the same arithmetic in the same order, so the two
+    agree bit for bit."""
     a = make_inputs("twochannel512", shape=shape)["a"]
     ctxs = [gmg.gmg_setup(_params(shape, coarse_min=cm, smoother_kernel=k), _t(a)) for k in (0, 1, 2)]
     ops = _olevels(a, ctxs[0].params)
