@@ -25,9 +25,10 @@
 //   24 thread rows computes: the tile grows from 56 x 18 to 56 x 20 cells on
 //   the same 768 threads.
 //
-// The kernel runs the smoothing steps of the V-cycle.  The eigen estimate's
-// basis steps stay on k_smooth_fused.cu: on this kernel they measured 10%
-// slower (0.97 against 0.88 ms at 512^3), where the V-cycle's steps gained 2-7%.
+// The kernel runs the smoothing steps of the V-cycle (6-10% faster than on
+// k_smooth_fused.cu at 512^3).  The eigen estimate's basis steps stay on
+// k_smooth_fused.cu: on an earlier form of this kernel they measured 10%
+// slower (0.97 against 0.88 ms at 512^3).
 //
 // Every wait on an mbarrier is bounded (about a second of the global timer);
 // a thread whose wait runs out counts it in *status, stops waiting and runs
@@ -206,7 +207,8 @@ __device__ __forceinline__ void tma_segment(const TmaArgs& P, unsigned char* sm,
   // pair's values for the next step, the neighbours' two steps later), b of
   // plane c - 1 (residual stage) and d of plane c - 3 (final stage).  Planes a
   // step never reads are not copied.  Issued by thread 0 only, after the
-  // block barrier that retires every read of the slots they overwrite.
+  // block barrier that retires every read of the slots they overwrite (for
+  // the first groups of a segment, the barrier that ends the previous one).
   auto issue = [&](const int c, const bool ax_only) {
     const int x0 = seg[0], y0 = seg[1];
     const uint32_t mb = mb0 + 8u * (uint32_t)(c & (NMB - 1));
