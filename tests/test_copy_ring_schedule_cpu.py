@@ -161,3 +161,24 @@ def test_a_smaller_ring_fails_the_replay(monkeypatch):
     monkeypatch.setattr(sys.modules[__name__], "NMB", PF - 1)
     with pytest.raises(AssertionError):
         _replay(0, 16, 16, False, False)
+
+
+def test_copy_boxes_keep_the_16_byte_rule():
+    """Every copy starts at an x coordinate whose byte offset is a multiple of
+    16 (a and x_in, b: bx FTX - HX; d: bx FTX), every box row is a multiple of
+    16 bytes, and every box dimension is at most 256 elements: the conditions a
+    tiled bulk-tensor copy needs (an unaligned x origin is an illegal
+    instruction on the GPU, which no check catches before the copy runs)."""
+    rp, hx, tr = C["RP"], C["HX"], C["TR"]
+    rw, dr = 2 * rp, tr + 2
+    ftx, fty = rw - 2 * hx, tr - 4
+    elem = 4   # FP32
+    for bx in range(0, 64):
+        assert ((bx * ftx - hx) * elem) % 16 == 0
+        assert (bx * ftx * elem) % 16 == 0
+    for width in (rw, ftx):
+        assert (width * elem) % 16 == 0
+    for dim in (rw, dr, tr, ftx, fty):
+        assert 0 < dim <= 256
+    # the slots the copies land in start on 128-byte boundaries
+    assert (rp * dr * 8) % 128 == 0 and (rp * tr * 8) % 128 == 0 and ((ftx // 2) * fty * 8) % 128 == 0
