@@ -37,6 +37,10 @@
  *  - Errors: every call returns a gmg_status; nothing aborts and no C++
  *    exception crosses the ABI.  CUDA failures map to GMG_ERR_CUDA, failed
  *    device allocations to GMG_ERR_ALLOC, invalid arguments to GMG_ERR_ARG.
+ *    The finest level's smoother waits for its bulk-tensor copies for about
+ *    a second at most; a wait that runs out is counted on the device, and
+ *    gmg_setup, gmg_update_coefficient and every solve then return
+ *    GMG_ERR_CUDA (the context should be destroyed).
  *  - Threads: a context must not be used by two host threads at once.
  */
 #ifndef GMG_H_
