@@ -48,7 +48,7 @@ NCU_TRAFFIC = {
         # the class of fused-smoother launches: the finest level's smoothing steps on the copy-fed kernel and the
         # plain kernel's eigen basis steps and face-form levels
         "sources": ["paper_1812_08606_gb300/csrc/k_smooth_tma.cu", "paper_1812_08606_gb300/csrc/k_smooth_fused.cu"],
-        "sha": "b88bd2542264af18d5d24854501a1d0a180a79c3",
+        "sha": "d227098ff3f7252772877225b35307b62bff780c",
         # twochannel 512^3, a copy-fed middle step (x_in and d present), one-pass ncu metrics: 4.02e9 DRAM bytes
         # (2.96e9 read + 1.06e9 written) / 3,221,225,472 algorithmic
         "dram_over_algorithmic": 4.02e9 / 3221225472,

@@ -203,6 +203,8 @@ cudaError_t launch_sgs_half(const Grid3& g, const T* a, const T* r, T* z, int co
 // With tma_status non-null the step runs, where tma_smoother_eligible allows
 // it, on the kernel fed by bulk-tensor copies (k_smooth_tma.cu), which counts
 // in *tma_status the waits for its copies that ran out (none when correct).
+// launch_cheb_sgs_tma returns cudaErrorNotSupported, having launched nothing,
+// when the driver gives no tensor-map encoder or an encoding fails.
 bool fused_smoother_eligible(const Grid3& g);
 cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b, const float* xin, float* xout,
                                   float* d, double c1, double c2, double ce, int flags, int* tma_status,

@@ -549,8 +549,12 @@ bool fused_smoother_eligible(const Grid3& g) {
 cudaError_t launch_cheb_sgs_fused(const Grid3& g, const float* a, const float* b, const float* xin, float* xout,
                                     float* d, double c1, double c2, double ce, int flags, int* tma_status,
                                     cudaStream_t s) {
-  if (tma_status && tma_smoother_eligible(g, a, b, xin, xout, d, flags))
-    return launch_cheb_sgs_tma(g, a, b, xin, xout, d, c1, c2, flags, tma_status, s);
+  if (tma_status && tma_smoother_eligible(g, a, b, xin, xout, d, flags)) {
+    // cudaErrorNotSupported: no tensor map could be made and nothing was
+    // launched; the step runs on this kernel (the same arithmetic)
+    const cudaError_t e = launch_cheb_sgs_tma(g, a, b, xin, xout, d, c1, c2, flags, tma_status, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (!pair_aligned(a) || !pair_aligned(b) || (xin && !pair_aligned(xin)) || !pair_aligned(xout) || !pair_aligned(d))
     return cudaErrorMisalignedAddress;
   const int tx = (g.nx + FTX - 1) / FTX, ty = (g.ny + FTY - 1) / FTY;

@@ -531,7 +531,7 @@ cudaError_t launch_cheb_sgs_tma(const Grid3& g, const float* a, const float* b, 
   PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   const cudaError_t e = tma_slots(&slots, &enc);
   if (e != cudaSuccess) return e;
-  if (!enc) return cudaErrorNotSupported;
+  if (!enc) return cudaErrorNotSupported;  // no tensor-map encoder in this driver
   const int tx = (g.nx + FTX - 1) / FTX, ty = (g.ny + FTY - 1) / FTY;
   const long long units = (long long)tx * ty * g.nz;
   int mode = ((flags & CHEB_FIRST) ? M_FIRST : 0) | (xin ? 0 : M_XZERO) | ((flags & CHEB_LAST) ? M_LAST : 0);
@@ -553,7 +553,7 @@ cudaError_t launch_cheb_sgs_tma(const Grid3& g, const float* a, const float* b, 
   const bool rd_x = (mode & M_XZERO) == 0, rd_d = (mode & M_FIRST) == 0;
   if (!encode(enc, &P.ma, a, g, RW, DR) || (rd_x && !encode(enc, &P.mx, xin, g, RW, DR)) ||
       !encode(enc, &P.mb, b, g, RW, TR) || (rd_d && !encode(enc, &P.md, d, g, FTX, FTY)))
-    return cudaErrorInvalidValue;
+    return cudaErrorNotSupported;  // nothing launched: the caller runs the plain kernel
   // one block per resident slot, but at least 4 planes per block on small grids
   const long long blocks = std::max(1LL, std::min((long long)slots, units / 4));
   const dim3 grid((unsigned)blocks), block(RP, TR);
